@@ -1,0 +1,725 @@
+/*
+ * tfhe_oracle.c -- plain, slow, CPU reference for the oblivious scan-select
+ * of FHE-SQL (arXiv 2510.15413).  TEST INFRASTRUCTURE ONLY: it is linked by
+ * the test-suite, by the package's smoke check and by the CPU-baseline leg of
+ * the benchmark, never by the product path.  It shares no code, header or
+ * table with the CUDA library; both sides only agree on the published
+ * SplitMix64 generator, which each implements on its own.
+ *
+ * What it computes (every output word is a fixed function of seed and inputs):
+ *   - the scan of Alg. 2 (ProcessQuery): per row, evaluate the WHERE
+ *     predicate homomorphically into one encrypted mask bit, then apply the
+ *     mask to the selected payload columns with If-Then-Else (§4.2, §6 D,
+ *     eq. (1)-(3)); for one-bit payloads cmux(m, v, 0) is AND(m, v);
+ *   - every binary gate is a TFHE gate bootstrap (the TFHE construction the
+ *     paper cites in §1 and §2.2): linear combination, modulus switch, blind
+ *     rotation of a GLWE accumulator by n CMux external products, sample
+ *     extraction, LWE keyswitch;
+ *   - polynomial products are exact negacyclic products over Z/2^32, by
+ *     schoolbook or Karatsuba (no transform of any kind).
+ *
+ * Readings where the paper is silent (it delegates all of TFHE to a library):
+ * bits are encoded as +-q/8, phase = b - <a,s>, gadget base 2^7 with 3 signed
+ * digits in [-64,63], keyswitch base 4 with 8 unsigned digits, test vector
+ * q/8 everywhere, rotation X^{-b} then X^{+a_i}, SplitMix64 randomness,
+ * Box-Muller noise rounded half away from zero.  Each function below names the
+ * reading it follows.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#define ORC_API __attribute__((visibility("default")))
+
+typedef struct {
+    int32_t n;            /* LWE dimension */
+    int32_t N;            /* GLWE polynomial size (power of two), k = 1 */
+    int32_t bg_bits;      /* log2 of the bootstrap gadget base */
+    int32_t l;            /* bootstrap gadget levels */
+    int32_t ks_base_bits; /* log2 of the keyswitch base */
+    int32_t ks_t;         /* keyswitch levels */
+    double lwe_sigma;     /* LWE noise std-dev (fraction of the torus) */
+    double glwe_sigma;    /* GLWE noise std-dev (fraction of the torus) */
+} orc_params;
+
+typedef struct {
+    orc_params p;
+    uint64_t seed;
+    uint8_t *s;    /* LWE key, n bits */
+    uint8_t *S;    /* GLWE key, N bits */
+    uint32_t *bk;  /* [n][2l][2][N]: row r = u*l + (j-1), poly 0 = mask A, 1 = body B */
+    uint32_t *ksk; /* [N][t][base-1][n+1]: LWE_s(v * S_i * 2^(32 - bb*(j+1))) */
+} orc_ctx;
+
+/* ------------------------------------------------------------------ */
+/* Randomness: SplitMix64 (Steele, Lea, Flood, OOPSLA 2014).           */
+/* The generator's state advances by the golden-ratio increment        */
+/* gamma; each output is the state after k+1 increments, mixed.        */
+/* word(seed, stream, ctr) = output #ctr of the generator whose start  */
+/* state is output #stream of the generator started at seed.           */
+/* ------------------------------------------------------------------ */
+static uint64_t sm_output(uint64_t start, uint64_t k)
+{
+    uint64_t z = start + (k + 1) * 0x9e3779b97f4a7c15ULL;
+    z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ULL;
+    z = (z ^ (z >> 27)) * 0x94d049bb133111ebULL;
+    return z ^ (z >> 31);
+}
+
+ORC_API uint64_t orc_splitmix64(uint64_t start, uint64_t k) { return sm_output(start, k); }
+
+static uint64_t rnd_word(uint64_t seed, uint64_t stream, uint64_t ctr)
+{
+    return sm_output(sm_output(seed, stream), ctr);
+}
+
+static uint32_t rnd_u32(uint64_t seed, uint64_t stream, uint64_t ctr)
+{
+    return (uint32_t)(rnd_word(seed, stream, ctr) >> 32);
+}
+
+/* Gaussian torus noise from two consecutive words: Box-Muller cosine branch,
+ * then round half away from zero of sigma * z * 2^32, reduced mod 2^32. */
+static uint32_t rnd_noise(uint64_t seed, uint64_t stream, uint64_t ctr, double sigma)
+{
+    uint64_t w1 = rnd_word(seed, stream, ctr);
+    uint64_t w2 = rnd_word(seed, stream, ctr + 1);
+    double u1 = (double)((w1 >> 11) + 1) * 0x1p-53; /* (0, 1] */
+    double u2 = (double)(w2 >> 11) * 0x1p-53;       /* [0, 1) */
+    double z = sqrt(-2.0 * log(u1)) * cos(2.0 * M_PI * u2);
+    double t = sigma * z;
+    long long e = llround(t * 4294967296.0);
+    return (uint32_t)(uint64_t)e;
+}
+
+/* ------------------------------------------------------------------ */
+/* Negacyclic polynomial products in Z[X]/(X^N + 1), coefficients      */
+/* mod 2^32 (uint32 wrap-around is the ring Z/2^32).                   */
+/* ------------------------------------------------------------------ */
+
+/* Definition: c_k = sum_{i+j=k} a_i b_j - sum_{i+j=k+N} a_i b_j. */
+ORC_API void orc_negacyclic_schoolbook(const uint32_t *a, const uint32_t *b, uint32_t *c, int N)
+{
+    for (int k = 0; k < N; k++) c[k] = 0;
+    for (int i = 0; i < N; i++)
+        for (int j = 0; j < N; j++) {
+            uint32_t prod = a[i] * b[j];
+            int k = i + j;
+            if (k < N) c[k] += prod;
+            else c[k - N] -= prod;
+        }
+}
+
+/* Full product r[0..2m-2] (r[2m-1] = 0) of two length-m polys, schoolbook. */
+static void full_school(const uint32_t *a, const uint32_t *b, uint32_t *r, int m)
+{
+    for (int k = 0; k < 2 * m; k++) r[k] = 0;
+    for (int i = 0; i < m; i++) {
+        uint32_t ai = a[i];
+        for (int j = 0; j < m; j++) r[i + j] += ai * b[j];
+    }
+}
+
+/* Full product by Karatsuba: a*b = z0 + (z1 - z0 - z2) X^h + z2 X^{2h},
+ * z0 = a_lo b_lo, z2 = a_hi b_hi, z1 = (a_lo + a_hi)(b_lo + b_hi).
+ * r has 2m slots, tmp has 8m slots. */
+static void full_kara(const uint32_t *a, const uint32_t *b, uint32_t *r, int m, uint32_t *tmp)
+{
+    if (m <= 32) {
+        full_school(a, b, r, m);
+        return;
+    }
+    int h = m / 2;
+    uint32_t *sa = tmp, *sb = tmp + h, *z1 = tmp + 2 * h, *rest = tmp + 4 * h;
+    for (int i = 0; i < h; i++) {
+        sa[i] = a[i] + a[i + h];
+        sb[i] = b[i] + b[i + h];
+    }
+    full_kara(a, b, r, h, rest);                 /* z0 -> r[0 .. 2h-1]  */
+    full_kara(a + h, b + h, r + 2 * h, h, rest); /* z2 -> r[2h .. 4h-1] */
+    full_kara(sa, sb, z1, h, rest);              /* z1 -> z1[0 .. 2h-1] */
+    for (int i = 0; i < 2 * h; i++) z1[i] -= r[i] + r[2 * h + i];
+    for (int i = 0; i < 2 * h; i++) r[h + i] += z1[i];
+}
+
+/* Negacyclic product via Karatsuba, then fold X^N = -1. */
+ORC_API void orc_negacyclic_karatsuba(const uint32_t *a, const uint32_t *b, uint32_t *c, int N)
+{
+    uint32_t *r = (uint32_t *)malloc(sizeof(uint32_t) * 2 * N);
+    uint32_t *tmp = (uint32_t *)malloc(sizeof(uint32_t) * 8 * N);
+    full_kara(a, b, r, N, tmp);
+    for (int k = 0; k < N; k++) c[k] = r[k] - r[k + N];
+    free(r);
+    free(tmp);
+}
+
+/* acc += a * b (negacyclic), using caller scratch r (2N) and tmp (8N). */
+static void negacyclic_mac(const uint32_t *a, const uint32_t *b, uint32_t *acc, int N,
+                           uint32_t *r, uint32_t *tmp)
+{
+    full_kara(a, b, r, N, tmp);
+    for (int k = 0; k < N; k++) acc[k] += r[k] - r[k + N];
+}
+
+/* out = X^e * in in Z[X]/(X^N+1), e in [0, 2N): each coefficient moves up by e
+ * places and changes sign every time it passes X^N. */
+ORC_API void orc_monomial_mul(const uint32_t *in, uint32_t *out, int N, int e)
+{
+    for (int x = 0; x < N; x++) {
+        int pos = x + e;
+        uint32_t v = in[x];
+        while (pos >= N) {
+            pos -= N;
+            v = (uint32_t)0 - v;
+        }
+        out[pos] = v;
+    }
+}
+
+/* ------------------------------------------------------------------ */
+/* Params and key generation                                            */
+/* ------------------------------------------------------------------ */
+
+ORC_API void orc_params_default(orc_params *p)
+{
+    p->n = 630;
+    p->N = 1024;
+    p->bg_bits = 7;
+    p->l = 3;
+    p->ks_base_bits = 2;
+    p->ks_t = 8;
+    p->lwe_sigma = 0x1p-15;
+    p->glwe_sigma = 0x1p-25;
+}
+
+ORC_API void orc_params_toy(orc_params *p)
+{
+    p->n = 16;
+    p->N = 64;
+    p->bg_bits = 7;
+    p->l = 3;
+    p->ks_base_bits = 2;
+    p->ks_t = 8;
+    p->lwe_sigma = 0x1p-25;
+    p->glwe_sigma = 0x1p-25;
+}
+
+static size_t bk_words(const orc_params *p) { return (size_t)p->n * 2 * p->l * 2 * p->N; }
+static int ks_digits(const orc_params *p) { return (1 << p->ks_base_bits) - 1; }
+static size_t ksk_words(const orc_params *p)
+{
+    return (size_t)p->N * p->ks_t * ks_digits(p) * (p->n + 1);
+}
+
+ORC_API size_t orc_bk_words(const orc_ctx *c) { return bk_words(&c->p); }
+ORC_API size_t orc_ksk_words(const orc_ctx *c) { return ksk_words(&c->p); }
+ORC_API const uint8_t *orc_lwe_key(const orc_ctx *c) { return c->s; }
+ORC_API const uint8_t *orc_glwe_key(const orc_ctx *c) { return c->S; }
+ORC_API const uint32_t *orc_bk(const orc_ctx *c) { return c->bk; }
+ORC_API const uint32_t *orc_ksk(const orc_ctx *c) { return c->ksk; }
+
+/* LWE encryption of torus message mu under key s (dimension n):
+ * a_x uniform, e Gaussian, b = <a, s> + e + mu.  Randomness: words
+ * [base, base+n) for the mask, [base+n, base+n+2) for the noise. */
+static void lwe_encrypt(const uint8_t *s, int n, uint32_t mu, double sigma, uint64_t seed,
+                        uint64_t stream, uint64_t base, uint32_t *ct)
+{
+    uint32_t dot = 0;
+    for (int x = 0; x < n; x++) {
+        ct[x] = rnd_u32(seed, stream, base + x);
+        if (s[x]) dot += ct[x];
+    }
+    ct[n] = dot + rnd_noise(seed, stream, base + n, sigma) + mu;
+}
+
+/* Key generation.  Streams: 0 LWE key, 1 GLWE key, 2 bootstrapping key,
+ * 3 keyswitching key.  Key bits are the top bit of one word each. */
+ORC_API orc_ctx *orc_create(const orc_params *p, uint64_t seed)
+{
+    orc_ctx *c = (orc_ctx *)calloc(1, sizeof(orc_ctx));
+    c->p = *p;
+    c->seed = seed;
+    int n = p->n, N = p->N, l = p->l;
+    c->s = (uint8_t *)malloc(n);
+    c->S = (uint8_t *)malloc(N);
+    for (int i = 0; i < n; i++) c->s[i] = (uint8_t)(rnd_word(seed, 0, i) >> 63);
+    for (int j = 0; j < N; j++) c->S[j] = (uint8_t)(rnd_word(seed, 1, j) >> 63);
+
+    /* Bootstrapping key: BK_i = GGSW_S(s_i).  Row r = (u, j): a GLWE
+     * encryption of zero (A uniform, B = A*S + e), plus s_i * 2^(32 - bg*j)
+     * on the constant coefficient of polynomial u (0 = A, 1 = B). */
+    c->bk = (uint32_t *)malloc(sizeof(uint32_t) * bk_words(p));
+#pragma omp parallel
+    {
+        uint32_t *r = (uint32_t *)malloc(sizeof(uint32_t) * 2 * N);
+        uint32_t *tmp = (uint32_t *)malloc(sizeof(uint32_t) * 8 * N);
+        uint32_t *Spoly = (uint32_t *)malloc(sizeof(uint32_t) * N);
+        for (int j = 0; j < N; j++) Spoly[j] = c->S[j];
+#pragma omp for schedule(static)
+        for (int R = 0; R < n * 2 * l; R++) {
+            int i = R / (2 * l), row = R % (2 * l);
+            int u = row / l, j = row % l + 1;
+            uint64_t base = (uint64_t)R * 3 * N;
+            uint32_t *A = c->bk + (size_t)R * 2 * N, *B = A + N;
+            for (int x = 0; x < N; x++) A[x] = rnd_u32(seed, 2, base + x);
+            for (int x = 0; x < N; x++) B[x] = rnd_noise(seed, 2, base + N + 2 * x, p->glwe_sigma);
+            negacyclic_mac(A, Spoly, B, N, r, tmp);
+            uint32_t g = (uint32_t)1u << (32 - p->bg_bits * j);
+            if (c->s[i]) {
+                if (u == 0) A[0] += g;
+                else B[0] += g;
+            }
+        }
+        free(r);
+        free(tmp);
+        free(Spoly);
+    }
+
+    /* Keyswitching key: KSK[i][j][v-1] = LWE_s(v * S_i * 2^(32 - kb*(j+1))),
+     * v = 1 .. base-1, noise lwe_sigma. */
+    int nd = ks_digits(p);
+    c->ksk = (uint32_t *)malloc(sizeof(uint32_t) * ksk_words(p));
+#pragma omp parallel for schedule(static)
+    for (int idx = 0; idx < N * p->ks_t * nd; idx++) {
+        int i = idx / (p->ks_t * nd);
+        int j = (idx / nd) % p->ks_t;
+        int v = idx % nd + 1;
+        uint32_t mu = (uint32_t)v * (uint32_t)c->S[i] * ((uint32_t)1u << (32 - p->ks_base_bits * (j + 1)));
+        lwe_encrypt(c->s, n, mu, p->lwe_sigma, seed, 3, (uint64_t)idx * (n + 2),
+                    c->ksk + (size_t)idx * (n + 1));
+    }
+    return c;
+}
+
+ORC_API void orc_destroy(orc_ctx *c)
+{
+    if (!c) return;
+    free(c->s);
+    free(c->S);
+    free(c->bk);
+    free(c->ksk);
+    free(c);
+}
+
+/* Encrypt torus messages; ciphertext number first_index + c draws words
+ * starting at (first_index + c) * (n + 2) of the given stream. */
+ORC_API void orc_encrypt(const orc_ctx *c, const uint32_t *mu, size_t count, uint64_t stream,
+                         uint64_t first_index, uint32_t *out)
+{
+    int n = c->p.n;
+#pragma omp parallel for schedule(static)
+    for (long long k = 0; k < (long long)count; k++)
+        lwe_encrypt(c->s, n, mu[k], c->p.lwe_sigma, c->seed, stream,
+                    (first_index + (uint64_t)k) * (n + 2), out + (size_t)k * (n + 1));
+}
+
+/* Bit encoding: true -> +q/8, false -> -q/8. */
+ORC_API void orc_encrypt_bits(const orc_ctx *c, const uint8_t *bits, size_t count, uint64_t stream,
+                              uint64_t first_index, uint32_t *out)
+{
+    uint32_t *mu = (uint32_t *)malloc(sizeof(uint32_t) * (count ? count : 1));
+    for (size_t k = 0; k < count; k++) mu[k] = bits[k] ? (1u << 29) : (uint32_t)(0u - (1u << 29));
+    orc_encrypt(c, mu, count, stream, first_index, out);
+    free(mu);
+}
+
+/* phase = b - <a, key> mod 2^32, for a ciphertext of dimension dim. */
+static uint32_t lwe_phase(const uint32_t *ct, const uint8_t *key, int dim)
+{
+    uint32_t dot = 0;
+    for (int x = 0; x < dim; x++)
+        if (key[x]) dot += ct[x];
+    return ct[dim] - dot;
+}
+
+ORC_API void orc_phase(const orc_ctx *c, const uint32_t *ct, size_t count, uint32_t *out)
+{
+    for (size_t k = 0; k < count; k++) out[k] = lwe_phase(ct + k * (c->p.n + 1), c->s, c->p.n);
+}
+
+/* Phase under the GLWE key read as an LWE key of dimension N (for extracted samples). */
+ORC_API void orc_phase_big(const orc_ctx *c, const uint32_t *ct, size_t count, uint32_t *out)
+{
+    for (size_t k = 0; k < count; k++) out[k] = lwe_phase(ct + k * (c->p.N + 1), c->S, c->p.N);
+}
+
+/* Decryption: the bit is 1 when the phase, read as a signed 32-bit value, is positive. */
+ORC_API void orc_decrypt_bits(const orc_ctx *c, const uint32_t *ct, size_t count, uint8_t *out)
+{
+    for (size_t k = 0; k < count; k++)
+        out[k] = (int32_t)lwe_phase(ct + k * (c->p.n + 1), c->s, c->p.n) > 0;
+}
+
+/* ------------------------------------------------------------------ */
+/* Gate bootstrap pieces                                                */
+/* ------------------------------------------------------------------ */
+
+/* Modulus switch q -> 2N: round(x * 2N / q) mod 2N, ties rounded up. */
+ORC_API uint32_t orc_modswitch(uint32_t x, int N)
+{
+    uint64_t twoN = 2 * (uint64_t)N;
+    return (uint32_t)((((uint64_t)x * twoN + (1ULL << 31)) >> 32) % twoN);
+}
+
+/* Signed gadget decomposition: round x to the nearest multiple of
+ * 2^(32 - bg*l) (ties up), then write the rounded value, mod 2^(bg*l), in
+ * balanced base 2^bg with digits in [-2^(bg-1), 2^(bg-1)), least significant
+ * digit first, carrying into the next digit; the carry out of the top digit
+ * wraps mod q.  digits[j-1] multiplies 2^(32 - bg*j). */
+ORC_API void orc_decompose(uint32_t x, int bg_bits, int l, int32_t *digits)
+{
+    int drop = 32 - bg_bits * l;
+    uint64_t v = (((uint64_t)x + (1ULL << (drop - 1))) >> drop) & ((1ULL << (bg_bits * l)) - 1);
+    int64_t base = 1LL << bg_bits, half = base / 2;
+    for (int j = l; j >= 1; j--) {
+        int64_t d = (int64_t)(v % (uint64_t)base);
+        v /= (uint64_t)base;
+        if (d >= half) {
+            d -= base;
+            v += 1;
+        }
+        digits[j - 1] = (int32_t)d;
+    }
+}
+
+/* Keyswitch digits: round x to its top kb*t bits (ties up), unsigned base-2^kb
+ * digits, most significant first: x ~ sum_j d_j 2^(32 - kb*(j+1)). */
+static void ks_decompose(uint32_t x, int kb, int t, int32_t *digits)
+{
+    int drop = 32 - kb * t;
+    uint64_t v = (((uint64_t)x + (1ULL << (drop - 1))) >> drop) & ((1ULL << (kb * t)) - 1);
+    for (int j = t - 1; j >= 0; j--) {
+        digits[j] = (int32_t)(v & ((1u << kb) - 1));
+        v >>= kb;
+    }
+}
+
+/* External product BK_i [] (A, B): decompose both polynomials, then
+ * out_c = sum over rows r = (u, j) of digitpoly(u, j) * BK_i[r][c]. */
+static void external_product(const orc_ctx *c, const uint32_t *bki, const uint32_t *in,
+                             uint32_t *out, uint32_t *scratch)
+{
+    int N = c->p.N, l = c->p.l;
+    uint32_t *dig = scratch;                /* [2l][N] digit polys (two's complement) */
+    uint32_t *r = dig + (size_t)2 * l * N;  /* 2N */
+    uint32_t *tmp = r + 2 * N;              /* 8N */
+    int32_t d[16];
+    for (int u = 0; u < 2; u++)
+        for (int x = 0; x < N; x++) {
+            orc_decompose(in[u * N + x], c->p.bg_bits, l, d);
+            for (int j = 0; j < l; j++) dig[(size_t)(u * l + j) * N + x] = (uint32_t)d[j];
+        }
+    memset(out, 0, sizeof(uint32_t) * 2 * N);
+    for (int row = 0; row < 2 * l; row++)
+        for (int cc = 0; cc < 2; cc++)
+            negacyclic_mac(dig + (size_t)row * N, bki + ((size_t)row * 2 + cc) * N, out + cc * N, N, r, tmp);
+}
+
+static size_t ep_scratch_words(const orc_params *p) { return (size_t)2 * p->l * p->N + 10 * p->N; }
+
+ORC_API void orc_external_product(const orc_ctx *c, int i, const uint32_t *in, uint32_t *out)
+{
+    uint32_t *scratch = (uint32_t *)malloc(sizeof(uint32_t) * ep_scratch_words(&c->p));
+    external_product(c, c->bk + (size_t)i * 2 * c->p.l * 2 * c->p.N, in, out, scratch);
+    free(scratch);
+}
+
+/* Blind rotation: ACC = X^{-b~} (0, v) with v_j = q/8 for every j, then for
+ * each i: ACC <- ACC + BK_i [] (X^{a~_i} ACC - ACC).  Input is the LWE sample
+ * of dimension n already linearly combined (mod q). */
+ORC_API void orc_blind_rotate(const orc_ctx *c, const uint32_t *lwe, uint32_t *acc)
+{
+    int n = c->p.n, N = c->p.N;
+    uint32_t *tv = (uint32_t *)malloc(sizeof(uint32_t) * N);
+    uint32_t *rot = (uint32_t *)malloc(sizeof(uint32_t) * 2 * N);
+    uint32_t *prod = (uint32_t *)malloc(sizeof(uint32_t) * 2 * N);
+    uint32_t *scratch = (uint32_t *)malloc(sizeof(uint32_t) * ep_scratch_words(&c->p));
+    for (int x = 0; x < N; x++) tv[x] = 1u << 29;
+    uint32_t bbar = orc_modswitch(lwe[n], N);
+    memset(acc, 0, sizeof(uint32_t) * N);
+    orc_monomial_mul(tv, acc + N, N, (int)((2 * N - bbar) % (2 * N)));
+    for (int i = 0; i < n; i++) {
+        uint32_t abar = orc_modswitch(lwe[i], N);
+        for (int u = 0; u < 2; u++) {
+            orc_monomial_mul(acc + u * N, rot + u * N, N, (int)abar);
+            for (int x = 0; x < N; x++) rot[u * N + x] -= acc[u * N + x];
+        }
+        external_product(c, c->bk + (size_t)i * 2 * c->p.l * 2 * N, rot, prod, scratch);
+        for (int x = 0; x < 2 * N; x++) acc[x] += prod[x];
+    }
+    free(tv);
+    free(rot);
+    free(prod);
+    free(scratch);
+}
+
+/* Sample extraction of coefficient 0: a'_0 = A_0, a'_j = -A_{N-j}, b' = B_0;
+ * the result is an LWE sample of dimension N under the GLWE key's coefficients. */
+ORC_API void orc_sample_extract(int N, const uint32_t *acc, uint32_t *out)
+{
+    out[0] = acc[0];
+    for (int j = 1; j < N; j++) out[j] = (uint32_t)0 - acc[N - j];
+    out[N] = acc[N];
+}
+
+/* Keyswitch from the N-bit key to the n-bit key:
+ * out = (0, .., 0, b') - sum_{i, j} KSK[i][j][d_ij] (digit 0 contributes nothing). */
+ORC_API void orc_keyswitch(const orc_ctx *c, const uint32_t *big, uint32_t *out)
+{
+    int n = c->p.n, N = c->p.N, t = c->p.ks_t, nd = ks_digits(&c->p);
+    int32_t d[32];
+    memset(out, 0, sizeof(uint32_t) * (n + 1));
+    out[n] = big[N];
+    for (int i = 0; i < N; i++) {
+        ks_decompose(big[i], c->p.ks_base_bits, t, d);
+        for (int j = 0; j < t; j++) {
+            if (d[j] == 0) continue;
+            const uint32_t *row = c->ksk + ((size_t)(i * t + j) * nd + (d[j] - 1)) * (n + 1);
+            for (int x = 0; x <= n; x++) out[x] -= row[x];
+        }
+    }
+}
+
+/* Gate types (numbering fixed by the library's C interface). */
+enum { G_NAND = 0, G_AND, G_OR, G_XOR, G_XNOR, G_NOR, G_ANDNY, G_ANDYN, G_ORNY, G_ORYN, G_COUNT };
+
+/* Linear combination before the bootstrap: constant (0, ..., 0, k) plus
+ * ca * c1 + cb * c2, all mod q, with q/8 = 2^29.  The sign of the resulting
+ * phase (about +-q/8 or +-q/4 away from zero) is the gate's truth value. */
+ORC_API int orc_gate_lincomb(int type, int n, const uint32_t *c1, const uint32_t *c2, uint32_t *out)
+{
+    const uint32_t E = 1u << 29; /* q/8 */
+    uint32_t k;
+    int32_t ca, cb;
+    switch (type) {
+    case G_NAND:  k = E;         ca = -1; cb = -1; break;
+    case G_AND:   k = 0u - E;    ca = 1;  cb = 1;  break;
+    case G_OR:    k = E;         ca = 1;  cb = 1;  break;
+    case G_XOR:   k = 2 * E;     ca = 2;  cb = 2;  break;
+    case G_XNOR:  k = 0u - 2 * E; ca = -2; cb = -2; break;
+    case G_NOR:   k = 0u - E;    ca = -1; cb = -1; break;
+    case G_ANDNY: k = 0u - E;    ca = -1; cb = 1;  break;
+    case G_ANDYN: k = 0u - E;    ca = 1;  cb = -1; break;
+    case G_ORNY:  k = E;         ca = -1; cb = 1;  break;
+    case G_ORYN:  k = E;         ca = 1;  cb = -1; break;
+    default: return -1;
+    }
+    for (int x = 0; x <= n; x++) out[x] = (uint32_t)ca * c1[x] + (uint32_t)cb * c2[x];
+    out[n] += k;
+    return 0;
+}
+
+/* One gate bootstrap: lincomb -> blind rotation -> extract -> keyswitch. */
+ORC_API int orc_gate(const orc_ctx *c, int type, const uint32_t *c1, const uint32_t *c2, uint32_t *out)
+{
+    int n = c->p.n, N = c->p.N;
+    uint32_t *lin = (uint32_t *)malloc(sizeof(uint32_t) * (n + 1));
+    uint32_t *acc = (uint32_t *)malloc(sizeof(uint32_t) * 2 * N);
+    uint32_t *big = (uint32_t *)malloc(sizeof(uint32_t) * (N + 1));
+    int rc = orc_gate_lincomb(type, n, c1, c2, lin);
+    if (rc == 0) {
+        orc_blind_rotate(c, lin, acc);
+        orc_sample_extract(N, acc, big);
+        orc_keyswitch(c, big, out);
+    }
+    free(lin);
+    free(acc);
+    free(big);
+    return rc;
+}
+
+/* Independent gates, one per thread. */
+ORC_API int orc_gate_batch(const orc_ctx *c, const int32_t *types, const uint32_t *a, const uint32_t *b,
+                           uint32_t *out, size_t count)
+{
+    size_t w = (size_t)c->p.n + 1;
+    int bad = 0;
+#pragma omp parallel for schedule(dynamic, 1) reduction(| : bad)
+    for (long long k = 0; k < (long long)count; k++)
+        bad |= orc_gate(c, types[k], a + k * w, b + k * w, out + k * w) != 0;
+    return bad ? -1 : 0;
+}
+
+/* NOT needs no bootstrap: negate every word. */
+ORC_API void orc_not(int n, const uint32_t *in, uint32_t *out)
+{
+    for (int x = 0; x <= n; x++) out[x] = (uint32_t)0 - in[x];
+}
+
+/* ------------------------------------------------------------------ */
+/* Predicate netlists (per row).  Wires: column bits 0..w-1 (LSB first),   */
+/* then constant bits (w for EQ/LT: k; 2w for RANGE: lo then hi), then     */
+/* payload bits (column-major, LSB first), then gate outputs in order.     */
+/* ------------------------------------------------------------------ */
+
+enum { P_EQ = 0, P_LT = 1, P_RANGE = 2 };
+
+typedef struct {
+    int32_t *type, *a, *b; /* one entry per gate; gate g writes wire first_gate_wire + g */
+    int count, cap, next_wire;
+} netlist;
+
+static int nl_add(netlist *nl, int type, int a, int b)
+{
+    if (nl->type) {
+        nl->type[nl->count] = type;
+        nl->a[nl->count] = a;
+        nl->b[nl->count] = b;
+    }
+    nl->count++;
+    return nl->next_wire++;
+}
+
+/* x_i = XNOR(c_i, k_i); then a pairwise AND tree: each round pairs (2j, 2j+1)
+ * in order and moves a trailing odd element to the end of the next round. */
+static int nl_eq(netlist *nl, int cbase, int kbase, int w)
+{
+    int list[64], m = w;
+    for (int i = 0; i < w; i++) list[i] = nl_add(nl, G_XNOR, cbase + i, kbase + i);
+    while (m > 1) {
+        int nm = 0;
+        for (int j = 0; j + 1 < m; j += 2) list[nm++] = nl_add(nl, G_AND, list[j], list[j + 1]);
+        if (m & 1) list[nm++] = list[m - 1];
+        m = nm;
+    }
+    return list[0];
+}
+
+/* Unsigned c < k, ripple from the LSB:
+ * lt_0 = (not c_0) and k_0;  lt_i = ((not c_i) and k_i) or (XNOR(c_i, k_i) and lt_{i-1}). */
+static int nl_lt(netlist *nl, int cbase, int kbase, int w)
+{
+    int lt = nl_add(nl, G_ANDNY, cbase, kbase);
+    for (int i = 1; i < w; i++) {
+        int g = nl_add(nl, G_ANDNY, cbase + i, kbase + i);
+        int e = nl_add(nl, G_XNOR, cbase + i, kbase + i);
+        int t = nl_add(nl, G_AND, e, lt);
+        lt = nl_add(nl, G_OR, g, t);
+    }
+    return lt;
+}
+
+/* Build the per-row netlist.  Returns the number of gates; fills the arrays
+ * when non-null (each of capacity >= the count).  *match_wire receives the
+ * wire of the match bit; mask gate outputs are the last n_payload*pw wires. */
+ORC_API int orc_netlist(int pred, int w, int n_payload, int pw, int32_t *type, int32_t *a, int32_t *b,
+                        int32_t *match_wire, int32_t *n_inputs)
+{
+    if (w < 1 || w > 64 || pw < 0 || n_payload < 0) return -1;
+    int nconst = pred == P_RANGE ? 2 * w : w;
+    int ninp = w + nconst + n_payload * pw;
+    netlist nl = {type, a, b, 0, 0, ninp};
+    int m;
+    if (pred == P_EQ) m = nl_eq(&nl, 0, w, w);
+    else if (pred == P_LT) m = nl_lt(&nl, 0, w, w);
+    else if (pred == P_RANGE) {
+        int ge_lo = nl_lt(&nl, 0, w, w);
+        int lt_hi = nl_lt(&nl, 0, 2 * w, w);
+        m = nl_add(&nl, G_ANDNY, ge_lo, lt_hi); /* not(c < lo) and (c < hi) */
+    } else return -1;
+    for (int p = 0; p < n_payload; p++)
+        for (int bit = 0; bit < pw; bit++) nl_add(&nl, G_AND, m, w + nconst + p * pw + bit);
+    if (match_wire) *match_wire = m;
+    if (n_inputs) *n_inputs = ninp;
+    return nl.count;
+}
+
+/* Plaintext evaluation of a gate type on bits (truth-table reference). */
+ORC_API int orc_gate_plain(int type, int x, int y)
+{
+    switch (type) {
+    case G_NAND: return !(x && y);
+    case G_AND: return x && y;
+    case G_OR: return x || y;
+    case G_XOR: return x != y;
+    case G_XNOR: return x == y;
+    case G_NOR: return !(x || y);
+    case G_ANDNY: return !x && y;
+    case G_ANDYN: return x && !y;
+    case G_ORNY: return !x || y;
+    case G_ORYN: return x || !y;
+    }
+    return -1;
+}
+
+/* Plaintext evaluation of the netlist on one row's input bits. */
+ORC_API int orc_netlist_eval_plain(int pred, int w, int n_payload, int pw, const uint8_t *inputs, uint8_t *wires_out)
+{
+    int32_t m, ninp;
+    int g = orc_netlist(pred, w, n_payload, pw, NULL, NULL, NULL, &m, &ninp);
+    if (g < 0) return -1;
+    int32_t *t = (int32_t *)malloc(sizeof(int32_t) * g), *a = (int32_t *)malloc(sizeof(int32_t) * g),
+            *b = (int32_t *)malloc(sizeof(int32_t) * g);
+    orc_netlist(pred, w, n_payload, pw, t, a, b, &m, &ninp);
+    for (int i = 0; i < ninp; i++) wires_out[i] = inputs[i];
+    for (int k = 0; k < g; k++) wires_out[ninp + k] = (uint8_t)orc_gate_plain(t[k], wires_out[a[k]], wires_out[b[k]]);
+    free(t);
+    free(a);
+    free(b);
+    return m;
+}
+
+/* ------------------------------------------------------------------ */
+/* The scan (Alg. 2): rows [row_begin, row_end) of a table.               */
+/* column: [rows][w][n+1]; consts: [w or 2w][n+1]; payload p: [rows][pw][n+1] */
+/* (payloads[p] points at row 0); match: [rows][n+1]; out p: [rows][pw][n+1]. */
+/* Rows are independent and run one per thread; within a row the gates run  */
+/* in netlist order.                                                         */
+/* ------------------------------------------------------------------ */
+ORC_API int orc_scan(const orc_ctx *c, int pred, int w, const uint32_t *column, const uint32_t *consts,
+                     int n_payload, int pw, const uint32_t *const *payloads, uint32_t *match,
+                     uint32_t *const *out_payloads, long long row_begin, long long row_end)
+{
+    int32_t m, ninp;
+    int g = orc_netlist(pred, w, n_payload, pw, NULL, NULL, NULL, &m, &ninp);
+    if (g < 0) return -1;
+    int32_t *t = (int32_t *)malloc(sizeof(int32_t) * g), *a = (int32_t *)malloc(sizeof(int32_t) * g),
+            *b = (int32_t *)malloc(sizeof(int32_t) * g);
+    orc_netlist(pred, w, n_payload, pw, t, a, b, &m, &ninp);
+    size_t W = (size_t)c->p.n + 1;
+    int nconst = pred == P_RANGE ? 2 * w : w;
+    int bad = 0;
+#pragma omp parallel for schedule(dynamic, 1) reduction(| : bad)
+    for (long long row = row_begin; row < row_end; row++) {
+        uint32_t *wires = (uint32_t *)malloc(sizeof(uint32_t) * W * (ninp + g));
+        for (int i = 0; i < w; i++) memcpy(wires + i * W, column + ((size_t)row * w + i) * W, W * 4);
+        for (int i = 0; i < nconst; i++) memcpy(wires + (w + i) * W, consts + (size_t)i * W, W * 4);
+        for (int p = 0; p < n_payload; p++)
+            for (int bit = 0; bit < pw; bit++)
+                memcpy(wires + (size_t)(w + nconst + p * pw + bit) * W, payloads[p] + ((size_t)row * pw + bit) * W, W * 4);
+        for (int k = 0; k < g; k++)
+            bad |= orc_gate(c, t[k], wires + (size_t)a[k] * W, wires + (size_t)b[k] * W, wires + (size_t)(ninp + k) * W) != 0;
+        memcpy(match + (size_t)row * W, wires + (size_t)m * W, W * 4);
+        int first_mask = ninp + g - n_payload * pw;
+        for (int p = 0; p < n_payload; p++)
+            for (int bit = 0; bit < pw; bit++)
+                memcpy(out_payloads[p] + ((size_t)row * pw + bit) * W, wires + (size_t)(first_mask + p * pw + bit) * W, W * 4);
+        free(wires);
+    }
+    free(t);
+    free(a);
+    free(b);
+    return bad ? -1 : 0;
+}
+
+ORC_API void orc_set_threads(int k)
+{
+#ifdef _OPENMP
+    if (k > 0) omp_set_num_threads(k);
+#else
+    (void)k;
+#endif
+}
+
+ORC_API int orc_max_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}

@@ -1,0 +1,395 @@
+"""Pins for the CPU oracle: each check ties it to something other than itself
+(a published test vector, a closed form, an invariant of the TFHE
+construction the paper cites, brute force on tiny inputs), so that a dropped
+term, a wrong sign or index, or a transposed operand fails at least one."""
+import os
+
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+Q = 1 << 32
+E8 = 1 << 29
+
+
+def centered(x):
+    x = np.asarray(x, dtype=np.int64) & 0xFFFFFFFF
+    return np.where(x >= (1 << 31), x - Q, x)
+
+
+def read_golden(name):
+    rows = []
+    with open(os.path.join(GOLD, name)) as f:
+        for line in f:
+            line = line.strip()
+            if line and not line.startswith("#"):
+                rows.append(line.split())
+    return rows
+
+
+# --------------------------------------------------------------------------
+# randomness
+# --------------------------------------------------------------------------
+def test_splitmix64_published_vector():
+    for idx, hexval in read_golden("splitmix64_seed0.txt"):
+        assert O.splitmix64(0, int(idx)) == int(hexval, 16)
+
+
+def test_key_bits_balanced_and_seeded(real_oracle):
+    s, S = real_oracle.lwe_key(), real_oracle.glwe_key()
+    assert set(np.unique(s)) <= {0, 1} and set(np.unique(S)) <= {0, 1}
+    assert 250 < s.sum() < 380 and 430 < S.sum() < 600
+    other = O.Oracle(12)
+    assert not np.array_equal(other.lwe_key(), s)
+    again = O.Oracle(11)
+    assert np.array_equal(again.lwe_key(), s) and np.array_equal(again.bk(), real_oracle.bk())
+
+
+# --------------------------------------------------------------------------
+# negacyclic products
+# --------------------------------------------------------------------------
+def test_negacyclic_hand_example():
+    # (1 + X)(1 + X^3) = 1 + X + X^3 + X^4 = X + X^3 in Z[X]/(X^4 + 1)
+    a = np.array([1, 1, 0, 0], np.uint32)
+    b = np.array([1, 0, 0, 1], np.uint32)
+    for f in (O.negacyclic_schoolbook, O.negacyclic_karatsuba):
+        assert list(f(a, b)) == [0, 1, 0, 1]
+
+
+def test_negacyclic_x_to_the_n_is_minus_one():
+    for N in (8, 64, 1024):
+        xn1 = np.zeros(N, np.uint32)
+        xn1[N - 1] = 1
+        x = np.zeros(N, np.uint32)
+        x[1] = 1
+        want = np.zeros(N, np.uint32)
+        want[0] = 0xFFFFFFFF
+        assert np.array_equal(O.negacyclic_karatsuba(xn1, x), want)
+        assert np.array_equal(O.negacyclic_schoolbook(xn1, x), want)
+
+
+@pytest.mark.parametrize("N", [4, 8, 64, 256, 1024])
+def test_schoolbook_equals_karatsuba(N):
+    rng = np.random.default_rng(N)
+    a = rng.integers(0, Q, N, dtype=np.uint64).astype(np.uint32)
+    b = rng.integers(0, Q, N, dtype=np.uint64).astype(np.uint32)
+    assert np.array_equal(O.negacyclic_schoolbook(a, b), O.negacyclic_karatsuba(a, b))
+
+
+def test_negacyclic_against_numpy_convolution():
+    # small coefficients: the integer convolution (a library routine) is exact in int64
+    rng = np.random.default_rng(5)
+    N = 64
+    a = rng.integers(-64, 64, N)
+    b = rng.integers(0, 1 << 20, N)
+    full = np.convolve(a, b)  # length 2N-1
+    full = np.concatenate([full, [0]])
+    want = (full[:N] - full[N:]) % Q
+    got = O.negacyclic_karatsuba((a % Q).astype(np.uint32), b.astype(np.uint32))
+    assert np.array_equal(got.astype(np.int64), want)
+
+
+def test_monomial_mul_is_product_with_monomial():
+    rng = np.random.default_rng(9)
+    N = 16
+    a = rng.integers(0, Q, N, dtype=np.uint64).astype(np.uint32)
+    for e in range(2 * N):
+        mono = np.zeros(N, np.uint32)
+        if e < N:
+            mono[e] = 1
+        else:
+            mono[e - N] = 0xFFFFFFFF
+        assert np.array_equal(O.monomial_mul(a, e), O.negacyclic_schoolbook(mono, a)), e
+
+
+# --------------------------------------------------------------------------
+# modulus switch and decompositions
+# --------------------------------------------------------------------------
+def test_modswitch_closed_form():
+    rng = np.random.default_rng(1)
+    xs = list(rng.integers(0, Q, 2000)) + [0, 1, Q - 1, 1 << 20, (1 << 20) - 1, (1 << 21) + (1 << 20), Q - (1 << 20)]
+    for N in (64, 1024):
+        twoN = 2 * N
+        for x in xs:
+            x = int(x)
+            # nearest integer to x*2N/q, ties up, computed with exact rationals
+            num = x * twoN
+            want = ((2 * num + Q) // (2 * Q)) % twoN
+            assert O.modswitch(x, N) == want
+
+
+def test_gadget_decomposition_reconstructs_and_matches_offset_form():
+    rng = np.random.default_rng(2)
+    xs = np.concatenate([np.arange(1 << 12, dtype=np.uint64),
+                         rng.integers(0, Q, 20000, dtype=np.uint64),
+                         Q - 1 - np.arange(1 << 12, dtype=np.uint64)]).astype(np.uint64)
+    bg, l = 7, 3
+    off = sum(64 << (32 - bg * j) for j in range(1, l + 1)) + (1 << (32 - bg * l - 1))
+    for x in xs[::7]:
+        x = int(x)
+        d = O.decompose(x, bg, l)
+        assert all(-64 <= v < 64 for v in d)
+        recon = sum(int(d[j - 1]) << (32 - bg * j) for j in range(1, l + 1))
+        err = (x - recon) % Q
+        err = err - Q if err >= Q // 2 else err
+        assert -(1 << 10) <= err < (1 << 10)  # ties round up
+        # the offset form of the same balanced decomposition
+        y = (x + off) % Q
+        alt = [((y >> (32 - bg * j)) & 127) - 64 for j in range(1, l + 1)]
+        assert list(d) == alt
+
+
+# --------------------------------------------------------------------------
+# keys
+# --------------------------------------------------------------------------
+def test_bootstrapping_key_rows_encrypt_gadget_times_key_bit(real_oracle):
+    o = real_oracle
+    s, S = o.lwe_key(), o.glwe_key().astype(np.uint32)
+    bk = o.bk()
+    l, N = o.params.l, o.N
+    for i in (0, 1, 2, 317, o.n - 1):
+        for row in range(2 * l):
+            u, j = row // l, row % l + 1
+            A, B = bk[i, row, 0], bk[i, row, 1]
+            phase = (B.astype(np.int64) - O.negacyclic_schoolbook(A, S).astype(np.int64)) % Q
+            g = 1 << (32 - 7 * j)
+            want = np.zeros(N, np.int64)
+            if s[i]:
+                if u == 1:
+                    want[0] = g
+                else:
+                    want = (-(g * S.astype(np.int64))) % Q
+            err = centered((phase - want) % Q)
+            assert np.abs(err).max() < (1 << 10), (i, row)
+
+
+def test_keyswitching_key_rows(real_oracle):
+    o = real_oracle
+    S = o.glwe_key()
+    ksk = o.ksk()
+    for i in (0, 5, 1023):
+        for j in range(8):
+            for v in (1, 2, 3):
+                ph = int(o.phase(ksk[i, j, v - 1])[0])
+                want = (v * int(S[i]) << (30 - 2 * j)) % Q
+                assert abs(int(centered((ph - want) % Q))) < (1 << 21)
+
+
+def test_encryption_noise_statistics(real_oracle):
+    o = real_oracle
+    mu = np.full(20000, 12345, np.uint32)
+    ct = o.encrypt(mu, stream=5)
+    err = centered(o.phase(ct).astype(np.int64) - 12345).astype(np.float64)
+    sigma = o.params.lwe_sigma * Q
+    assert abs(err.mean()) < 0.05 * sigma
+    assert 0.95 < err.std() / sigma < 1.05
+    # encryption is deterministic in (seed, stream, index) and differs across streams
+    assert np.array_equal(o.encrypt(mu[:3], stream=5), ct[:3])
+    assert np.array_equal(o.encrypt(mu[:3], stream=5, first_index=10), ct[10:13])
+    assert not np.array_equal(o.encrypt(mu[:3], stream=6), ct[:3])
+
+
+def test_bit_encoding_decrypts(real_oracle):
+    bits = np.array([0, 1, 1, 0, 1], np.uint8)
+    ct = real_oracle.encrypt_bits(bits, stream=7)
+    assert list(real_oracle.decrypt_bits(ct)) == list(bits)
+    ph = centered(real_oracle.phase(ct))
+    assert np.all(np.abs(ph - np.where(bits == 1, E8, -E8)) < (1 << 20))
+
+
+# --------------------------------------------------------------------------
+# bootstrap pieces
+# --------------------------------------------------------------------------
+def glwe_encrypt_manual(o, msg, rng):
+    """(A, B) with B = A*S + msg + e, built in the test from the oracle's key."""
+    N = o.N
+    S = o.glwe_key().astype(np.uint32)
+    A = rng.integers(0, Q, N, dtype=np.uint64).astype(np.uint32)
+    e = rng.integers(-8, 9, N)
+    B = (O.negacyclic_schoolbook(A, S).astype(np.int64) + msg + e) % Q
+    return np.concatenate([A, B.astype(np.uint32)])
+
+
+def test_sample_extract_identity(toy_oracle):
+    o = toy_oracle
+    rng = np.random.default_rng(3)
+    S = o.glwe_key().astype(np.uint32)
+    acc = rng.integers(0, Q, 2 * o.N, dtype=np.uint64).astype(np.uint32)
+    big = o.sample_extract(acc)
+    phase_poly = (acc[o.N:].astype(np.int64) - O.negacyclic_schoolbook(acc[:o.N], S).astype(np.int64)) % Q
+    assert int(o.phase_big(big)[0]) == int(phase_poly[0])
+
+
+@pytest.mark.parametrize("which", ["toy", "real"])
+def test_external_product_multiplies_phase_by_key_bit(which, toy_oracle, real_oracle):
+    o = toy_oracle if which == "toy" else real_oracle
+    rng = np.random.default_rng(4)
+    N = o.N
+    S = o.glwe_key().astype(np.uint32)
+    msg = rng.integers(0, Q, N).astype(np.int64)
+    ct = glwe_encrypt_manual(o, msg, rng)
+    s = o.lwe_key()
+    for i in [int(np.argmax(s == 0)), int(np.argmax(s == 1))]:
+        out = o.external_product(i, ct)
+        phase = (out[N:].astype(np.int64) - O.negacyclic_schoolbook(out[:N], S).astype(np.int64)) % Q
+        want = msg * int(s[i]) % Q
+        err = centered((phase - want) % Q)
+        # decomposition error N * 2^10 at most, plus key noise times digits
+        assert np.abs(err).max() < (1 << 22), (which, i, int(np.abs(err).max()))
+
+
+@pytest.mark.parametrize("which", ["toy", "real"])
+def test_blind_rotation_sign_follows_rounded_phase(which, toy_oracle, real_oracle):
+    o = toy_oracle if which == "toy" else real_oracle
+    rng = np.random.default_rng(6)
+    s = o.lwe_key().astype(np.int64)
+    N = o.N
+    trials = 12 if which == "toy" else 2
+    for _ in range(trials):
+        lwe = rng.integers(0, Q, o.n + 1, dtype=np.uint64).astype(np.uint32)
+        bar = np.array([O.modswitch(int(x), N) for x in lwe], np.int64)
+        phi = (bar[-1] - (bar[:-1] * s).sum()) % (2 * N)
+        acc = o.blind_rotate(lwe)
+        big = o.sample_extract(acc)
+        ph = int(centered(o.phase_big(big))[0])
+        want = E8 if phi < N else -E8
+        assert abs(ph - want) < (1 << 26), (phi, ph)
+
+
+def test_keyswitch_preserves_phase(real_oracle):
+    o = real_oracle
+    rng = np.random.default_rng(8)
+    S = o.glwe_key().astype(np.int64)
+    for mu in (E8, Q - E8, 12345678):
+        a = rng.integers(0, Q, o.N).astype(np.int64)
+        b = ((a * S).sum() + mu + 3) % Q
+        big = np.concatenate([a, [b]]).astype(np.uint32)
+        out = o.keyswitch(big)
+        err = int(centered((int(o.phase(out)[0]) - mu) % Q))
+        assert abs(err) < (1 << 26), err
+
+
+# --------------------------------------------------------------------------
+# gates: full truth tables
+# --------------------------------------------------------------------------
+TRUTH = {"NAND": [1, 1, 1, 0], "AND": [0, 0, 0, 1], "OR": [0, 1, 1, 1], "XOR": [0, 1, 1, 0],
+         "XNOR": [1, 0, 0, 1], "NOR": [1, 0, 0, 0], "ANDNY": [0, 1, 0, 0], "ANDYN": [0, 0, 1, 0],
+         "ORNY": [1, 1, 0, 1], "ORYN": [1, 0, 1, 1]}  # index = 2*x + y
+
+
+def test_gate_plain_truth_tables():
+    for name, tt in TRUTH.items():
+        for x in (0, 1):
+            for y in (0, 1):
+                assert O.gate_plain(O.GATES[name], x, y) == tt[2 * x + y], name
+
+
+def test_all_gates_truth_tables_toy(toy_oracle):
+    o = toy_oracle
+    xs = np.array([0, 0, 1, 1], np.uint8)
+    ys = np.array([0, 1, 0, 1], np.uint8)
+    for rep in range(3):
+        cx = o.encrypt_bits(xs, stream=20 + rep)
+        cy = o.encrypt_bits(ys, stream=40 + rep)
+        for name, tt in TRUTH.items():
+            gates = np.full(4, O.GATES[name], np.int32)
+            out = o.gate_batch(gates, cx, cy)
+            assert list(o.decrypt_bits(out)) == tt, name
+            # fresh-looking output: phase within q/16 of +-q/8
+            ph = centered(o.phase(out))
+            assert np.all(np.abs(np.abs(ph) - E8) < (1 << 27))
+
+
+def test_chained_gates_toy(toy_oracle):
+    o = toy_oracle
+    rng = np.random.default_rng(10)
+    bits = rng.integers(0, 2, 64).astype(np.uint8)
+    ct = o.encrypt_bits(bits, stream=60)
+    val, cval = bits[0], ct[0]
+    names = list(TRUTH)
+    for k in range(1, 64):
+        name = names[k % len(names)]
+        cval = o.gate(O.GATES[name], cval, ct[k])
+        val = TRUTH[name][2 * int(val) + int(bits[k])]
+        assert o.decrypt_bits(cval)[0] == val
+
+
+def test_not_is_free_negation(toy_oracle):
+    o = toy_oracle
+    ct = o.encrypt_bits(np.array([1, 0], np.uint8), stream=3)
+    assert list(o.decrypt_bits(np.stack([o.not_(ct[0]), o.not_(ct[1])]))) == [0, 1]
+
+
+def test_gates_real_params(real_oracle):
+    o = real_oracle
+    cx = o.encrypt_bits(np.array([0, 1, 1, 1], np.uint8), stream=21)
+    cy = o.encrypt_bits(np.array([1, 1, 0, 1], np.uint8), stream=22)
+    gates = np.array([O.GATES[g] for g in ("AND", "XNOR", "ANDNY", "OR")], np.int32)
+    out = o.gate_batch(gates, cx, cy)
+    assert list(o.decrypt_bits(out)) == [0, 1, 0, 1]
+    # different keys, same inputs: different words (the words depend on the keys)
+    assert not np.array_equal(out[0], cx[0])
+
+
+# --------------------------------------------------------------------------
+# netlists
+# --------------------------------------------------------------------------
+def test_netlist_gate_counts_match_workload_definitions():
+    preds = {"EQ": O.P_EQ, "LT": O.P_LT, "RANGE": O.P_RANGE}
+    for pred, w, npay, pw, rows, per_row, total, nx, nand, _ in read_golden("netlist_gate_counts.txt"):
+        t, a, b, m, ninp = O.netlist(preds[pred], int(w), int(npay), int(pw))
+        assert t.size == int(per_row) and t.size * int(rows) == int(total)
+        if nx != "-":
+            assert int((t == O.GATES["XNOR"]).sum()) == int(nx)
+            assert int((t == O.GATES["AND"]).sum()) == int(nand)
+
+
+@pytest.mark.parametrize("pred", [O.P_EQ, O.P_LT, O.P_RANGE])
+@pytest.mark.parametrize("w", [1, 2, 3, 4])
+def test_netlist_brute_force(pred, w):
+    for c in range(1 << w):
+        for k in range(1 << w):
+            for k2 in (range(1 << w) if pred == O.P_RANGE else [None]):
+                pay = (c * 5 + 3) % (1 << w)
+                inp = [(c >> i) & 1 for i in range(w)] + [(k >> i) & 1 for i in range(w)]
+                if pred == O.P_RANGE:
+                    inp += [(k2 >> i) & 1 for i in range(w)]
+                inp += [(pay >> i) & 1 for i in range(w)]
+                wires, m = O.netlist_eval_plain(pred, w, 1, w, np.array(inp, np.uint8))
+                want = {O.P_EQ: c == k, O.P_LT: c < k, O.P_RANGE: k <= c < (k2 or 0)}[pred]
+                assert wires[m] == int(want)
+                out = wires[-w:]
+                assert int(sum(int(out[i]) << i for i in range(w))) == (pay if want else 0)
+
+
+# --------------------------------------------------------------------------
+# the scan end to end (toy parameters) against the plaintext SQL answer
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("pred", [O.P_EQ, O.P_LT, O.P_RANGE])
+def test_scan_toy_matches_plaintext_sql(pred, toy_oracle):
+    o = toy_oracle
+    rng = np.random.default_rng(100 + pred)
+    w, rows = 4, 16
+    c = rng.integers(0, 16, rows)
+    pay = rng.integers(0, 16, rows)
+    if pred == O.P_RANGE:
+        lo, hi = 3, 11
+        kbits = [(lo >> i) & 1 for i in range(w)] + [(hi >> i) & 1 for i in range(w)]
+    else:
+        k = int(c[5])
+        kbits = [(k >> i) & 1 for i in range(w)]
+    col = o.encrypt_bits(np.array([(v >> i) & 1 for v in c for i in range(w)], np.uint8), stream=5)
+    pct = o.encrypt_bits(np.array([(v >> i) & 1 for v in pay for i in range(w)], np.uint8), stream=9)
+    kct = o.encrypt_bits(np.array(kbits, np.uint8), stream=7)
+    match, (outp,) = o.scan(pred, w, col, kct, [pct], w)
+    mbits = o.decrypt_bits(match)
+    obits = o.decrypt_bits(outp.reshape(-1, o.n + 1)).reshape(rows, w)
+    for r in range(rows):
+        want = {O.P_EQ: c[r] == k if pred != O.P_RANGE else None,
+                O.P_LT: c[r] < k if pred != O.P_RANGE else None,
+                O.P_RANGE: lo <= c[r] < hi if pred == O.P_RANGE else None}[pred]
+        assert mbits[r] == int(want)
+        got = int(sum(int(obits[r, i]) << i for i in range(w)))
+        assert got == (int(pay[r]) if want else 0)
