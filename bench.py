@@ -1,0 +1,383 @@
+#!/usr/bin/env python
+"""Benchmark of the oblivious scan-select hot path on B300.
+
+One step = one full oblivious scan (all rows, every circuit level: XNOR
+layer, AND tree, payload masks; each gate one TFHE gate bootstrap) of the
+4096-row uint32 equality workload by default, with inputs resident in HBM.
+Prints one JSON line (rank 0).  `--impl reference` times the CPU oracle
+instead, on a bounded sample of the same workload.
+
+Multi-GPU (torchrun): every rank scans its own replica of the table on its own
+GPU (rows are independent; no data-path collective); the barrier and the
+max-over-ranks time use torch.distributed.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+MODMULS_PER_BOOTSTRAP = 630 * (8 * 5120 + 12 * 1024)  # n CMux x (8 NTTs x N/2 log N + 2l*2*N MAC)
+IMAD_PER_CLK_PER_SM = 64   # 32-bit integer multiply-add throughput per SM per clock
+WIDE_MULS_PER_MODMUL = 4   # 64x64 -> 128-bit product from four 32x32 -> 64-bit products
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default="eq32x4096",
+                    choices=["eq32x4096", "eq4x16", "range16x65536", "lt8x64", "range4x16"])
+    ap.add_argument("--rows", type=int, default=None, help="override the workload's row count")
+    ap.add_argument("--e2e-steps", type=int, default=1)
+    ap.add_argument("--cpu-rows", type=int, default=1, help="rows of the workload the oracle times")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-per-gate", action="store_true", help="skip the per-gate-launch baseline")
+    ap.add_argument("--seed", type=int, default=1)
+    return ap.parse_args()
+
+
+# ------------------------------------------------------------------ helpers
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except Exception:
+        return {"hbm_gbs": 6400.0, "bf16_tflops": 1800.0, "sm_max_mhz": 2032.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons, sampled every 200 ms."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, bus_id: str | None):
+        self.bus_id = bus_id
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "200"]
+        if self.bus_id:
+            cmd += ["-i", self.bus_id]
+        try:
+            self.proc = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=5)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        busy = [s for s in sm if smax and s > 0.5 * max(smax)] or sm
+        return {"sm_mhz": statistics.median(busy) if busy else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def bus_id_of(dev: int) -> str | None:
+    try:
+        import torch
+        p = torch.cuda.get_device_properties(dev)
+        return "%08X:%02X:%02X.0" % (p.pci_domain_id, p.pci_bus_id, p.pci_device_id)
+    except Exception:
+        return None
+
+
+class Dist:
+    def __init__(self):
+        self.world = int(os.environ.get("WORLD_SIZE", "1"))
+        self.rank = int(os.environ.get("RANK", "0"))
+        self.local = int(os.environ.get("LOCAL_RANK", "0"))
+        self.pg = None
+
+    def init(self, use_cuda: bool):
+        if self.world > 1:
+            import torch.distributed as dist
+            dist.init_process_group("nccl" if use_cuda else "gloo")
+            self.pg = dist
+
+    def barrier(self):
+        if self.pg:
+            if self.pg.get_backend() == "nccl":
+                import torch
+                self.pg.barrier(device_ids=[self.local])
+                torch.cuda.synchronize()
+            else:
+                self.pg.barrier()
+
+    def max(self, x: float) -> float:
+        if not self.pg:
+            return x
+        import torch
+        dev = "cuda" if self.pg.get_backend() == "nccl" else "cpu"
+        t = torch.tensor([x], dtype=torch.float64, device=dev)
+        self.pg.all_reduce(t, op=self.pg.ReduceOp.MAX)
+        return float(t.item())
+
+    def close(self):
+        if self.pg:
+            self.pg.destroy_process_group()
+
+
+# ------------------------------------------------------------------ CPU oracle timing
+def oracle_rate(table, seed: int, rows: int):
+    """Time the oracle on `rows` rows of the table (own encryption, untimed);
+    returns (gate bootstraps/s, threads, seconds, gates)."""
+    from oracle import oracle as O
+    from paper_2510_15413_b300 import workloads as WL
+
+    threads = os.cpu_count() or 1
+    O.set_threads(threads)
+    o = O.Oracle(seed)
+    idx = list(range(rows))
+    w, pw = table.width, table.payload_width
+    col = np.concatenate([o.encrypt_bits(table.column_bits().reshape(table.rows, w)[r], WL.STREAM_COLUMN, r * w)
+                          for r in idx])
+    cst = o.encrypt_bits(table.const_bits(), WL.STREAM_CONST, 0)
+    pays = [np.concatenate([o.encrypt_bits(table.payload_bits(q).reshape(table.rows, pw)[r], WL.STREAM_PAYLOAD,
+                                           q * table.rows * pw + r * pw) for r in idx])
+            for q in range(len(table.payloads))]
+    t0 = time.perf_counter()
+    o.scan(table.pred, w, col, cst, pays, pw)
+    dt = time.perf_counter() - t0
+    gates = rows * table.gates_per_row
+    o.close()
+    return gates / dt, O.max_threads(), dt, gates
+
+
+def run_reference(args, dist):
+    from paper_2510_15413_b300 import workloads as WL
+
+    if dist.rank != 0:
+        return
+    t = WL.table(args.workload, seed=args.seed, rows=args.rows)
+    rates = []
+    for _ in range(args.warmup):
+        oracle_rate(t, args.seed, args.cpu_rows)
+    for _ in range(args.steps):
+        r, threads, dt, gates = oracle_rate(t, args.seed, args.cpu_rows)
+        rates.append(r)
+    value = statistics.median(rates)
+    sample = f"{args.cpu_rows} row(s) of {args.workload} = {args.cpu_rows * t.gates_per_row} gate bootstraps per step"
+    line = {"impl": "reference", "metric": "gate bootstraps/s", "value": value, "unit": "gate bootstraps/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32/u64 (exact integer)",
+            "data": "synthetic", "rows_per_s": value / t.gates_per_row,
+            "config": {"workload": args.workload, "rows": t.rows, "width": t.width,
+                       "gates_per_row": t.gates_per_row, "parallelism": "oracle threads over independent gates"},
+            "cpu_baseline": {"value": value, "unit": "gate bootstraps/s", "cores": threads, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": "gate bootstraps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------ GPU run
+def run_ours(args, dist):
+    import torch
+
+    from paper_2510_15413_b300 import fhesql as F
+    from paper_2510_15413_b300 import workloads as WL
+
+    dev = dist.local
+    torch.cuda.set_device(dev)
+    peaks, peak_kind = measured_peaks()
+    props = torch.cuda.get_device_properties(dev)
+    sms = props.multi_processor_count
+
+    ctx = F.Context(args.seed, device=dev)
+    t = WL.table(args.workload, seed=args.seed, rows=args.rows)
+    col, cst, pays = WL.encrypt_table(ctx, t)
+    W = ctx.words
+    dcol = torch.from_numpy(col.view(np.int32)).to(f"cuda:{dev}")
+    dcst = torch.from_numpy(cst.view(np.int32)).to(f"cuda:{dev}")
+    dpay = [torch.from_numpy(p.view(np.int32)).to(f"cuda:{dev}") for p in pays]
+    match = torch.zeros((t.rows, W), dtype=torch.int32, device=f"cuda:{dev}")
+    outs = [torch.zeros((t.rows, t.payload_width, W), dtype=torch.int32, device=f"cuda:{dev}") for _ in pays]
+    st = torch.cuda.current_stream()
+
+    def step():
+        ctx.scan_select(dcol, t.rows, t.width, t.pred, dcst, dpay, t.payload_width, match, outs, stream=st)
+
+    for _ in range(max(3, args.warmup)):
+        step()
+    torch.cuda.synchronize()
+
+    # ---- timed region: exactly K steps, device-resident inputs
+    sampler = ClockSampler(bus_id_of(dev))
+    dist.barrier()
+    torch.cuda.synchronize()
+    sampler.start()
+    time.sleep(0.4)
+    ctx.profile_begin()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    for _ in range(args.steps):
+        step()
+    e1.record(st)
+    torch.cuda.synchronize()
+    dist.barrier()
+    ktimes = ctx.profile_end()
+    clocks = sampler.stop()
+    ms = dist.max(e0.elapsed_time(e1))
+    gates_per_step = t.rows * t.gates_per_row
+    value = dist.world * gates_per_step * args.steps / (ms / 1e3)
+
+    # ---- correctness of the timed outputs (plaintext answer)
+    m_want, p_want = t.expected()
+    got_m = ctx.decrypt_bits(match.cpu().numpy().view(np.uint32))
+    correct = bool(np.array_equal(got_m, m_want))
+    for q, o_ in enumerate(outs):
+        correct &= bool(np.array_equal(ctx.decrypt_uint(o_.cpu().numpy().view(np.uint32), t.payload_width), p_want[q]))
+
+    # ---- roofline of the dominant kernel (blind rotation)
+    br_ms = ktimes["blind_rotate_ms"]
+    br_launches = max(1, ktimes["blind_rotate_launches"])
+    sm_max_mhz = float(peaks.get("sm_max_mhz", 2032.0))
+    peak_tmm = sms * IMAD_PER_CLK_PER_SM * sm_max_mhz * 1e6 / WIDE_MULS_PER_MODMUL / 1e12
+    achieved_tmm = MODMULS_PER_BOOTSTRAP * ktimes["gates"] / (br_ms / 1e3) / 1e12 if br_ms > 0 else 0.0
+    roofline = {"bound": "alu", "kernel": "blind_rotate_kernel", "achieved": achieved_tmm, "peak": peak_tmm,
+                "unit": "Tmodmul/s", "frac": achieved_tmm / peak_tmm if peak_tmm else None, "traffic": None,
+                "peak_kind": f"derived: {sms} SMs x {IMAD_PER_CLK_PER_SM} IMAD/clk x {sm_max_mhz:.0f} MHz / "
+                             f"{WIDE_MULS_PER_MODMUL} wide multiplies per modmul",
+                "avg_launch_ms": br_ms / br_launches, "share_of_step": br_ms / (ms * 1.0) if ms else None,
+                "keyswitch_ms": ktimes["keyswitch_ms"]}
+
+    # ---- end to end through the public C-ABI with host buffers (copies inside the timed region)
+    hcol = torch.from_numpy(col.view(np.int32)).pin_memory()
+    hcst = torch.from_numpy(cst.view(np.int32)).pin_memory()
+    hpay = [torch.from_numpy(p.view(np.int32)).pin_memory() for p in pays]
+    hmatch = torch.zeros((t.rows, W), dtype=torch.int32).pin_memory()
+    houts = [torch.zeros((t.rows, t.payload_width, W), dtype=torch.int32).pin_memory() for _ in pays]
+    h2d = (hcol.numel() + hcst.numel() + sum(p.numel() for p in hpay)) * 4
+    d2h = (hmatch.numel() + sum(o.numel() for o in houts)) * 4
+    ctx.scan_select_host(hcol, t.rows, t.width, t.pred, hcst, hpay, t.payload_width, hmatch, houts, stream=st)
+    dist.barrier()
+    torch.cuda.synchronize()
+    f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    f0.record(st)
+    for _ in range(args.e2e_steps):
+        ctx.scan_select_host(hcol, t.rows, t.width, t.pred, hcst, hpay, t.payload_width, hmatch, houts, stream=st)
+    f1.record(st)
+    torch.cuda.synchronize()
+    dist.barrier()
+    e2e_ms = dist.max(f0.elapsed_time(f1))
+    e2e_value = dist.world * gates_per_step * args.e2e_steps / (e2e_ms / 1e3)
+    e2e_ok = bool(np.array_equal(ctx.decrypt_bits(hmatch.numpy().view(np.uint32)), m_want))
+
+    # ---- per-gate launch baseline and batched rate on the 16-row table
+    small = None
+    if not args.no_per_gate:
+        ts = WL.table("eq4x16", seed=args.seed)
+        scol, scst, spay = WL.encrypt_table(ctx, ts)
+        s_dcol = torch.from_numpy(scol.view(np.int32)).cuda()
+        s_dcst = torch.from_numpy(scst.view(np.int32)).cuda()
+        s_dpay = [torch.from_numpy(p.view(np.int32)).cuda() for p in spay]
+        s_match = torch.zeros((ts.rows, W), dtype=torch.int32, device="cuda")
+        s_outs = [torch.zeros((ts.rows, ts.payload_width, W), dtype=torch.int32, device="cuda") for _ in spay]
+        res = {}
+        for mode in ("batched", "per_gate"):
+            run = lambda: ctx.scan_select(s_dcol, ts.rows, ts.width, ts.pred, s_dcst, s_dpay, ts.payload_width,
+                                          s_match, s_outs, per_gate=(mode == "per_gate"), stream=st)
+            run()
+            torch.cuda.synchronize()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(st)
+            run()
+            b.record(st)
+            torch.cuda.synchronize()
+            res[mode] = ts.rows * ts.gates_per_row / (a.elapsed_time(b) / 1e3)
+        small = {"workload": "eq4x16 (16 rows, 176 gate bootstraps)", "batched_gate_bootstraps_per_s": res["batched"],
+                 "per_gate_gate_bootstraps_per_s": res["per_gate"],
+                 "batched_over_per_gate": res["batched"] / res["per_gate"],
+                 "large_batched_over_per_gate": value / dist.world / res["per_gate"]}
+
+    cpu = None
+    if dist.rank == 0 and not args.no_cpu_baseline:
+        r, threads, dt, gates = oracle_rate(t, args.seed, args.cpu_rows)
+        cpu = {"value": r, "unit": "gate bootstraps/s", "cores": threads, "kind": "oracle",
+               "sample": f"{args.cpu_rows} row(s) of {args.workload} = {gates} gate bootstraps in {dt:.1f} s"}
+
+    line = {
+        "metric": "gate bootstraps/s", "value": value, "unit": "gate bootstraps/s", "n_gpus": dist.world,
+        "steps": args.steps, "warmup": max(3, args.warmup), "ms_per_step": ms / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32/u64 (exact integer)",
+        "data": "synthetic (seeded tables, seeded keys)",
+        "rows_per_s": dist.world * t.rows * args.steps / (ms / 1e3),
+        "config": {"workload": args.workload, "rows": t.rows, "width": t.width, "pred": t.pred,
+                   "payload_columns": len(t.payloads), "payload_width": t.payload_width,
+                   "gates_per_row": t.gates_per_row, "gate_bootstraps_per_step": gates_per_step,
+                   "params": "n=630 N=1024 Bg=2^7 l=3 ks 4^8 Torus32",
+                   "l2": "inputs larger than L2 (%.0f MB column+payload per step)" % (h2d / 1e6),
+                   "parallelism": f"replica per GPU x{dist.world}"},
+        "correct": correct and e2e_ok,
+        "roofline": roofline,
+        "cpu_baseline": cpu,
+        "e2e": {"value": e2e_value, "unit": "gate bootstraps/s", "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h},
+        "gpu_launches": int(ktimes["blind_rotate_launches"] + ktimes["keyswitch_launches"]),
+        "clocks": clocks,
+        "per_gate_baseline": small,
+        "peaks": {"kind": peak_kind, "hbm_gbs": peaks.get("hbm_gbs"), "sms": sms},
+    }
+    ctx.close()
+    if dist.rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    dist = Dist()
+    if args.impl == "reference":
+        dist.init(use_cuda=False)
+        run_reference(args, dist)
+    else:
+        dist.init(use_cuda=True)
+        run_ours(args, dist)
+    dist.close()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,212 @@
+/*
+ * fhesql.h -- C interface of the B300 (sm_103a) engine for the oblivious
+ * scan-select of FHE-SQL (arXiv 2510.15413).
+ *
+ * The paper's server (Alg. 2, ProcessQuery) evaluates the WHERE predicate of a
+ * query homomorphically on every encrypted row, collects the encrypted mask
+ * bits, and applies them to the selected columns with a homomorphic
+ * If-Then-Else so that non-matching rows become encryptions of zero (§4.2;
+ * §6 D, eq. (1)-(3)).  The client (Alg. 1) encrypts the query constants and
+ * decrypts the result.  FHE is the TFHE scheme the paper cites (§1, §2.2):
+ * here one LWE ciphertext per bit, every binary gate one gate bootstrap.
+ *
+ * Conventions shared by every call:
+ *   - A ciphertext is n+1 uint32 words (a_0 .. a_{n-1}, b), body last, a
+ *     Torus32 value mod 2^32; phase = b - sum a_i s_i.  A bit is encoded as
+ *     +2^29 (true) or -2^29 (false).
+ *   - Multi-bit values are [rows][width][n+1], bit 0 (LSB) first.
+ *   - Pointers named d_* are device pointers (any allocator, e.g. PyTorch's
+ *     caching allocator) owned by the caller; the library never frees them.
+ *     Pointers named h_* or without prefix are host pointers.
+ *   - Every call returns FSQL_OK (0) or an FSQL_ERR_* code and never throws;
+ *     fsql_last_error() gives a message for the calling thread.  Argument
+ *     checks are synchronous.  Device work is asynchronous on the given
+ *     cudaStream_t (passed as void*, NULL = legacy default stream); a CUDA
+ *     launch failure is reported by the call that launched it, a fault
+ *     during execution by the next synchronising call.
+ *   - One context must be driven from one stream at a time: its scratch and
+ *     plan buffers are reused by the next call on the same context.
+ */
+#ifndef FHESQL_H
+#define FHESQL_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define FSQL_API __attribute__((visibility("default")))
+#else
+#define FSQL_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define FSQL_OK 0
+#define FSQL_ERR_ARG 1         /* bad argument (null pointer, size, enum) */
+#define FSQL_ERR_OOM 2         /* device or host allocation failed */
+#define FSQL_ERR_CUDA 3        /* a CUDA runtime call failed */
+#define FSQL_ERR_TIMEOUT 4     /* a bounded device wait gave up */
+#define FSQL_ERR_ADMISSION 5   /* serving: request does not fit the memory budget */
+#define FSQL_ERR_UNSUPPORTED 6 /* parameters outside what the kernels implement */
+
+/* Gate types of the bootstrapped gates.  ANDNY(a,b) = (not a) and b,
+ * ANDYN(a,b) = a and (not b), ORNY(a,b) = (not a) or b, ORYN(a,b) = a or (not b).
+ * NOT needs no bootstrap (negate every word) and has no code here. */
+#define FSQL_NAND 0
+#define FSQL_AND 1
+#define FSQL_OR 2
+#define FSQL_XOR 3
+#define FSQL_XNOR 4
+#define FSQL_NOR 5
+#define FSQL_ANDNY 6
+#define FSQL_ANDYN 7
+#define FSQL_ORNY 8
+#define FSQL_ORYN 9
+
+/* Predicates of the WHERE clause (§4.3 B: equality and comparison).
+ * EQ: c = k.  LT: c < k (unsigned).  RANGE: lo <= c < hi (unsigned). */
+#define FSQL_EQ 0
+#define FSQL_LT 1
+#define FSQL_RANGE 2
+
+/* TFHE parameters.  Torus32; GLWE dimension k = 1.  The GPU kernels
+ * implement N = 1024, l = 3, 2 <= bg_bits <= 10, ks_base_bits = 2, ks_t = 8
+ * and n <= 639; other values are accepted by the host-side calls only. */
+typedef struct fsql_params {
+    uint32_t n;            /* LWE dimension */
+    uint32_t N;            /* GLWE polynomial size */
+    uint32_t bg_bits;      /* log2 bootstrap gadget base */
+    uint32_t l;            /* bootstrap gadget levels */
+    uint32_t ks_base_bits; /* log2 keyswitch base */
+    uint32_t ks_t;         /* keyswitch levels */
+    double lwe_sigma;      /* LWE noise std-dev as a fraction of the torus */
+    double glwe_sigma;     /* GLWE noise std-dev as a fraction of the torus */
+} fsql_params;
+
+typedef struct fsql_ctx fsql_ctx;
+
+/* Default parameter set: n=630, N=1024, base 2^7 x 3, keyswitch base 4 x 8,
+ * sigma 2^-15 (LWE) and 2^-25 (GLWE). */
+FSQL_API int fsql_params_default(fsql_params* out);
+/* Toy parameter set (n=16, N=64) for host-side tests; not runnable on the GPU. */
+FSQL_API int fsql_params_toy(fsql_params* out);
+
+/* Key generation (KeyGen of §2.2) from one 64-bit seed, with the SplitMix64
+ * generator (Steele, Lea & Flood 2014): stream 0 LWE key bits, 1 GLWE key
+ * bits, 2 bootstrapping key, 3 keyswitching key.  The secret keys stay in
+ * host memory (client side); the bootstrapping key is converted to the NTT
+ * domain and, with the keyswitching key, uploaded to `device` (-1 = no
+ * device: host-side calls only).  On success *out owns all of it. */
+FSQL_API int fsql_ctx_create(const fsql_params* params, uint64_t seed, int device, fsql_ctx** out);
+FSQL_API void fsql_ctx_destroy(fsql_ctx* ctx);
+FSQL_API int fsql_ctx_params(const fsql_ctx* ctx, fsql_params* out);
+/* Device bytes held by the context for keys (bootstrapping key in the NTT
+ * domain + keyswitching key) and for scratch currently allocated. */
+FSQL_API int fsql_ctx_device_bytes(const fsql_ctx* ctx, size_t* key_bytes, size_t* scratch_bytes);
+
+/* Copy keys out to host buffers (any may be NULL): lwe_key [n] bits,
+ * glwe_key [N] bits, bk [n][2l][2][N] standard domain (row u*l+j-1 holds
+ * GLWE(0) + s_i * 2^(32-bg*j) on polynomial u: 0 = mask, 1 = body),
+ * ksk [N][ks_t][2^ks_base_bits - 1][n+1] = LWE_s(v * S_i * 2^(32-kb*(j+1))). */
+FSQL_API int fsql_export_keys(const fsql_ctx* ctx, uint8_t* lwe_key, uint8_t* glwe_key, uint32_t* bk, uint32_t* ksk);
+
+/* ---------------- client side (host memory; Alg. 1 EncryptQuery / Decrypt) ---------------- */
+
+/* Encrypt `count` torus messages.  Ciphertext c draws SplitMix64 words
+ * (first_index + c) * (n + 2) .. + n + 1 of `stream` (mask, then two for
+ * Box-Muller noise), so chunks encrypt identically to one big call. */
+FSQL_API int fsql_encrypt(const fsql_ctx* ctx, const uint32_t* mu, size_t count, uint64_t stream, uint64_t first_index,
+                 uint32_t* out);
+/* Encrypt bits (0/1 bytes) as -q/8 / +q/8. */
+FSQL_API int fsql_encrypt_bits(const fsql_ctx* ctx, const uint8_t* bits, size_t count, uint64_t stream,
+                      uint64_t first_index, uint32_t* out);
+/* Encrypt `rows` unsigned values of `width` bits (1..64) into [rows][width][n+1];
+ * ciphertext index of (row, bit) is first_index + row*width + bit. */
+FSQL_API int fsql_encrypt_uint(const fsql_ctx* ctx, const uint64_t* values, size_t rows, uint32_t width, uint64_t stream,
+                      uint64_t first_index, uint32_t* out);
+/* Phases b - <a, s> of `count` ciphertexts. */
+FSQL_API int fsql_phase(const fsql_ctx* ctx, const uint32_t* ct, size_t count, uint32_t* out);
+/* Decrypt bits: 1 when the phase read as int32 is positive. */
+FSQL_API int fsql_decrypt_bits(const fsql_ctx* ctx, const uint32_t* ct, size_t count, uint8_t* out);
+/* Decrypt [rows][width][n+1] into unsigned values. */
+FSQL_API int fsql_decrypt_uint(const fsql_ctx* ctx, const uint32_t* ct, size_t rows, uint32_t width, uint64_t* out);
+
+/* ---------------- server side (device memory, asynchronous on `stream`) ---------------- */
+
+/* Gate bootstraps of `count` independent gates: out[g] = gate types[g] of
+ * (a[g], b[g]).  d_types: uint8 [count]; d_a, d_b, d_out: [count][n+1].
+ * Steps: linear combination, modulus switch, blind rotation (n CMux external
+ * products in the NTT domain over p = 2^64 - 2^32 + 1), sample extraction,
+ * keyswitch.  d_out may alias neither input.  Types must be FSQL_NAND ..
+ * FSQL_ORYN (a device array is not checked: other values compute ORYN). */
+FSQL_API int fsql_gate_batch(fsql_ctx* ctx, const uint8_t* d_types, const uint32_t* d_a, const uint32_t* d_b,
+                    uint32_t* d_out, size_t count, void* stream);
+
+/* The two halves of fsql_gate_batch, exposed for tests and profiling.
+ * fsql_blind_rotate_extract writes, per gate, the extracted sample of
+ * dimension N under the GLWE key: d_big [count][N+1]. */
+FSQL_API int fsql_blind_rotate_extract(fsql_ctx* ctx, const uint8_t* d_types, const uint32_t* d_a, const uint32_t* d_b,
+                              uint32_t* d_big, size_t count, void* stream);
+/* LWE keyswitch N -> n: d_big [count][N+1] -> d_out [count][n+1]. */
+FSQL_API int fsql_keyswitch(fsql_ctx* ctx, const uint32_t* d_big, uint32_t* d_out, size_t count, void* stream);
+
+/* Exact negacyclic product through the device NTT, for tests: out = d * a in
+ * Z[X]/(X^N+1) mod 2^32, where d_digits holds N signed values in
+ * [-2^(bg-1), 2^(bg-1)) and d_poly N uint32 coefficients. */
+FSQL_API int fsql_debug_ntt_mul(fsql_ctx* ctx, const int32_t* d_digits, const uint32_t* d_poly, uint32_t* d_out,
+                       void* stream);
+
+/* Number of gate bootstraps per row and the level widths of the predicate
+ * netlist (the circuit scheduler's lowering): *gates_per_row, *levels, and,
+ * if level_widths is non-NULL, up to max_levels per-row gate counts. */
+FSQL_API int fsql_plan_info(uint32_t pred, uint32_t width, uint32_t n_payloads, uint32_t payload_width,
+                   uint32_t* gates_per_row, uint32_t* levels, uint32_t* level_widths, uint32_t max_levels);
+
+/* Oblivious scan-select (Alg. 2 ProcessQuery over all rows; §4.2).
+ * d_column: [rows][width][n+1] encrypted column; d_const: the encrypted
+ * constant bits ([width][n+1] for EQ/LT, lo then hi [2*width][n+1] for
+ * RANGE); d_payloads: host array of n_payloads device pointers, each
+ * [rows][payload_width][n+1].  Outputs: d_match [rows][n+1] the encrypted
+ * predicate bit of each row; d_out_payloads: host array of n_payloads device
+ * pointers [rows][payload_width][n+1] = AND(match, payload bit), i.e. the
+ * payload where the row matches and an encryption of 0 elsewhere.  Every row
+ * runs the same gates: the work depends only on the sizes.  Outputs may not
+ * alias inputs.  per_gate != 0 launches one gate per kernel launch (the plain
+ * baseline); otherwise each circuit level runs as batched launches. */
+FSQL_API int fsql_scan_select(fsql_ctx* ctx, const uint32_t* d_column, size_t rows, uint32_t width, uint32_t pred,
+                     const uint32_t* d_const, uint32_t n_payloads, const uint32_t* const* d_payloads,
+                     uint32_t payload_width, uint32_t* d_match, uint32_t* const* d_out_payloads, int per_gate,
+                     void* stream);
+
+/* The same scan from host buffers (layouts as above, h_payloads / h_out_payloads
+ * are arrays of host pointers): copies inputs to the device, runs the batched
+ * scan, copies the outputs back and synchronises `stream` before returning.
+ * Device staging buffers are owned by the context and reused. */
+FSQL_API int fsql_scan_select_host(fsql_ctx* ctx, const uint32_t* h_column, size_t rows, uint32_t width, uint32_t pred,
+                          const uint32_t* h_const, uint32_t n_payloads, const uint32_t* const* h_payloads,
+                          uint32_t payload_width, uint32_t* h_match, uint32_t* const* h_out_payloads, void* stream);
+
+/* Kernel timing with CUDA events, recorded on the launch stream around every
+ * blind-rotation and keyswitch launch of this context between
+ * fsql_profile_begin and fsql_profile_end (which waits for the recorded
+ * events).  Durations are summed device times in milliseconds. */
+typedef struct fsql_kernel_times {
+    double blind_rotate_ms;
+    double keyswitch_ms;
+    uint64_t blind_rotate_launches;
+    uint64_t keyswitch_launches;
+    uint64_t gates;  /* gates bootstrapped by the recorded launches */
+} fsql_kernel_times;
+FSQL_API int fsql_profile_begin(fsql_ctx* ctx);
+FSQL_API int fsql_profile_end(fsql_ctx* ctx, fsql_kernel_times* out);
+
+/* Message for the last failed call on this thread ("" if none). */
+FSQL_API const char* fsql_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FHESQL_H */

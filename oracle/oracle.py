@@ -73,8 +73,7 @@ def lib():
         L.orc_gate_plain.argtypes = [C.c_int, C.c_int, C.c_int]
         L.orc_netlist_eval_plain.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int, u8p, u8p]
         L.orc_scan.argtypes = [C.c_void_p, C.c_int, C.c_int, u32p, u32p, C.c_int, C.c_int,
-                               C.POINTER(C.c_void_p), u32p, C.POINTER(C.c_void_p),
-                               C.c_longlong, C.c_longlong]
+                               C.POINTER(C.c_void_p), u32p, C.POINTER(C.c_void_p), C.c_longlong]
         L.orc_set_threads.argtypes = [C.c_int]
         L.orc_max_threads.restype = C.c_int
         _lib = L
@@ -291,21 +290,18 @@ class Oracle:
         lib().orc_not(self.n, a, out)
         return out
 
-    def scan(self, pred: int, w: int, column, consts, payloads, pw: int, row_begin: int = 0,
-             row_end: int | None = None):
-        """Scan rows [row_begin, row_end): returns (match [rows, n+1], [payload outs])."""
+    def scan(self, pred: int, w: int, column, consts, payloads, pw: int):
+        """Scan every row given: returns (match [rows, n+1], [payload outs [rows, pw, n+1]])."""
         W = self.n + 1
         column = _u32(column).reshape(-1, w, W)
         rows = column.shape[0]
-        row_end = rows if row_end is None else row_end
         consts = _u32(consts).reshape(-1, W)
         pays = [_u32(p).reshape(rows, pw, W) for p in payloads]
         match = np.zeros((rows, W), np.uint32)
         outs = [np.zeros((rows, pw, W), np.uint32) for _ in pays]
         pin = (C.c_void_p * max(1, len(pays)))(*[p.ctypes.data for p in pays])
         pout = (C.c_void_p * max(1, len(outs)))(*[o.ctypes.data for o in outs])
-        rc = lib().orc_scan(self._h, pred, w, column, consts, len(pays), pw, pin, match, pout,
-                            row_begin, row_end)
+        rc = lib().orc_scan(self._h, pred, w, column, consts, len(pays), pw, pin, match, pout, rows)
         if rc != 0:
             raise ValueError("scan failed")
         return match, outs

@@ -664,45 +664,63 @@ ORC_API int orc_netlist_eval_plain(int pred, int w, int n_payload, int pw, const
 }
 
 /* ------------------------------------------------------------------ */
-/* The scan (Alg. 2): rows [row_begin, row_end) of a table.               */
-/* column: [rows][w][n+1]; consts: [w or 2w][n+1]; payload p: [rows][pw][n+1] */
-/* (payloads[p] points at row 0); match: [rows][n+1]; out p: [rows][pw][n+1]. */
-/* Rows are independent and run one per thread; within a row the gates run  */
-/* in netlist order.                                                         */
+/* The scan (Alg. 2): every row of a table.                               */
+/* column: [rows][w][n+1]; consts: [w or 2w][n+1]; payload p: [rows][pw][n+1]; */
+/* match: [rows][n+1]; out p: [rows][pw][n+1].  Rows are independent; the  */
+/* gates of a row run in netlist order, except that gates whose inputs are */
+/* all ready (same depth) run side by side, over all rows at once.         */
 /* ------------------------------------------------------------------ */
 ORC_API int orc_scan(const orc_ctx *c, int pred, int w, const uint32_t *column, const uint32_t *consts,
                      int n_payload, int pw, const uint32_t *const *payloads, uint32_t *match,
-                     uint32_t *const *out_payloads, long long row_begin, long long row_end)
+                     uint32_t *const *out_payloads, long long rows)
 {
     int32_t m, ninp;
     int g = orc_netlist(pred, w, n_payload, pw, NULL, NULL, NULL, &m, &ninp);
     if (g < 0) return -1;
     int32_t *t = (int32_t *)malloc(sizeof(int32_t) * g), *a = (int32_t *)malloc(sizeof(int32_t) * g),
-            *b = (int32_t *)malloc(sizeof(int32_t) * g);
+            *b = (int32_t *)malloc(sizeof(int32_t) * g), *depth = (int32_t *)malloc(sizeof(int32_t) * (ninp + g));
     orc_netlist(pred, w, n_payload, pw, t, a, b, &m, &ninp);
-    size_t W = (size_t)c->p.n + 1;
-    int nconst = pred == P_RANGE ? 2 * w : w;
-    int bad = 0;
-#pragma omp parallel for schedule(dynamic, 1) reduction(| : bad)
-    for (long long row = row_begin; row < row_end; row++) {
-        uint32_t *wires = (uint32_t *)malloc(sizeof(uint32_t) * W * (ninp + g));
-        for (int i = 0; i < w; i++) memcpy(wires + i * W, column + ((size_t)row * w + i) * W, W * 4);
-        for (int i = 0; i < nconst; i++) memcpy(wires + (w + i) * W, consts + (size_t)i * W, W * 4);
-        for (int p = 0; p < n_payload; p++)
-            for (int bit = 0; bit < pw; bit++)
-                memcpy(wires + (size_t)(w + nconst + p * pw + bit) * W, payloads[p] + ((size_t)row * pw + bit) * W, W * 4);
-        for (int k = 0; k < g; k++)
-            bad |= orc_gate(c, t[k], wires + (size_t)a[k] * W, wires + (size_t)b[k] * W, wires + (size_t)(ninp + k) * W) != 0;
-        memcpy(match + (size_t)row * W, wires + (size_t)m * W, W * 4);
-        int first_mask = ninp + g - n_payload * pw;
-        for (int p = 0; p < n_payload; p++)
-            for (int bit = 0; bit < pw; bit++)
-                memcpy(out_payloads[p] + ((size_t)row * pw + bit) * W, wires + (size_t)(first_mask + p * pw + bit) * W, W * 4);
-        free(wires);
+    int maxd = 0;
+    for (int i = 0; i < ninp; i++) depth[i] = 0;
+    for (int k = 0; k < g; k++) {
+        int da = depth[a[k]], db = depth[b[k]];
+        depth[ninp + k] = 1 + (da > db ? da : db);
+        if (depth[ninp + k] > maxd) maxd = depth[ninp + k];
     }
+    size_t W = (size_t)c->p.n + 1, per_row = (size_t)(ninp + g) * W;
+    int nconst = pred == P_RANGE ? 2 * w : w;
+    uint32_t *wires = (uint32_t *)malloc(sizeof(uint32_t) * per_row * (size_t)(rows > 0 ? rows : 1));
+    for (long long row = 0; row < rows; row++) {
+        uint32_t *wr = wires + (size_t)row * per_row;
+        for (int i = 0; i < w; i++) memcpy(wr + i * W, column + ((size_t)row * w + i) * W, W * 4);
+        for (int i = 0; i < nconst; i++) memcpy(wr + (w + i) * W, consts + (size_t)i * W, W * 4);
+        for (int p = 0; p < n_payload; p++)
+            for (int bit = 0; bit < pw; bit++)
+                memcpy(wr + (size_t)(w + nconst + p * pw + bit) * W, payloads[p] + ((size_t)row * pw + bit) * W, W * 4);
+    }
+    int bad = 0;
+    for (int d = 1; d <= maxd; d++) {
+#pragma omp parallel for schedule(dynamic, 1) collapse(2) reduction(| : bad)
+        for (long long row = 0; row < rows; row++)
+            for (int k = 0; k < g; k++) {
+                if (depth[ninp + k] != d) continue;
+                uint32_t *wr = wires + (size_t)row * per_row;
+                bad |= orc_gate(c, t[k], wr + (size_t)a[k] * W, wr + (size_t)b[k] * W, wr + (size_t)(ninp + k) * W) != 0;
+            }
+    }
+    int first_mask = ninp + g - n_payload * pw;
+    for (long long row = 0; row < rows; row++) {
+        uint32_t *wr = wires + (size_t)row * per_row;
+        memcpy(match + (size_t)row * W, wr + (size_t)m * W, W * 4);
+        for (int p = 0; p < n_payload; p++)
+            for (int bit = 0; bit < pw; bit++)
+                memcpy(out_payloads[p] + ((size_t)row * pw + bit) * W, wr + (size_t)(first_mask + p * pw + bit) * W, W * 4);
+    }
+    free(wires);
     free(t);
     free(a);
     free(b);
+    free(depth);
     return bad ? -1 : 0;
 }
 

@@ -1,0 +1,107 @@
+// engine.h -- internal declarations shared by the host side (host.cpp) and
+// the device side (kernels.cu) of the library.  Not part of the C interface.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "../../include/fhesql.h"
+
+namespace fsql {
+
+// Goldilocks prime p = 2^64 - 2^32 + 1 used by the exact NTT.
+constexpr uint64_t kP = 0xFFFFFFFF00000001ull;
+
+// Fixed shape the GPU kernels implement (checked at context creation).
+constexpr int kN = 1024;     // GLWE polynomial size
+constexpr int kL = 3;        // bootstrap gadget levels
+constexpr int kRows = 2 * kL;  // rows of a GGSW (2 polynomials x l levels)
+constexpr int kKsT = 8;      // keyswitch levels
+constexpr int kKsBaseBits = 2;
+constexpr int kKsDigits = (1 << kKsBaseBits) - 1;  // nonzero digit values
+constexpr int kKsRowWords = 640;  // n+1 padded to a multiple of 4 words (16 B)
+constexpr int kMaxN = 1024;  // largest LWE dimension the kernels take
+
+// One bootstrapped gate: inputs a, b and output pointer, all [n+1] words.
+struct GateDesc {
+  const uint32_t* a;
+  const uint32_t* b;
+  uint32_t* out;
+  uint32_t type;
+  uint32_t pad;
+};
+
+// Twiddle tables of the 1024-point negacyclic NTT, in the register layout the
+// warp NTT uses (see kernels.cu).
+struct NttTables {
+  uint64_t fwd_uniform[32];      // psi^bitrev(k), k < 32 (stages with distance >= 32)
+  uint64_t inv_uniform[32];      // psi^-bitrev(k), k < 32
+  uint64_t fwd_lane[31 * 32];    // per-lane twiddles of the distance < 32 stages
+  uint64_t inv_lane[31 * 32];
+  uint64_t n_inv;                // N^-1 mod p
+};
+
+struct Plan;  // scan plan (kernels.cu)
+
+struct Ctx {
+  fsql_params p{};
+  uint64_t seed = 0;
+  int device = -1;
+  // host-side secrets and standard-domain keys (client side)
+  std::vector<uint8_t> s;    // LWE key [n]
+  std::vector<uint8_t> S;    // GLWE key [N]
+  std::vector<uint32_t> bk;  // [n][2l][2][N]
+  std::vector<uint32_t> ksk; // [N][t][digits][n+1]
+  // device-resident keys
+  uint64_t* d_bkhat = nullptr;   // [n][2l][32][32][2] u64, NTT domain, times N^-1
+  uint32_t* d_ksk = nullptr;     // [N][t][digits][kKsRowWords]
+  NttTables* d_tables = nullptr;
+  NttTables tables{};
+  size_t key_bytes = 0;
+  // scratch (grown on demand, freed with the context)
+  uint32_t* d_big = nullptr;     // extracted samples [cap][N+1]
+  size_t big_cap = 0;
+  GateDesc* d_desc = nullptr;
+  size_t desc_cap = 0;
+  uint32_t* d_wires = nullptr;   // intermediate wires of a scan
+  size_t wires_cap = 0;          // in words
+  GateDesc* h_desc = nullptr;    // pinned staging for descriptor uploads
+  size_t h_desc_cap = 0;
+  void* desc_event = nullptr;    // cudaEvent_t guarding h_desc reuse
+  uint32_t* d_stage = nullptr;   // device staging for the host-buffer scan
+  size_t stage_cap = 0;
+  Plan* plan = nullptr;
+  void* prof = nullptr;          // kernel-timing events while profiling (kernels.cu)
+  int sm_count = 0;
+  std::mutex mu;
+};
+
+// host.cpp
+void set_error(const std::string& msg);
+std::vector<uint8_t> sample_key_bits(uint64_t seed, uint64_t stream, size_t count);
+void keygen(Ctx& c);
+uint32_t encode_bit(bool b);
+
+// Per-row netlist of a predicate (circuit scheduler, host side).
+struct Netlist {
+  int n_inputs = 0;          // column bits, constant bits, payload bits
+  int match_wire = -1;
+  int first_mask_gate = 0;   // gates [first_mask_gate, count) are the payload masks
+  std::vector<int> type, a, b;  // gate g writes wire n_inputs + g
+  std::vector<int> level;       // 1-based level of each gate
+  int levels = 0;
+};
+bool build_netlist(uint32_t pred, uint32_t width, uint32_t n_payloads, uint32_t payload_width, Netlist* out);
+
+// kernels.cu
+int device_init(Ctx& c);     // tables, BK -> NTT domain, KSK upload
+void device_free(Ctx& c);
+int launch_gates(Ctx& c, const GateDesc* d_desc, size_t count, uint32_t* d_big, void* stream);
+int launch_blind_rotate(Ctx& c, const GateDesc* d_desc, size_t count, uint32_t* d_big, void* stream);
+int launch_keyswitch(Ctx& c, const uint32_t* d_big, const GateDesc* d_desc, uint32_t* d_out_contig,
+                     size_t count, void* stream);
+
+}  // namespace fsql

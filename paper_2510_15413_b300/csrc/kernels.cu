@@ -1,0 +1,980 @@
+// kernels.cu -- device half of the library: the gate-bootstrap engine
+// (linear combination, modulus switch, blind rotation, sample extraction,
+// keyswitch) and the scan driver that runs the predicate circuit level by
+// level over all rows (Alg. 2 ProcessQuery; §4.2 mask generation and
+// application).
+//
+// Blind rotation kernel.  One warp owns one gate for all n CMux steps; a CTA
+// of 8 warps runs 8 gates in lockstep so that the bootstrapping-key slice of
+// each CMux step and gadget row (16 KB in the NTT domain) is staged once into
+// shared memory by cp.async and read by all 8 warps.  Per CMux step a warp:
+//   for each of the 2l = 6 rows (u, j): forms digit j of X^a*ACC_u - ACC_u,
+//     runs the forward NTT in registers, and multiply-accumulates with the
+//     staged key row into two NTT-domain accumulators (one per output
+//     polynomial) that stay in registers;
+//   runs the two inverse NTTs, lifts the exact integers mod 2^32 and adds
+//   them into its accumulator polynomials in shared memory.
+// Keyswitch kernel.  A CTA takes 16 gates and all output columns; each
+// thread owns 4 columns, walks the (i, j) digit positions once and streams
+// the three nonzero-digit key rows for its columns, so each key row read from
+// L2 serves 16 gates.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstring>
+#include <vector>
+
+#include "engine.h"
+#include "ntt.cuh"
+
+namespace fsql {
+
+namespace {
+
+constexpr int kBrWarps = 8;
+constexpr int kBrThreads = kBrWarps * 32;
+constexpr int kChunkU64 = 32 * 32 * 2;           // one key row: 1024 slots x 2 output polys
+constexpr int kChunkBytes = kChunkU64 * 8;       // 16 KB
+constexpr int kStages = 3;
+constexpr int kTabBytes = (sizeof(NttTables) + 127) / 128 * 128;
+constexpr int kWarpTile = 1024 * 8;              // transpose tile
+constexpr int kWarpAcc = 2 * kN * 4;             // accumulator polynomials (u32)
+constexpr int kWarpAbar = kMaxN * 2;             // switched mask, u16
+constexpr int kWarpBytes = kWarpTile + kWarpAcc + kWarpAbar + 16;
+constexpr int kBrSmem = kTabBytes + kStages * kChunkBytes + kBrWarps * kWarpBytes;
+static_assert(kBrSmem <= 227 * 1024, "blind-rotation shared memory over budget");
+
+constexpr int kKsGates = 16;
+constexpr int kKsThreads = kKsRowWords / 4;      // 160 threads x 4 columns
+
+#define CK(call)                                                                 \
+  do {                                                                           \
+    cudaError_t e_ = (call);                                                     \
+    if (e_ != cudaSuccess) {                                                     \
+      set_error(std::string(#call) + ": " + cudaGetErrorString(e_));             \
+      return FSQL_ERR_CUDA;                                                      \
+    }                                                                            \
+  } while (0)
+
+// ------------------------------------------------------------------ host math
+uint64_t mulmod_host(uint64_t a, uint64_t b) {
+  return static_cast<uint64_t>((static_cast<unsigned __int128>(a) * b) % kP);
+}
+uint64_t powmod_host(uint64_t a, uint64_t e) {
+  uint64_t r = 1;
+  while (e) {
+    if (e & 1) r = mulmod_host(r, a);
+    a = mulmod_host(a, a);
+    e >>= 1;
+  }
+  return r;
+}
+uint32_t bitrev10(uint32_t k) {
+  uint32_t r = 0;
+  for (int b = 0; b < 10; ++b) r |= ((k >> b) & 1u) << (9 - b);
+  return r;
+}
+
+// psi = 7^((p-1)/2048): 7 generates the multiplicative group of Z_p, so psi
+// has order exactly 2048 (checked: psi^1024 = -1).
+bool make_tables(NttTables* T) {
+  const uint64_t psi = powmod_host(7, (kP - 1) / 2048);
+  if (powmod_host(psi, 1024) != kP - 1) return false;
+  const uint64_t psi_inv = powmod_host(psi, kP - 2);
+  std::vector<uint64_t> f(kN), g(kN);
+  for (uint32_t k = 0; k < static_cast<uint32_t>(kN); ++k) {
+    f[k] = powmod_host(psi, bitrev10(k));
+    g[k] = powmod_host(psi_inv, bitrev10(k));
+  }
+  for (int k = 0; k < 32; ++k) {
+    T->fwd_uniform[k] = f[k];
+    T->inv_uniform[k] = g[k];
+  }
+  for (int s = 0; s < 5; ++s) {
+    // forward, distance 16>>s: element 32L + j is in group (32L + j)/(2d) of stage m = 32<<s
+    const int per_lane = 1 << s, off = (1 << s) - 1;
+    for (int q = 0; q < per_lane; ++q)
+      for (int L = 0; L < 32; ++L) T->fwd_lane[(off + q) * 32 + L] = f[(32 << s) + L * per_lane + q];
+    // inverse, distance 1<<s: h = 512>>s groups
+    const int per_lane_i = 16 >> s, off_i = 32 - (32 >> s);
+    for (int q = 0; q < per_lane_i; ++q)
+      for (int L = 0; L < 32; ++L) T->inv_lane[(off_i + q) * 32 + L] = g[(512 >> s) + L * per_lane_i + q];
+  }
+  T->n_inv = powmod_host(kN, kP - 2);
+  return true;
+}
+
+// ------------------------------------------------------------------ device helpers
+__device__ __forceinline__ void cp_async16(void* smem_dst, const void* gsrc) {
+  const uint32_t s = static_cast<uint32_t>(__cvta_generic_to_shared(smem_dst));
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+// Gate linear forms on the +-q/8 encoding: out = (0, .., 0, k) + ca*c1 + cb*c2.
+struct Lin {
+  uint32_t k;
+  uint32_t ca, cb;
+};
+__device__ __forceinline__ Lin gate_lin(uint32_t type) {
+  const uint32_t E = 1u << 29, M = 0xFFFFFFFFu;  // q/8, -1
+  switch (type) {
+    case FSQL_NAND: return {E, M, M};
+    case FSQL_AND: return {0u - E, 1u, 1u};
+    case FSQL_OR: return {E, 1u, 1u};
+    case FSQL_XOR: return {2u * E, 2u, 2u};
+    case FSQL_XNOR: return {0u - 2u * E, 0u - 2u, 0u - 2u};
+    case FSQL_NOR: return {0u - E, M, M};
+    case FSQL_ANDNY: return {0u - E, M, 1u};
+    case FSQL_ANDYN: return {0u - E, 1u, M};
+    case FSQL_ORNY: return {E, M, 1u};
+    default: return {E, 1u, M};  // FSQL_ORYN (types are validated on the host)
+  }
+}
+
+// ------------------------------------------------------------------ kernels
+
+// Key conversion: one warp per key polynomial (i, row, c): forward NTT of the
+// coefficients read as integers in [0, 2^32), times 1/N, stored as
+// bkhat[i][row][j][L][c] so that lane L of a warp in layout B reads its
+// (j, c = 0..1) pair as one 16-byte word.
+__global__ void __launch_bounds__(128) bk_to_ntt_kernel(const uint32_t* __restrict__ bk, uint64_t* __restrict__ bkhat,
+                                                        const NttTables* __restrict__ gtab, int n) {
+  __shared__ NttTables T;
+  __shared__ uint64_t tiles[4][1024];
+  for (int k = threadIdx.x; k < static_cast<int>(sizeof(NttTables) / 8); k += blockDim.x)
+    reinterpret_cast<uint64_t*>(&T)[k] = reinterpret_cast<const uint64_t*>(gtab)[k];
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int w = blockIdx.x * 4 + warp;
+  if (w >= n * kRows * 2) return;
+  const int i = w / (kRows * 2), row = (w / 2) % kRows, c = w % 2;
+  const uint32_t* src = bk + (static_cast<size_t>(i * kRows + row) * 2 + c) * kN;
+  uint64_t x[32];
+#pragma unroll
+  for (int j = 0; j < 32; ++j) x[j] = src[lane + 32 * j];
+  dev::ntt_forward(x, tiles[warp], T, lane);
+  uint64_t* dst = bkhat + static_cast<size_t>(i * kRows + row) * kChunkU64;
+#pragma unroll
+  for (int j = 0; j < 32; ++j) dst[(j * 32 + lane) * 2 + c] = dev::gl_mul(x[j], T.n_inv);
+}
+
+// Contiguous gate arrays -> descriptors.
+__global__ void make_desc_kernel(GateDesc* __restrict__ desc, const uint8_t* __restrict__ types,
+                                 const uint32_t* a, const uint32_t* b, uint32_t* out, int count, int words) {
+  const int g = blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= count) return;
+  GateDesc d;
+  d.a = a + static_cast<size_t>(g) * words;
+  d.b = b + static_cast<size_t>(g) * words;
+  d.out = out ? out + static_cast<size_t>(g) * words : nullptr;
+  d.type = types[g];
+  d.pad = 0;
+  desc[g] = d;
+}
+
+__device__ __forceinline__ void issue_chunk(uint64_t* stage_slot, const uint64_t* __restrict__ bkhat, int k) {
+  const uint4* src = reinterpret_cast<const uint4*>(bkhat + static_cast<size_t>(k) * kChunkU64);
+  uint4* dst = reinterpret_cast<uint4*>(stage_slot);
+  for (int q = threadIdx.x; q < kChunkBytes / 16; q += kBrThreads) cp_async16(dst + q, src + q);
+}
+
+// Blind rotation + sample extraction for `count` gates (see file comment).
+// big: [count][N+1] extracted samples under the GLWE key.
+__global__ void __launch_bounds__(kBrThreads, 1)
+    blind_rotate_kernel(const GateDesc* __restrict__ desc, int count, const uint64_t* __restrict__ bkhat,
+                        const NttTables* __restrict__ gtab, int n, int bg_bits, uint32_t* __restrict__ big) {
+  extern __shared__ __align__(128) uint8_t smem[];
+  NttTables& T = *reinterpret_cast<NttTables*>(smem);
+  uint64_t* stage = reinterpret_cast<uint64_t*>(smem + kTabBytes);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  uint8_t* wb = smem + kTabBytes + kStages * kChunkBytes + warp * kWarpBytes;
+  uint64_t* tile = reinterpret_cast<uint64_t*>(wb);
+  uint32_t* acc_poly = reinterpret_cast<uint32_t*>(wb + kWarpTile);              // [2][N]
+  uint16_t* abar = reinterpret_cast<uint16_t*>(wb + kWarpTile + kWarpAcc);      // [n]
+  uint32_t* bbar_slot = reinterpret_cast<uint32_t*>(wb + kWarpTile + kWarpAcc + kWarpAbar);
+
+  for (int k = threadIdx.x; k < static_cast<int>(sizeof(NttTables) / 8); k += kBrThreads)
+    reinterpret_cast<uint64_t*>(&T)[k] = reinterpret_cast<const uint64_t*>(gtab)[k];
+
+  // Signed gadget digits by the offset form: y = x + sum_j 2^(bg-1) 2^(32-bg j)
+  // + 2^(31 - bg l); digit j = ((y >> (32 - bg j)) mod 2^bg) - 2^(bg-1).
+  uint32_t off = 1u << (31 - bg_bits * kL);
+  for (int j = 1; j <= kL; ++j) off += (1u << (bg_bits - 1)) << (32 - bg_bits * j);
+  const uint32_t dmask = (1u << bg_bits) - 1, dhalf = 1u << (bg_bits - 1);
+  const int total = n * kRows;
+
+  for (int g0 = blockIdx.x * kBrWarps; g0 < count; g0 += gridDim.x * kBrWarps) {
+    const int gi = g0 + warp;
+    const bool active = gi < count;
+    __syncthreads();  // tables loaded; previous group finished with the stages
+    issue_chunk(stage, bkhat, 0);
+    cp_async_commit();
+    issue_chunk(stage + kChunkU64, bkhat, 1);
+    cp_async_commit();
+
+    if (active) {
+      const GateDesc d = desc[gi];
+      const Lin lin = gate_lin(d.type);
+      // linear combination and modulus switch q -> 2N (round half up)
+      for (int x = lane; x <= n; x += 32) {
+        uint32_t v = lin.ca * d.a[x] + lin.cb * d.b[x];
+        if (x == n) v += lin.k;
+        const uint32_t ms = ((v + (1u << 20)) >> 21) & (2 * kN - 1);
+        if (x < n) abar[x] = static_cast<uint16_t>(ms);
+        else *bbar_slot = ms;
+      }
+      __syncwarp();
+      // ACC = (0, X^{-bbar} * v), v_k = q/8 for all k
+      const uint32_t e = (2 * kN - *bbar_slot) & (2 * kN - 1);
+#pragma unroll
+      for (int j = 0; j < 32; ++j) {
+        const uint32_t k = lane + 32 * j;
+        acc_poly[k] = 0u;
+        const uint32_t idx = (k - e) & (2 * kN - 1);
+        acc_poly[kN + k] = idx < static_cast<uint32_t>(kN) ? (1u << 29) : (0u - (1u << 29));
+      }
+      __syncwarp();
+    }
+
+    uint64_t acc0[32], acc1[32];
+    for (int i = 0; i < n; ++i) {
+      const uint32_t a_i = active ? abar[i] : 0u;
+#pragma unroll 1
+      for (int r = 0; r < kRows; ++r) {
+        const int k = i * kRows + r;
+        cp_async_wait<1>();
+        __syncthreads();  // key row k visible to all; everyone done with row k-1's slot
+        if (k + 2 < total) issue_chunk(stage + ((k + 2) % kStages) * kChunkU64, bkhat, k + 2);
+        cp_async_commit();
+        if (active) {
+          const uint32_t* P = acc_poly + (r / kL) * kN;
+          const int shift = 32 - bg_bits * (r % kL + 1);
+          uint64_t x[32];
+#pragma unroll
+          for (int j = 0; j < 32; ++j) {
+            const uint32_t kk = lane + 32 * j;
+            const uint32_t idx = (kk - a_i) & (2 * kN - 1);  // (X^a P)_kk = +-P[idx mod N]
+            const uint32_t rot = idx < static_cast<uint32_t>(kN) ? P[idx] : 0u - P[idx - kN];
+            const uint32_t y = rot - P[kk] + off;
+            x[j] = dev::gl_from_int(static_cast<int32_t>((y >> shift) & dmask) - static_cast<int32_t>(dhalf));
+          }
+          dev::ntt_forward(x, tile, T, lane);
+          const uint64_t* ch = stage + (k % kStages) * kChunkU64;
+#pragma unroll
+          for (int j = 0; j < 32; ++j) {
+            const ulonglong2 w = *reinterpret_cast<const ulonglong2*>(ch + (j * 32 + lane) * 2);
+            const uint64_t p0 = dev::gl_mul(x[j], w.x);
+            const uint64_t p1 = dev::gl_mul(x[j], w.y);
+            acc0[j] = r == 0 ? p0 : dev::gl_add(acc0[j], p0);
+            acc1[j] = r == 0 ? p1 : dev::gl_add(acc1[j], p1);
+          }
+        }
+      }
+      if (active) {
+#pragma unroll 1
+        for (int c = 0; c < 2; ++c) {
+          dev::ntt_inverse(acc0, tile, T, lane);
+          uint32_t* Pc = acc_poly + c * kN;
+#pragma unroll
+          for (int j = 0; j < 32; ++j) Pc[lane + 32 * j] += dev::gl_lift32(acc0[j]);
+          if (c == 0) {
+#pragma unroll
+            for (int j = 0; j < 32; ++j) acc0[j] = acc1[j];
+          }
+        }
+        __syncwarp();
+      }
+    }
+
+    if (active) {
+      // sample extraction of coefficient 0: a'_0 = A_0, a'_k = -A_{N-k}, b' = B_0
+      uint32_t* out = big + static_cast<size_t>(gi) * (kN + 1);
+#pragma unroll
+      for (int j = 0; j < 32; ++j) {
+        const int kk = lane + 32 * j;
+        out[kk] = kk == 0 ? acc_poly[0] : 0u - acc_poly[kN - kk];
+      }
+      if (lane == 0) out[kN] = acc_poly[kN];
+    }
+  }
+}
+
+// Keyswitch N -> n (see file comment).  Rounding: a + 2^15, keep the top 16
+// bits, 8 base-4 digits most significant first; digit v at level j selects
+// key row KSK[i][j][v-1]; out = (0, .., 0, b) - sum of the selected rows.
+// Output of gate g goes to desc[g].out when desc is given, else to
+// out_contig + g*(n+1).
+__global__ void __launch_bounds__(kKsThreads)
+    keyswitch_kernel(const uint32_t* __restrict__ big, const GateDesc* __restrict__ desc,
+                     uint32_t* __restrict__ out_contig, int count, const uint32_t* __restrict__ ksk, int n) {
+  __shared__ uint16_t dig[kKsGates][kN];
+  const int g0 = blockIdx.x * kKsGates;
+  const int ng = min(kKsGates, count - g0);
+  for (int q = threadIdx.x; q < kKsGates * kN; q += kKsThreads) {
+    const int g = q / kN, i = q % kN;
+    uint16_t v = 0;
+    if (g < ng) v = static_cast<uint16_t>((big[static_cast<size_t>(g0 + g) * (kN + 1) + i] + (1u << 15)) >> 16);
+    dig[g][i] = v;
+  }
+  __syncthreads();
+  uint4 acc[kKsGates];
+#pragma unroll
+  for (int g = 0; g < kKsGates; ++g) acc[g] = make_uint4(0, 0, 0, 0);
+  const int col = threadIdx.x * 4;
+  const uint4* base = reinterpret_cast<const uint4*>(ksk) + threadIdx.x;
+#pragma unroll 1
+  for (int i = 0; i < kN; ++i) {
+    uint32_t dv[kKsGates];
+#pragma unroll
+    for (int g = 0; g < kKsGates; ++g) dv[g] = dig[g][i];
+#pragma unroll
+    for (int j = 0; j < kKsT; ++j) {
+      const uint4* rows = base + static_cast<size_t>((i * kKsT + j) * kKsDigits) * (kKsRowWords / 4);
+      const uint4 r1 = __ldg(rows);
+      const uint4 r2 = __ldg(rows + kKsRowWords / 4);
+      const uint4 r3 = __ldg(rows + 2 * (kKsRowWords / 4));
+      const int sh = 14 - 2 * j;
+#pragma unroll
+      for (int g = 0; g < kKsGates; ++g) {
+        const uint32_t dgt = (dv[g] >> sh) & 3u;
+        const uint4 sel = dgt == 1 ? r1 : (dgt == 2 ? r2 : r3);
+        const uint32_t on = dgt ? 0xFFFFFFFFu : 0u;
+        acc[g].x -= sel.x & on;
+        acc[g].y -= sel.y & on;
+        acc[g].z -= sel.z & on;
+        acc[g].w -= sel.w & on;
+      }
+    }
+  }
+#pragma unroll
+  for (int g = 0; g < kKsGates; ++g) {
+    if (g >= ng) break;
+    uint32_t* out = desc ? desc[g0 + g].out : out_contig + static_cast<size_t>(g0 + g) * (n + 1);
+    const uint32_t body = big[static_cast<size_t>(g0 + g) * (kN + 1) + kN];
+    if (col + 0 <= n) out[col + 0] = acc[g].x + (col + 0 == n ? body : 0u);
+    if (col + 1 <= n) out[col + 1] = acc[g].y + (col + 1 == n ? body : 0u);
+    if (col + 2 <= n) out[col + 2] = acc[g].z + (col + 2 == n ? body : 0u);
+    if (col + 3 <= n) out[col + 3] = acc[g].w + (col + 3 == n ? body : 0u);
+  }
+}
+
+// Exact negacyclic product through the device NTT (test hook).
+__global__ void ntt_mul_kernel(const int32_t* __restrict__ digits, const uint32_t* __restrict__ poly,
+                               uint32_t* __restrict__ out, const NttTables* __restrict__ gtab) {
+  __shared__ NttTables T;
+  __shared__ uint64_t tile[1024];
+  for (int k = threadIdx.x; k < static_cast<int>(sizeof(NttTables) / 8); k += 32)
+    reinterpret_cast<uint64_t*>(&T)[k] = reinterpret_cast<const uint64_t*>(gtab)[k];
+  __syncwarp();
+  const int lane = threadIdx.x;
+  uint64_t x[32], y[32];
+#pragma unroll
+  for (int j = 0; j < 32; ++j) {
+    x[j] = dev::gl_from_int(digits[lane + 32 * j]);
+    y[j] = poly[lane + 32 * j];
+  }
+  dev::ntt_forward(x, tile, T, lane);
+  dev::ntt_forward(y, tile, T, lane);
+#pragma unroll
+  for (int j = 0; j < 32; ++j) x[j] = dev::gl_mul(x[j], dev::gl_mul(y[j], T.n_inv));
+  dev::ntt_inverse(x, tile, T, lane);
+#pragma unroll
+  for (int j = 0; j < 32; ++j) out[lane + 32 * j] = dev::gl_lift32(x[j]);
+}
+
+bool g_br_attr_set[64] = {};
+
+}  // namespace
+
+// ------------------------------------------------------------------ host side
+
+// ------------------------------------------------------------------ scan plan
+
+struct Plan {
+  // key of the cached plan
+  const uint32_t* column = nullptr;
+  size_t rows = 0;
+  uint32_t width = 0, pred = 0, n_payloads = 0, payload_width = 0;
+  const uint32_t* cst = nullptr;
+  std::vector<const uint32_t*> payloads;
+  uint32_t* match = nullptr;
+  std::vector<uint32_t*> outs;
+  uint32_t* wires = nullptr;
+  // plan
+  std::vector<size_t> level_offset;  // descriptors of level L: [level_offset[L], level_offset[L+1])
+  size_t total = 0;
+};
+
+
+// Kernel timing: an event pair around each launch while profiling.
+struct Profile {
+  std::vector<cudaEvent_t> pool;
+  std::vector<std::pair<int, int>> br, ks;  // indices into pool
+  size_t used = 0;
+  uint64_t gates = 0;
+  bool recording = false;
+  cudaEvent_t get() {
+    if (used == pool.size()) {
+      cudaEvent_t e;
+      if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+      pool.push_back(e);
+    }
+    return pool[used++];
+  }
+  ~Profile() {
+    for (cudaEvent_t e : pool) cudaEventDestroy(e);
+  }
+};
+
+// Records an event pair around one launch when the context is profiling.
+struct LaunchTimer {
+  Profile* p;
+  cudaStream_t st;
+  int a = -1;
+  LaunchTimer(Ctx& c, cudaStream_t s) : p(static_cast<Profile*>(c.prof)), st(s) {
+    if (p && !p->recording) p = nullptr;
+    if (p) {
+      a = static_cast<int>(p->used);
+      cudaEvent_t e = p->get();
+      if (e) cudaEventRecord(e, st);
+      else a = -1;
+    }
+  }
+  void done(bool is_br, size_t gates) {
+    if (!p || a < 0) return;
+    const int b = static_cast<int>(p->used);
+    cudaEvent_t e = p->get();
+    if (!e) return;
+    cudaEventRecord(e, st);
+    (is_br ? p->br : p->ks).emplace_back(a, b);
+    if (is_br) p->gates += gates;
+  }
+};
+
+int device_init(Ctx& c) {
+  const fsql_params& p = c.p;
+  if (p.N != static_cast<uint32_t>(kN) || p.l != static_cast<uint32_t>(kL) || p.bg_bits < 2 || p.bg_bits > 10 ||
+      p.ks_base_bits != static_cast<uint32_t>(kKsBaseBits) || p.ks_t != static_cast<uint32_t>(kKsT) ||
+      p.n > static_cast<uint32_t>(kMaxN) || p.n + 1 > static_cast<uint32_t>(kKsRowWords)) {
+    set_error("the GPU kernels implement N=1024, l=3, bg_bits in [2,10], ks base 4 x 8 levels, n <= 639");
+    return FSQL_ERR_UNSUPPORTED;
+  }
+  CK(cudaSetDevice(c.device));
+  int sms = 0;
+  CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c.device));
+  c.sm_count = sms;
+  if (!make_tables(&c.tables)) {
+    set_error("NTT root of unity check failed");
+    return FSQL_ERR_ARG;
+  }
+  const size_t bkhat_words = static_cast<size_t>(p.n) * kRows * kChunkU64;
+  const size_t ksk_words = static_cast<size_t>(kN) * kKsT * kKsDigits * kKsRowWords;
+  CK(cudaMalloc(&c.d_tables, sizeof(NttTables)));
+  CK(cudaMalloc(&c.d_bkhat, bkhat_words * 8));
+  CK(cudaMalloc(&c.d_ksk, ksk_words * 4));
+  c.key_bytes = bkhat_words * 8 + ksk_words * 4 + sizeof(NttTables);
+  CK(cudaMemcpy(c.d_tables, &c.tables, sizeof(NttTables), cudaMemcpyHostToDevice));
+
+  // keyswitching key rows padded to kKsRowWords
+  std::vector<uint32_t> kp(ksk_words, 0u);
+  const size_t rows = static_cast<size_t>(kN) * kKsT * kKsDigits;
+  for (size_t r = 0; r < rows; ++r)
+    std::memcpy(kp.data() + r * kKsRowWords, c.ksk.data() + r * (p.n + 1), (p.n + 1) * 4);
+  CK(cudaMemcpy(c.d_ksk, kp.data(), ksk_words * 4, cudaMemcpyHostToDevice));
+
+  uint32_t* d_bk = nullptr;
+  CK(cudaMalloc(&d_bk, c.bk.size() * 4));
+  cudaError_t e = cudaMemcpy(d_bk, c.bk.data(), c.bk.size() * 4, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) {
+    const int polys = static_cast<int>(p.n) * kRows * 2;
+    bk_to_ntt_kernel<<<(polys + 3) / 4, 128>>>(d_bk, c.d_bkhat, c.d_tables, static_cast<int>(p.n));
+    e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  }
+  cudaFree(d_bk);
+  if (e != cudaSuccess) {
+    set_error(std::string("bootstrapping key conversion: ") + cudaGetErrorString(e));
+    return FSQL_ERR_CUDA;
+  }
+  CK(cudaEventCreateWithFlags(reinterpret_cast<cudaEvent_t*>(&c.desc_event), cudaEventDisableTiming));
+  return FSQL_OK;
+}
+
+void device_free(Ctx& c) {
+  if (c.device < 0) return;
+  cudaSetDevice(c.device);
+  cudaFree(c.d_bkhat);
+  cudaFree(c.d_ksk);
+  cudaFree(c.d_tables);
+  cudaFree(c.d_big);
+  cudaFree(c.d_desc);
+  cudaFree(c.d_wires);
+  cudaFree(c.d_stage);
+  if (c.h_desc) cudaFreeHost(c.h_desc);
+  if (c.desc_event) cudaEventDestroy(static_cast<cudaEvent_t>(c.desc_event));
+  delete static_cast<Profile*>(c.prof);
+  c.prof = nullptr;
+  delete c.plan;
+  c.plan = nullptr;
+  c.d_bkhat = nullptr;
+  c.d_ksk = nullptr;
+  c.d_tables = nullptr;
+  c.d_big = nullptr;
+  c.d_desc = nullptr;
+  c.d_wires = nullptr;
+  c.d_stage = nullptr;
+  c.h_desc = nullptr;
+  c.desc_event = nullptr;
+}
+
+int launch_blind_rotate(Ctx& c, const GateDesc* d_desc, size_t count, uint32_t* d_big, void* stream) {
+  if (count == 0) return FSQL_OK;
+  if (c.device < 64 && !g_br_attr_set[c.device]) {
+    CK(cudaFuncSetAttribute(blind_rotate_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kBrSmem));
+    g_br_attr_set[c.device] = true;
+  }
+  const size_t groups = (count + kBrWarps - 1) / kBrWarps;
+  const int grid = static_cast<int>(std::min<size_t>(groups, static_cast<size_t>(c.sm_count)));
+  LaunchTimer tm(c, static_cast<cudaStream_t>(stream));
+  blind_rotate_kernel<<<grid, kBrThreads, kBrSmem, static_cast<cudaStream_t>(stream)>>>(
+      d_desc, static_cast<int>(count), c.d_bkhat, c.d_tables, static_cast<int>(c.p.n), static_cast<int>(c.p.bg_bits),
+      d_big);
+  CK(cudaGetLastError());
+  tm.done(true, count);
+  return FSQL_OK;
+}
+
+int launch_keyswitch(Ctx& c, const uint32_t* d_big, const GateDesc* d_desc, uint32_t* d_out_contig, size_t count,
+                     void* stream) {
+  if (count == 0) return FSQL_OK;
+  const int grid = static_cast<int>((count + kKsGates - 1) / kKsGates);
+  LaunchTimer tm(c, static_cast<cudaStream_t>(stream));
+  keyswitch_kernel<<<grid, kKsThreads, 0, static_cast<cudaStream_t>(stream)>>>(
+      d_big, d_desc, d_out_contig, static_cast<int>(count), c.d_ksk, static_cast<int>(c.p.n));
+  CK(cudaGetLastError());
+  tm.done(false, count);
+  return FSQL_OK;
+}
+
+static int ensure_big(Ctx& c, size_t count) {
+  if (count <= c.big_cap) return FSQL_OK;
+  cudaFree(c.d_big);
+  c.d_big = nullptr;
+  c.big_cap = 0;
+  CK(cudaMalloc(&c.d_big, count * (kN + 1) * 4));
+  c.big_cap = count;
+  return FSQL_OK;
+}
+
+static int ensure_desc(Ctx& c, size_t count) {
+  if (count <= c.desc_cap) return FSQL_OK;
+  cudaFree(c.d_desc);
+  c.d_desc = nullptr;
+  c.desc_cap = 0;
+  CK(cudaMalloc(&c.d_desc, count * sizeof(GateDesc)));
+  c.desc_cap = count;
+  return FSQL_OK;
+}
+
+// Largest number of gates one blind-rotation launch takes (bounds the
+// extracted-sample scratch to 1 GiB).
+constexpr size_t kMaxChunk = 1u << 18;
+
+int launch_gates(Ctx& c, const GateDesc* d_desc, size_t count, uint32_t* d_big, void* stream) {
+  for (size_t off = 0; off < count; off += kMaxChunk) {
+    const size_t cnt = std::min(kMaxChunk, count - off);
+    int rc = launch_blind_rotate(c, d_desc + off, cnt, d_big, stream);
+    if (rc) return rc;
+    rc = launch_keyswitch(c, d_big, d_desc + off, nullptr, cnt, stream);
+    if (rc) return rc;
+  }
+  return FSQL_OK;
+}
+
+}  // namespace fsql
+
+using fsql::Ctx;
+using fsql::GateDesc;
+
+namespace {
+
+int arg_error(const char* msg) {
+  fsql::set_error(msg);
+  return FSQL_ERR_ARG;
+}
+
+Ctx* device_ctx(fsql_ctx* ctx) {
+  Ctx* c = reinterpret_cast<Ctx*>(ctx);
+  if (!c) {
+    fsql::set_error("null context");
+    return nullptr;
+  }
+  if (c->device < 0 || !c->d_bkhat) {
+    fsql::set_error("context has no device keys (created with device = -1)");
+    return nullptr;
+  }
+  if (cudaSetDevice(c->device) != cudaSuccess) {
+    fsql::set_error("cudaSetDevice failed");
+    return nullptr;
+  }
+  return c;
+}
+
+int check_types_host(size_t count) { return count > (size_t(1) << 31) ? arg_error("too many gates") : FSQL_OK; }
+
+// Build (or reuse) the descriptor plan of a scan and upload it to c.d_desc.
+int prepare_scan(Ctx& c, const uint32_t* d_column, size_t rows, uint32_t width, uint32_t pred,
+                 const uint32_t* d_const, uint32_t n_payloads, const uint32_t* const* d_payloads,
+                 uint32_t payload_width, uint32_t* d_match, uint32_t* const* d_out_payloads, void* stream) {
+  fsql::Netlist nl;
+  if (!fsql::build_netlist(pred, width, n_payloads, payload_width, &nl)) return arg_error("bad predicate shape");
+  const size_t W = c.p.n + 1;
+  const int G = static_cast<int>(nl.type.size());
+  // internal (scratch) wires: every gate that is neither the match bit nor a mask gate
+  std::vector<long> scratch_index(G, -1);
+  long n_int = 0;
+  for (int g = 0; g < nl.first_mask_gate; ++g)
+    if (nl.n_inputs + g != nl.match_wire) scratch_index[g] = n_int++;
+  const size_t wire_words = rows * static_cast<size_t>(n_int) * W;
+  if (wire_words > c.wires_cap) {
+    cudaFree(c.d_wires);
+    c.d_wires = nullptr;
+    c.wires_cap = 0;
+    if (cudaMalloc(&c.d_wires, wire_words * 4) != cudaSuccess) {
+      fsql::set_error("scan scratch allocation failed");
+      return FSQL_ERR_OOM;
+    }
+    c.wires_cap = wire_words;
+    delete c.plan;
+    c.plan = nullptr;
+  }
+
+  fsql::Plan* pl = c.plan;
+  bool same = pl && pl->column == d_column && pl->rows == rows && pl->width == width && pl->pred == pred &&
+              pl->n_payloads == n_payloads && pl->payload_width == payload_width && pl->cst == d_const &&
+              pl->match == d_match && pl->wires == c.d_wires;
+  for (uint32_t q = 0; same && q < n_payloads; ++q)
+    same = pl->payloads[q] == d_payloads[q] && pl->outs[q] == d_out_payloads[q];
+  if (same) return FSQL_OK;
+
+  delete c.plan;
+  c.plan = nullptr;
+  pl = new fsql::Plan();
+  pl->column = d_column;
+  pl->rows = rows;
+  pl->width = width;
+  pl->pred = pred;
+  pl->n_payloads = n_payloads;
+  pl->payload_width = payload_width;
+  pl->cst = d_const;
+  pl->payloads.assign(d_payloads, d_payloads + n_payloads);
+  pl->match = d_match;
+  pl->outs.assign(d_out_payloads, d_out_payloads + n_payloads);
+  pl->wires = c.d_wires;
+
+  const int w = static_cast<int>(width);
+  const int nconst = pred == FSQL_RANGE ? 2 * w : w;
+  auto gate_out = [&](int g, size_t row) -> uint32_t* {
+    if (g >= nl.first_mask_gate) {
+      const int m = g - nl.first_mask_gate;
+      const int q = m / static_cast<int>(payload_width), bit = m % static_cast<int>(payload_width);
+      return d_out_payloads[q] + (row * payload_width + bit) * W;
+    }
+    if (nl.n_inputs + g == nl.match_wire) return d_match + row * W;
+    return c.d_wires + (row * n_int + scratch_index[g]) * W;
+  };
+  auto wire_ptr = [&](int id, size_t row) -> const uint32_t* {
+    if (id < w) return d_column + (row * width + id) * W;
+    if (id < w + nconst) return d_const + static_cast<size_t>(id - w) * W;
+    if (id < nl.n_inputs) {
+      const int m = id - w - nconst;
+      const int q = m / static_cast<int>(payload_width), bit = m % static_cast<int>(payload_width);
+      return d_payloads[q] + (row * payload_width + bit) * W;
+    }
+    return gate_out(id - nl.n_inputs, row);
+  };
+
+  const size_t total = rows * static_cast<size_t>(G);
+  if (total > c.h_desc_cap) {
+    if (c.h_desc) {
+      cudaEventSynchronize(static_cast<cudaEvent_t>(c.desc_event));
+      cudaFreeHost(c.h_desc);
+    }
+    c.h_desc = nullptr;
+    c.h_desc_cap = 0;
+    if (cudaMallocHost(&c.h_desc, total * sizeof(GateDesc)) != cudaSuccess) {
+      fsql::set_error("pinned staging allocation failed");
+      delete pl;
+      return FSQL_ERR_OOM;
+    }
+    c.h_desc_cap = total;
+  } else {
+    cudaEventSynchronize(static_cast<cudaEvent_t>(c.desc_event));  // previous upload done
+  }
+  // descriptors level by level, gate-major within a level
+  pl->level_offset.assign(nl.levels + 1, 0);
+  size_t pos = 0;
+  for (int L = 1; L <= nl.levels; ++L) {
+    pl->level_offset[L - 1] = pos;
+    for (int g = 0; g < G; ++g) {
+      if (nl.level[g] != L) continue;
+      for (size_t row = 0; row < rows; ++row) {
+        GateDesc& d = c.h_desc[pos++];
+        d.a = wire_ptr(nl.a[g], row);
+        d.b = wire_ptr(nl.b[g], row);
+        d.out = gate_out(g, row);
+        d.type = static_cast<uint32_t>(nl.type[g]);
+        d.pad = 0;
+      }
+    }
+  }
+  pl->level_offset[nl.levels] = pos;
+  pl->total = pos;
+  int rc = fsql::ensure_desc(c, total);
+  if (rc) {
+    delete pl;
+    return rc;
+  }
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (cudaMemcpyAsync(c.d_desc, c.h_desc, total * sizeof(GateDesc), cudaMemcpyHostToDevice, st) != cudaSuccess ||
+      cudaEventRecord(static_cast<cudaEvent_t>(c.desc_event), st) != cudaSuccess) {
+    fsql::set_error("descriptor upload failed");
+    delete pl;
+    return FSQL_ERR_CUDA;
+  }
+  c.plan = pl;
+  return FSQL_OK;
+}
+
+int validate_scan(Ctx* c, const uint32_t* column, size_t rows, uint32_t width, uint32_t pred, const uint32_t* cst,
+                  uint32_t n_payloads, const uint32_t* const* payloads, uint32_t payload_width, uint32_t* match,
+                  uint32_t* const* outs) {
+  if (rows == 0) return FSQL_OK;
+  if (!column || !cst || !match) return arg_error("null column, constant or match pointer");
+  if (width < 1 || width > 64) return arg_error("width must be in [1, 64]");
+  if (pred > FSQL_RANGE) return arg_error("unknown predicate");
+  if (n_payloads > 64 || (n_payloads && (!payloads || !outs || payload_width < 1 || payload_width > 64)))
+    return arg_error("bad payload arguments");
+  for (uint32_t q = 0; q < n_payloads; ++q)
+    if (!payloads[q] || !outs[q]) return arg_error("null payload pointer");
+  if (rows > (size_t(1) << 26)) return arg_error("too many rows");
+  (void)c;
+  return FSQL_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int fsql_gate_batch(fsql_ctx* ctx, const uint8_t* d_types, const uint32_t* d_a, const uint32_t* d_b,
+                    uint32_t* d_out, size_t count, void* stream) {
+  Ctx* c = device_ctx(ctx);
+  if (!c) return FSQL_ERR_ARG;
+  if (count == 0) return FSQL_OK;
+  if (!d_types || !d_a || !d_b || !d_out) return arg_error("null device pointer");
+  if (int rc = check_types_host(count)) return rc;
+  std::lock_guard<std::mutex> lk(c->mu);
+  int rc = fsql::ensure_desc(*c, count);
+  if (!rc) rc = fsql::ensure_big(*c, std::min(count, fsql::kMaxChunk));
+  if (rc) return rc;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  fsql::make_desc_kernel<<<static_cast<unsigned>((count + 255) / 256), 256, 0, st>>>(
+      c->d_desc, d_types, d_a, d_b, d_out, static_cast<int>(count), static_cast<int>(c->p.n + 1));
+  if (cudaGetLastError() != cudaSuccess) return arg_error("descriptor kernel launch failed");
+  delete c->plan;  // descriptors overwritten
+  c->plan = nullptr;
+  return fsql::launch_gates(*c, c->d_desc, count, c->d_big, stream);
+}
+
+int fsql_blind_rotate_extract(fsql_ctx* ctx, const uint8_t* d_types, const uint32_t* d_a, const uint32_t* d_b,
+                              uint32_t* d_big, size_t count, void* stream) {
+  Ctx* c = device_ctx(ctx);
+  if (!c) return FSQL_ERR_ARG;
+  if (count == 0) return FSQL_OK;
+  if (!d_types || !d_a || !d_b || !d_big) return arg_error("null device pointer");
+  if (int rc = check_types_host(count)) return rc;
+  std::lock_guard<std::mutex> lk(c->mu);
+  int rc = fsql::ensure_desc(*c, count);
+  if (rc) return rc;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  fsql::make_desc_kernel<<<static_cast<unsigned>((count + 255) / 256), 256, 0, st>>>(
+      c->d_desc, d_types, d_a, d_b, nullptr, static_cast<int>(count), static_cast<int>(c->p.n + 1));
+  if (cudaGetLastError() != cudaSuccess) return arg_error("descriptor kernel launch failed");
+  delete c->plan;
+  c->plan = nullptr;
+  for (size_t off = 0; off < count; off += fsql::kMaxChunk) {
+    const size_t cnt = std::min(fsql::kMaxChunk, count - off);
+    rc = fsql::launch_blind_rotate(*c, c->d_desc + off, cnt, d_big + off * (fsql::kN + 1), stream);
+    if (rc) return rc;
+  }
+  return FSQL_OK;
+}
+
+int fsql_keyswitch(fsql_ctx* ctx, const uint32_t* d_big, uint32_t* d_out, size_t count, void* stream) {
+  Ctx* c = device_ctx(ctx);
+  if (!c) return FSQL_ERR_ARG;
+  if (count == 0) return FSQL_OK;
+  if (!d_big || !d_out) return arg_error("null device pointer");
+  if (int rc = check_types_host(count)) return rc;
+  return fsql::launch_keyswitch(*c, d_big, nullptr, d_out, count, stream);
+}
+
+int fsql_debug_ntt_mul(fsql_ctx* ctx, const int32_t* d_digits, const uint32_t* d_poly, uint32_t* d_out,
+                       void* stream) {
+  Ctx* c = device_ctx(ctx);
+  if (!c) return FSQL_ERR_ARG;
+  if (!d_digits || !d_poly || !d_out) return arg_error("null device pointer");
+  fsql::ntt_mul_kernel<<<1, 32, 0, static_cast<cudaStream_t>(stream)>>>(d_digits, d_poly, d_out, c->d_tables);
+  if (cudaGetLastError() != cudaSuccess) return arg_error("ntt test kernel launch failed");
+  return FSQL_OK;
+}
+
+int fsql_scan_select(fsql_ctx* ctx, const uint32_t* d_column, size_t rows, uint32_t width, uint32_t pred,
+                     const uint32_t* d_const, uint32_t n_payloads, const uint32_t* const* d_payloads,
+                     uint32_t payload_width, uint32_t* d_match, uint32_t* const* d_out_payloads, int per_gate,
+                     void* stream) {
+  Ctx* c = device_ctx(ctx);
+  if (!c) return FSQL_ERR_ARG;
+  if (int rc = validate_scan(c, d_column, rows, width, pred, d_const, n_payloads, d_payloads, payload_width,
+                             d_match, d_out_payloads))
+    return rc;
+  if (rows == 0) return FSQL_OK;
+  std::lock_guard<std::mutex> lk(c->mu);
+  int rc = prepare_scan(*c, d_column, rows, width, pred, d_const, n_payloads, d_payloads, payload_width, d_match,
+                        d_out_payloads, stream);
+  if (rc) return rc;
+  const fsql::Plan& pl = *c->plan;
+  size_t widest = 0;
+  for (size_t L = 0; L + 1 < pl.level_offset.size(); ++L)
+    widest = std::max(widest, pl.level_offset[L + 1] - pl.level_offset[L]);
+  rc = fsql::ensure_big(*c, per_gate ? 1 : std::min(widest, fsql::kMaxChunk));
+  if (rc) return rc;
+  if (per_gate) {
+    for (size_t g = 0; g < pl.total; ++g) {
+      rc = fsql::launch_gates(*c, c->d_desc + g, 1, c->d_big, stream);
+      if (rc) return rc;
+    }
+    return FSQL_OK;
+  }
+  for (size_t L = 0; L + 1 < pl.level_offset.size(); ++L) {
+    rc = fsql::launch_gates(*c, c->d_desc + pl.level_offset[L], pl.level_offset[L + 1] - pl.level_offset[L],
+                            c->d_big, stream);
+    if (rc) return rc;
+  }
+  return FSQL_OK;
+}
+
+int fsql_scan_select_host(fsql_ctx* ctx, const uint32_t* h_column, size_t rows, uint32_t width, uint32_t pred,
+                          const uint32_t* h_const, uint32_t n_payloads, const uint32_t* const* h_payloads,
+                          uint32_t payload_width, uint32_t* h_match, uint32_t* const* h_out_payloads, void* stream) {
+  Ctx* c = device_ctx(ctx);
+  if (!c) return FSQL_ERR_ARG;
+  if (int rc = validate_scan(c, h_column, rows, width, pred, h_const, n_payloads, h_payloads, payload_width,
+                             h_match, h_out_payloads))
+    return rc;
+  if (rows == 0) return FSQL_OK;
+  const size_t W = c->p.n + 1;
+  const size_t col_w = rows * width * W;
+  const size_t cst_w = (pred == FSQL_RANGE ? 2 : 1) * static_cast<size_t>(width) * W;
+  const size_t pay_w = rows * static_cast<size_t>(payload_width) * W;
+  const size_t total = col_w + cst_w + 2 * n_payloads * pay_w + rows * W;
+  {
+    std::lock_guard<std::mutex> lk(c->mu);
+    if (total > c->stage_cap) {
+      cudaFree(c->d_stage);
+      c->d_stage = nullptr;
+      c->stage_cap = 0;
+      if (cudaMalloc(&c->d_stage, total * 4) != cudaSuccess) {
+        fsql::set_error("device staging allocation failed");
+        return FSQL_ERR_OOM;
+      }
+      c->stage_cap = total;
+    }
+  }
+  uint32_t* d_col = c->d_stage;
+  uint32_t* d_cst = d_col + col_w;
+  uint32_t* d_match = d_cst + cst_w;
+  std::vector<const uint32_t*> d_pay(n_payloads);
+  std::vector<uint32_t*> d_out(n_payloads);
+  uint32_t* q = d_match + rows * W;
+  for (uint32_t k = 0; k < n_payloads; ++k) {
+    d_pay[k] = q;
+    q += pay_w;
+    d_out[k] = q;
+    q += pay_w;
+  }
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  auto h2d = [&](void* dst, const void* src, size_t words) {
+    return cudaMemcpyAsync(dst, src, words * 4, cudaMemcpyHostToDevice, st) == cudaSuccess;
+  };
+  bool ok = h2d(d_col, h_column, col_w) && h2d(d_cst, h_const, cst_w);
+  for (uint32_t k = 0; ok && k < n_payloads; ++k) ok = h2d(const_cast<uint32_t*>(d_pay[k]), h_payloads[k], pay_w);
+  if (!ok) {
+    fsql::set_error("host to device copy failed");
+    return FSQL_ERR_CUDA;
+  }
+  int rc = fsql_scan_select(ctx, d_col, rows, width, pred, d_cst, n_payloads, d_pay.data(), payload_width, d_match,
+                            d_out.data(), 0, stream);
+  if (rc) return rc;
+  ok = cudaMemcpyAsync(h_match, d_match, rows * W * 4, cudaMemcpyDeviceToHost, st) == cudaSuccess;
+  for (uint32_t k = 0; ok && k < n_payloads; ++k)
+    ok = cudaMemcpyAsync(h_out_payloads[k], d_out[k], pay_w * 4, cudaMemcpyDeviceToHost, st) == cudaSuccess;
+  if (!ok || cudaStreamSynchronize(st) != cudaSuccess) {
+    fsql::set_error(std::string("device to host copy or scan failed: ") + cudaGetErrorString(cudaGetLastError()));
+    return FSQL_ERR_CUDA;
+  }
+  return FSQL_OK;
+}
+
+int fsql_profile_begin(fsql_ctx* ctx) {
+  Ctx* c = device_ctx(ctx);
+  if (!c) return FSQL_ERR_ARG;
+  std::lock_guard<std::mutex> lk(c->mu);
+  auto* p = static_cast<fsql::Profile*>(c->prof);
+  if (!p) c->prof = p = new fsql::Profile();
+  p->used = 0;
+  p->br.clear();
+  p->ks.clear();
+  p->gates = 0;
+  p->recording = true;
+  return FSQL_OK;
+}
+
+int fsql_profile_end(fsql_ctx* ctx, fsql_kernel_times* out) {
+  Ctx* c = device_ctx(ctx);
+  if (!c) return FSQL_ERR_ARG;
+  if (!out) return arg_error("null output");
+  std::lock_guard<std::mutex> lk(c->mu);
+  auto* p = static_cast<fsql::Profile*>(c->prof);
+  *out = fsql_kernel_times{0.0, 0.0, 0, 0, 0};
+  if (!p) return FSQL_OK;
+  auto sum = [&](const std::vector<std::pair<int, int>>& v, double* ms) -> bool {
+    for (auto& ab : v) {
+      if (cudaEventSynchronize(p->pool[ab.second]) != cudaSuccess) return false;
+      float t = 0.f;
+      if (cudaEventElapsedTime(&t, p->pool[ab.first], p->pool[ab.second]) != cudaSuccess) return false;
+      *ms += t;
+    }
+    return true;
+  };
+  const bool ok = sum(p->br, &out->blind_rotate_ms) && sum(p->ks, &out->keyswitch_ms);
+  out->blind_rotate_launches = p->br.size();
+  out->keyswitch_launches = p->ks.size();
+  out->gates = p->gates;
+  p->recording = false;  // keep the event pool for the next session
+  p->used = 0;
+  p->br.clear();
+  p->ks.clear();
+  if (!ok) {
+    fsql::set_error("kernel timing events failed");
+    return FSQL_ERR_CUDA;
+  }
+  return FSQL_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,265 @@
+"""Python binding of libfhesql.so (include/fhesql.h): argument marshalling only.
+
+Every homomorphic step runs in the library's CUDA kernels; this module only
+turns numpy arrays / torch tensors into pointers and checks return codes.
+If the in-tree library is missing, loading raises: there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libfhesql.so")
+
+FSQL_OK, FSQL_ERR_ARG, FSQL_ERR_OOM, FSQL_ERR_CUDA, FSQL_ERR_TIMEOUT, FSQL_ERR_ADMISSION, FSQL_ERR_UNSUPPORTED = range(7)
+GATES = {"NAND": 0, "AND": 1, "OR": 2, "XOR": 3, "XNOR": 4, "NOR": 5, "ANDNY": 6, "ANDYN": 7, "ORNY": 8, "ORYN": 9}
+FSQL_EQ, FSQL_LT, FSQL_RANGE = 0, 1, 2
+
+# every symbol include/fhesql.h declares
+API = ["fsql_params_default", "fsql_params_toy", "fsql_ctx_create", "fsql_ctx_destroy", "fsql_ctx_params",
+       "fsql_ctx_device_bytes", "fsql_export_keys", "fsql_encrypt", "fsql_encrypt_bits", "fsql_encrypt_uint",
+       "fsql_phase", "fsql_decrypt_bits", "fsql_decrypt_uint", "fsql_gate_batch", "fsql_blind_rotate_extract",
+       "fsql_keyswitch", "fsql_debug_ntt_mul", "fsql_plan_info", "fsql_scan_select", "fsql_scan_select_host",
+       "fsql_profile_begin", "fsql_profile_end", "fsql_last_error"]
+
+
+class FsqlError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"fhesql error {code}: {msg}")
+        self.code = code
+
+
+class fsql_kernel_times(C.Structure):
+    _fields_ = [("blind_rotate_ms", C.c_double), ("keyswitch_ms", C.c_double),
+                ("blind_rotate_launches", C.c_uint64), ("keyswitch_launches", C.c_uint64), ("gates", C.c_uint64)]
+
+
+class fsql_params(C.Structure):
+    _fields_ = [("n", C.c_uint32), ("N", C.c_uint32), ("bg_bits", C.c_uint32), ("l", C.c_uint32),
+                ("ks_base_bits", C.c_uint32), ("ks_t", C.c_uint32),
+                ("lwe_sigma", C.c_double), ("glwe_sigma", C.c_double)]
+
+
+_lib = None
+
+
+def load() -> C.CDLL:
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"{LIB_PATH} is missing: build it with paper_2510_15413_b300/build.py "
+                           "(there is no CPU fallback)")
+    L = C.CDLL(LIB_PATH)
+    vp, sz, u32, u64, i32 = C.c_void_p, C.c_size_t, C.c_uint32, C.c_uint64, C.c_int
+    sig = {
+        "fsql_params_default": (i32, [C.POINTER(fsql_params)]),
+        "fsql_params_toy": (i32, [C.POINTER(fsql_params)]),
+        "fsql_ctx_create": (i32, [C.POINTER(fsql_params), u64, i32, C.POINTER(vp)]),
+        "fsql_ctx_destroy": (None, [vp]),
+        "fsql_ctx_params": (i32, [vp, C.POINTER(fsql_params)]),
+        "fsql_ctx_device_bytes": (i32, [vp, C.POINTER(sz), C.POINTER(sz)]),
+        "fsql_export_keys": (i32, [vp, vp, vp, vp, vp]),
+        "fsql_encrypt": (i32, [vp, vp, sz, u64, u64, vp]),
+        "fsql_encrypt_bits": (i32, [vp, vp, sz, u64, u64, vp]),
+        "fsql_encrypt_uint": (i32, [vp, vp, sz, u32, u64, u64, vp]),
+        "fsql_phase": (i32, [vp, vp, sz, vp]),
+        "fsql_decrypt_bits": (i32, [vp, vp, sz, vp]),
+        "fsql_decrypt_uint": (i32, [vp, vp, sz, u32, vp]),
+        "fsql_gate_batch": (i32, [vp, vp, vp, vp, vp, sz, vp]),
+        "fsql_blind_rotate_extract": (i32, [vp, vp, vp, vp, vp, sz, vp]),
+        "fsql_keyswitch": (i32, [vp, vp, vp, sz, vp]),
+        "fsql_debug_ntt_mul": (i32, [vp, vp, vp, vp, vp]),
+        "fsql_plan_info": (i32, [u32, u32, u32, u32, C.POINTER(u32), C.POINTER(u32), vp, u32]),
+        "fsql_scan_select": (i32, [vp, vp, sz, u32, u32, vp, u32, vp, u32, vp, vp, i32, vp]),
+        "fsql_scan_select_host": (i32, [vp, vp, sz, u32, u32, vp, u32, vp, u32, vp, vp, vp]),
+        "fsql_profile_begin": (i32, [vp]),
+        "fsql_profile_end": (i32, [vp, C.POINTER(fsql_kernel_times)]),
+        "fsql_last_error": (C.c_char_p, []),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = L
+    return L
+
+
+def _check(rc: int) -> None:
+    if rc != FSQL_OK:
+        raise FsqlError(rc, load().fsql_last_error().decode())
+
+
+def _ptr(x) -> int:
+    """Device or host address of a torch tensor or numpy array (must be contiguous)."""
+    if isinstance(x, np.ndarray):
+        assert x.flags["C_CONTIGUOUS"]
+        return x.ctypes.data
+    if hasattr(x, "data_ptr"):
+        assert x.is_contiguous()
+        return x.data_ptr()
+    if x is None:
+        return 0
+    return int(x)
+
+
+def _count(x) -> int:
+    return int(x.numel()) if hasattr(x, "numel") else int(np.asarray(x).size)
+
+
+def _stream(stream) -> int:
+    if stream is None:
+        try:
+            import torch
+            return torch.cuda.current_stream().cuda_stream
+        except Exception:
+            return 0
+    return int(getattr(stream, "cuda_stream", stream))
+
+
+def params_default() -> fsql_params:
+    p = fsql_params()
+    _check(load().fsql_params_default(C.byref(p)))
+    return p
+
+
+def params_toy() -> fsql_params:
+    p = fsql_params()
+    _check(load().fsql_params_toy(C.byref(p)))
+    return p
+
+
+def plan_info(pred: int, width: int, n_payloads: int, payload_width: int, max_levels: int = 256):
+    g, lv = C.c_uint32(), C.c_uint32()
+    widths = np.zeros(max_levels, np.uint32)
+    _check(load().fsql_plan_info(pred, width, n_payloads, payload_width, C.byref(g), C.byref(lv),
+                                 widths.ctypes.data, max_levels))
+    return int(g.value), [int(x) for x in widths[: lv.value]]
+
+
+class Context:
+    """A seeded key set (client secrets on the host, server keys on the device)."""
+
+    def __init__(self, seed: int, params: fsql_params | None = None, device: int = 0):
+        self.params = params if params is not None else params_default()
+        h = C.c_void_p()
+        _check(load().fsql_ctx_create(C.byref(self.params), int(seed), int(device), C.byref(h)))
+        self._h = h
+        self.seed = int(seed)
+        self.device = device
+        self.n = int(self.params.n)
+        self.N = int(self.params.N)
+        self.words = self.n + 1
+
+    def close(self) -> None:
+        if self._h:
+            load().fsql_ctx_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def handle(self) -> C.c_void_p:
+        return self._h
+
+    def device_bytes(self):
+        k, s = C.c_size_t(), C.c_size_t()
+        _check(load().fsql_ctx_device_bytes(self._h, C.byref(k), C.byref(s)))
+        return int(k.value), int(s.value)
+
+    # ---------------------------------------------------------------- keys
+    def export_keys(self):
+        p = self.params
+        s = np.zeros(p.n, np.uint8)
+        S = np.zeros(p.N, np.uint8)
+        bk = np.zeros((p.n, 2 * p.l, 2, p.N), np.uint32)
+        ksk = np.zeros((p.N, p.ks_t, (1 << p.ks_base_bits) - 1, p.n + 1), np.uint32)
+        _check(load().fsql_export_keys(self._h, s.ctypes.data, S.ctypes.data, bk.ctypes.data, ksk.ctypes.data))
+        return s, S, bk, ksk
+
+    # ---------------------------------------------------------------- client side
+    def encrypt(self, mu, stream: int, first_index: int = 0) -> np.ndarray:
+        mu = np.ascontiguousarray(mu, dtype=np.uint32).ravel()
+        out = np.zeros((mu.size, self.words), np.uint32)
+        _check(load().fsql_encrypt(self._h, mu.ctypes.data, mu.size, stream, first_index, out.ctypes.data))
+        return out
+
+    def encrypt_bits(self, bits, stream: int, first_index: int = 0) -> np.ndarray:
+        bits = np.ascontiguousarray(bits, dtype=np.uint8).ravel()
+        out = np.zeros((bits.size, self.words), np.uint32)
+        _check(load().fsql_encrypt_bits(self._h, bits.ctypes.data, bits.size, stream, first_index, out.ctypes.data))
+        return out
+
+    def encrypt_uint(self, values, width: int, stream: int, first_index: int = 0) -> np.ndarray:
+        values = np.ascontiguousarray(values, dtype=np.uint64).ravel()
+        out = np.zeros((values.size, width, self.words), np.uint32)
+        _check(load().fsql_encrypt_uint(self._h, values.ctypes.data, values.size, width, stream, first_index,
+                                        out.ctypes.data))
+        return out
+
+    def phase(self, ct) -> np.ndarray:
+        ct = np.ascontiguousarray(ct, dtype=np.uint32).reshape(-1, self.words)
+        out = np.zeros(ct.shape[0], np.uint32)
+        _check(load().fsql_phase(self._h, ct.ctypes.data, ct.shape[0], out.ctypes.data))
+        return out
+
+    def decrypt_bits(self, ct) -> np.ndarray:
+        ct = np.ascontiguousarray(ct, dtype=np.uint32).reshape(-1, self.words)
+        out = np.zeros(ct.shape[0], np.uint8)
+        _check(load().fsql_decrypt_bits(self._h, ct.ctypes.data, ct.shape[0], out.ctypes.data))
+        return out
+
+    def decrypt_uint(self, ct, width: int) -> np.ndarray:
+        ct = np.ascontiguousarray(ct, dtype=np.uint32).reshape(-1, width, self.words)
+        out = np.zeros(ct.shape[0], np.uint64)
+        _check(load().fsql_decrypt_uint(self._h, ct.ctypes.data, ct.shape[0], width, out.ctypes.data))
+        return out
+
+    # ---------------------------------------------------------------- server side (device tensors)
+    def gate_batch(self, types, a, b, out, stream=None) -> None:
+        count = _count(types)
+        _check(load().fsql_gate_batch(self._h, _ptr(types), _ptr(a), _ptr(b), _ptr(out), count, _stream(stream)))
+
+    def blind_rotate_extract(self, types, a, b, big, stream=None) -> None:
+        count = _count(types)
+        _check(load().fsql_blind_rotate_extract(self._h, _ptr(types), _ptr(a), _ptr(b), _ptr(big), count,
+                                                _stream(stream)))
+
+    def keyswitch(self, big, out, count: int, stream=None) -> None:
+        _check(load().fsql_keyswitch(self._h, _ptr(big), _ptr(out), count, _stream(stream)))
+
+    def debug_ntt_mul(self, digits, poly, out, stream=None) -> None:
+        _check(load().fsql_debug_ntt_mul(self._h, _ptr(digits), _ptr(poly), _ptr(out), _stream(stream)))
+
+    def scan_select(self, column, rows: int, width: int, pred: int, const, payloads, payload_width: int, match,
+                    out_payloads, per_gate: bool = False, stream=None) -> None:
+        k = len(payloads)
+        pin = (C.c_void_p * max(1, k))(*[_ptr(p) for p in payloads])
+        pout = (C.c_void_p * max(1, k))(*[_ptr(p) for p in out_payloads])
+        _check(load().fsql_scan_select(self._h, _ptr(column), rows, width, pred, _ptr(const), k, pin,
+                                       payload_width, _ptr(match), pout, int(bool(per_gate)), _stream(stream)))
+
+    def scan_select_host(self, column, rows: int, width: int, pred: int, const, payloads, payload_width: int,
+                         match, out_payloads, stream=None) -> None:
+        k = len(payloads)
+        pin = (C.c_void_p * max(1, k))(*[_ptr(p) for p in payloads])
+        pout = (C.c_void_p * max(1, k))(*[_ptr(p) for p in out_payloads])
+        _check(load().fsql_scan_select_host(self._h, _ptr(column), rows, width, pred, _ptr(const), k, pin,
+                                            payload_width, _ptr(match), pout, _stream(stream)))
+
+    def profile_begin(self) -> None:
+        _check(load().fsql_profile_begin(self._h))
+
+    def profile_end(self) -> dict:
+        t = fsql_kernel_times()
+        _check(load().fsql_profile_end(self._h, C.byref(t)))
+        return {"blind_rotate_ms": t.blind_rotate_ms, "keyswitch_ms": t.keyswitch_ms,
+                "blind_rotate_launches": int(t.blind_rotate_launches),
+                "keyswitch_launches": int(t.keyswitch_launches), "gates": int(t.gates)}

@@ -1,0 +1,128 @@
+"""Host-side checks of the C-ABI library (no GPU needed): every declared symbol
+is exported, and its client-side half (key generation, encryption, decryption,
+circuit scheduler) agrees with the independent CPU oracle."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2510_15413_b300 import build as B
+from paper_2510_15413_b300 import fhesql as F
+from paper_2510_15413_b300 import workloads as WL
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    B.build()
+
+
+def declared_symbols():
+    names = []
+    for hdr in sorted(os.listdir(os.path.join(ROOT, "include"))):
+        if hdr.endswith(".h"):
+            text = open(os.path.join(ROOT, "include", hdr)).read()
+            names += re.findall(r"FSQL_API\s+[\w\s\*]*?\b(fsql_\w+)\s*\(", text)
+    return names
+
+
+def test_library_exports_every_declared_symbol():
+    names = declared_symbols()
+    assert len(names) >= 20
+    lib = ctypes.CDLL(F.LIB_PATH)
+    for name in names:
+        assert hasattr(lib, name), name
+    assert set(F.API) <= set(names)
+
+
+@pytest.mark.parametrize("which", ["default", "toy"])
+def test_keys_equal_oracle_keys(which):
+    seed = 11 if which == "default" else 7
+    params = F.params_default() if which == "default" else F.params_toy()
+    ctx = F.Context(seed, params, device=-1)
+    o = O.Oracle(seed, O.default_params() if which == "default" else O.toy_params())
+    s, S, bk, ksk = ctx.export_keys()
+    assert np.array_equal(s, o.lwe_key())
+    assert np.array_equal(S, o.glwe_key())
+    assert np.array_equal(bk, o.bk())
+    assert np.array_equal(ksk, o.ksk())
+
+
+def test_encryption_equals_oracle_encryption():
+    ctx = F.Context(11, device=-1)
+    o = O.Oracle(11)
+    rng = np.random.default_rng(0)
+    bits = rng.integers(0, 2, 300).astype(np.uint8)
+    full = ctx.encrypt_bits(bits, 5, 0)
+    assert np.array_equal(full, o.encrypt_bits(bits, 5, 0))
+    # chunked encryption with first_index reproduces the single call
+    assert np.array_equal(ctx.encrypt_bits(bits[100:], 5, 100), full[100:])
+    mu = rng.integers(0, 1 << 32, 50, dtype=np.uint64).astype(np.uint32)
+    assert np.array_equal(ctx.encrypt(mu, 9, 4), o.encrypt(mu, 9, 4))
+    vals = rng.integers(0, 1 << 32, 20, dtype=np.uint64)
+    ct = ctx.encrypt_uint(vals, 32, 5, 0)
+    assert ct.shape == (20, 32, 631)
+    assert np.array_equal(ctx.decrypt_uint(ct, 32), vals)
+    assert np.array_equal(ctx.decrypt_bits(full), bits)
+    assert np.array_equal(ctx.phase(full[:10]), o.phase(full[:10]))
+
+
+def _oracle_levels(pred, w, npay, pw):
+    t, a, b, m, ninp = O.netlist(pred, w, npay, pw)
+    depth = [0] * ninp
+    for k in range(t.size):
+        depth.append(1 + max(depth[a[k]], depth[b[k]]))
+    d = np.array(depth[ninp:])
+    return int(t.size), [int((d == L).sum()) for L in range(1, d.max() + 1)]
+
+
+@pytest.mark.parametrize("shape", [(WL.PRED_EQ, 4, 1, 4), (WL.PRED_EQ, 32, 1, 32), (WL.PRED_LT, 8, 1, 8),
+                                   (WL.PRED_RANGE, 16, 2, 16), (WL.PRED_EQ, 1, 0, 0), (WL.PRED_RANGE, 3, 3, 5)])
+def test_scheduler_levels_equal_oracle_netlist_depths(shape):
+    assert F.plan_info(*shape) == _oracle_levels(*shape)
+
+
+def test_scheduler_known_level_widths():
+    # 16-row 4-bit equality scan: 64 XNOR, 32 + 16 AND, 64 mask gates
+    g, widths = F.plan_info(WL.PRED_EQ, 4, 1, 4)
+    assert g * 16 == 176 and [16 * x for x in widths] == [64, 32, 16, 64]
+    g, widths = F.plan_info(WL.PRED_EQ, 32, 1, 32)
+    assert g * 4096 == 389120 and [4096 * x for x in widths] == [131072, 65536, 32768, 16384, 8192, 4096, 131072]
+    g, widths = F.plan_info(WL.PRED_RANGE, 16, 2, 16)
+    assert g * 65536 == 10158080 and widths[0] * 65536 == 65536 * 62
+
+
+def test_argument_errors_are_codes_not_crashes():
+    p = F.params_default()
+    p.N = 1000  # not a power of two
+    with pytest.raises(F.FsqlError) as e:
+        F.Context(1, p, device=-1)
+    assert e.value.code == F.FSQL_ERR_ARG
+    # the kernels implement N = 1024 only: a device context with toy params is refused before any CUDA call
+    with pytest.raises(F.FsqlError) as e:
+        F.Context(1, F.params_toy(), device=0)
+    assert e.value.code == F.FSQL_ERR_UNSUPPORTED
+    ctx = F.Context(1, F.params_toy(), device=-1)
+    with pytest.raises(F.FsqlError):  # host-only context has no device keys
+        ctx.gate_batch(np.zeros(1, np.uint8), 1, 2, 3)
+    with pytest.raises(F.FsqlError):
+        F.plan_info(7, 4, 1, 4)
+    with pytest.raises(F.FsqlError):
+        F.plan_info(WL.PRED_EQ, 0, 1, 4)
+
+
+def test_workload_tables_plaintext_semantics():
+    t = WL.table("eq32x4096")
+    m, (p,) = t.expected()
+    assert t.rows == 4096 and m.sum() >= 1 and t.gates_per_row == 95
+    assert np.all(p[m == 0] == 0) and np.all(p[m == 1] == t.payloads[0][m == 1])
+    r = WL.table("range16x65536")
+    m, _ = r.expected()
+    assert abs(m.mean() - 0.1) < 0.01 and r.gates_per_row == 155
+    assert WL.table("eq4x16").gates_per_row * 16 == 176
+    types, x, y = WL.gates(1000)
+    assert set(np.unique(types)) == {0, 1, 2, 3, 4}

@@ -1,0 +1,214 @@
+"""GPU parity: the CUDA path against the CPU oracle, bit-exact on every output
+word (this is integer cryptographic work; nothing is rounded), through the
+C-ABI library.  Inputs: both sides encrypt the same seeded plaintexts with
+their own code (their ciphertexts are asserted equal first)."""
+import os
+
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2510_15413_b300 import fhesql as F
+from paper_2510_15413_b300 import workloads as WL
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+SEED = 2510
+
+
+@pytest.fixture(scope="module")
+def env():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    O.set_threads(os.cpu_count() or 1)
+    ctx = F.Context(SEED, device=0)
+    o = O.Oracle(SEED)
+    yield ctx, o
+    ctx.close()
+    o.close()
+
+
+def dev(x):
+    return torch.from_numpy(np.ascontiguousarray(x)).cuda()
+
+
+def host(t):
+    torch.cuda.synchronize()
+    return t.cpu().numpy()
+
+
+def both_encrypt_bits(ctx, o, bits, stream, first=0):
+    a = ctx.encrypt_bits(bits, stream, first)
+    b = o.encrypt_bits(bits, stream, first)
+    assert np.array_equal(a, b)
+    return a
+
+
+# ---------------------------------------------------------------- NTT
+def test_ntt_product_matches_schoolbook(env):
+    ctx, _ = env
+    rng = np.random.default_rng(1)
+    cases = [
+        (rng.integers(-64, 64, 1024), rng.integers(0, 1 << 32, 1024, dtype=np.uint64)),
+        (np.full(1024, -64), np.full(1024, 0xFFFFFFFF, np.uint64)),  # largest |integer coefficient|
+        (np.full(1024, 63), np.full(1024, 0xFFFFFFFF, np.uint64)),
+        (np.eye(1, 1024, 1023, dtype=np.int64)[0], np.eye(1, 1024, 1, dtype=np.uint64)[0]),  # X^1023 * X = -1
+    ]
+    for d, a in cases:
+        d = d.astype(np.int32)
+        a = a.astype(np.uint32)
+        out = torch.zeros(1024, dtype=torch.int32, device="cuda")
+        ctx.debug_ntt_mul(dev(d), dev(a.view(np.int32)), out)
+        got = host(out).view(np.uint32)
+        want = O.negacyclic_schoolbook(d.astype(np.int64).astype(np.uint32), a)
+        assert np.array_equal(got, want)
+
+
+# ---------------------------------------------------------------- pieces of one bootstrap
+def test_blind_rotate_extract_matches_oracle(env):
+    ctx, o = env
+    rng = np.random.default_rng(2)
+    count = 11  # one full 8-warp group plus a ragged one
+    types = rng.integers(0, 10, count).astype(np.uint8)
+    x = both_encrypt_bits(ctx, o, rng.integers(0, 2, count).astype(np.uint8), 30)
+    y = both_encrypt_bits(ctx, o, rng.integers(0, 2, count).astype(np.uint8), 31)
+    big = torch.zeros((count, 1025), dtype=torch.int32, device="cuda")
+    ctx.blind_rotate_extract(dev(types), dev(x.view(np.int32)), dev(y.view(np.int32)), big)
+    got = host(big).view(np.uint32)
+    for g in [0, 5, 8, 10]:
+        lin = o.lincomb(int(types[g]), x[g], y[g])
+        want = o.sample_extract(o.blind_rotate(lin))
+        assert np.array_equal(got[g], want), g
+
+
+def test_keyswitch_matches_oracle(env):
+    ctx, o = env
+    rng = np.random.default_rng(3)
+    count = 37  # two full 16-gate groups and a ragged one
+    big = rng.integers(0, 1 << 32, (count, 1025), dtype=np.uint64).astype(np.uint32)
+    big[0, :1024] = 0
+    big[1, :1024] = 0xFFFFFFFF
+    big[2, :1024] = 1 << 15  # rounding ties
+    out = torch.zeros((count, 631), dtype=torch.int32, device="cuda")
+    ctx.keyswitch(dev(big.view(np.int32)), out, count)
+    got = host(out).view(np.uint32)
+    for g in range(count):
+        assert np.array_equal(got[g], o.keyswitch(big[g])), g
+
+
+# ---------------------------------------------------------------- whole gates
+def test_gate_batch_every_type_and_input_pair(env):
+    ctx, o = env
+    types = np.repeat(np.arange(10, dtype=np.uint8), 4)
+    xb = np.tile(np.array([0, 0, 1, 1], np.uint8), 10)
+    yb = np.tile(np.array([0, 1, 0, 1], np.uint8), 10)
+    x = both_encrypt_bits(ctx, o, xb, 40)
+    y = both_encrypt_bits(ctx, o, yb, 41)
+    out = torch.zeros((40, 631), dtype=torch.int32, device="cuda")
+    ctx.gate_batch(dev(types), dev(x.view(np.int32)), dev(y.view(np.int32)), out)
+    got = host(out).view(np.uint32)
+    want = o.gate_batch(types.astype(np.int32), x, y)
+    assert np.array_equal(got, want)
+    truth = np.array([O.gate_plain(int(t), int(a), int(b)) for t, a, b in zip(types, xb, yb)], np.uint8)
+    assert np.array_equal(ctx.decrypt_bits(got), truth)
+
+
+def test_gate_batch_random_microbench_inputs(env):
+    ctx, o = env
+    B = 150  # > one CTA wave of 8-gate groups on a partial grid, ragged tails everywhere
+    types, xb, yb = WL.gates(B, seed=5)
+    x = both_encrypt_bits(ctx, o, xb, WL.STREAM_GATES, 0)
+    y = both_encrypt_bits(ctx, o, yb, WL.STREAM_GATES, B)
+    out = torch.zeros((B, 631), dtype=torch.int32, device="cuda")
+    ctx.gate_batch(dev(types), dev(x.view(np.int32)), dev(y.view(np.int32)), out)
+    got = host(out).view(np.uint32)
+    sample = np.random.default_rng(6).choice(B, 24, replace=False)
+    want = o.gate_batch(types[sample].astype(np.int32), x[sample], y[sample])
+    assert np.array_equal(got[sample], want)
+    truth = np.array([O.gate_plain(int(t), int(a), int(b)) for t, a, b in zip(types, xb, yb)], np.uint8)
+    assert np.array_equal(ctx.decrypt_bits(got), truth)
+
+
+def test_empty_batches_are_no_ops(env):
+    ctx, _ = env
+    e = torch.zeros(0, dtype=torch.uint8, device="cuda")
+    ctx.gate_batch(e, 0, 0, 0)
+    ctx.keyswitch(0, 0, 0)
+
+
+# ---------------------------------------------------------------- scans
+def run_scan(ctx, t, col, cst, pays, per_gate=False):
+    W = ctx.words
+    dcol, dcst = dev(col.view(np.int32)), dev(cst.view(np.int32))
+    dp = [dev(p.view(np.int32)) for p in pays]
+    match = torch.zeros((t.rows, W), dtype=torch.int32, device="cuda")
+    outs = [torch.zeros((t.rows, t.payload_width, W), dtype=torch.int32, device="cuda") for _ in pays]
+    ctx.scan_select(dcol, t.rows, t.width, t.pred, dcst, dp, t.payload_width, match, outs, per_gate=per_gate)
+    return host(match).view(np.uint32), [host(x).view(np.uint32) for x in outs]
+
+
+def check_plaintext(ctx, t, match, outs):
+    m_want, p_want = t.expected()
+    assert np.array_equal(ctx.decrypt_bits(match), m_want)
+    for q, o_ in enumerate(outs):
+        assert np.array_equal(ctx.decrypt_uint(o_, t.payload_width), p_want[q])
+
+
+def encrypt_both(ctx, o, t):
+    lib_ct = WL.encrypt_table(ctx, t)
+    orc_ct = WL.encrypt_table(o, t)
+    assert all(np.array_equal(a, b) for a, b in zip(lib_ct[:2], orc_ct[:2]))
+    assert all(np.array_equal(a, b) for a, b in zip(lib_ct[2], orc_ct[2]))
+    return lib_ct, orc_ct
+
+
+@pytest.mark.parametrize("name,rows", [("eq4x16", 16), ("lt8x64", 5), ("range4x16", 6)])
+def test_scan_small_tables_bit_exact(env, name, rows):
+    ctx, o = env
+    t = WL.table(name, seed=3, rows=rows)
+    (col, cst, pays), (ocol, ocst, opays) = encrypt_both(ctx, o, t)
+    match, outs = run_scan(ctx, t, col, cst, pays)
+    om, oouts = o.scan(t.pred, t.width, ocol, ocst, opays, t.payload_width)
+    assert np.array_equal(match.reshape(om.shape), om)
+    for a, b in zip(outs, oouts):
+        assert np.array_equal(a.reshape(b.shape), b)
+    check_plaintext(ctx, t, match, outs)
+
+
+def test_scan_per_gate_and_host_paths_equal_batched(env):
+    ctx, o = env
+    t = WL.table("eq4x16", seed=4)
+    col, cst, pays = WL.encrypt_table(ctx, t)
+    m1, o1 = run_scan(ctx, t, col, cst, pays, per_gate=False)
+    m2, o2 = run_scan(ctx, t, col, cst, pays, per_gate=True)
+    assert np.array_equal(m1, m2) and all(np.array_equal(a, b) for a, b in zip(o1, o2))
+    m3 = np.zeros_like(m1)
+    o3 = [np.zeros_like(x) for x in o1]
+    ctx.scan_select_host(col, t.rows, t.width, t.pred, cst, pays, t.payload_width, m3, o3)
+    assert np.array_equal(m1, m3) and all(np.array_equal(a, b) for a, b in zip(o1, o3))
+
+
+def test_scan_eq32x4096_full_size_sampled_rows(env):
+    """The benchmark workload at full size, in the benchmark's launch
+    configuration; the oracle recomputes whole sampled rows (the matching row
+    and the last row), every row is decrypted against the SQL answer."""
+    ctx, o = env
+    t = WL.table("eq32x4096", seed=1)
+    col, cst, pays = WL.encrypt_table(ctx, t)
+    match, outs = run_scan(ctx, t, col, cst, pays)
+    check_plaintext(ctx, t, match, outs)
+    m_want, _ = t.expected()
+    rows = sorted({int(np.argmax(m_want)), t.rows - 1})
+    sub = WL.Table(t.name, len(rows), t.width, t.pred, t.column[rows], [p[rows] for p in t.payloads],
+                   t.payload_width, t.consts)
+    # oracle encrypts the sampled rows at their own positions in the column stream
+    ocol = np.concatenate([o.encrypt_bits(t.column_bits().reshape(t.rows, t.width)[r], WL.STREAM_COLUMN,
+                                          r * t.width) for r in rows])
+    opay = np.concatenate([o.encrypt_bits(t.payload_bits(0).reshape(t.rows, t.payload_width)[r],
+                                          WL.STREAM_PAYLOAD, r * t.payload_width) for r in rows])
+    ocst = o.encrypt_bits(t.const_bits(), WL.STREAM_CONST, 0)
+    assert np.array_equal(ocol.reshape(len(rows), t.width, -1), col.reshape(t.rows, t.width, -1)[rows])
+    om, (oout,) = o.scan(sub.pred, sub.width, ocol, ocst, [opay], sub.payload_width)
+    assert np.array_equal(match.reshape(t.rows, -1)[rows], om)
+    assert np.array_equal(outs[0].reshape(t.rows, t.payload_width, -1)[rows], oout)
