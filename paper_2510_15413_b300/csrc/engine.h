@@ -34,14 +34,16 @@ struct GateDesc {
   uint32_t pad;
 };
 
-// Twiddle tables of the 1024-point negacyclic NTT, in the register layout the
-// warp NTT uses (see kernels.cu).
+// Twiddle tables of the 1024-point negacyclic NTT (see ntt.cuh for the
+// thread layouts).  f = psi^bitrev(k), g = psi^-bitrev(k).
 struct NttTables {
-  uint64_t fwd_uniform[32];      // psi^bitrev(k), k < 32 (stages with distance >= 32)
-  uint64_t inv_uniform[32];      // psi^-bitrev(k), k < 32
-  uint64_t fwd_lane[31 * 32];    // per-lane twiddles of the distance < 32 stages
-  uint64_t inv_lane[31 * 32];
-  uint64_t n_inv;                // N^-1 mod p
+  uint64_t f_small[64];   // f[k], k < 64 (forward passes 1-2)
+  uint64_t g_small[128];  // g[k], k < 128 (inverse passes 2-4)
+  uint64_t f3[7][128];    // forward pass 3, per thread: f[64+h], f[128+2h+c], f[256+4h+c], h = t>>1
+  uint64_t f4[4][128];    // forward pass 4, per thread: f[512+4t+c]
+  uint64_t i1[7][128];    // inverse pass 1, per thread: g[512+4t+c], g[256+2t+c], g[128+t]
+  uint64_t n_inv;         // N^-1 mod p
+  uint64_t pad;
 };
 
 struct Plan;  // scan plan (kernels.cu)

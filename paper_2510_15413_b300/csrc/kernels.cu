@@ -4,14 +4,16 @@
 // level over all rows (Alg. 2 ProcessQuery; §4.2 mask generation and
 // application).
 //
-// Blind rotation kernel.  One warp owns one gate for all n CMux steps; a CTA
-// of 8 warps runs 8 gates in lockstep so that the bootstrapping-key slice of
-// each CMux step and gadget row (16 KB in the NTT domain) is staged once into
-// shared memory by cp.async and read by all 8 warps.  Per CMux step a warp:
+// Blind rotation kernel.  A group of 128 threads owns one gate for all n CMux
+// steps; each thread holds 8 of the 1024 coefficients of every polynomial it
+// transforms (ntt.cuh).  A CTA runs G gates in lockstep so that the
+// bootstrapping-key slice of each CMux step and gadget row (16 KB in the NTT
+// domain) is staged once into shared memory by cp.async (3-slot ring) and
+// read by all G groups.  Per CMux step a group:
 //   for each of the 2l = 6 rows (u, j): forms digit j of X^a*ACC_u - ACC_u,
-//     runs the forward NTT in registers, and multiply-accumulates with the
-//     staged key row into two NTT-domain accumulators (one per output
-//     polynomial) that stay in registers;
+//     runs the forward NTT, and multiply-accumulates with the staged key row
+//     into two NTT-domain accumulators (one per output polynomial) held in
+//     registers;
 //   runs the two inverse NTTs, lifts the exact integers mod 2^32 and adds
 //   them into its accumulator polynomials in shared memory.
 // Keyswitch kernel.  A CTA takes 16 gates and all output columns; each
@@ -31,17 +33,18 @@ namespace fsql {
 
 namespace {
 
-constexpr int kBrWarps = 8;
-constexpr int kBrThreads = kBrWarps * 32;
-constexpr int kChunkU64 = 32 * 32 * 2;           // one key row: 1024 slots x 2 output polys
+constexpr int kGroup = 128;                      // threads per gate
+constexpr int kBrGates = 4;                      // gates per CTA
+constexpr int kBrThreads = kBrGates * kGroup;
+constexpr int kChunkU64 = 8 * kGroup * 2;        // one key row: 1024 slots x 2 output polys
 constexpr int kChunkBytes = kChunkU64 * 8;       // 16 KB
 constexpr int kStages = 3;
 constexpr int kTabBytes = (sizeof(NttTables) + 127) / 128 * 128;
-constexpr int kWarpTile = 1024 * 8;              // transpose tile
-constexpr int kWarpAcc = 2 * kN * 4;             // accumulator polynomials (u32)
-constexpr int kWarpAbar = kMaxN * 2;             // switched mask, u16
-constexpr int kWarpBytes = kWarpTile + kWarpAcc + kWarpAbar + 16;
-constexpr int kBrSmem = kTabBytes + kStages * kChunkBytes + kBrWarps * kWarpBytes;
+constexpr int kGateXbuf = 2 * kN * 8;            // two exchange buffers
+constexpr int kGateAcc = 2 * kN * 4;             // accumulator polynomials (u32)
+constexpr int kGateAbar = kMaxN * 2;             // switched mask, u16
+constexpr int kGateBytes = kGateXbuf + kGateAcc + kGateAbar + 16;
+constexpr int kBrSmem = kTabBytes + kStages * kChunkBytes + kBrGates * kGateBytes;
 static_assert(kBrSmem <= 227 * 1024, "blind-rotation shared memory over budget");
 
 constexpr int kKsGates = 16;
@@ -86,21 +89,20 @@ bool make_tables(NttTables* T) {
     f[k] = powmod_host(psi, bitrev10(k));
     g[k] = powmod_host(psi_inv, bitrev10(k));
   }
-  for (int k = 0; k < 32; ++k) {
-    T->fwd_uniform[k] = f[k];
-    T->inv_uniform[k] = g[k];
-  }
-  for (int s = 0; s < 5; ++s) {
-    // forward, distance 16>>s: element 32L + j is in group (32L + j)/(2d) of stage m = 32<<s
-    const int per_lane = 1 << s, off = (1 << s) - 1;
-    for (int q = 0; q < per_lane; ++q)
-      for (int L = 0; L < 32; ++L) T->fwd_lane[(off + q) * 32 + L] = f[(32 << s) + L * per_lane + q];
-    // inverse, distance 1<<s: h = 512>>s groups
-    const int per_lane_i = 16 >> s, off_i = 32 - (32 >> s);
-    for (int q = 0; q < per_lane_i; ++q)
-      for (int L = 0; L < 32; ++L) T->inv_lane[(off_i + q) * 32 + L] = g[(512 >> s) + L * per_lane_i + q];
+  for (int k = 0; k < 64; ++k) T->f_small[k] = f[k];
+  for (int k = 0; k < 128; ++k) T->g_small[k] = g[k];
+  for (int t = 0; t < kGroup; ++t) {
+    const int h = t >> 1;
+    T->f3[0][t] = f[64 + h];
+    for (int c = 0; c < 2; ++c) T->f3[1 + c][t] = f[128 + 2 * h + c];
+    for (int c = 0; c < 4; ++c) T->f3[3 + c][t] = f[256 + 4 * h + c];
+    for (int c = 0; c < 4; ++c) T->f4[c][t] = f[512 + 4 * t + c];
+    for (int c = 0; c < 4; ++c) T->i1[c][t] = g[512 + 4 * t + c];
+    for (int c = 0; c < 2; ++c) T->i1[4 + c][t] = g[256 + 2 * t + c];
+    T->i1[6][t] = g[128 + t];
   }
   T->n_inv = powmod_host(kN, kP - 2);
+  T->pad = 0;
   return true;
 }
 
@@ -138,29 +140,33 @@ __device__ __forceinline__ Lin gate_lin(uint32_t type) {
 
 // ------------------------------------------------------------------ kernels
 
-// Key conversion: one warp per key polynomial (i, row, c): forward NTT of the
-// coefficients read as integers in [0, 2^32), times 1/N, stored as
-// bkhat[i][row][j][L][c] so that lane L of a warp in layout B reads its
-// (j, c = 0..1) pair as one 16-byte word.
-__global__ void __launch_bounds__(128) bk_to_ntt_kernel(const uint32_t* __restrict__ bk, uint64_t* __restrict__ bkhat,
-                                                        const NttTables* __restrict__ gtab, int n) {
-  __shared__ NttTables T;
-  __shared__ uint64_t tiles[4][1024];
+__device__ __forceinline__ void load_tables(NttTables& T, const NttTables* __restrict__ gtab) {
   for (int k = threadIdx.x; k < static_cast<int>(sizeof(NttTables) / 8); k += blockDim.x)
     reinterpret_cast<uint64_t*>(&T)[k] = reinterpret_cast<const uint64_t*>(gtab)[k];
+}
+
+// Key conversion: one 128-thread CTA per key polynomial (i, row, c): forward
+// NTT of the coefficients read as integers in [0, 2^32), times 1/N, stored as
+// bkhat[i][row][k][t][c] (slot 8t + k) so that thread t of a gate group reads
+// its (k, c = 0..1) pair as one 16-byte word.
+__global__ void __launch_bounds__(kGroup) bk_to_ntt_kernel(const uint32_t* __restrict__ bk,
+                                                           uint64_t* __restrict__ bkhat,
+                                                           const NttTables* __restrict__ gtab) {
+  __shared__ NttTables T;
+  __shared__ uint64_t bufs[2 * kN];
+  load_tables(T, gtab);
   __syncthreads();
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int w = blockIdx.x * 4 + warp;
-  if (w >= n * kRows * 2) return;
+  const int w = blockIdx.x, t = threadIdx.x;
   const int i = w / (kRows * 2), row = (w / 2) % kRows, c = w % 2;
   const uint32_t* src = bk + (static_cast<size_t>(i * kRows + row) * 2 + c) * kN;
-  uint64_t x[32];
+  uint64_t x[8];
 #pragma unroll
-  for (int j = 0; j < 32; ++j) x[j] = src[lane + 32 * j];
-  dev::ntt_forward(x, tiles[warp], T, lane);
+  for (int k = 0; k < 8; ++k) x[k] = src[t + 128 * k];
+  int parity = 0;
+  dev::ntt_forward(x, bufs, parity, T, t, 1);
   uint64_t* dst = bkhat + static_cast<size_t>(i * kRows + row) * kChunkU64;
 #pragma unroll
-  for (int j = 0; j < 32; ++j) dst[(j * 32 + lane) * 2 + c] = dev::gl_mul(x[j], T.n_inv);
+  for (int k = 0; k < 8; ++k) dst[(k * kGroup + t) * 2 + c] = dev::gl_mul(x[k], T.n_inv);
 }
 
 // Contiguous gate arrays -> descriptors.
@@ -191,15 +197,15 @@ __global__ void __launch_bounds__(kBrThreads, 1)
   extern __shared__ __align__(128) uint8_t smem[];
   NttTables& T = *reinterpret_cast<NttTables*>(smem);
   uint64_t* stage = reinterpret_cast<uint64_t*>(smem + kTabBytes);
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  uint8_t* wb = smem + kTabBytes + kStages * kChunkBytes + warp * kWarpBytes;
-  uint64_t* tile = reinterpret_cast<uint64_t*>(wb);
-  uint32_t* acc_poly = reinterpret_cast<uint32_t*>(wb + kWarpTile);              // [2][N]
-  uint16_t* abar = reinterpret_cast<uint16_t*>(wb + kWarpTile + kWarpAcc);      // [n]
-  uint32_t* bbar_slot = reinterpret_cast<uint32_t*>(wb + kWarpTile + kWarpAcc + kWarpAbar);
+  const int grp = threadIdx.x / kGroup, t = threadIdx.x % kGroup;
+  const int bar = 1 + grp;  // named barrier of this gate's 128 threads
+  uint8_t* gb = smem + kTabBytes + kStages * kChunkBytes + grp * kGateBytes;
+  uint64_t* xbufs = reinterpret_cast<uint64_t*>(gb);                         // [2][N] u64
+  uint32_t* acc_poly = reinterpret_cast<uint32_t*>(gb + kGateXbuf);          // [2][N] u32
+  uint16_t* abar = reinterpret_cast<uint16_t*>(gb + kGateXbuf + kGateAcc);   // [n]
+  uint32_t* bbar_slot = reinterpret_cast<uint32_t*>(gb + kGateXbuf + kGateAcc + kGateAbar);
 
-  for (int k = threadIdx.x; k < static_cast<int>(sizeof(NttTables) / 8); k += kBrThreads)
-    reinterpret_cast<uint64_t*>(&T)[k] = reinterpret_cast<const uint64_t*>(gtab)[k];
+  load_tables(T, gtab);
 
   // Signed gadget digits by the offset form: y = x + sum_j 2^(bg-1) 2^(32-bg j)
   // + 2^(31 - bg l); digit j = ((y >> (32 - bg j)) mod 2^bg) - 2^(bg-1).
@@ -208,8 +214,8 @@ __global__ void __launch_bounds__(kBrThreads, 1)
   const uint32_t dmask = (1u << bg_bits) - 1, dhalf = 1u << (bg_bits - 1);
   const int total = n * kRows;
 
-  for (int g0 = blockIdx.x * kBrWarps; g0 < count; g0 += gridDim.x * kBrWarps) {
-    const int gi = g0 + warp;
+  for (int g0 = blockIdx.x * kBrGates; g0 < count; g0 += gridDim.x * kBrGates) {
+    const int gi = g0 + grp;
     const bool active = gi < count;
     __syncthreads();  // tables loaded; previous group finished with the stages
     issue_chunk(stage, bkhat, 0);
@@ -221,85 +227,83 @@ __global__ void __launch_bounds__(kBrThreads, 1)
       const GateDesc d = desc[gi];
       const Lin lin = gate_lin(d.type);
       // linear combination and modulus switch q -> 2N (round half up)
-      for (int x = lane; x <= n; x += 32) {
+      for (int x = t; x <= n; x += kGroup) {
         uint32_t v = lin.ca * d.a[x] + lin.cb * d.b[x];
         if (x == n) v += lin.k;
         const uint32_t ms = ((v + (1u << 20)) >> 21) & (2 * kN - 1);
         if (x < n) abar[x] = static_cast<uint16_t>(ms);
         else *bbar_slot = ms;
       }
-      __syncwarp();
+      dev::named_sync(bar);
       // ACC = (0, X^{-bbar} * v), v_k = q/8 for all k
       const uint32_t e = (2 * kN - *bbar_slot) & (2 * kN - 1);
 #pragma unroll
-      for (int j = 0; j < 32; ++j) {
-        const uint32_t k = lane + 32 * j;
-        acc_poly[k] = 0u;
-        const uint32_t idx = (k - e) & (2 * kN - 1);
-        acc_poly[kN + k] = idx < static_cast<uint32_t>(kN) ? (1u << 29) : (0u - (1u << 29));
+      for (int k = 0; k < 8; ++k) {
+        const uint32_t c = t + 128 * k;
+        acc_poly[c] = 0u;
+        const uint32_t idx = (c - e) & (2 * kN - 1);
+        acc_poly[kN + c] = idx < static_cast<uint32_t>(kN) ? (1u << 29) : (0u - (1u << 29));
       }
-      __syncwarp();
     }
 
-    uint64_t acc0[32], acc1[32];
+    int parity = 0;
+    uint64_t acc0[8], acc1[8];
     for (int i = 0; i < n; ++i) {
-      const uint32_t a_i = active ? abar[i] : 0u;
 #pragma unroll 1
       for (int r = 0; r < kRows; ++r) {
         const int k = i * kRows + r;
         cp_async_wait<1>();
-        __syncthreads();  // key row k visible to all; everyone done with row k-1's slot
+        __syncthreads();  // key row k visible; everyone done with row k-1's slot and the ACC update
         if (k + 2 < total) issue_chunk(stage + ((k + 2) % kStages) * kChunkU64, bkhat, k + 2);
         cp_async_commit();
         if (active) {
+          const uint32_t a_i = abar[i];
           const uint32_t* P = acc_poly + (r / kL) * kN;
           const int shift = 32 - bg_bits * (r % kL + 1);
-          uint64_t x[32];
+          uint64_t x[8];
 #pragma unroll
-          for (int j = 0; j < 32; ++j) {
-            const uint32_t kk = lane + 32 * j;
-            const uint32_t idx = (kk - a_i) & (2 * kN - 1);  // (X^a P)_kk = +-P[idx mod N]
+          for (int q = 0; q < 8; ++q) {
+            const uint32_t c = t + 128 * q;
+            const uint32_t idx = (c - a_i) & (2 * kN - 1);  // (X^a P)_c = +-P[idx mod N]
             const uint32_t rot = idx < static_cast<uint32_t>(kN) ? P[idx] : 0u - P[idx - kN];
-            const uint32_t y = rot - P[kk] + off;
-            x[j] = dev::gl_from_int(static_cast<int32_t>((y >> shift) & dmask) - static_cast<int32_t>(dhalf));
+            const uint32_t y = rot - P[c] + off;
+            x[q] = dev::gl_from_int(static_cast<int32_t>((y >> shift) & dmask) - static_cast<int32_t>(dhalf));
           }
-          dev::ntt_forward(x, tile, T, lane);
+          dev::ntt_forward(x, xbufs, parity, T, t, bar);
           const uint64_t* ch = stage + (k % kStages) * kChunkU64;
 #pragma unroll
-          for (int j = 0; j < 32; ++j) {
-            const ulonglong2 w = *reinterpret_cast<const ulonglong2*>(ch + (j * 32 + lane) * 2);
-            const uint64_t p0 = dev::gl_mul(x[j], w.x);
-            const uint64_t p1 = dev::gl_mul(x[j], w.y);
-            acc0[j] = r == 0 ? p0 : dev::gl_add(acc0[j], p0);
-            acc1[j] = r == 0 ? p1 : dev::gl_add(acc1[j], p1);
+          for (int q = 0; q < 8; ++q) {
+            const ulonglong2 w = *reinterpret_cast<const ulonglong2*>(ch + (q * kGroup + t) * 2);
+            const uint64_t p0 = dev::gl_mul(x[q], w.x);
+            const uint64_t p1 = dev::gl_mul(x[q], w.y);
+            acc0[q] = r == 0 ? p0 : dev::gl_add(acc0[q], p0);
+            acc1[q] = r == 0 ? p1 : dev::gl_add(acc1[q], p1);
           }
         }
       }
       if (active) {
 #pragma unroll 1
         for (int c = 0; c < 2; ++c) {
-          dev::ntt_inverse(acc0, tile, T, lane);
+          dev::ntt_inverse(acc0, xbufs, parity, T, t, bar);
           uint32_t* Pc = acc_poly + c * kN;
 #pragma unroll
-          for (int j = 0; j < 32; ++j) Pc[lane + 32 * j] += dev::gl_lift32(acc0[j]);
-          if (c == 0) {
+          for (int q = 0; q < 8; ++q) Pc[t + 128 * q] += dev::gl_lift32(acc0[q]);
 #pragma unroll
-            for (int j = 0; j < 32; ++j) acc0[j] = acc1[j];
-          }
+          for (int q = 0; q < 8; ++q) acc0[q] = acc1[q];
         }
-        __syncwarp();
       }
     }
 
     if (active) {
-      // sample extraction of coefficient 0: a'_0 = A_0, a'_k = -A_{N-k}, b' = B_0
+      dev::named_sync(bar);
+      // sample extraction of coefficient 0: a'_0 = A_0, a'_c = -A_{N-c}, b' = B_0
       uint32_t* out = big + static_cast<size_t>(gi) * (kN + 1);
 #pragma unroll
-      for (int j = 0; j < 32; ++j) {
-        const int kk = lane + 32 * j;
-        out[kk] = kk == 0 ? acc_poly[0] : 0u - acc_poly[kN - kk];
+      for (int q = 0; q < 8; ++q) {
+        const int c = t + 128 * q;
+        out[c] = c == 0 ? acc_poly[0] : 0u - acc_poly[kN - c];
       }
-      if (lane == 0) out[kN] = acc_poly[kN];
+      if (t == 0) out[kN] = acc_poly[kN];
     }
   }
 }
@@ -363,28 +367,30 @@ __global__ void __launch_bounds__(kKsThreads)
   }
 }
 
-// Exact negacyclic product through the device NTT (test hook).
-__global__ void ntt_mul_kernel(const int32_t* __restrict__ digits, const uint32_t* __restrict__ poly,
-                               uint32_t* __restrict__ out, const NttTables* __restrict__ gtab) {
+// Exact negacyclic product through the device NTT (test hook), 128 threads.
+__global__ void __launch_bounds__(kGroup) ntt_mul_kernel(const int32_t* __restrict__ digits,
+                                                         const uint32_t* __restrict__ poly,
+                                                         uint32_t* __restrict__ out,
+                                                         const NttTables* __restrict__ gtab) {
   __shared__ NttTables T;
-  __shared__ uint64_t tile[1024];
-  for (int k = threadIdx.x; k < static_cast<int>(sizeof(NttTables) / 8); k += 32)
-    reinterpret_cast<uint64_t*>(&T)[k] = reinterpret_cast<const uint64_t*>(gtab)[k];
-  __syncwarp();
-  const int lane = threadIdx.x;
-  uint64_t x[32], y[32];
+  __shared__ uint64_t bufs[2 * kN];
+  load_tables(T, gtab);
+  __syncthreads();
+  const int t = threadIdx.x;
+  uint64_t x[8], y[8];
 #pragma unroll
-  for (int j = 0; j < 32; ++j) {
-    x[j] = dev::gl_from_int(digits[lane + 32 * j]);
-    y[j] = poly[lane + 32 * j];
+  for (int k = 0; k < 8; ++k) {
+    x[k] = dev::gl_from_int(digits[t + 128 * k]);
+    y[k] = poly[t + 128 * k];
   }
-  dev::ntt_forward(x, tile, T, lane);
-  dev::ntt_forward(y, tile, T, lane);
+  int parity = 0;
+  dev::ntt_forward(x, bufs, parity, T, t, 1);
+  dev::ntt_forward(y, bufs, parity, T, t, 1);
 #pragma unroll
-  for (int j = 0; j < 32; ++j) x[j] = dev::gl_mul(x[j], dev::gl_mul(y[j], T.n_inv));
-  dev::ntt_inverse(x, tile, T, lane);
+  for (int k = 0; k < 8; ++k) x[k] = dev::gl_mul(x[k], dev::gl_mul(y[k], T.n_inv));
+  dev::ntt_inverse(x, bufs, parity, T, t, 1);
 #pragma unroll
-  for (int j = 0; j < 32; ++j) out[lane + 32 * j] = dev::gl_lift32(x[j]);
+  for (int k = 0; k < 8; ++k) out[t + 128 * k] = dev::gl_lift32(x[k]);
 }
 
 bool g_br_attr_set[64] = {};
@@ -492,7 +498,7 @@ int device_init(Ctx& c) {
   cudaError_t e = cudaMemcpy(d_bk, c.bk.data(), c.bk.size() * 4, cudaMemcpyHostToDevice);
   if (e == cudaSuccess) {
     const int polys = static_cast<int>(p.n) * kRows * 2;
-    bk_to_ntt_kernel<<<(polys + 3) / 4, 128>>>(d_bk, c.d_bkhat, c.d_tables, static_cast<int>(p.n));
+    bk_to_ntt_kernel<<<polys, kGroup>>>(d_bk, c.d_bkhat, c.d_tables);
     e = cudaGetLastError();
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
   }
@@ -538,7 +544,7 @@ int launch_blind_rotate(Ctx& c, const GateDesc* d_desc, size_t count, uint32_t* 
     CK(cudaFuncSetAttribute(blind_rotate_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kBrSmem));
     g_br_attr_set[c.device] = true;
   }
-  const size_t groups = (count + kBrWarps - 1) / kBrWarps;
+  const size_t groups = (count + kBrGates - 1) / kBrGates;
   const int grid = static_cast<int>(std::min<size_t>(groups, static_cast<size_t>(c.sm_count)));
   LaunchTimer tm(c, static_cast<cudaStream_t>(stream));
   blind_rotate_kernel<<<grid, kBrThreads, kBrSmem, static_cast<cudaStream_t>(stream)>>>(
@@ -829,7 +835,8 @@ int fsql_debug_ntt_mul(fsql_ctx* ctx, const int32_t* d_digits, const uint32_t* d
   Ctx* c = device_ctx(ctx);
   if (!c) return FSQL_ERR_ARG;
   if (!d_digits || !d_poly || !d_out) return arg_error("null device pointer");
-  fsql::ntt_mul_kernel<<<1, 32, 0, static_cast<cudaStream_t>(stream)>>>(d_digits, d_poly, d_out, c->d_tables);
+  fsql::ntt_mul_kernel<<<1, fsql::kGroup, 0, static_cast<cudaStream_t>(stream)>>>(d_digits, d_poly, d_out,
+                                                                                  c->d_tables);
   if (cudaGetLastError() != cudaSuccess) return arg_error("ntt test kernel launch failed");
   return FSQL_OK;
 }

@@ -1,5 +1,6 @@
 // ntt.cuh -- exact arithmetic mod the Goldilocks prime p = 2^64 - 2^32 + 1 and
-// a warp-resident 1024-point negacyclic NTT.
+// a 1024-point negacyclic NTT computed by 128 threads holding 8 coefficients
+// each.
 //
 // Why this transform is exact for the blind rotation: the external product
 // multiplies digit polynomials with coefficients in [-2^(bg-1), 2^(bg-1)) by
@@ -9,21 +10,24 @@
 // The product computed mod p therefore lifts back to the exact integer, and
 // reducing that mod 2^32 gives the Torus32 result with no rounding.
 //
-// Register layout.  A warp holds one polynomial of 1024 coefficients, 32 per
-// lane.  Layout A: lane L, register j holds element L + 32 j.  Layout B: lane
-// L, register j holds element 32 L + j.  A butterfly whose distance is a
-// multiple of 32 pairs registers of one lane in layout A; one with distance
-// below 32 pairs registers of one lane in layout B.  Each transform runs its
-// five long-distance stages in one layout, transposes once through a
-// swizzled 8 KB shared-memory tile, and runs the five short-distance stages
-// in the other layout, so butterflies never cross lanes.
+// Transform.  Forward: Cooley-Tukey, natural order in, bit-reversed order out,
+// negacyclic twist folded into the twiddles psi^bitrev(k) (psi a primitive
+// 2048-th root of unity; Longa & Naehrig, CANS 2016).  Inverse: Gentleman-Sande
+// with psi^-bitrev(k), bit-reversed in, natural out, without the final 1/N
+// (the caller folds 1/N into one operand).
 //
-// Forward: Cooley-Tukey, natural order in, bit-reversed order out, with the
-// negacyclic twist folded into the twiddles psi^bitrev(k), psi a primitive
-// 2048-th root of unity (Longa & Naehrig, CANS 2016).  Inverse: Gentleman-
-// Sande with psi^-bitrev(k), bit-reversed in, natural out, without the final
-// 1/N (the caller folds 1/N into one operand).  Forward input is layout A,
-// forward output and inverse input are layout B, inverse output is layout A.
+// Work split.  The 10 radix-2 stages run as four passes over registers:
+// 3 + 3 + 3 + 1 stages forward, 3 + 3 + 3 + 1 inverse.  Within a pass every
+// butterfly pairs two registers of one thread; between passes the 1024
+// values go through an 8 KB shared-memory buffer (one named barrier of the
+// 128 threads).  Thread t, register k holds element
+//   F1: t + 128k         F2: 128(t>>4) + 16k + (t&15)     F3: 16(t>>1) + 2k + (t&1)
+//   F4 = I1: 8t + k      I2: 64(t>>3) + 8k + (t&7)         I3: 512(t>>6) + 64k + (t&63)
+//   I4 = F1.
+// The forward output layout (F4) is the inverse input layout (I1), so the
+// pointwise products need no exchange.  The buffer index of element e is
+// swizzled, e ^ ((e >> 3) & 15) on its low four bits, which makes every one
+// of these patterns hit 16 distinct 8-byte bank pairs per half warp.
 #pragma once
 
 #include <cstdint>
@@ -38,7 +42,7 @@ constexpr uint64_t kEps = 0xFFFFFFFFull;  // 2^64 mod p
 // a, b in [0, p): a + b mod p.  On carry out of 64 bits the dropped 2^64 is
 // worth kEps; a + b < 2p keeps the corrected sum below p.
 __device__ __forceinline__ uint64_t gl_add(uint64_t a, uint64_t b) {
-  uint64_t s = a + b;
+  const uint64_t s = a + b;
   if (s < a) return s + kEps;
   return s >= kP ? s - kP : s;
 }
@@ -46,24 +50,30 @@ __device__ __forceinline__ uint64_t gl_add(uint64_t a, uint64_t b) {
 // a, b in [0, p): a - b mod p.  On borrow the wrapped value is 2^64 too big,
 // i.e. kEps too big modulo p.
 __device__ __forceinline__ uint64_t gl_sub(uint64_t a, uint64_t b) {
-  uint64_t d = a - b;
+  const uint64_t d = a - b;
   return a < b ? d - kEps : d;
 }
 
-// 128-bit value hi*2^64 + lo reduced mod p, using 2^64 = 2^32 - 1 and
-// 2^96 = -1 (mod p): with hi = h1*2^32 + h0, value = lo - h1 + h0*(2^32 - 1).
-__device__ __forceinline__ uint64_t gl_reduce(uint64_t lo, uint64_t hi) {
-  const uint64_t h1 = hi >> 32;
-  const uint64_t h0 = hi & kEps;
-  uint64_t t = lo - h1;
-  if (lo < h1) t -= kEps;
-  const uint64_t m = (h0 << 32) - h0;
+// a * b mod p for a, b < 2^64.  The 128-bit product is formed from four
+// 32 x 32 -> 64-bit products (r3:r2:r1:r0 in 32-bit words) and reduced with
+// 2^64 = 2^32 - 1 and 2^96 = -1 (mod p):
+//   value = (r1:r0) + r2 * (2^32 - 1) - r3.
+__device__ __forceinline__ uint64_t gl_mul(uint64_t a, uint64_t b) {
+  const uint32_t a0 = static_cast<uint32_t>(a), a1 = static_cast<uint32_t>(a >> 32);
+  const uint32_t b0 = static_cast<uint32_t>(b), b1 = static_cast<uint32_t>(b >> 32);
+  const uint64_t p00 = static_cast<uint64_t>(a0) * b0;
+  const uint64_t p01 = static_cast<uint64_t>(a0) * b1 + (p00 >> 32);
+  const uint64_t p10 = static_cast<uint64_t>(a1) * b0 + static_cast<uint32_t>(p01);
+  const uint64_t p11 = static_cast<uint64_t>(a1) * b1 + (p01 >> 32) + (p10 >> 32);
+  const uint64_t lo = (p10 << 32) | static_cast<uint32_t>(p00);
+  const uint64_t r2 = p11 & kEps, r3 = p11 >> 32;
+  uint64_t t = lo - r3;
+  if (lo < r3) t -= kEps;
+  const uint64_t m = (r2 << 32) - r2;
   uint64_t r = t + m;
   if (r < m) r += kEps;
   return r >= kP ? r - kP : r;
 }
-
-__device__ __forceinline__ uint64_t gl_mul(uint64_t a, uint64_t b) { return gl_reduce(a * b, __umul64hi(a, b)); }
 
 // Signed integer v (|v| < p/2) as an element of Z_p.
 __device__ __forceinline__ uint64_t gl_from_int(int32_t v) {
@@ -76,86 +86,121 @@ __device__ __forceinline__ uint32_t gl_lift32(uint64_t x) {
   return static_cast<uint32_t>(x) - (x > (kP >> 1) ? 1u : 0u);
 }
 
-// Swizzled slot of element (row r, column c) of a 32 x 32 tile of u64:
-// row-wise and column-wise warp accesses both touch 16 distinct 8-byte bank
-// pairs per half warp.
-__device__ __forceinline__ int tile_slot(int r, int c) { return r * 32 + (c ^ r); }
-
-// Forward negacyclic NTT of one polynomial held by the warp (layout A in,
-// layout B out).  tile: this warp's 1024-u64 shared-memory tile.
-__device__ __forceinline__ void ntt_forward(uint64_t (&x)[32], uint64_t* tile, const NttTables& T, int lane) {
-  // distances 512 .. 32 (m = 1 .. 16 groups): partner register j + 16>>s
-#pragma unroll
-  for (int s = 0; s < 5; ++s) {
-    const int d = 16 >> s;
-#pragma unroll
-    for (int j = 0; j < 32; ++j) {
-      if (j & d) continue;
-      const uint64_t w = T.fwd_uniform[(1 << s) + j / (2 * d)];
-      const uint64_t v = gl_mul(x[j + d], w);
-      const uint64_t u = x[j];
-      x[j] = gl_add(u, v);
-      x[j + d] = gl_sub(u, v);
-    }
-  }
-  __syncwarp();
-#pragma unroll
-  for (int j = 0; j < 32; ++j) tile[tile_slot(j, lane)] = x[j];
-  __syncwarp();
-#pragma unroll
-  for (int j = 0; j < 32; ++j) x[j] = tile[tile_slot(lane, j)];
-  // distances 16 .. 1: partner register j + 16>>s, per-lane twiddles
-#pragma unroll
-  for (int s = 0; s < 5; ++s) {
-    const int d = 16 >> s;
-    const int off = (1 << s) - 1;
-#pragma unroll
-    for (int j = 0; j < 32; ++j) {
-      if (j & d) continue;
-      const uint64_t w = T.fwd_lane[(off + j / (2 * d)) * 32 + lane];
-      const uint64_t v = gl_mul(x[j + d], w);
-      const uint64_t u = x[j];
-      x[j] = gl_add(u, v);
-      x[j + d] = gl_sub(u, v);
-    }
-  }
+__device__ __forceinline__ void named_sync(int id) {
+  asm volatile("bar.sync %0, 128;\n" ::"r"(id) : "memory");
 }
 
-// Inverse negacyclic NTT without the 1/N factor (layout B in, layout A out).
-__device__ __forceinline__ void ntt_inverse(uint64_t (&x)[32], uint64_t* tile, const NttTables& T, int lane) {
-  // distances 1 .. 16: partner register j + (1<<s), per-lane twiddles
+__device__ __forceinline__ int swz(int e) { return (e & ~15) | ((e ^ (e >> 3)) & 15); }
+
+// element index held by thread t in register k, per layout
+struct LF1 { static __device__ __forceinline__ int at(int t, int k) { return t + 128 * k; } };
+struct LF2 { static __device__ __forceinline__ int at(int t, int k) { return 128 * (t >> 4) + 16 * k + (t & 15); } };
+struct LF3 { static __device__ __forceinline__ int at(int t, int k) { return 16 * (t >> 1) + 2 * k + (t & 1); } };
+struct LF4 { static __device__ __forceinline__ int at(int t, int k) { return 8 * t + k; } };
+struct LI2 { static __device__ __forceinline__ int at(int t, int k) { return 64 * (t >> 3) + 8 * k + (t & 7); } };
+struct LI3 { static __device__ __forceinline__ int at(int t, int k) { return 512 * (t >> 6) + 64 * k + (t & 63); } };
+
+// Move the 1024 values from layout S to layout D through one of the group's
+// two exchange buffers.  Consecutive exchanges alternate buffers, so the
+// barrier of exchange j also guarantees that every thread has finished
+// reading the buffer of exchange j-1 before exchange j+1 overwrites it.
+template <class S, class D>
+__device__ __forceinline__ void exchange(uint64_t (&x)[8], uint64_t* bufs, int& parity, int t, int bar) {
+  uint64_t* buf = bufs + (parity << 10);
+  parity ^= 1;
 #pragma unroll
-  for (int s = 0; s < 5; ++s) {
-    const int d = 1 << s;
-    const int off = 32 - (32 >> s);
+  for (int k = 0; k < 8; ++k) buf[swz(S::at(t, k))] = x[k];
+  named_sync(bar);
 #pragma unroll
-    for (int j = 0; j < 32; ++j) {
-      if (j & d) continue;
-      const uint64_t w = T.inv_lane[(off + j / (2 * d)) * 32 + lane];
-      const uint64_t u = x[j], v = x[j + d];
-      x[j] = gl_add(u, v);
-      x[j + d] = gl_mul(gl_sub(u, v), w);
-    }
-  }
-  __syncwarp();
+  for (int k = 0; k < 8; ++k) x[k] = buf[swz(D::at(t, k))];
+}
+
+// Cooley-Tukey butterfly on registers (k, k+d) with twiddle w.
+__device__ __forceinline__ void ct(uint64_t& lo, uint64_t& hi, uint64_t w) {
+  const uint64_t v = gl_mul(hi, w);
+  const uint64_t u = lo;
+  lo = gl_add(u, v);
+  hi = gl_sub(u, v);
+}
+// Gentleman-Sande butterfly.
+__device__ __forceinline__ void gs(uint64_t& lo, uint64_t& hi, uint64_t w) {
+  const uint64_t u = lo, v = hi;
+  lo = gl_add(u, v);
+  hi = gl_mul(gl_sub(u, v), w);
+}
+
+// Forward transform: x in layout F1 -> layout F4.  bufs: this group's two
+// 1024-u64 exchange buffers; parity: which one the next exchange uses.
+__device__ __forceinline__ void ntt_forward(uint64_t (&x)[8], uint64_t* bufs, int& parity, const NttTables& T,
+                                            int t, int bar) {
+  // F1: distances 512, 256, 128 (register bits 2, 1, 0), twiddles uniform
 #pragma unroll
-  for (int j = 0; j < 32; ++j) tile[tile_slot(lane, j)] = x[j];
-  __syncwarp();
+  for (int k = 0; k < 4; ++k) ct(x[k], x[k + 4], T.f_small[1]);
 #pragma unroll
-  for (int j = 0; j < 32; ++j) x[j] = tile[tile_slot(j, lane)];
-  // distances 32 .. 512: partner register j + (1<<s), uniform twiddles
+  for (int k = 0; k < 8; ++k)
+    if (!(k & 2)) ct(x[k], x[k + 2], T.f_small[2 + (k >> 2)]);
 #pragma unroll
-  for (int s = 0; s < 5; ++s) {
-    const int d = 1 << s;
+  for (int k = 0; k < 8; k += 2) ct(x[k], x[k + 1], T.f_small[4 + (k >> 1)]);
+  exchange<LF1, LF2>(x, bufs, parity, t, bar);
+  // F2: distances 64, 32, 16
+  const int h3 = t >> 4;
 #pragma unroll
-    for (int j = 0; j < 32; ++j) {
-      if (j & d) continue;
-      const uint64_t w = T.inv_uniform[(16 >> s) + j / (2 * d)];
-      const uint64_t u = x[j], v = x[j + d];
-      x[j] = gl_add(u, v);
-      x[j + d] = gl_mul(gl_sub(u, v), w);
-    }
-  }
+  for (int k = 0; k < 4; ++k) ct(x[k], x[k + 4], T.f_small[8 + h3]);
+#pragma unroll
+  for (int k = 0; k < 8; ++k)
+    if (!(k & 2)) ct(x[k], x[k + 2], T.f_small[16 + 2 * h3 + (k >> 2)]);
+#pragma unroll
+  for (int k = 0; k < 8; k += 2) ct(x[k], x[k + 1], T.f_small[32 + 4 * h3 + (k >> 1)]);
+  exchange<LF2, LF3>(x, bufs, parity, t, bar);
+  // F3: distances 8, 4, 2 (per-thread twiddles)
+#pragma unroll
+  for (int k = 0; k < 4; ++k) ct(x[k], x[k + 4], T.f3[0][t]);
+#pragma unroll
+  for (int k = 0; k < 8; ++k)
+    if (!(k & 2)) ct(x[k], x[k + 2], T.f3[1 + (k >> 2)][t]);
+#pragma unroll
+  for (int k = 0; k < 8; k += 2) ct(x[k], x[k + 1], T.f3[3 + (k >> 1)][t]);
+  exchange<LF3, LF4>(x, bufs, parity, t, bar);
+  // F4: distance 1
+#pragma unroll
+  for (int k = 0; k < 8; k += 2) ct(x[k], x[k + 1], T.f4[k >> 1][t]);
+}
+
+// Inverse transform (no 1/N): x in layout F4 -> layout F1 (natural order).
+__device__ __forceinline__ void ntt_inverse(uint64_t (&x)[8], uint64_t* bufs, int& parity, const NttTables& T,
+                                            int t, int bar) {
+  // I1: distances 1, 2, 4 (per-thread twiddles)
+#pragma unroll
+  for (int k = 0; k < 8; k += 2) gs(x[k], x[k + 1], T.i1[k >> 1][t]);
+#pragma unroll
+  for (int k = 0; k < 8; ++k)
+    if (!(k & 2)) gs(x[k], x[k + 2], T.i1[4 + (k >> 2)][t]);
+#pragma unroll
+  for (int k = 0; k < 4; ++k) gs(x[k], x[k + 4], T.i1[6][t]);
+  exchange<LF4, LI2>(x, bufs, parity, t, bar);
+  // I2: distances 8, 16, 32
+  const int h4 = t >> 3;
+#pragma unroll
+  for (int k = 0; k < 8; k += 2) gs(x[k], x[k + 1], T.g_small[64 + 4 * h4 + (k >> 1)]);
+#pragma unroll
+  for (int k = 0; k < 8; ++k)
+    if (!(k & 2)) gs(x[k], x[k + 2], T.g_small[32 + 2 * h4 + (k >> 2)]);
+#pragma unroll
+  for (int k = 0; k < 4; ++k) gs(x[k], x[k + 4], T.g_small[16 + h4]);
+  exchange<LI2, LI3>(x, bufs, parity, t, bar);
+  // I3: distances 64, 128, 256
+  const int b9 = t >> 6;
+#pragma unroll
+  for (int k = 0; k < 8; k += 2) gs(x[k], x[k + 1], T.g_small[8 + 4 * b9 + (k >> 1)]);
+#pragma unroll
+  for (int k = 0; k < 8; ++k)
+    if (!(k & 2)) gs(x[k], x[k + 2], T.g_small[4 + 2 * b9 + (k >> 2)]);
+#pragma unroll
+  for (int k = 0; k < 4; ++k) gs(x[k], x[k + 4], T.g_small[2 + b9]);
+  exchange<LI3, LF1>(x, bufs, parity, t, bar);
+  // I4: distance 512
+#pragma unroll
+  for (int k = 0; k < 4; ++k) gs(x[k], x[k + 4], T.g_small[1]);
 }
 
 }  // namespace dev
