@@ -144,6 +144,23 @@ FSQL_API int fsql_decrypt_uint(const fsql_ctx* ctx, const uint32_t* ct, size_t r
 FSQL_API int fsql_gate_batch(fsql_ctx* ctx, const uint8_t* d_types, const uint32_t* d_a, const uint32_t* d_b,
                     uint32_t* d_out, size_t count, void* stream);
 
+/* fsql_gate_batch for callers that must not allocate device memory.  The
+ * paper has no counterpart: this exists for host programs that hand the whole
+ * GPU to their own allocator (for example a caching allocator that reserved
+ * it up front) or that cannot afford the device-wide synchronisation and
+ * possible failure of a cudaMalloc in the middle of a query, and so cannot
+ * let fsql_gate_batch grow the context's scratch.  Same arguments and result
+ * as fsql_gate_batch (bit-identical outputs), at most 1024 gates per call
+ * (FSQL_ERR_ARG above that).  Its scratch is a fixed 4 MiB array compiled
+ * into the library, which every GPU that loads the library keeps until the
+ * process exits; the call allocates nothing.  The first call on a device
+ * looks up that array's device address (cudaGetSymbolAddress), so make that
+ * first call before any stream capture.  All calls on one GPU share the
+ * array: calls that can overlap on the GPU (other streams, other contexts on
+ * the same device) race and must be ordered by the caller. */
+FSQL_API int fsql_gate_batch_noalloc(fsql_ctx* ctx, const uint8_t* d_types, const uint32_t* d_a, const uint32_t* d_b,
+                                     uint32_t* d_out, size_t count, void* stream);
+
 /* The two halves of fsql_gate_batch, exposed for tests and profiling.
  * fsql_blind_rotate_extract writes, per gate, the extracted sample of
  * dimension N under the GLWE key: d_big [count][N+1]. */

@@ -604,6 +604,53 @@ int launch_gates(Ctx& c, const GateDesc* d_desc, size_t count, uint32_t* d_big, 
 
 }  // namespace fsql
 
+// ------------------------------------------------------------------ no-allocation gate path
+// Scratch of fsql_gate_batch_noalloc: the extracted samples between the
+// blind-rotation and keyswitch kernels and the gate descriptors, for at most
+// kNoAllocMaxGates gates.  These arrays live in the library's device image,
+// so every GPU that loads the library holds them (4.0 MiB + 32 KiB) until the
+// process exits, and every call of the entry point on that GPU reuses them.
+namespace fsql {
+constexpr size_t kNoAllocMaxGates = 1024;
+static __device__ __align__(256) uint32_t g_noalloc_big[kNoAllocMaxGates * (kN + 1)];
+static __device__ __align__(256) GateDesc g_noalloc_desc[kNoAllocMaxGates];
+
+// Device addresses of the two arrays, looked up once per device.  In host
+// code the array names are host-side stand-ins, not device addresses, so
+// kernels only ever receive the addresses cudaGetSymbolAddress returns.
+struct NoAllocScratch {
+  uint32_t* big = nullptr;
+  GateDesc* desc = nullptr;
+  bool ready = false;
+};
+static NoAllocScratch g_noalloc[64];
+static std::mutex g_noalloc_mu;
+
+static int noalloc_setup(int device, NoAllocScratch* out) {
+  if (device < 0 || device >= 64) {
+    set_error("device ordinal out of range for the no-allocation gate path");
+    return FSQL_ERR_ARG;
+  }
+  std::lock_guard<std::mutex> lk(g_noalloc_mu);
+  NoAllocScratch& s = g_noalloc[device];
+  if (!s.ready) {
+    void* big = nullptr;
+    void* desc = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&big, g_noalloc_big);
+    if (e == cudaSuccess) e = cudaGetSymbolAddress(&desc, g_noalloc_desc);
+    if (e != cudaSuccess) {
+      set_error(std::string("cudaGetSymbolAddress of the no-allocation scratch: ") + cudaGetErrorString(e));
+      return FSQL_ERR_CUDA;
+    }
+    s.big = static_cast<uint32_t*>(big);
+    s.desc = static_cast<GateDesc*>(desc);
+    s.ready = true;
+  }
+  *out = s;
+  return FSQL_OK;
+}
+}  // namespace fsql
+
 using fsql::Ctx;
 using fsql::GateDesc;
 
@@ -979,6 +1026,49 @@ int fsql_profile_end(fsql_ctx* ctx, fsql_kernel_times* out) {
   p->ks.clear();
   if (!ok) {
     fsql::set_error("kernel timing events failed");
+    return FSQL_ERR_CUDA;
+  }
+  return FSQL_OK;
+}
+
+int fsql_gate_batch_noalloc(fsql_ctx* ctx, const uint8_t* d_types, const uint32_t* d_a, const uint32_t* d_b,
+                            uint32_t* d_out, size_t count, void* stream) {
+  Ctx* c = device_ctx(ctx);
+  if (!c) return FSQL_ERR_ARG;
+  if (count == 0) return FSQL_OK;
+  if (count > fsql::kNoAllocMaxGates) {
+    fsql::set_error("fsql_gate_batch_noalloc takes at most 1024 gates per call (its scratch is a fixed array)");
+    return FSQL_ERR_ARG;
+  }
+  if (!d_types || !d_a || !d_b || !d_out) return arg_error("null device pointer");
+  fsql::NoAllocScratch scr;
+  int rc = fsql::noalloc_setup(c->device, &scr);
+  if (rc) return rc;
+  std::lock_guard<std::mutex> lk(c->mu);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const int n = static_cast<int>(c->p.n);
+  // Descriptors and extracted samples are fully rewritten by this call before
+  // they are read, so nothing left by an earlier call needs clearing.
+  fsql::make_desc_kernel<<<static_cast<unsigned>((count + 255) / 256), 256, 0, st>>>(
+      scr.desc, d_types, d_a, d_b, d_out, static_cast<int>(count), n + 1);
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(fsql::blind_rotate_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, fsql::kBrSmem);
+  if (e == cudaSuccess) {
+    const size_t groups = (count + fsql::kBrGates - 1) / fsql::kBrGates;
+    const int grid = static_cast<int>(std::min<size_t>(groups, static_cast<size_t>(c->sm_count)));
+    fsql::blind_rotate_kernel<<<grid, fsql::kBrThreads, fsql::kBrSmem, st>>>(
+        scr.desc, static_cast<int>(count), c->d_bkhat, c->d_tables, n, static_cast<int>(c->p.bg_bits), scr.big);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) {
+    const int grid = static_cast<int>((count + fsql::kKsGates - 1) / fsql::kKsGates);
+    fsql::keyswitch_kernel<<<grid, fsql::kKsThreads, 0, st>>>(scr.big, scr.desc, nullptr, static_cast<int>(count),
+                                                               c->d_ksk, n);
+    e = cudaGetLastError();
+  }
+  if (e != cudaSuccess) {
+    fsql::set_error(std::string("no-allocation gate path launch: ") + cudaGetErrorString(e));
     return FSQL_ERR_CUDA;
   }
   return FSQL_OK;

@@ -23,7 +23,7 @@ API = ["fsql_params_default", "fsql_params_toy", "fsql_ctx_create", "fsql_ctx_de
        "fsql_ctx_device_bytes", "fsql_export_keys", "fsql_encrypt", "fsql_encrypt_bits", "fsql_encrypt_uint",
        "fsql_phase", "fsql_decrypt_bits", "fsql_decrypt_uint", "fsql_gate_batch", "fsql_blind_rotate_extract",
        "fsql_keyswitch", "fsql_debug_ntt_mul", "fsql_plan_info", "fsql_scan_select", "fsql_scan_select_host",
-       "fsql_profile_begin", "fsql_profile_end", "fsql_last_error"]
+       "fsql_profile_begin", "fsql_profile_end", "fsql_gate_batch_noalloc", "fsql_last_error"]
 
 
 class FsqlError(RuntimeError):
@@ -70,6 +70,7 @@ def load() -> C.CDLL:
         "fsql_decrypt_bits": (i32, [vp, vp, sz, vp]),
         "fsql_decrypt_uint": (i32, [vp, vp, sz, u32, vp]),
         "fsql_gate_batch": (i32, [vp, vp, vp, vp, vp, sz, vp]),
+        "fsql_gate_batch_noalloc": (i32, [vp, vp, vp, vp, vp, sz, vp]),
         "fsql_blind_rotate_extract": (i32, [vp, vp, vp, vp, vp, sz, vp]),
         "fsql_keyswitch": (i32, [vp, vp, vp, sz, vp]),
         "fsql_debug_ntt_mul": (i32, [vp, vp, vp, vp, vp]),
@@ -226,6 +227,12 @@ class Context:
     def gate_batch(self, types, a, b, out, stream=None) -> None:
         count = _count(types)
         _check(load().fsql_gate_batch(self._h, _ptr(types), _ptr(a), _ptr(b), _ptr(out), count, _stream(stream)))
+
+    def gate_batch_noalloc(self, types, a, b, out, stream=None) -> None:
+        """fsql_gate_batch without any device allocation (at most 1024 gates)."""
+        count = _count(types)
+        _check(load().fsql_gate_batch_noalloc(self._h, _ptr(types), _ptr(a), _ptr(b), _ptr(out), count,
+                                              _stream(stream)))
 
     def blind_rotate_extract(self, types, a, b, big, stream=None) -> None:
         count = _count(types)
