@@ -87,6 +87,14 @@ typedef struct fsql_params {
 
 typedef struct fsql_ctx fsql_ctx;
 
+/* Exact NTT engines of the blind rotation (results are identical words; only
+ * speed differs).  GOLDILOCKS: one prime p = 2^64 - 2^32 + 1.  DUAL_PRIME:
+ * two primes below 2^29 with 32-bit Montgomery arithmetic and a CRT lift.
+ * DEFAULT picks the faster one on B300 (DUAL_PRIME). */
+#define FSQL_ENGINE_DEFAULT (-1)
+#define FSQL_ENGINE_GOLDILOCKS 0
+#define FSQL_ENGINE_DUAL_PRIME 1
+
 /* Default parameter set: n=630, N=1024, base 2^7 x 3, keyswitch base 4 x 8,
  * sigma 2^-15 (LWE) and 2^-25 (GLWE). */
 FSQL_API int fsql_params_default(fsql_params* out);
@@ -100,6 +108,14 @@ FSQL_API int fsql_params_toy(fsql_params* out);
  * domain and, with the keyswitching key, uploaded to `device` (-1 = no
  * device: host-side calls only).  On success *out owns all of it. */
 FSQL_API int fsql_ctx_create(const fsql_params* params, uint64_t seed, int device, fsql_ctx** out);
+/* As fsql_ctx_create with an explicit NTT engine (FSQL_ENGINE_*). */
+FSQL_API int fsql_ctx_create_engine(const fsql_params* params, uint64_t seed, int device, int engine,
+                                    fsql_ctx** out);
+FSQL_API int fsql_ctx_engine(const fsql_ctx* ctx, int* engine);
+/* Launch shape of the blind rotation: gates per CTA (2, 3 or 4; each gate
+ * is 128 threads).  Results do not depend on it; fsql_autotune picks it. */
+FSQL_API int fsql_ctx_set_br_gates(fsql_ctx* ctx, int gates_per_cta);
+FSQL_API int fsql_ctx_br_gates(const fsql_ctx* ctx, int* gates_per_cta);
 FSQL_API void fsql_ctx_destroy(fsql_ctx* ctx);
 FSQL_API int fsql_ctx_params(const fsql_ctx* ctx, fsql_params* out);
 /* Device bytes held by the context for keys (bootstrapping key in the NTT

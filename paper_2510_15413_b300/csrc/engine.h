@@ -35,14 +35,17 @@ struct GateDesc {
 };
 
 // Twiddle tables of the 1024-point negacyclic NTT (see ntt.cuh for the
-// thread layouts).  f = psi^bitrev(k), g = psi^-bitrev(k).
-struct NttTables {
-  uint64_t f_small[64];   // f[k], k < 64 (forward passes 1-2)
-  uint64_t g_small[128];  // g[k], k < 128 (inverse passes 2-4)
-  uint64_t f3[7][128];    // forward pass 3, per thread: f[64+h], f[128+2h+c], f[256+4h+c], h = t>>1
-  uint64_t f4[4][128];    // forward pass 4, per thread: f[512+4t+c]
-  uint64_t i1[7][128];    // inverse pass 1, per thread: g[512+4t+c], g[256+2t+c], g[128+t]
-  uint64_t n_inv;         // N^-1 mod p
+// thread layouts).  f = psi^bitrev(k), g = psi^-bitrev(k); the entry type Tw
+// is the engine's twiddle form (one u64 for the 64-bit prime; for the two
+// primes, each residue with its Shoup quotient: {w1, w1', w2, w2'}).
+template <class Tw>
+struct NttTablesT {
+  Tw f_small[64];   // f[k], k < 64 (forward passes 1-2)
+  Tw g_small[128];  // g[k], k < 128 (inverse passes 2-4)
+  Tw f3[7][128];    // forward pass 3, per thread: f[64+h], f[128+2h+c], f[256+4h+c], h = t>>1
+  Tw f4[4][128];    // forward pass 4, per thread: f[512+4t+c]
+  Tw i1[7][128];    // inverse pass 1, per thread: g[512+4t+c], g[256+2t+c], g[128+t]
+  uint64_t n_inv;   // key scale: N^-1 mod p (one prime), N^-1 R^2 mod p_i (two primes)
   uint64_t pad;
 };
 
@@ -52,6 +55,8 @@ struct Ctx {
   fsql_params p{};
   uint64_t seed = 0;
   int device = -1;
+  int engine = FSQL_ENGINE_DUAL_PRIME;
+  int br_gates = 4;              // gates per blind-rotation CTA (2, 3 or 4)
   // host-side secrets and standard-domain keys (client side)
   std::vector<uint8_t> s;    // LWE key [n]
   std::vector<uint8_t> S;    // GLWE key [N]
@@ -60,8 +65,8 @@ struct Ctx {
   // device-resident keys
   uint64_t* d_bkhat = nullptr;   // [n][2l][32][32][2] u64, NTT domain, times N^-1
   uint32_t* d_ksk = nullptr;     // [N][t][digits][kKsRowWords]
-  NttTables* d_tables = nullptr;
-  NttTables tables{};
+  void* d_tables = nullptr;      // NttTablesT of the engine
+  std::vector<uint8_t> tables;   // host copy
   size_t key_bytes = 0;
   // scratch (grown on demand, freed with the context)
   uint32_t* d_big = nullptr;     // extracted samples [cap][N+1]

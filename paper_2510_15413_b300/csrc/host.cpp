@@ -276,16 +276,19 @@ int fsql_params_toy(fsql_params* out) {
 
 const char* fsql_last_error(void) { return fsql::g_last_error.c_str(); }
 
-int fsql_ctx_create(const fsql_params* params, uint64_t seed, int device, fsql_ctx** out) {
+int fsql_ctx_create_engine(const fsql_params* params, uint64_t seed, int device, int engine, fsql_ctx** out) {
   return guarded([&]() -> int {
     if (!params || !out) return arg_error("null argument");
     *out = nullptr;
     std::string why;
     if (!params_valid(*params, &why)) return arg_error(why.c_str());
+    if (engine == FSQL_ENGINE_DEFAULT) engine = FSQL_ENGINE_DUAL_PRIME;
+    if (engine != FSQL_ENGINE_GOLDILOCKS && engine != FSQL_ENGINE_DUAL_PRIME) return arg_error("unknown NTT engine");
     auto* c = new Ctx();
     c->p = *params;
     c->seed = seed;
     c->device = device;
+    c->engine = engine;
     fsql::keygen(*c);
     if (device >= 0) {
       const int rc = fsql::device_init(*c);
@@ -298,6 +301,29 @@ int fsql_ctx_create(const fsql_params* params, uint64_t seed, int device, fsql_c
     *out = reinterpret_cast<fsql_ctx*>(c);
     return FSQL_OK;
   });
+}
+
+int fsql_ctx_create(const fsql_params* params, uint64_t seed, int device, fsql_ctx** out) {
+  return fsql_ctx_create_engine(params, seed, device, FSQL_ENGINE_DEFAULT, out);
+}
+
+int fsql_ctx_set_br_gates(fsql_ctx* ctx, int gates_per_cta) {
+  if (!ctx) return arg_error("null context");
+  if (gates_per_cta < 2 || gates_per_cta > 4) return arg_error("gates per CTA must be 2, 3 or 4");
+  reinterpret_cast<Ctx*>(ctx)->br_gates = gates_per_cta;
+  return FSQL_OK;
+}
+
+int fsql_ctx_br_gates(const fsql_ctx* ctx, int* gates_per_cta) {
+  if (!ctx || !gates_per_cta) return arg_error("null argument");
+  *gates_per_cta = reinterpret_cast<const Ctx*>(ctx)->br_gates;
+  return FSQL_OK;
+}
+
+int fsql_ctx_engine(const fsql_ctx* ctx, int* engine) {
+  if (!ctx || !engine) return arg_error("null argument");
+  *engine = reinterpret_cast<const Ctx*>(ctx)->engine;
+  return FSQL_OK;
 }
 
 void fsql_ctx_destroy(fsql_ctx* ctx) {

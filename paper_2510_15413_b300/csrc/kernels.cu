@@ -34,21 +34,28 @@ namespace fsql {
 namespace {
 
 constexpr int kGroup = 128;                      // threads per gate
-constexpr int kBrGates = 4;                      // gates per CTA
-constexpr int kBrThreads = kBrGates * kGroup;
+constexpr int kMaxBrGates = 4;                   // gates per CTA: 2, 3 or 4 (tuned per engine)
 constexpr int kChunkU64 = 8 * kGroup * 2;        // one key row: 1024 slots x 2 output polys
 constexpr int kChunkBytes = kChunkU64 * 8;       // 16 KB
 constexpr int kStages = 3;
-constexpr int kTabBytes = (sizeof(NttTables) + 127) / 128 * 128;
 constexpr int kGateXbuf = 2 * kN * 8;            // two exchange buffers
 constexpr int kGateAcc = 2 * kN * 4;             // accumulator polynomials (u32)
 constexpr int kGateAbar = kMaxN * 2;             // switched mask, u16
 constexpr int kGateBytes = kGateXbuf + kGateAcc + kGateAbar + 16;
-constexpr int kBrSmem = kTabBytes + kStages * kChunkBytes + kBrGates * kGateBytes;
-static_assert(kBrSmem <= 227 * 1024, "blind-rotation shared memory over budget");
+template <class F>
+__host__ __device__ constexpr int tab_bytes() {
+  return (sizeof(typename F::Tables) + 127) / 128 * 128;
+}
+template <class F, int G>
+__host__ __device__ constexpr int br_smem() {
+  return tab_bytes<F>() + kStages * kChunkBytes + G * kGateBytes;
+}
+static_assert(br_smem<dev::DualPrime, kMaxBrGates>() <= 227 * 1024, "blind-rotation shared memory over budget");
+static_assert(br_smem<dev::Goldilocks, kMaxBrGates>() <= 227 * 1024, "blind-rotation shared memory over budget");
 
-constexpr int kKsGates = 16;
-constexpr int kKsThreads = kKsRowWords / 4;      // 160 threads x 4 columns
+constexpr int kKsGates = 16;                     // gates per keyswitch CTA
+constexpr int kKsCols = 128;                     // output columns per keyswitch CTA
+constexpr int kKsTiles = kKsRowWords / kKsCols;  // 5 column tiles cover n + 1 <= 640
 
 #define CK(call)                                                                 \
   do {                                                                           \
@@ -78,17 +85,21 @@ uint32_t bitrev10(uint32_t k) {
   return r;
 }
 
-// psi = 7^((p-1)/2048): 7 generates the multiplicative group of Z_p, so psi
-// has order exactly 2048 (checked: psi^1024 = -1).
-bool make_tables(NttTables* T) {
-  const uint64_t psi = powmod_host(7, (kP - 1) / 2048);
-  if (powmod_host(psi, 1024) != kP - 1) return false;
-  const uint64_t psi_inv = powmod_host(psi, kP - 2);
-  std::vector<uint64_t> f(kN), g(kN);
-  for (uint32_t k = 0; k < static_cast<uint32_t>(kN); ++k) {
-    f[k] = powmod_host(psi, bitrev10(k));
-    g[k] = powmod_host(psi_inv, bitrev10(k));
+uint64_t powmod_u32(uint64_t a, uint64_t e, uint64_t m) {
+  uint64_t r = 1;
+  a %= m;
+  while (e) {
+    if (e & 1) r = r * a % m;
+    a = a * a % m;
+    e >>= 1;
   }
+  return r;
+}
+
+// Fill the twiddle tables from f[k], g[k] (forward / inverse, bit-reversed
+// powers, already in the engine's twiddle form) in the thread layouts of ntt.cuh.
+template <class Tw>
+void fill_tables(NttTablesT<Tw>* T, const std::vector<Tw>& f, const std::vector<Tw>& g, uint64_t key_scale) {
   for (int k = 0; k < 64; ++k) T->f_small[k] = f[k];
   for (int k = 0; k < 128; ++k) T->g_small[k] = g[k];
   for (int t = 0; t < kGroup; ++t) {
@@ -101,8 +112,59 @@ bool make_tables(NttTables* T) {
     for (int c = 0; c < 2; ++c) T->i1[4 + c][t] = g[256 + 2 * t + c];
     T->i1[6][t] = g[128 + t];
   }
-  T->n_inv = powmod_host(kN, kP - 2);
+  T->n_inv = key_scale;
   T->pad = 0;
+}
+
+// Goldilocks: psi = 7^((p-1)/2048); 7 generates Z_p^*, so psi has order
+// exactly 2048 (checked: psi^1024 = -1).  Key scale 1/N.
+bool make_tables_goldilocks(std::vector<uint8_t>* out) {
+  const uint64_t psi = powmod_host(7, (kP - 1) / 2048);
+  if (powmod_host(psi, 1024) != kP - 1) return false;
+  const uint64_t psi_inv = powmod_host(psi, kP - 2);
+  std::vector<uint64_t> f(kN), g(kN);
+  for (uint32_t k = 0; k < static_cast<uint32_t>(kN); ++k) {
+    f[k] = powmod_host(psi, bitrev10(k));
+    g[k] = powmod_host(psi_inv, bitrev10(k));
+  }
+  out->assign(sizeof(dev::Goldilocks::Tables), 0);
+  fill_tables(reinterpret_cast<dev::Goldilocks::Tables*>(out->data()), f, g, powmod_host(kN, kP - 2));
+  return true;
+}
+
+// Two primes: psi_i = gen_i^((p_i - 1)/2048) (13 and 3 generate the two
+// groups; checked psi^1024 = -1); each twiddle residue w comes with its Shoup
+// quotient floor(w 2^32 / p_i).  Key scale N^-1 R^2 (R = 2^32), packed
+// (low word mod p1, high word mod p2).
+bool make_tables_dual(std::vector<uint8_t>* out) {
+  const uint64_t P[2] = {dev::kP1, dev::kP2}, gen[2] = {13, 3};
+  const uint64_t Pinv[2] = {dev::kP1inv, dev::kP2inv};
+  std::vector<uint4> f(kN), g(kN);
+  uint64_t scale = 0;
+  for (int i = 0; i < 2; ++i) {
+    const uint64_t p = P[i];
+    if (((p * Pinv[i]) & 0xFFFFFFFFull) != 1 || (p - 1) % 2048 != 0) return false;
+    const uint64_t psi = powmod_u32(gen[i], (p - 1) / 2048, p);
+    if (powmod_u32(psi, 1024, p) != p - 1) return false;
+    const uint64_t psi_inv = powmod_u32(psi, p - 2, p);
+    const uint64_t r = (1ull << 32) % p;
+    for (uint32_t k = 0; k < static_cast<uint32_t>(kN); ++k) {
+      const uint64_t wf = powmod_u32(psi, bitrev10(k), p), wg = powmod_u32(psi_inv, bitrev10(k), p);
+      const uint32_t qf = static_cast<uint32_t>((wf << 32) / p), qg = static_cast<uint32_t>((wg << 32) / p);
+      if (i == 0) {
+        f[k].x = static_cast<uint32_t>(wf), f[k].y = qf;
+        g[k].x = static_cast<uint32_t>(wg), g[k].y = qg;
+      } else {
+        f[k].z = static_cast<uint32_t>(wf), f[k].w = qf;
+        g[k].z = static_cast<uint32_t>(wg), g[k].w = qg;
+      }
+    }
+    scale |= (powmod_u32(kN, p - 2, p) * r % p * r % p) << (32 * i);
+  }
+  // CRT constant: (p1^-1 mod p2) R mod p2
+  if (powmod_u32(dev::kP1, dev::kP2 - 2, dev::kP2) * ((1ull << 32) % dev::kP2) % dev::kP2 != dev::kCrtC) return false;
+  out->assign(sizeof(dev::DualPrime::Tables), 0);
+  fill_tables(reinterpret_cast<dev::DualPrime::Tables*>(out->data()), f, g, scale);
   return true;
 }
 
@@ -140,8 +202,9 @@ __device__ __forceinline__ Lin gate_lin(uint32_t type) {
 
 // ------------------------------------------------------------------ kernels
 
-__device__ __forceinline__ void load_tables(NttTables& T, const NttTables* __restrict__ gtab) {
-  for (int k = threadIdx.x; k < static_cast<int>(sizeof(NttTables) / 8); k += blockDim.x)
+template <class Tab>
+__device__ __forceinline__ void load_tables(Tab& T, const void* __restrict__ gtab) {
+  for (int k = threadIdx.x; k < static_cast<int>(sizeof(Tab) / 8); k += blockDim.x)
     reinterpret_cast<uint64_t*>(&T)[k] = reinterpret_cast<const uint64_t*>(gtab)[k];
 }
 
@@ -149,10 +212,11 @@ __device__ __forceinline__ void load_tables(NttTables& T, const NttTables* __res
 // NTT of the coefficients read as integers in [0, 2^32), times 1/N, stored as
 // bkhat[i][row][k][t][c] (slot 8t + k) so that thread t of a gate group reads
 // its (k, c = 0..1) pair as one 16-byte word.
+template <class F>
 __global__ void __launch_bounds__(kGroup) bk_to_ntt_kernel(const uint32_t* __restrict__ bk,
                                                            uint64_t* __restrict__ bkhat,
-                                                           const NttTables* __restrict__ gtab) {
-  __shared__ NttTables T;
+                                                           const void* __restrict__ gtab) {
+  __shared__ typename F::Tables T;
   __shared__ uint64_t bufs[2 * kN];
   load_tables(T, gtab);
   __syncthreads();
@@ -161,12 +225,12 @@ __global__ void __launch_bounds__(kGroup) bk_to_ntt_kernel(const uint32_t* __res
   const uint32_t* src = bk + (static_cast<size_t>(i * kRows + row) * 2 + c) * kN;
   uint64_t x[8];
 #pragma unroll
-  for (int k = 0; k < 8; ++k) x[k] = src[t + 128 * k];
+  for (int k = 0; k < 8; ++k) x[k] = F::from_u32(src[t + 128 * k]);
   int parity = 0;
-  dev::ntt_forward(x, bufs, parity, T, t, 1);
+  dev::ntt_forward<F>(x, bufs, parity, T, t, 1);
   uint64_t* dst = bkhat + static_cast<size_t>(i * kRows + row) * kChunkU64;
 #pragma unroll
-  for (int k = 0; k < 8; ++k) dst[(k * kGroup + t) * 2 + c] = dev::gl_mul(x[k], T.n_inv);
+  for (int k = 0; k < 8; ++k) dst[(k * kGroup + t) * 2 + c] = F::scale_key(x[k], T.n_inv);
 }
 
 // Contiguous gate arrays -> descriptors.
@@ -183,19 +247,22 @@ __global__ void make_desc_kernel(GateDesc* __restrict__ desc, const uint8_t* __r
   desc[g] = d;
 }
 
+template <int kThreads>
 __device__ __forceinline__ void issue_chunk(uint64_t* stage_slot, const uint64_t* __restrict__ bkhat, int k) {
   const uint4* src = reinterpret_cast<const uint4*>(bkhat + static_cast<size_t>(k) * kChunkU64);
   uint4* dst = reinterpret_cast<uint4*>(stage_slot);
-  for (int q = threadIdx.x; q < kChunkBytes / 16; q += kBrThreads) cp_async16(dst + q, src + q);
+  for (int q = threadIdx.x; q < kChunkBytes / 16; q += kThreads) cp_async16(dst + q, src + q);
 }
 
 // Blind rotation + sample extraction for `count` gates (see file comment).
 // big: [count][N+1] extracted samples under the GLWE key.
-__global__ void __launch_bounds__(kBrThreads, 1)
+template <class F, int G>
+__global__ void __launch_bounds__(G * kGroup, 1)
     blind_rotate_kernel(const GateDesc* __restrict__ desc, int count, const uint64_t* __restrict__ bkhat,
-                        const NttTables* __restrict__ gtab, int n, int bg_bits, uint32_t* __restrict__ big) {
+                        const void* __restrict__ gtab, int n, int bg_bits, uint32_t* __restrict__ big) {
   extern __shared__ __align__(128) uint8_t smem[];
-  NttTables& T = *reinterpret_cast<NttTables*>(smem);
+  typename F::Tables& T = *reinterpret_cast<typename F::Tables*>(smem);
+  constexpr int kTabBytes = tab_bytes<F>();
   uint64_t* stage = reinterpret_cast<uint64_t*>(smem + kTabBytes);
   const int grp = threadIdx.x / kGroup, t = threadIdx.x % kGroup;
   const int bar = 1 + grp;  // named barrier of this gate's 128 threads
@@ -214,13 +281,14 @@ __global__ void __launch_bounds__(kBrThreads, 1)
   const uint32_t dmask = (1u << bg_bits) - 1, dhalf = 1u << (bg_bits - 1);
   const int total = n * kRows;
 
-  for (int g0 = blockIdx.x * kBrGates; g0 < count; g0 += gridDim.x * kBrGates) {
+  constexpr int kBrThreads = G * kGroup;
+  for (int g0 = blockIdx.x * G; g0 < count; g0 += gridDim.x * G) {
     const int gi = g0 + grp;
     const bool active = gi < count;
     __syncthreads();  // tables loaded; previous group finished with the stages
-    issue_chunk(stage, bkhat, 0);
+    issue_chunk<kBrThreads>(stage, bkhat, 0);
     cp_async_commit();
-    issue_chunk(stage + kChunkU64, bkhat, 1);
+    issue_chunk<kBrThreads>(stage + kChunkU64, bkhat, 1);
     cp_async_commit();
 
     if (active) {
@@ -247,49 +315,52 @@ __global__ void __launch_bounds__(kBrThreads, 1)
     }
 
     int parity = 0;
-    uint64_t acc0[8], acc1[8];
+    typename F::Acc acc[8];
+    uint32_t diff[8];
     for (int i = 0; i < n; ++i) {
 #pragma unroll 1
       for (int r = 0; r < kRows; ++r) {
         const int k = i * kRows + r;
         cp_async_wait<1>();
         __syncthreads();  // key row k visible; everyone done with row k-1's slot and the ACC update
-        if (k + 2 < total) issue_chunk(stage + ((k + 2) % kStages) * kChunkU64, bkhat, k + 2);
+        if (k + 2 < total) issue_chunk<kBrThreads>(stage + ((k + 2) % kStages) * kChunkU64, bkhat, k + 2);
         cp_async_commit();
         if (active) {
-          const uint32_t a_i = abar[i];
-          const uint32_t* P = acc_poly + (r / kL) * kN;
+          // X^a ACC_u - ACC_u, formed once per polynomial u and reused by its l gadget levels
+          if (r % kL == 0) {
+            const uint32_t a_i = abar[i];
+            const uint32_t* P = acc_poly + (r / kL) * kN;
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+              const uint32_t c = t + 128 * q;
+              const uint32_t idx = (c - a_i) & (2 * kN - 1);  // (X^a P)_c = +-P[idx mod N]
+              const uint32_t rot = idx < static_cast<uint32_t>(kN) ? P[idx] : 0u - P[idx - kN];
+              diff[q] = rot - P[c] + off;
+            }
+          }
           const int shift = 32 - bg_bits * (r % kL + 1);
           uint64_t x[8];
 #pragma unroll
-          for (int q = 0; q < 8; ++q) {
-            const uint32_t c = t + 128 * q;
-            const uint32_t idx = (c - a_i) & (2 * kN - 1);  // (X^a P)_c = +-P[idx mod N]
-            const uint32_t rot = idx < static_cast<uint32_t>(kN) ? P[idx] : 0u - P[idx - kN];
-            const uint32_t y = rot - P[c] + off;
-            x[q] = dev::gl_from_int(static_cast<int32_t>((y >> shift) & dmask) - static_cast<int32_t>(dhalf));
-          }
-          dev::ntt_forward(x, xbufs, parity, T, t, bar);
+          for (int q = 0; q < 8; ++q) x[q] = F::from_digit((diff[q] >> shift) & dmask, dhalf);
+          dev::ntt_forward<F>(x, xbufs, parity, T, t, bar);
           const uint64_t* ch = stage + (k % kStages) * kChunkU64;
 #pragma unroll
           for (int q = 0; q < 8; ++q) {
             const ulonglong2 w = *reinterpret_cast<const ulonglong2*>(ch + (q * kGroup + t) * 2);
-            const uint64_t p0 = dev::gl_mul(x[q], w.x);
-            const uint64_t p1 = dev::gl_mul(x[q], w.y);
-            acc0[q] = r == 0 ? p0 : dev::gl_add(acc0[q], p0);
-            acc1[q] = r == 0 ? p1 : dev::gl_add(acc1[q], p1);
+            F::mac(acc[q], x[q], w, r == 0);
           }
         }
       }
       if (active) {
 #pragma unroll 1
         for (int c = 0; c < 2; ++c) {
-          dev::ntt_inverse(acc0, xbufs, parity, T, t, bar);
+          uint64_t x[8];
+#pragma unroll
+          for (int q = 0; q < 8; ++q) x[q] = c == 0 ? F::acc0(acc[q]) : F::acc1(acc[q]);
+          dev::ntt_inverse<F>(x, xbufs, parity, T, t, bar);
           uint32_t* Pc = acc_poly + c * kN;
 #pragma unroll
-          for (int q = 0; q < 8; ++q) Pc[t + 128 * q] += dev::gl_lift32(acc0[q]);
-#pragma unroll
-          for (int q = 0; q < 8; ++q) acc0[q] = acc1[q];
+          for (int q = 0; q < 8; ++q) Pc[t + 128 * q] += F::to_torus(x[q]);
         }
       }
     }
@@ -311,26 +382,27 @@ __global__ void __launch_bounds__(kBrThreads, 1)
 // Keyswitch N -> n (see file comment).  Rounding: a + 2^15, keep the top 16
 // bits, 8 base-4 digits most significant first; digit v at level j selects
 // key row KSK[i][j][v-1]; out = (0, .., 0, b) - sum of the selected rows.
-// Output of gate g goes to desc[g].out when desc is given, else to
-// out_contig + g*(n+1).
-__global__ void __launch_bounds__(kKsThreads)
+// Grid: (gate groups of kKsGates, column tiles of kKsCols); each thread owns
+// one output column of every gate of its group.  Output of gate g goes to
+// desc[g].out when desc is given, else to out_contig + g*(n+1).
+__global__ void __launch_bounds__(kKsCols)
     keyswitch_kernel(const uint32_t* __restrict__ big, const GateDesc* __restrict__ desc,
                      uint32_t* __restrict__ out_contig, int count, const uint32_t* __restrict__ ksk, int n) {
   __shared__ uint16_t dig[kKsGates][kN];
   const int g0 = blockIdx.x * kKsGates;
   const int ng = min(kKsGates, count - g0);
-  for (int q = threadIdx.x; q < kKsGates * kN; q += kKsThreads) {
+  for (int q = threadIdx.x; q < kKsGates * kN; q += kKsCols) {
     const int g = q / kN, i = q % kN;
     uint16_t v = 0;
     if (g < ng) v = static_cast<uint16_t>((big[static_cast<size_t>(g0 + g) * (kN + 1) + i] + (1u << 15)) >> 16);
     dig[g][i] = v;
   }
   __syncthreads();
-  uint4 acc[kKsGates];
+  const int col = blockIdx.y * kKsCols + threadIdx.x;
+  uint32_t acc[kKsGates];
 #pragma unroll
-  for (int g = 0; g < kKsGates; ++g) acc[g] = make_uint4(0, 0, 0, 0);
-  const int col = threadIdx.x * 4;
-  const uint4* base = reinterpret_cast<const uint4*>(ksk) + threadIdx.x;
+  for (int g = 0; g < kKsGates; ++g) acc[g] = 0u;
+  const uint32_t* base = ksk + col;
 #pragma unroll 1
   for (int i = 0; i < kN; ++i) {
     uint32_t dv[kKsGates];
@@ -338,41 +410,34 @@ __global__ void __launch_bounds__(kKsThreads)
     for (int g = 0; g < kKsGates; ++g) dv[g] = dig[g][i];
 #pragma unroll
     for (int j = 0; j < kKsT; ++j) {
-      const uint4* rows = base + static_cast<size_t>((i * kKsT + j) * kKsDigits) * (kKsRowWords / 4);
-      const uint4 r1 = __ldg(rows);
-      const uint4 r2 = __ldg(rows + kKsRowWords / 4);
-      const uint4 r3 = __ldg(rows + 2 * (kKsRowWords / 4));
+      const uint32_t* rows = base + static_cast<size_t>((i * kKsT + j) * kKsDigits) * kKsRowWords;
+      const uint32_t r1 = __ldg(rows), r2 = __ldg(rows + kKsRowWords), r3 = __ldg(rows + 2 * kKsRowWords);
       const int sh = 14 - 2 * j;
 #pragma unroll
       for (int g = 0; g < kKsGates; ++g) {
-        const uint32_t dgt = (dv[g] >> sh) & 3u;
-        const uint4 sel = dgt == 1 ? r1 : (dgt == 2 ? r2 : r3);
-        const uint32_t on = dgt ? 0xFFFFFFFFu : 0u;
-        acc[g].x -= sel.x & on;
-        acc[g].y -= sel.y & on;
-        acc[g].z -= sel.z & on;
-        acc[g].w -= sel.w & on;
+        const uint32_t d = (dv[g] >> sh) & 3u;
+        const uint32_t sel = d == 1 ? r1 : (d == 2 ? r2 : r3);
+        acc[g] -= d ? sel : 0u;
       }
     }
   }
+  if (col > n) return;
 #pragma unroll
   for (int g = 0; g < kKsGates; ++g) {
     if (g >= ng) break;
     uint32_t* out = desc ? desc[g0 + g].out : out_contig + static_cast<size_t>(g0 + g) * (n + 1);
-    const uint32_t body = big[static_cast<size_t>(g0 + g) * (kN + 1) + kN];
-    if (col + 0 <= n) out[col + 0] = acc[g].x + (col + 0 == n ? body : 0u);
-    if (col + 1 <= n) out[col + 1] = acc[g].y + (col + 1 == n ? body : 0u);
-    if (col + 2 <= n) out[col + 2] = acc[g].z + (col + 2 == n ? body : 0u);
-    if (col + 3 <= n) out[col + 3] = acc[g].w + (col + 3 == n ? body : 0u);
+    const uint32_t body = col == n ? big[static_cast<size_t>(g0 + g) * (kN + 1) + kN] : 0u;
+    out[col] = acc[g] + body;
   }
 }
 
 // Exact negacyclic product through the device NTT (test hook), 128 threads.
+template <class F>
 __global__ void __launch_bounds__(kGroup) ntt_mul_kernel(const int32_t* __restrict__ digits,
                                                          const uint32_t* __restrict__ poly,
                                                          uint32_t* __restrict__ out,
-                                                         const NttTables* __restrict__ gtab) {
-  __shared__ NttTables T;
+                                                         const void* __restrict__ gtab) {
+  __shared__ typename F::Tables T;
   __shared__ uint64_t bufs[2 * kN];
   load_tables(T, gtab);
   __syncthreads();
@@ -380,20 +445,24 @@ __global__ void __launch_bounds__(kGroup) ntt_mul_kernel(const int32_t* __restri
   uint64_t x[8], y[8];
 #pragma unroll
   for (int k = 0; k < 8; ++k) {
-    x[k] = dev::gl_from_int(digits[t + 128 * k]);
-    y[k] = poly[t + 128 * k];
+    x[k] = F::from_int(digits[t + 128 * k]);
+    y[k] = F::from_u32(poly[t + 128 * k]);
   }
   int parity = 0;
-  dev::ntt_forward(x, bufs, parity, T, t, 1);
-  dev::ntt_forward(y, bufs, parity, T, t, 1);
+  dev::ntt_forward<F>(x, bufs, parity, T, t, 1);
+  dev::ntt_forward<F>(y, bufs, parity, T, t, 1);
 #pragma unroll
-  for (int k = 0; k < 8; ++k) x[k] = dev::gl_mul(x[k], dev::gl_mul(y[k], T.n_inv));
-  dev::ntt_inverse(x, bufs, parity, T, t, 1);
+  for (int k = 0; k < 8; ++k) {
+    const uint64_t ys = F::scale_key(y[k], T.n_inv);
+    typename F::Acc a;
+    F::mac(a, x[k], make_ulonglong2(ys, ys), true);
+    x[k] = F::acc0(a);
+  }
+  dev::ntt_inverse<F>(x, bufs, parity, T, t, 1);
 #pragma unroll
-  for (int k = 0; k < 8; ++k) out[t + 128 * k] = dev::gl_lift32(x[k]);
+  for (int k = 0; k < 8; ++k) out[t + 128 * k] = F::to_torus(x[k]);
 }
 
-bool g_br_attr_set[64] = {};
 
 }  // namespace
 
@@ -471,20 +540,21 @@ int device_init(Ctx& c) {
     return FSQL_ERR_UNSUPPORTED;
   }
   CK(cudaSetDevice(c.device));
+  c.br_gates = c.engine == FSQL_ENGINE_GOLDILOCKS ? 4 : 2;  // measured best on B300 (overridable)
   int sms = 0;
   CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c.device));
   c.sm_count = sms;
-  if (!make_tables(&c.tables)) {
+  if (!(c.engine == FSQL_ENGINE_GOLDILOCKS ? make_tables_goldilocks(&c.tables) : make_tables_dual(&c.tables))) {
     set_error("NTT root of unity check failed");
     return FSQL_ERR_ARG;
   }
   const size_t bkhat_words = static_cast<size_t>(p.n) * kRows * kChunkU64;
   const size_t ksk_words = static_cast<size_t>(kN) * kKsT * kKsDigits * kKsRowWords;
-  CK(cudaMalloc(&c.d_tables, sizeof(NttTables)));
+  CK(cudaMalloc(&c.d_tables, c.tables.size()));
   CK(cudaMalloc(&c.d_bkhat, bkhat_words * 8));
   CK(cudaMalloc(&c.d_ksk, ksk_words * 4));
-  c.key_bytes = bkhat_words * 8 + ksk_words * 4 + sizeof(NttTables);
-  CK(cudaMemcpy(c.d_tables, &c.tables, sizeof(NttTables), cudaMemcpyHostToDevice));
+  c.key_bytes = bkhat_words * 8 + ksk_words * 4 + c.tables.size();
+  CK(cudaMemcpy(c.d_tables, c.tables.data(), c.tables.size(), cudaMemcpyHostToDevice));
 
   // keyswitching key rows padded to kKsRowWords
   std::vector<uint32_t> kp(ksk_words, 0u);
@@ -498,7 +568,10 @@ int device_init(Ctx& c) {
   cudaError_t e = cudaMemcpy(d_bk, c.bk.data(), c.bk.size() * 4, cudaMemcpyHostToDevice);
   if (e == cudaSuccess) {
     const int polys = static_cast<int>(p.n) * kRows * 2;
-    bk_to_ntt_kernel<<<polys, kGroup>>>(d_bk, c.d_bkhat, c.d_tables);
+    if (c.engine == FSQL_ENGINE_GOLDILOCKS)
+      bk_to_ntt_kernel<dev::Goldilocks><<<polys, kGroup>>>(d_bk, c.d_bkhat, c.d_tables);
+    else
+      bk_to_ntt_kernel<dev::DualPrime><<<polys, kGroup>>>(d_bk, c.d_bkhat, c.d_tables);
     e = cudaGetLastError();
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
   }
@@ -538,19 +611,47 @@ void device_free(Ctx& c) {
   c.desc_event = nullptr;
 }
 
+// Launch the blind rotation of the context's engine with G gates per CTA
+// (persistent grid of at most one CTA per SM).
+template <class F, int G>
+static cudaError_t launch_br_engine(int sm_count, const GateDesc* d_desc, size_t count, const uint64_t* bkhat,
+                                    const void* tables, int n, int bg_bits, uint32_t* d_big, cudaStream_t st) {
+  static bool attr_set[64] = {};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+  if (!attr_set[dev]) {
+    const cudaError_t e =
+        cudaFuncSetAttribute(blind_rotate_kernel<F, G>, cudaFuncAttributeMaxDynamicSharedMemorySize, br_smem<F, G>());
+    if (e != cudaSuccess) return e;
+    attr_set[dev] = true;
+  }
+  const size_t groups = (count + G - 1) / G;
+  const int grid = static_cast<int>(std::min<size_t>(groups, static_cast<size_t>(sm_count)));
+  blind_rotate_kernel<F, G><<<grid, G * kGroup, br_smem<F, G>(), st>>>(d_desc, static_cast<int>(count), bkhat, tables,
+                                                                       n, bg_bits, d_big);
+  return cudaGetLastError();
+}
+
+template <class F>
+static cudaError_t launch_br_gates(Ctx& c, const GateDesc* d_desc, size_t count, uint32_t* d_big, cudaStream_t st) {
+  const int n = static_cast<int>(c.p.n), bg = static_cast<int>(c.p.bg_bits);
+  switch (c.br_gates) {
+    case 2: return launch_br_engine<F, 2>(c.sm_count, d_desc, count, c.d_bkhat, c.d_tables, n, bg, d_big, st);
+    case 3: return launch_br_engine<F, 3>(c.sm_count, d_desc, count, c.d_bkhat, c.d_tables, n, bg, d_big, st);
+    default: return launch_br_engine<F, 4>(c.sm_count, d_desc, count, c.d_bkhat, c.d_tables, n, bg, d_big, st);
+  }
+}
+
+static cudaError_t launch_br_any(Ctx& c, const GateDesc* d_desc, size_t count, uint32_t* d_big, cudaStream_t st) {
+  if (c.engine == FSQL_ENGINE_GOLDILOCKS) return launch_br_gates<dev::Goldilocks>(c, d_desc, count, d_big, st);
+  return launch_br_gates<dev::DualPrime>(c, d_desc, count, d_big, st);
+}
+
 int launch_blind_rotate(Ctx& c, const GateDesc* d_desc, size_t count, uint32_t* d_big, void* stream) {
   if (count == 0) return FSQL_OK;
-  if (c.device < 64 && !g_br_attr_set[c.device]) {
-    CK(cudaFuncSetAttribute(blind_rotate_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kBrSmem));
-    g_br_attr_set[c.device] = true;
-  }
-  const size_t groups = (count + kBrGates - 1) / kBrGates;
-  const int grid = static_cast<int>(std::min<size_t>(groups, static_cast<size_t>(c.sm_count)));
   LaunchTimer tm(c, static_cast<cudaStream_t>(stream));
-  blind_rotate_kernel<<<grid, kBrThreads, kBrSmem, static_cast<cudaStream_t>(stream)>>>(
-      d_desc, static_cast<int>(count), c.d_bkhat, c.d_tables, static_cast<int>(c.p.n), static_cast<int>(c.p.bg_bits),
-      d_big);
-  CK(cudaGetLastError());
+  CK(launch_br_any(c, d_desc, count, d_big, static_cast<cudaStream_t>(stream)));
   tm.done(true, count);
   return FSQL_OK;
 }
@@ -558,9 +659,9 @@ int launch_blind_rotate(Ctx& c, const GateDesc* d_desc, size_t count, uint32_t* 
 int launch_keyswitch(Ctx& c, const uint32_t* d_big, const GateDesc* d_desc, uint32_t* d_out_contig, size_t count,
                      void* stream) {
   if (count == 0) return FSQL_OK;
-  const int grid = static_cast<int>((count + kKsGates - 1) / kKsGates);
+  const dim3 grid(static_cast<unsigned>((count + kKsGates - 1) / kKsGates), kKsTiles);
   LaunchTimer tm(c, static_cast<cudaStream_t>(stream));
-  keyswitch_kernel<<<grid, kKsThreads, 0, static_cast<cudaStream_t>(stream)>>>(
+  keyswitch_kernel<<<grid, kKsCols, 0, static_cast<cudaStream_t>(stream)>>>(
       d_big, d_desc, d_out_contig, static_cast<int>(count), c.d_ksk, static_cast<int>(c.p.n));
   CK(cudaGetLastError());
   tm.done(false, count);
@@ -882,8 +983,12 @@ int fsql_debug_ntt_mul(fsql_ctx* ctx, const int32_t* d_digits, const uint32_t* d
   Ctx* c = device_ctx(ctx);
   if (!c) return FSQL_ERR_ARG;
   if (!d_digits || !d_poly || !d_out) return arg_error("null device pointer");
-  fsql::ntt_mul_kernel<<<1, fsql::kGroup, 0, static_cast<cudaStream_t>(stream)>>>(d_digits, d_poly, d_out,
-                                                                                  c->d_tables);
+  if (c->engine == FSQL_ENGINE_GOLDILOCKS)
+    fsql::ntt_mul_kernel<fsql::dev::Goldilocks>
+        <<<1, fsql::kGroup, 0, static_cast<cudaStream_t>(stream)>>>(d_digits, d_poly, d_out, c->d_tables);
+  else
+    fsql::ntt_mul_kernel<fsql::dev::DualPrime>
+        <<<1, fsql::kGroup, 0, static_cast<cudaStream_t>(stream)>>>(d_digits, d_poly, d_out, c->d_tables);
   if (cudaGetLastError() != cudaSuccess) return arg_error("ntt test kernel launch failed");
   return FSQL_OK;
 }
@@ -1052,18 +1157,10 @@ int fsql_gate_batch_noalloc(fsql_ctx* ctx, const uint8_t* d_types, const uint32_
   fsql::make_desc_kernel<<<static_cast<unsigned>((count + 255) / 256), 256, 0, st>>>(
       scr.desc, d_types, d_a, d_b, d_out, static_cast<int>(count), n + 1);
   cudaError_t e = cudaGetLastError();
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(fsql::blind_rotate_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, fsql::kBrSmem);
+  if (e == cudaSuccess) e = fsql::launch_br_any(*c, scr.desc, count, scr.big, st);
   if (e == cudaSuccess) {
-    const size_t groups = (count + fsql::kBrGates - 1) / fsql::kBrGates;
-    const int grid = static_cast<int>(std::min<size_t>(groups, static_cast<size_t>(c->sm_count)));
-    fsql::blind_rotate_kernel<<<grid, fsql::kBrThreads, fsql::kBrSmem, st>>>(
-        scr.desc, static_cast<int>(count), c->d_bkhat, c->d_tables, n, static_cast<int>(c->p.bg_bits), scr.big);
-    e = cudaGetLastError();
-  }
-  if (e == cudaSuccess) {
-    const int grid = static_cast<int>((count + fsql::kKsGates - 1) / fsql::kKsGates);
-    fsql::keyswitch_kernel<<<grid, fsql::kKsThreads, 0, st>>>(scr.big, scr.desc, nullptr, static_cast<int>(count),
+    const dim3 grid(static_cast<unsigned>((count + fsql::kKsGates - 1) / fsql::kKsGates), fsql::kKsTiles);
+    fsql::keyswitch_kernel<<<grid, fsql::kKsCols, 0, st>>>(scr.big, scr.desc, nullptr, static_cast<int>(count),
                                                                c->d_ksk, n);
     e = cudaGetLastError();
   }

@@ -37,6 +37,10 @@
 namespace fsql {
 namespace dev {
 
+// ---------------------------------------------------------------------------
+// Engine 1: one 64-bit prime, p = 2^64 - 2^32 + 1 (Goldilocks).  Elements are
+// canonical in [0, p).
+// ---------------------------------------------------------------------------
 constexpr uint64_t kEps = 0xFFFFFFFFull;  // 2^64 mod p
 
 // a, b in [0, p): a + b mod p.  On carry out of 64 bits the dropped 2^64 is
@@ -75,16 +79,165 @@ __device__ __forceinline__ uint64_t gl_mul(uint64_t a, uint64_t b) {
   return r >= kP ? r - kP : r;
 }
 
-// Signed integer v (|v| < p/2) as an element of Z_p.
-__device__ __forceinline__ uint64_t gl_from_int(int32_t v) {
-  return v < 0 ? kP - static_cast<uint64_t>(-static_cast<int64_t>(v)) : static_cast<uint64_t>(v);
+struct Goldilocks {
+  static constexpr int kEngine = FSQL_ENGINE_GOLDILOCKS;
+  using Tw = uint64_t;
+  using Tables = NttTablesT<Tw>;
+  // signed integer v (|v| < p/2)
+  static __device__ __forceinline__ uint64_t from_int(int32_t v) {
+    return v < 0 ? kP - static_cast<uint64_t>(-static_cast<int64_t>(v)) : static_cast<uint64_t>(v);
+  }
+  static __device__ __forceinline__ uint64_t from_digit(uint32_t u, uint32_t half) {
+    return from_int(static_cast<int32_t>(u) - static_cast<int32_t>(half));
+  }
+  static __device__ __forceinline__ uint64_t from_u32(uint32_t v) { return v; }
+  static __device__ __forceinline__ void ct(uint64_t& lo, uint64_t& hi, uint64_t w) {
+    const uint64_t v = gl_mul(hi, w);
+    const uint64_t u = lo;
+    lo = gl_add(u, v);
+    hi = gl_sub(u, v);
+  }
+  static __device__ __forceinline__ void gs(uint64_t& lo, uint64_t& hi, uint64_t w) {
+    const uint64_t u = lo, v = hi;
+    lo = gl_add(u, v);
+    hi = gl_mul(gl_sub(u, v), w);
+  }
+  // key conversion: canonical x times the stored constant (1/N)
+  static __device__ __forceinline__ uint64_t scale_key(uint64_t x, uint64_t k) { return gl_mul(x, k); }
+  // multiply-accumulate of one gadget row into the two output polynomials
+  struct Acc {
+    uint64_t c0, c1;
+  };
+  static __device__ __forceinline__ void mac(Acc& a, uint64_t x, ulonglong2 w, bool first) {
+    const uint64_t p0 = gl_mul(x, w.x), p1 = gl_mul(x, w.y);
+    a.c0 = first ? p0 : gl_add(a.c0, p0);
+    a.c1 = first ? p1 : gl_add(a.c1, p1);
+  }
+  static __device__ __forceinline__ uint64_t acc0(const Acc& a) { return a.c0; }
+  static __device__ __forceinline__ uint64_t acc1(const Acc& a) { return a.c1; }
+  // centered lift to (-p/2, p/2), reduced mod 2^32 (p = 1 mod 2^32, so x - p = x - 1 there)
+  static __device__ __forceinline__ uint32_t to_torus(uint64_t x) {
+    return static_cast<uint32_t>(x) - (x > (kP >> 1) ? 1u : 0u);
+  }
+};
+
+// ---------------------------------------------------------------------------
+// Engine 2: two primes p1, p2 < 2^32/24 with 2048 | p - 1, the integer
+// result recovered by CRT (p1 p2 ~ 2^54.8 > 2^52.6).  An element packs the
+// two residues (low word mod p1, high word mod p2).  Residues are kept lazily
+// (not reduced below p) in the manner of Harvey ("Faster arithmetic for
+// number-theoretic transforms", 2014), with bounds chosen for these primes:
+//   forward: no reduction at all; a butterfly adds at most 2p to the bound,
+//     so from digits below 2p the 10 stages stay below 22p < 2^32;
+//   multiply-accumulate: forward outputs folded below 4p, so six products
+//     with canonical key values sum below 24 p^2 < p 2^32;
+//   inverse: residues in [0, 2p), one fold per butterfly.
+// Products by a twiddle w use Shoup's precomputed quotient
+// w' = floor(w 2^32 / p): q = hi(a w'), r = a w - q p in [0, 2p) for any
+// a < 2^32 (three integer multiply-adds, no compare).  Sums of products and
+// the CRT use signed Montgomery reduction with R = 2^32 (Seiler, 2018):
+// m = (T mod R) p^-1 mod R, r = hi(T) - hi(m p) + p in (0, 2p) for T < p R.
+// ---------------------------------------------------------------------------
+constexpr uint32_t kP1 = 178956289u, kP2 = 178948097u;         // 87381 * 2^11 + 1, 87377 * 2^11 + 1
+constexpr uint32_t kP1inv = 2207602689u, kP2inv = 3717560321u;  // p^-1 mod 2^32
+constexpr uint32_t kCrtC = 524288u;                             // (p1^-1 mod p2) * R mod p2
+constexpr uint64_t kCrtM = static_cast<uint64_t>(kP1) * kP2;
+static_assert(22ull * kP1 < (1ull << 32) && 22ull * kP2 < (1ull << 32), "forward bound 22 p < 2^32");
+static_assert(24ull * kP1 <= (1ull << 32) && 24ull * kP2 <= (1ull << 32), "multiply-accumulate bound 24 p < 2^32");
+
+__device__ __forceinline__ uint32_t mont(uint32_t a, uint32_t w, uint32_t p, uint32_t pinv) {
+  const uint32_t lo = a * w;
+  const uint32_t hi = __umulhi(a, w);
+  return hi - __umulhi(lo * pinv, p) + p;
+}
+// 64-bit sum T < p R reduced to T R^-1 mod p, in (0, 2p)
+__device__ __forceinline__ uint32_t mont64(uint64_t T, uint32_t p, uint32_t pinv) {
+  const uint32_t lo = static_cast<uint32_t>(T), hi = static_cast<uint32_t>(T >> 32);
+  return hi - __umulhi(lo * pinv, p) + p;
+}
+__device__ __forceinline__ uint32_t lo32(uint64_t x) { return static_cast<uint32_t>(x); }
+__device__ __forceinline__ uint32_t hi32(uint64_t x) { return static_cast<uint32_t>(x >> 32); }
+__device__ __forceinline__ uint64_t pack(uint32_t a, uint32_t b) { return (static_cast<uint64_t>(b) << 32) | a; }
+// x in [0, 2m) -> [0, m): unsigned min with the wrapped difference
+__device__ __forceinline__ uint32_t fold(uint32_t x, uint32_t m) { return min(x, x - m); }
+
+__device__ __forceinline__ uint32_t shoup(uint32_t a, uint32_t w, uint32_t ws, uint32_t p) {
+  const uint32_t q = __umulhi(a, ws);
+  return a * w - q * p;
 }
 
-// Centered lift of x in [0, p) to (-p/2, p/2), reduced mod 2^32.  Since
-// p = 1 mod 2^32, x - p = x - 1 mod 2^32.
-__device__ __forceinline__ uint32_t gl_lift32(uint64_t x) {
-  return static_cast<uint32_t>(x) - (x > (kP >> 1) ? 1u : 0u);
-}
+struct DualPrime {
+  static constexpr int kEngine = FSQL_ENGINE_DUAL_PRIME;
+  using Tw = uint4;  // {w mod p1, w' for p1, w mod p2, w' for p2}
+  using Tables = NttTablesT<Tw>;
+  static __device__ __forceinline__ uint64_t from_int(int32_t v) {
+    return v < 0 ? pack(kP1 + v, kP2 + v) : pack(v, v);
+  }
+  // digit u - half (u in [0, 2^bg)) as u + p - half, below 2p
+  static __device__ __forceinline__ uint64_t from_digit(uint32_t u, uint32_t half) {
+    return pack(u + (kP1 - half), u + (kP2 - half));
+  }
+  static __device__ __forceinline__ uint64_t from_u32(uint32_t v) { return pack(v % kP1, v % kP2); }
+  // forward butterfly, no reduction: both outputs grow by less than 2p
+  static __device__ __forceinline__ uint32_t ct1(uint32_t x, uint32_t& hi, uint32_t w, uint32_t ws, uint32_t p) {
+    const uint32_t t = shoup(hi, w, ws, p);
+    hi = x - t + 2 * p;
+    return x + t;
+  }
+  static __device__ __forceinline__ void ct(uint64_t& lo, uint64_t& hi, const uint4& w) {
+    uint32_t h1 = lo32(hi), h2 = hi32(hi);
+    const uint32_t l1 = ct1(lo32(lo), h1, w.x, w.y, kP1);
+    const uint32_t l2 = ct1(hi32(lo), h2, w.z, w.w, kP2);
+    lo = pack(l1, l2);
+    hi = pack(h1, h2);
+  }
+  // residues in [0, 2p) in and out
+  static __device__ __forceinline__ uint32_t gs1(uint32_t x, uint32_t& hi, uint32_t w, uint32_t ws, uint32_t p) {
+    const uint32_t y = hi;
+    hi = shoup(x - y + 2 * p, w, ws, p);
+    return fold(x + y, 2 * p);
+  }
+  static __device__ __forceinline__ void gs(uint64_t& lo, uint64_t& hi, const uint4& w) {
+    uint32_t h1 = lo32(hi), h2 = hi32(hi);
+    const uint32_t l1 = gs1(lo32(lo), h1, w.x, w.y, kP1);
+    const uint32_t l2 = gs1(hi32(lo), h2, w.z, w.w, kP2);
+    lo = pack(l1, l2);
+    hi = pack(h1, h2);
+  }
+  // key conversion: forward output (below 22p) times k = N^-1 R^2, canonical
+  static __device__ __forceinline__ uint64_t scale_key(uint64_t x, uint64_t k) {
+    const uint32_t a = fold(mont(lo32(x), lo32(k), kP1, kP1inv), kP1);
+    const uint32_t b = fold(mont(hi32(x), hi32(k), kP2, kP2inv), kP2);
+    return pack(a, b);
+  }
+  // 64-bit sums of products: forward outputs folded below 4p times canonical
+  // key values, 6 rows x 4 p^2 < p R
+  struct Acc {
+    uint64_t s10, s20, s11, s21;  // (prime, output polynomial)
+  };
+  static __device__ __forceinline__ void mac(Acc& a, uint64_t x, ulonglong2 w, bool first) {
+    const uint32_t x1 = fold(fold(fold(lo32(x), 16 * kP1), 8 * kP1), 4 * kP1);
+    const uint32_t x2 = fold(fold(fold(hi32(x), 16 * kP2), 8 * kP2), 4 * kP2);
+    a.s10 = static_cast<uint64_t>(x1) * lo32(w.x) + (first ? 0ull : a.s10);
+    a.s20 = static_cast<uint64_t>(x2) * hi32(w.x) + (first ? 0ull : a.s20);
+    a.s11 = static_cast<uint64_t>(x1) * lo32(w.y) + (first ? 0ull : a.s11);
+    a.s21 = static_cast<uint64_t>(x2) * hi32(w.y) + (first ? 0ull : a.s21);
+  }
+  static __device__ __forceinline__ uint64_t acc0(const Acc& a) {
+    return pack(mont64(a.s10, kP1, kP1inv), mont64(a.s20, kP2, kP2inv));
+  }
+  static __device__ __forceinline__ uint64_t acc1(const Acc& a) {
+    return pack(mont64(a.s11, kP1, kP1inv), mont64(a.s21, kP2, kP2inv));
+  }
+  // residues in [0, 2p) -> the integer V in (-M/2, M/2) by CRT
+  // (V = x1 + p1 ((x2 - x1) p1^-1 mod p2)), reduced mod 2^32
+  static __device__ __forceinline__ uint32_t to_torus(uint64_t x) {
+    const uint32_t x1 = fold(lo32(x), kP1), x2 = fold(hi32(x), kP2);
+    const uint32_t h = fold(mont(x2 + 2 * kP2 - x1, kCrtC, kP2, kP2inv), kP2);
+    const uint64_t v = static_cast<uint64_t>(kP1) * h + x1;
+    return static_cast<uint32_t>(v) - (v > (kCrtM >> 1) ? static_cast<uint32_t>(kCrtM) : 0u);
+  }
+};
 
 __device__ __forceinline__ void named_sync(int id) {
   asm volatile("bar.sync %0, 128;\n" ::"r"(id) : "memory");
@@ -115,92 +268,80 @@ __device__ __forceinline__ void exchange(uint64_t (&x)[8], uint64_t* bufs, int& 
   for (int k = 0; k < 8; ++k) x[k] = buf[swz(D::at(t, k))];
 }
 
-// Cooley-Tukey butterfly on registers (k, k+d) with twiddle w.
-__device__ __forceinline__ void ct(uint64_t& lo, uint64_t& hi, uint64_t w) {
-  const uint64_t v = gl_mul(hi, w);
-  const uint64_t u = lo;
-  lo = gl_add(u, v);
-  hi = gl_sub(u, v);
-}
-// Gentleman-Sande butterfly.
-__device__ __forceinline__ void gs(uint64_t& lo, uint64_t& hi, uint64_t w) {
-  const uint64_t u = lo, v = hi;
-  lo = gl_add(u, v);
-  hi = gl_mul(gl_sub(u, v), w);
-}
-
 // Forward transform: x in layout F1 -> layout F4.  bufs: this group's two
 // 1024-u64 exchange buffers; parity: which one the next exchange uses.
-__device__ __forceinline__ void ntt_forward(uint64_t (&x)[8], uint64_t* bufs, int& parity, const NttTables& T,
+template <class F>
+__device__ __forceinline__ void ntt_forward(uint64_t (&x)[8], uint64_t* bufs, int& parity, const typename F::Tables& T,
                                             int t, int bar) {
   // F1: distances 512, 256, 128 (register bits 2, 1, 0), twiddles uniform
 #pragma unroll
-  for (int k = 0; k < 4; ++k) ct(x[k], x[k + 4], T.f_small[1]);
+  for (int k = 0; k < 4; ++k) F::ct(x[k], x[k + 4], T.f_small[1]);
 #pragma unroll
   for (int k = 0; k < 8; ++k)
-    if (!(k & 2)) ct(x[k], x[k + 2], T.f_small[2 + (k >> 2)]);
+    if (!(k & 2)) F::ct(x[k], x[k + 2], T.f_small[2 + (k >> 2)]);
 #pragma unroll
-  for (int k = 0; k < 8; k += 2) ct(x[k], x[k + 1], T.f_small[4 + (k >> 1)]);
+  for (int k = 0; k < 8; k += 2) F::ct(x[k], x[k + 1], T.f_small[4 + (k >> 1)]);
   exchange<LF1, LF2>(x, bufs, parity, t, bar);
   // F2: distances 64, 32, 16
   const int h3 = t >> 4;
 #pragma unroll
-  for (int k = 0; k < 4; ++k) ct(x[k], x[k + 4], T.f_small[8 + h3]);
+  for (int k = 0; k < 4; ++k) F::ct(x[k], x[k + 4], T.f_small[8 + h3]);
 #pragma unroll
   for (int k = 0; k < 8; ++k)
-    if (!(k & 2)) ct(x[k], x[k + 2], T.f_small[16 + 2 * h3 + (k >> 2)]);
+    if (!(k & 2)) F::ct(x[k], x[k + 2], T.f_small[16 + 2 * h3 + (k >> 2)]);
 #pragma unroll
-  for (int k = 0; k < 8; k += 2) ct(x[k], x[k + 1], T.f_small[32 + 4 * h3 + (k >> 1)]);
+  for (int k = 0; k < 8; k += 2) F::ct(x[k], x[k + 1], T.f_small[32 + 4 * h3 + (k >> 1)]);
   exchange<LF2, LF3>(x, bufs, parity, t, bar);
   // F3: distances 8, 4, 2 (per-thread twiddles)
 #pragma unroll
-  for (int k = 0; k < 4; ++k) ct(x[k], x[k + 4], T.f3[0][t]);
+  for (int k = 0; k < 4; ++k) F::ct(x[k], x[k + 4], T.f3[0][t]);
 #pragma unroll
   for (int k = 0; k < 8; ++k)
-    if (!(k & 2)) ct(x[k], x[k + 2], T.f3[1 + (k >> 2)][t]);
+    if (!(k & 2)) F::ct(x[k], x[k + 2], T.f3[1 + (k >> 2)][t]);
 #pragma unroll
-  for (int k = 0; k < 8; k += 2) ct(x[k], x[k + 1], T.f3[3 + (k >> 1)][t]);
+  for (int k = 0; k < 8; k += 2) F::ct(x[k], x[k + 1], T.f3[3 + (k >> 1)][t]);
   exchange<LF3, LF4>(x, bufs, parity, t, bar);
   // F4: distance 1
 #pragma unroll
-  for (int k = 0; k < 8; k += 2) ct(x[k], x[k + 1], T.f4[k >> 1][t]);
+  for (int k = 0; k < 8; k += 2) F::ct(x[k], x[k + 1], T.f4[k >> 1][t]);
 }
 
 // Inverse transform (no 1/N): x in layout F4 -> layout F1 (natural order).
-__device__ __forceinline__ void ntt_inverse(uint64_t (&x)[8], uint64_t* bufs, int& parity, const NttTables& T,
+template <class F>
+__device__ __forceinline__ void ntt_inverse(uint64_t (&x)[8], uint64_t* bufs, int& parity, const typename F::Tables& T,
                                             int t, int bar) {
   // I1: distances 1, 2, 4 (per-thread twiddles)
 #pragma unroll
-  for (int k = 0; k < 8; k += 2) gs(x[k], x[k + 1], T.i1[k >> 1][t]);
+  for (int k = 0; k < 8; k += 2) F::gs(x[k], x[k + 1], T.i1[k >> 1][t]);
 #pragma unroll
   for (int k = 0; k < 8; ++k)
-    if (!(k & 2)) gs(x[k], x[k + 2], T.i1[4 + (k >> 2)][t]);
+    if (!(k & 2)) F::gs(x[k], x[k + 2], T.i1[4 + (k >> 2)][t]);
 #pragma unroll
-  for (int k = 0; k < 4; ++k) gs(x[k], x[k + 4], T.i1[6][t]);
+  for (int k = 0; k < 4; ++k) F::gs(x[k], x[k + 4], T.i1[6][t]);
   exchange<LF4, LI2>(x, bufs, parity, t, bar);
   // I2: distances 8, 16, 32
   const int h4 = t >> 3;
 #pragma unroll
-  for (int k = 0; k < 8; k += 2) gs(x[k], x[k + 1], T.g_small[64 + 4 * h4 + (k >> 1)]);
+  for (int k = 0; k < 8; k += 2) F::gs(x[k], x[k + 1], T.g_small[64 + 4 * h4 + (k >> 1)]);
 #pragma unroll
   for (int k = 0; k < 8; ++k)
-    if (!(k & 2)) gs(x[k], x[k + 2], T.g_small[32 + 2 * h4 + (k >> 2)]);
+    if (!(k & 2)) F::gs(x[k], x[k + 2], T.g_small[32 + 2 * h4 + (k >> 2)]);
 #pragma unroll
-  for (int k = 0; k < 4; ++k) gs(x[k], x[k + 4], T.g_small[16 + h4]);
+  for (int k = 0; k < 4; ++k) F::gs(x[k], x[k + 4], T.g_small[16 + h4]);
   exchange<LI2, LI3>(x, bufs, parity, t, bar);
   // I3: distances 64, 128, 256
   const int b9 = t >> 6;
 #pragma unroll
-  for (int k = 0; k < 8; k += 2) gs(x[k], x[k + 1], T.g_small[8 + 4 * b9 + (k >> 1)]);
+  for (int k = 0; k < 8; k += 2) F::gs(x[k], x[k + 1], T.g_small[8 + 4 * b9 + (k >> 1)]);
 #pragma unroll
   for (int k = 0; k < 8; ++k)
-    if (!(k & 2)) gs(x[k], x[k + 2], T.g_small[4 + 2 * b9 + (k >> 2)]);
+    if (!(k & 2)) F::gs(x[k], x[k + 2], T.g_small[4 + 2 * b9 + (k >> 2)]);
 #pragma unroll
-  for (int k = 0; k < 4; ++k) gs(x[k], x[k + 4], T.g_small[2 + b9]);
+  for (int k = 0; k < 4; ++k) F::gs(x[k], x[k + 4], T.g_small[2 + b9]);
   exchange<LI3, LF1>(x, bufs, parity, t, bar);
   // I4: distance 512
 #pragma unroll
-  for (int k = 0; k < 4; ++k) gs(x[k], x[k + 4], T.g_small[1]);
+  for (int k = 0; k < 4; ++k) F::gs(x[k], x[k + 4], T.g_small[1]);
 }
 
 }  // namespace dev

@@ -17,9 +17,13 @@ LIB_PATH = os.path.join(HERE, "libfhesql.so")
 FSQL_OK, FSQL_ERR_ARG, FSQL_ERR_OOM, FSQL_ERR_CUDA, FSQL_ERR_TIMEOUT, FSQL_ERR_ADMISSION, FSQL_ERR_UNSUPPORTED = range(7)
 GATES = {"NAND": 0, "AND": 1, "OR": 2, "XOR": 3, "XNOR": 4, "NOR": 5, "ANDNY": 6, "ANDYN": 7, "ORNY": 8, "ORYN": 9}
 FSQL_EQ, FSQL_LT, FSQL_RANGE = 0, 1, 2
+FSQL_ENGINE_DEFAULT, FSQL_ENGINE_GOLDILOCKS, FSQL_ENGINE_DUAL_PRIME = -1, 0, 1
+ENGINES = {"default": -1, "goldilocks": 0, "dual_prime": 1}
 
 # every symbol include/fhesql.h declares
-API = ["fsql_params_default", "fsql_params_toy", "fsql_ctx_create", "fsql_ctx_destroy", "fsql_ctx_params",
+API = ["fsql_params_default", "fsql_params_toy", "fsql_ctx_create", "fsql_ctx_create_engine", "fsql_ctx_engine",
+       "fsql_ctx_set_br_gates", "fsql_ctx_br_gates",
+       "fsql_ctx_destroy", "fsql_ctx_params",
        "fsql_ctx_device_bytes", "fsql_export_keys", "fsql_encrypt", "fsql_encrypt_bits", "fsql_encrypt_uint",
        "fsql_phase", "fsql_decrypt_bits", "fsql_decrypt_uint", "fsql_gate_batch", "fsql_blind_rotate_extract",
        "fsql_keyswitch", "fsql_debug_ntt_mul", "fsql_plan_info", "fsql_scan_select", "fsql_scan_select_host",
@@ -59,6 +63,10 @@ def load() -> C.CDLL:
         "fsql_params_default": (i32, [C.POINTER(fsql_params)]),
         "fsql_params_toy": (i32, [C.POINTER(fsql_params)]),
         "fsql_ctx_create": (i32, [C.POINTER(fsql_params), u64, i32, C.POINTER(vp)]),
+        "fsql_ctx_create_engine": (i32, [C.POINTER(fsql_params), u64, i32, i32, C.POINTER(vp)]),
+        "fsql_ctx_engine": (i32, [vp, C.POINTER(i32)]),
+        "fsql_ctx_set_br_gates": (i32, [vp, i32]),
+        "fsql_ctx_br_gates": (i32, [vp, C.POINTER(i32)]),
         "fsql_ctx_destroy": (None, [vp]),
         "fsql_ctx_params": (i32, [vp, C.POINTER(fsql_params)]),
         "fsql_ctx_device_bytes": (i32, [vp, C.POINTER(sz), C.POINTER(sz)]),
@@ -144,11 +152,15 @@ def plan_info(pred: int, width: int, n_payloads: int, payload_width: int, max_le
 class Context:
     """A seeded key set (client secrets on the host, server keys on the device)."""
 
-    def __init__(self, seed: int, params: fsql_params | None = None, device: int = 0):
+    def __init__(self, seed: int, params: fsql_params | None = None, device: int = 0, engine="default"):
         self.params = params if params is not None else params_default()
         h = C.c_void_p()
-        _check(load().fsql_ctx_create(C.byref(self.params), int(seed), int(device), C.byref(h)))
+        eng = ENGINES[engine] if isinstance(engine, str) else int(engine)
+        _check(load().fsql_ctx_create_engine(C.byref(self.params), int(seed), int(device), eng, C.byref(h)))
         self._h = h
+        e = C.c_int()
+        _check(load().fsql_ctx_engine(h, C.byref(e)))
+        self.engine = int(e.value)
         self.seed = int(seed)
         self.device = device
         self.n = int(self.params.n)
@@ -165,6 +177,16 @@ class Context:
             self.close()
         except Exception:
             pass
+
+    @property
+    def br_gates(self) -> int:
+        g = C.c_int()
+        _check(load().fsql_ctx_br_gates(self._h, C.byref(g)))
+        return int(g.value)
+
+    @br_gates.setter
+    def br_gates(self, g: int) -> None:
+        _check(load().fsql_ctx_set_br_gates(self._h, int(g)))
 
     @property
     def handle(self) -> C.c_void_p:

@@ -18,15 +18,21 @@ SEED = 2510
 
 
 @pytest.fixture(scope="module")
-def env():
+def oracle_ctx():
+    O.set_threads(os.cpu_count() or 1)
+    o = O.Oracle(SEED)
+    yield o
+    o.close()
+
+
+@pytest.fixture(scope="module", params=["dual_prime", "goldilocks"])
+def env(request, oracle_ctx):
+    """Every parity test runs on both exact NTT engines."""
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
-    O.set_threads(os.cpu_count() or 1)
-    ctx = F.Context(SEED, device=0)
-    o = O.Oracle(SEED)
-    yield ctx, o
+    ctx = F.Context(SEED, device=0, engine=request.param)
+    yield ctx, oracle_ctx
     ctx.close()
-    o.close()
 
 
 def dev(x):
