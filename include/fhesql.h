@@ -112,8 +112,10 @@ FSQL_API int fsql_ctx_create(const fsql_params* params, uint64_t seed, int devic
 FSQL_API int fsql_ctx_create_engine(const fsql_params* params, uint64_t seed, int device, int engine,
                                     fsql_ctx** out);
 FSQL_API int fsql_ctx_engine(const fsql_ctx* ctx, int* engine);
-/* Launch shape of the blind rotation: gates per CTA (2, 3 or 4; each gate
- * is 128 threads).  Results do not depend on it; fsql_autotune picks it. */
+/* Launch shape of the blind rotation for large batches: gates per CTA, each
+ * gate 128 threads (1, 2 or 4 for the Goldilocks engine, 1 or 2 for the
+ * dual-prime engine; batches under two gates per SM always use 1).  Results
+ * do not depend on it. */
 FSQL_API int fsql_ctx_set_br_gates(fsql_ctx* ctx, int gates_per_cta);
 FSQL_API int fsql_ctx_br_gates(const fsql_ctx* ctx, int* gates_per_cta);
 FSQL_API void fsql_ctx_destroy(fsql_ctx* ctx);

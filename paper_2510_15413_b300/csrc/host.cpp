@@ -289,6 +289,7 @@ int fsql_ctx_create_engine(const fsql_params* params, uint64_t seed, int device,
     c->seed = seed;
     c->device = device;
     c->engine = engine;
+    c->br_gates = engine == FSQL_ENGINE_GOLDILOCKS ? 4 : 2;
     fsql::keygen(*c);
     if (device >= 0) {
       const int rc = fsql::device_init(*c);
@@ -309,8 +310,12 @@ int fsql_ctx_create(const fsql_params* params, uint64_t seed, int device, fsql_c
 
 int fsql_ctx_set_br_gates(fsql_ctx* ctx, int gates_per_cta) {
   if (!ctx) return arg_error("null context");
-  if (gates_per_cta < 2 || gates_per_cta > 4) return arg_error("gates per CTA must be 2, 3 or 4");
-  reinterpret_cast<Ctx*>(ctx)->br_gates = gates_per_cta;
+  Ctx* c = reinterpret_cast<Ctx*>(ctx);
+  const bool ok = c->engine == FSQL_ENGINE_GOLDILOCKS
+                      ? (gates_per_cta == 1 || gates_per_cta == 2 || gates_per_cta == 4)
+                      : (gates_per_cta == 1 || gates_per_cta == 2);
+  if (!ok) return arg_error("gates per CTA: 1, 2 or 4 (Goldilocks engine), 1 or 2 (dual-prime engine)");
+  c->br_gates = gates_per_cta;
   return FSQL_OK;
 }
 

@@ -34,24 +34,29 @@ namespace fsql {
 namespace {
 
 constexpr int kGroup = 128;                      // threads per gate
-constexpr int kMaxBrGates = 4;                   // gates per CTA: 2, 3 or 4 (tuned per engine)
 constexpr int kChunkU64 = 8 * kGroup * 2;        // one key row: 1024 slots x 2 output polys
-constexpr int kChunkBytes = kChunkU64 * 8;       // 16 KB
-constexpr int kStages = 3;
-constexpr int kGateXbuf = 2 * kN * 8;            // two exchange buffers
+constexpr int kStages = 2;                       // cp.async ring of steps
 constexpr int kGateAcc = 2 * kN * 4;             // accumulator polynomials (u32)
 constexpr int kGateAbar = kMaxN * 2;             // switched mask, u16
-constexpr int kGateBytes = kGateXbuf + kGateAcc + kGateAbar + 16;
+// Polynomials per exchange buffer of the blind rotation: a step transforms
+// P gadget rows at once, the inverse transforms the two output polynomials.
+template <int P>
+__host__ __device__ constexpr int xbuf_polys() {
+  return P > 2 ? P : 2;
+}
+// Per gate: two exchange buffers, the accumulator, the switched mask.
+template <int P>
+__host__ __device__ constexpr int gate_bytes() {
+  return 2 * xbuf_polys<P>() * kN * 8 + kGateAcc + kGateAbar + 16;
+}
 template <class F>
 __host__ __device__ constexpr int tab_bytes() {
   return (sizeof(typename F::Tables) + 127) / 128 * 128;
 }
-template <class F, int G>
+template <class F, int G, int P>
 __host__ __device__ constexpr int br_smem() {
-  return tab_bytes<F>() + kStages * kChunkBytes + G * kGateBytes;
+  return tab_bytes<F>() + kStages * P * kChunkU64 * 8 + G * gate_bytes<P>();
 }
-static_assert(br_smem<dev::DualPrime, kMaxBrGates>() <= 227 * 1024, "blind-rotation shared memory over budget");
-static_assert(br_smem<dev::Goldilocks, kMaxBrGates>() <= 227 * 1024, "blind-rotation shared memory over budget");
 
 constexpr int kKsGates = 16;                     // gates per keyswitch CTA
 constexpr int kKsCols = 128;                     // output columns per keyswitch CTA
@@ -223,14 +228,14 @@ __global__ void __launch_bounds__(kGroup) bk_to_ntt_kernel(const uint32_t* __res
   const int w = blockIdx.x, t = threadIdx.x;
   const int i = w / (kRows * 2), row = (w / 2) % kRows, c = w % 2;
   const uint32_t* src = bk + (static_cast<size_t>(i * kRows + row) * 2 + c) * kN;
-  uint64_t x[8];
+  uint64_t x[1][8];
 #pragma unroll
-  for (int k = 0; k < 8; ++k) x[k] = F::from_u32(src[t + 128 * k]);
+  for (int k = 0; k < 8; ++k) x[0][k] = F::from_u32(src[t + 128 * k]);
   int parity = 0;
-  dev::ntt_forward<F>(x, bufs, parity, T, t, 1);
+  dev::ntt_forward<F, 1, 1>(x, bufs, parity, T, t, 1);
   uint64_t* dst = bkhat + static_cast<size_t>(i * kRows + row) * kChunkU64;
 #pragma unroll
-  for (int k = 0; k < 8; ++k) dst[(k * kGroup + t) * 2 + c] = F::scale_key(x[k], T.n_inv);
+  for (int k = 0; k < 8; ++k) dst[(k * kGroup + t) * 2 + c] = F::scale_key(x[0][k], T.n_inv);
 }
 
 // Contiguous gate arrays -> descriptors.
@@ -247,27 +252,35 @@ __global__ void make_desc_kernel(GateDesc* __restrict__ desc, const uint8_t* __r
   desc[g] = d;
 }
 
-template <int kThreads>
-__device__ __forceinline__ void issue_chunk(uint64_t* stage_slot, const uint64_t* __restrict__ bkhat, int k) {
-  const uint4* src = reinterpret_cast<const uint4*>(bkhat + static_cast<size_t>(k) * kChunkU64);
-  uint4* dst = reinterpret_cast<uint4*>(stage_slot);
-  for (int q = threadIdx.x; q < kChunkBytes / 16; q += kThreads) cp_async16(dst + q, src + q);
+// Stage the key rows of step k (kPolys rows, 32 KB, contiguous) into a ring slot.
+template <int kThreads, int kStepU64>
+__device__ __forceinline__ void issue_step(uint64_t* slot, const uint64_t* __restrict__ bkhat, int k) {
+  const uint4* src = reinterpret_cast<const uint4*>(bkhat + static_cast<size_t>(k) * kStepU64);
+  uint4* dst = reinterpret_cast<uint4*>(slot);
+  for (int q = threadIdx.x; q < kStepU64 * 8 / 16; q += kThreads) cp_async16(dst + q, src + q);
 }
 
 // Blind rotation + sample extraction for `count` gates (see file comment).
 // big: [count][N+1] extracted samples under the GLWE key.
-template <class F, int G>
+template <class F, int G, int kPolys>
 __global__ void __launch_bounds__(G * kGroup, 1)
     blind_rotate_kernel(const GateDesc* __restrict__ desc, int count, const uint64_t* __restrict__ bkhat,
                         const void* __restrict__ gtab, int n, int bg_bits, uint32_t* __restrict__ big) {
+  static_assert(kRows % kPolys == 0 && kPolys <= kL, "gadget rows per step must divide 2l and not exceed l");
+  constexpr int kThreads = G * kGroup;
+  constexpr int kTabBytes = tab_bytes<F>();
+  constexpr int kStepsPerCmux = kRows / kPolys;
+  constexpr int kStepU64 = kPolys * kChunkU64;
+  constexpr int kBufPolys = xbuf_polys<kPolys>();
+  constexpr int kGateXbuf = 2 * kBufPolys * kN * 8;
+  constexpr int kGateBytes = gate_bytes<kPolys>();
   extern __shared__ __align__(128) uint8_t smem[];
   typename F::Tables& T = *reinterpret_cast<typename F::Tables*>(smem);
-  constexpr int kTabBytes = tab_bytes<F>();
   uint64_t* stage = reinterpret_cast<uint64_t*>(smem + kTabBytes);
   const int grp = threadIdx.x / kGroup, t = threadIdx.x % kGroup;
   const int bar = 1 + grp;  // named barrier of this gate's 128 threads
-  uint8_t* gb = smem + kTabBytes + kStages * kChunkBytes + grp * kGateBytes;
-  uint64_t* xbufs = reinterpret_cast<uint64_t*>(gb);                         // [2][N] u64
+  uint8_t* gb = smem + kTabBytes + kStages * kStepU64 * 8 + grp * kGateBytes;
+  uint64_t* xbufs = reinterpret_cast<uint64_t*>(gb);                         // [2][kBufPolys][N] u64
   uint32_t* acc_poly = reinterpret_cast<uint32_t*>(gb + kGateXbuf);          // [2][N] u32
   uint16_t* abar = reinterpret_cast<uint16_t*>(gb + kGateXbuf + kGateAcc);   // [n]
   uint32_t* bbar_slot = reinterpret_cast<uint32_t*>(gb + kGateXbuf + kGateAcc + kGateAbar);
@@ -279,16 +292,13 @@ __global__ void __launch_bounds__(G * kGroup, 1)
   uint32_t off = 1u << (31 - bg_bits * kL);
   for (int j = 1; j <= kL; ++j) off += (1u << (bg_bits - 1)) << (32 - bg_bits * j);
   const uint32_t dmask = (1u << bg_bits) - 1, dhalf = 1u << (bg_bits - 1);
-  const int total = n * kRows;
+  const int total = n * kStepsPerCmux;
 
-  constexpr int kBrThreads = G * kGroup;
   for (int g0 = blockIdx.x * G; g0 < count; g0 += gridDim.x * G) {
     const int gi = g0 + grp;
     const bool active = gi < count;
     __syncthreads();  // tables loaded; previous group finished with the stages
-    issue_chunk<kBrThreads>(stage, bkhat, 0);
-    cp_async_commit();
-    issue_chunk<kBrThreads>(stage + kChunkU64, bkhat, 1);
+    issue_step<kThreads, kStepU64>(stage, bkhat, 0);
     cp_async_commit();
 
     if (active) {
@@ -316,52 +326,66 @@ __global__ void __launch_bounds__(G * kGroup, 1)
 
     int parity = 0;
     typename F::Acc acc[8];
-    uint32_t diff[8];
+    uint32_t diff0[8], diff1[8];
     for (int i = 0; i < n; ++i) {
 #pragma unroll 1
-      for (int r = 0; r < kRows; ++r) {
-        const int k = i * kRows + r;
-        cp_async_wait<1>();
-        __syncthreads();  // key row k visible; everyone done with row k-1's slot and the ACC update
-        if (k + 2 < total) issue_chunk<kBrThreads>(stage + ((k + 2) % kStages) * kChunkU64, bkhat, k + 2);
+      for (int s = 0; s < kStepsPerCmux; ++s) {
+        const int k = i * kStepsPerCmux + s;
+        cp_async_wait<0>();
+        __syncthreads();  // key rows of step k visible; everyone done with step k-1 and the ACC update
+        if (k + 1 < total) issue_step<kThreads, kStepU64>(stage + ((k + 1) % kStages) * kStepU64, bkhat, k + 1);
         cp_async_commit();
         if (active) {
-          // X^a ACC_u - ACC_u, formed once per polynomial u and reused by its l gadget levels
-          if (r % kL == 0) {
+          // X^a ACC_u - ACC_u, formed by the step holding row 3u and reused by
+          // the l gadget levels of polynomial u (rows 3u .. 3u+2)
+          if (s == 0 || s == kL / kPolys) {
             const uint32_t a_i = abar[i];
-            const uint32_t* P = acc_poly + (r / kL) * kN;
+            const uint32_t* P = acc_poly + (s == 0 ? 0 : kN);
 #pragma unroll
             for (int q = 0; q < 8; ++q) {
               const uint32_t c = t + 128 * q;
               const uint32_t idx = (c - a_i) & (2 * kN - 1);  // (X^a P)_c = +-P[idx mod N]
               const uint32_t rot = idx < static_cast<uint32_t>(kN) ? P[idx] : 0u - P[idx - kN];
-              diff[q] = rot - P[c] + off;
+              const uint32_t v = rot - P[c] + off;
+              if (s == 0) diff0[q] = v;
+              else diff1[q] = v;
             }
           }
-          const int shift = 32 - bg_bits * (r % kL + 1);
-          uint64_t x[8];
+          uint64_t x[kPolys][8];
 #pragma unroll
-          for (int q = 0; q < 8; ++q) x[q] = F::from_digit((diff[q] >> shift) & dmask, dhalf);
-          dev::ntt_forward<F>(x, xbufs, parity, T, t, bar);
-          const uint64_t* ch = stage + (k % kStages) * kChunkU64;
+          for (int p = 0; p < kPolys; ++p) {
+            const int row = s * kPolys + p;
+            const int shift = 32 - bg_bits * (row % kL + 1);
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+              const uint32_t v = row < kL ? diff0[q] : diff1[q];
+              x[p][q] = F::from_digit((v >> shift) & dmask, dhalf);
+            }
+          }
+          dev::ntt_forward<F, kPolys, kBufPolys>(x, xbufs, parity, T, t, bar);
+          const uint64_t* ch = stage + (k % kStages) * kStepU64;
 #pragma unroll
           for (int q = 0; q < 8; ++q) {
-            const ulonglong2 w = *reinterpret_cast<const ulonglong2*>(ch + (q * kGroup + t) * 2);
-            F::mac(acc[q], x[q], w, r == 0);
+#pragma unroll
+            for (int p = 0; p < kPolys; ++p) {
+              const ulonglong2 w = *reinterpret_cast<const ulonglong2*>(ch + p * kChunkU64 + (q * kGroup + t) * 2);
+              F::mac(acc[q], x[p][q], w, s == 0 && p == 0);
+            }
           }
         }
       }
       if (active) {
-#pragma unroll 1
-        for (int c = 0; c < 2; ++c) {
-          uint64_t x[8];
+        uint64_t y[2][8];
 #pragma unroll
-          for (int q = 0; q < 8; ++q) x[q] = c == 0 ? F::acc0(acc[q]) : F::acc1(acc[q]);
-          dev::ntt_inverse<F>(x, xbufs, parity, T, t, bar);
-          uint32_t* Pc = acc_poly + c * kN;
-#pragma unroll
-          for (int q = 0; q < 8; ++q) Pc[t + 128 * q] += F::to_torus(x[q]);
+        for (int q = 0; q < 8; ++q) {
+          y[0][q] = F::acc0(acc[q]);
+          y[1][q] = F::acc1(acc[q]);
         }
+        dev::ntt_inverse<F, 2, kBufPolys>(y, xbufs, parity, T, t, bar);
+#pragma unroll
+        for (int c = 0; c < 2; ++c)
+#pragma unroll
+          for (int q = 0; q < 8; ++q) acc_poly[c * kN + t + 128 * q] += F::to_torus(y[c][q]);
       }
     }
 
@@ -442,27 +466,26 @@ __global__ void __launch_bounds__(kGroup) ntt_mul_kernel(const int32_t* __restri
   load_tables(T, gtab);
   __syncthreads();
   const int t = threadIdx.x;
-  uint64_t x[8], y[8];
+  uint64_t x[1][8], y[1][8];
 #pragma unroll
   for (int k = 0; k < 8; ++k) {
-    x[k] = F::from_int(digits[t + 128 * k]);
-    y[k] = F::from_u32(poly[t + 128 * k]);
+    x[0][k] = F::from_int(digits[t + 128 * k]);
+    y[0][k] = F::from_u32(poly[t + 128 * k]);
   }
   int parity = 0;
-  dev::ntt_forward<F>(x, bufs, parity, T, t, 1);
-  dev::ntt_forward<F>(y, bufs, parity, T, t, 1);
+  dev::ntt_forward<F, 1, 1>(x, bufs, parity, T, t, 1);
+  dev::ntt_forward<F, 1, 1>(y, bufs, parity, T, t, 1);
 #pragma unroll
   for (int k = 0; k < 8; ++k) {
-    const uint64_t ys = F::scale_key(y[k], T.n_inv);
+    const uint64_t ys = F::scale_key(y[0][k], T.n_inv);
     typename F::Acc a;
-    F::mac(a, x[k], make_ulonglong2(ys, ys), true);
-    x[k] = F::acc0(a);
+    F::mac(a, x[0][k], make_ulonglong2(ys, ys), true);
+    x[0][k] = F::acc0(a);
   }
-  dev::ntt_inverse<F>(x, bufs, parity, T, t, 1);
+  dev::ntt_inverse<F, 1, 1>(x, bufs, parity, T, t, 1);
 #pragma unroll
-  for (int k = 0; k < 8; ++k) out[t + 128 * k] = F::to_torus(x[k]);
+  for (int k = 0; k < 8; ++k) out[t + 128 * k] = F::to_torus(x[0][k]);
 }
-
 
 }  // namespace
 
@@ -540,7 +563,7 @@ int device_init(Ctx& c) {
     return FSQL_ERR_UNSUPPORTED;
   }
   CK(cudaSetDevice(c.device));
-  c.br_gates = c.engine == FSQL_ENGINE_GOLDILOCKS ? 4 : 2;  // measured best on B300 (overridable)
+  c.br_gates = c.engine == FSQL_ENGINE_GOLDILOCKS ? 4 : 2;  // gates per CTA for large batches
   int sms = 0;
   CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c.device));
   c.sm_count = sms;
@@ -611,41 +634,49 @@ void device_free(Ctx& c) {
   c.desc_event = nullptr;
 }
 
-// Launch the blind rotation of the context's engine with G gates per CTA
+// Launch the blind rotation with G gates per CTA and P gadget rows per step
 // (persistent grid of at most one CTA per SM).
-template <class F, int G>
+template <class F, int G, int P>
 static cudaError_t launch_br_engine(int sm_count, const GateDesc* d_desc, size_t count, const uint64_t* bkhat,
                                     const void* tables, int n, int bg_bits, uint32_t* d_big, cudaStream_t st) {
+  static_assert(br_smem<F, G, P>() <= 227 * 1024, "blind-rotation shared memory over budget");
   static bool attr_set[64] = {};
   int dev = 0;
   cudaGetDevice(&dev);
   if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
   if (!attr_set[dev]) {
-    const cudaError_t e =
-        cudaFuncSetAttribute(blind_rotate_kernel<F, G>, cudaFuncAttributeMaxDynamicSharedMemorySize, br_smem<F, G>());
+    const cudaError_t e = cudaFuncSetAttribute(blind_rotate_kernel<F, G, P>,
+                                               cudaFuncAttributeMaxDynamicSharedMemorySize, br_smem<F, G, P>());
     if (e != cudaSuccess) return e;
     attr_set[dev] = true;
   }
   const size_t groups = (count + G - 1) / G;
   const int grid = static_cast<int>(std::min<size_t>(groups, static_cast<size_t>(sm_count)));
-  blind_rotate_kernel<F, G><<<grid, G * kGroup, br_smem<F, G>(), st>>>(d_desc, static_cast<int>(count), bkhat, tables,
-                                                                       n, bg_bits, d_big);
+  blind_rotate_kernel<F, G, P><<<grid, G * kGroup, br_smem<F, G, P>(), st>>>(
+      d_desc, static_cast<int>(count), bkhat, tables, n, bg_bits, d_big);
   return cudaGetLastError();
 }
 
-template <class F>
-static cudaError_t launch_br_gates(Ctx& c, const GateDesc* d_desc, size_t count, uint32_t* d_big, cudaStream_t st) {
-  const int n = static_cast<int>(c.p.n), bg = static_cast<int>(c.p.bg_bits);
-  switch (c.br_gates) {
-    case 2: return launch_br_engine<F, 2>(c.sm_count, d_desc, count, c.d_bkhat, c.d_tables, n, bg, d_big, st);
-    case 3: return launch_br_engine<F, 3>(c.sm_count, d_desc, count, c.d_bkhat, c.d_tables, n, bg, d_big, st);
-    default: return launch_br_engine<F, 4>(c.sm_count, d_desc, count, c.d_bkhat, c.d_tables, n, bg, d_big, st);
-  }
-}
-
+// Launch shapes measured best on B300 per engine: the 64-bit prime is ALU
+// bound and wants more resident gates (one gadget row per step, up to 4
+// gates per CTA); the two-prime engine is latency bound and wants more
+// independent work per thread (two rows per step, up to 2 gates per CTA).
+// Batches smaller than two gates per SM always use one gate per CTA.
 static cudaError_t launch_br_any(Ctx& c, const GateDesc* d_desc, size_t count, uint32_t* d_big, cudaStream_t st) {
-  if (c.engine == FSQL_ENGINE_GOLDILOCKS) return launch_br_gates<dev::Goldilocks>(c, d_desc, count, d_big, st);
-  return launch_br_gates<dev::DualPrime>(c, d_desc, count, d_big, st);
+  const int n = static_cast<int>(c.p.n), bg = static_cast<int>(c.p.bg_bits);
+  const bool small = count < static_cast<size_t>(2 * c.sm_count);
+  if (c.engine == FSQL_ENGINE_GOLDILOCKS) {
+    using F = dev::Goldilocks;
+    if (small || c.br_gates == 1)
+      return launch_br_engine<F, 1, 1>(c.sm_count, d_desc, count, c.d_bkhat, c.d_tables, n, bg, d_big, st);
+    if (c.br_gates == 2)
+      return launch_br_engine<F, 2, 1>(c.sm_count, d_desc, count, c.d_bkhat, c.d_tables, n, bg, d_big, st);
+    return launch_br_engine<F, 4, 1>(c.sm_count, d_desc, count, c.d_bkhat, c.d_tables, n, bg, d_big, st);
+  }
+  using F = dev::DualPrime;
+  if (small || c.br_gates == 1)
+    return launch_br_engine<F, 1, 2>(c.sm_count, d_desc, count, c.d_bkhat, c.d_tables, n, bg, d_big, st);
+  return launch_br_engine<F, 2, 2>(c.sm_count, d_desc, count, c.d_bkhat, c.d_tables, n, bg, d_big, st);
 }
 
 int launch_blind_rotate(Ctx& c, const GateDesc* d_desc, size_t count, uint32_t* d_big, void* stream) {

@@ -129,8 +129,8 @@ struct Goldilocks {
 // number-theoretic transforms", 2014), with bounds chosen for these primes:
 //   forward: no reduction at all; a butterfly adds at most 2p to the bound,
 //     so from digits below 2p the 10 stages stay below 22p < 2^32;
-//   multiply-accumulate: forward outputs folded below 4p, so six products
-//     with canonical key values sum below 24 p^2 < p 2^32;
+//   multiply-accumulate: six products of forward outputs (below 22p) and
+//     canonical key values summed in 64 bits (below 132 p^2), reduced once;
 //   inverse: residues in [0, 2p), one fold per butterfly.
 // Products by a twiddle w use Shoup's precomputed quotient
 // w' = floor(w 2^32 / p): q = hi(a w'), r = a w - q p in [0, 2p) for any
@@ -150,7 +150,8 @@ __device__ __forceinline__ uint32_t mont(uint32_t a, uint32_t w, uint32_t p, uin
   const uint32_t hi = __umulhi(a, w);
   return hi - __umulhi(lo * pinv, p) + p;
 }
-// 64-bit sum T < p R reduced to T R^-1 mod p, in (0, 2p)
+// 64-bit T reduced to T R^-1 mod p: hi(T) - hi(m p) + p, in (0, hi(T) + p]
+// (in (0, 2p) when T < p R)
 __device__ __forceinline__ uint32_t mont64(uint64_t T, uint32_t p, uint32_t pinv) {
   const uint32_t lo = static_cast<uint32_t>(T), hi = static_cast<uint32_t>(T >> 32);
   return hi - __umulhi(lo * pinv, p) + p;
@@ -210,24 +211,29 @@ struct DualPrime {
     const uint32_t b = fold(mont(hi32(x), hi32(k), kP2, kP2inv), kP2);
     return pack(a, b);
   }
-  // 64-bit sums of products: forward outputs folded below 4p times canonical
-  // key values, 6 rows x 4 p^2 < p R
+  // Multiply-accumulate: 64-bit sums of six products x w (x a forward
+  // output below 22p, w a canonical key value in Montgomery form), so
+  // T < 132 p^2 < 2^64.  Signed Montgomery reduction of any 64-bit T gives
+  // hi(T) - hi(m p) in (-p, hi(T)], here (-p, 5.5p); adding p and two folds
+  // bring it into [0, 2p), the input range of the inverse transform.
   struct Acc {
     uint64_t s10, s20, s11, s21;  // (prime, output polynomial)
   };
   static __device__ __forceinline__ void mac(Acc& a, uint64_t x, ulonglong2 w, bool first) {
-    const uint32_t x1 = fold(fold(fold(lo32(x), 16 * kP1), 8 * kP1), 4 * kP1);
-    const uint32_t x2 = fold(fold(fold(hi32(x), 16 * kP2), 8 * kP2), 4 * kP2);
+    const uint32_t x1 = lo32(x), x2 = hi32(x);
     a.s10 = static_cast<uint64_t>(x1) * lo32(w.x) + (first ? 0ull : a.s10);
     a.s20 = static_cast<uint64_t>(x2) * hi32(w.x) + (first ? 0ull : a.s20);
     a.s11 = static_cast<uint64_t>(x1) * lo32(w.y) + (first ? 0ull : a.s11);
     a.s21 = static_cast<uint64_t>(x2) * hi32(w.y) + (first ? 0ull : a.s21);
   }
+  static __device__ __forceinline__ uint32_t settle(uint64_t T, uint32_t p, uint32_t pinv) {
+    return fold(fold(mont64(T, p, pinv), 4 * p), 2 * p);
+  }
   static __device__ __forceinline__ uint64_t acc0(const Acc& a) {
-    return pack(mont64(a.s10, kP1, kP1inv), mont64(a.s20, kP2, kP2inv));
+    return pack(settle(a.s10, kP1, kP1inv), settle(a.s20, kP2, kP2inv));
   }
   static __device__ __forceinline__ uint64_t acc1(const Acc& a) {
-    return pack(mont64(a.s11, kP1, kP1inv), mont64(a.s21, kP2, kP2inv));
+    return pack(settle(a.s11, kP1, kP1inv), settle(a.s21, kP2, kP2inv));
   }
   // residues in [0, 2p) -> the integer V in (-M/2, M/2) by CRT
   // (V = x1 + p1 ((x2 - x1) p1^-1 mod p2)), reduced mod 2^32
@@ -253,95 +259,100 @@ struct LF4 { static __device__ __forceinline__ int at(int t, int k) { return 8 *
 struct LI2 { static __device__ __forceinline__ int at(int t, int k) { return 64 * (t >> 3) + 8 * k + (t & 7); } };
 struct LI3 { static __device__ __forceinline__ int at(int t, int k) { return 512 * (t >> 6) + 64 * k + (t & 63); } };
 
-// Move the 1024 values from layout S to layout D through one of the group's
-// two exchange buffers.  Consecutive exchanges alternate buffers, so the
+// Move the P x 1024 values of P polynomials from layout S to layout D
+// through one of the group's two exchange buffers.  Each buffer holds B >= P
+// polynomials (B is the same for every exchange of a kernel, so buffer 0 and
+// buffer 1 never overlap).  Consecutive exchanges alternate buffers, so the
 // barrier of exchange j also guarantees that every thread has finished
 // reading the buffer of exchange j-1 before exchange j+1 overwrites it.
-template <class S, class D>
-__device__ __forceinline__ void exchange(uint64_t (&x)[8], uint64_t* bufs, int& parity, int t, int bar) {
-  uint64_t* buf = bufs + (parity << 10);
+template <int P, int B, class S, class D>
+__device__ __forceinline__ void exchange(uint64_t (&x)[P][8], uint64_t* bufs, int& parity, int t, int bar) {
+  static_assert(P <= B, "exchange buffer too small");
+  uint64_t* buf = bufs + parity * (B * 1024);
   parity ^= 1;
 #pragma unroll
-  for (int k = 0; k < 8; ++k) buf[swz(S::at(t, k))] = x[k];
+  for (int p = 0; p < P; ++p)
+#pragma unroll
+    for (int k = 0; k < 8; ++k) buf[p * 1024 + swz(S::at(t, k))] = x[p][k];
   named_sync(bar);
 #pragma unroll
-  for (int k = 0; k < 8; ++k) x[k] = buf[swz(D::at(t, k))];
+  for (int p = 0; p < P; ++p)
+#pragma unroll
+    for (int k = 0; k < 8; ++k) x[p][k] = buf[p * 1024 + swz(D::at(t, k))];
 }
 
-// Forward transform: x in layout F1 -> layout F4.  bufs: this group's two
-// 1024-u64 exchange buffers; parity: which one the next exchange uses.
-template <class F>
-__device__ __forceinline__ void ntt_forward(uint64_t (&x)[8], uint64_t* bufs, int& parity, const typename F::Tables& T,
-                                            int t, int bar) {
+// One radix-2 stage on registers (k, k + d) of P polynomials, twiddle by
+// the lower register index.
+template <class F, int P, int D, class TwOf>
+__device__ __forceinline__ void ct_stage(uint64_t (&x)[P][8], TwOf tw) {
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    if (k & D) continue;
+    const typename F::Tw w = tw(k);
+#pragma unroll
+    for (int p = 0; p < P; ++p) F::ct(x[p][k], x[p][k + D], w);
+  }
+}
+template <class F, int P, int D, class TwOf>
+__device__ __forceinline__ void gs_stage(uint64_t (&x)[P][8], TwOf tw) {
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    if (k & D) continue;
+    const typename F::Tw w = tw(k);
+#pragma unroll
+    for (int p = 0; p < P; ++p) F::gs(x[p][k], x[p][k + D], w);
+  }
+}
+
+// Forward transform of P polynomials: layout F1 -> layout F4.  bufs: this
+// group's two exchange buffers of B polynomials each; parity: which one the
+// next exchange uses.
+template <class F, int P, int B>
+__device__ __forceinline__ void ntt_forward(uint64_t (&x)[P][8], uint64_t* bufs, int& parity,
+                                            const typename F::Tables& T, int t, int bar) {
   // F1: distances 512, 256, 128 (register bits 2, 1, 0), twiddles uniform
-#pragma unroll
-  for (int k = 0; k < 4; ++k) F::ct(x[k], x[k + 4], T.f_small[1]);
-#pragma unroll
-  for (int k = 0; k < 8; ++k)
-    if (!(k & 2)) F::ct(x[k], x[k + 2], T.f_small[2 + (k >> 2)]);
-#pragma unroll
-  for (int k = 0; k < 8; k += 2) F::ct(x[k], x[k + 1], T.f_small[4 + (k >> 1)]);
-  exchange<LF1, LF2>(x, bufs, parity, t, bar);
+  ct_stage<F, P, 4>(x, [&](int) { return T.f_small[1]; });
+  ct_stage<F, P, 2>(x, [&](int k) { return T.f_small[2 + (k >> 2)]; });
+  ct_stage<F, P, 1>(x, [&](int k) { return T.f_small[4 + (k >> 1)]; });
+  exchange<P, B, LF1, LF2>(x, bufs, parity, t, bar);
   // F2: distances 64, 32, 16
   const int h3 = t >> 4;
-#pragma unroll
-  for (int k = 0; k < 4; ++k) F::ct(x[k], x[k + 4], T.f_small[8 + h3]);
-#pragma unroll
-  for (int k = 0; k < 8; ++k)
-    if (!(k & 2)) F::ct(x[k], x[k + 2], T.f_small[16 + 2 * h3 + (k >> 2)]);
-#pragma unroll
-  for (int k = 0; k < 8; k += 2) F::ct(x[k], x[k + 1], T.f_small[32 + 4 * h3 + (k >> 1)]);
-  exchange<LF2, LF3>(x, bufs, parity, t, bar);
+  ct_stage<F, P, 4>(x, [&](int) { return T.f_small[8 + h3]; });
+  ct_stage<F, P, 2>(x, [&](int k) { return T.f_small[16 + 2 * h3 + (k >> 2)]; });
+  ct_stage<F, P, 1>(x, [&](int k) { return T.f_small[32 + 4 * h3 + (k >> 1)]; });
+  exchange<P, B, LF2, LF3>(x, bufs, parity, t, bar);
   // F3: distances 8, 4, 2 (per-thread twiddles)
-#pragma unroll
-  for (int k = 0; k < 4; ++k) F::ct(x[k], x[k + 4], T.f3[0][t]);
-#pragma unroll
-  for (int k = 0; k < 8; ++k)
-    if (!(k & 2)) F::ct(x[k], x[k + 2], T.f3[1 + (k >> 2)][t]);
-#pragma unroll
-  for (int k = 0; k < 8; k += 2) F::ct(x[k], x[k + 1], T.f3[3 + (k >> 1)][t]);
-  exchange<LF3, LF4>(x, bufs, parity, t, bar);
+  ct_stage<F, P, 4>(x, [&](int) { return T.f3[0][t]; });
+  ct_stage<F, P, 2>(x, [&](int k) { return T.f3[1 + (k >> 2)][t]; });
+  ct_stage<F, P, 1>(x, [&](int k) { return T.f3[3 + (k >> 1)][t]; });
+  exchange<P, B, LF3, LF4>(x, bufs, parity, t, bar);
   // F4: distance 1
-#pragma unroll
-  for (int k = 0; k < 8; k += 2) F::ct(x[k], x[k + 1], T.f4[k >> 1][t]);
+  ct_stage<F, P, 1>(x, [&](int k) { return T.f4[k >> 1][t]; });
 }
 
-// Inverse transform (no 1/N): x in layout F4 -> layout F1 (natural order).
-template <class F>
-__device__ __forceinline__ void ntt_inverse(uint64_t (&x)[8], uint64_t* bufs, int& parity, const typename F::Tables& T,
-                                            int t, int bar) {
+// Inverse transform of P polynomials (no 1/N): layout F4 -> layout F1 (natural order).
+template <class F, int P, int B>
+__device__ __forceinline__ void ntt_inverse(uint64_t (&x)[P][8], uint64_t* bufs, int& parity,
+                                            const typename F::Tables& T, int t, int bar) {
   // I1: distances 1, 2, 4 (per-thread twiddles)
-#pragma unroll
-  for (int k = 0; k < 8; k += 2) F::gs(x[k], x[k + 1], T.i1[k >> 1][t]);
-#pragma unroll
-  for (int k = 0; k < 8; ++k)
-    if (!(k & 2)) F::gs(x[k], x[k + 2], T.i1[4 + (k >> 2)][t]);
-#pragma unroll
-  for (int k = 0; k < 4; ++k) F::gs(x[k], x[k + 4], T.i1[6][t]);
-  exchange<LF4, LI2>(x, bufs, parity, t, bar);
+  gs_stage<F, P, 1>(x, [&](int k) { return T.i1[k >> 1][t]; });
+  gs_stage<F, P, 2>(x, [&](int k) { return T.i1[4 + (k >> 2)][t]; });
+  gs_stage<F, P, 4>(x, [&](int) { return T.i1[6][t]; });
+  exchange<P, B, LF4, LI2>(x, bufs, parity, t, bar);
   // I2: distances 8, 16, 32
   const int h4 = t >> 3;
-#pragma unroll
-  for (int k = 0; k < 8; k += 2) F::gs(x[k], x[k + 1], T.g_small[64 + 4 * h4 + (k >> 1)]);
-#pragma unroll
-  for (int k = 0; k < 8; ++k)
-    if (!(k & 2)) F::gs(x[k], x[k + 2], T.g_small[32 + 2 * h4 + (k >> 2)]);
-#pragma unroll
-  for (int k = 0; k < 4; ++k) F::gs(x[k], x[k + 4], T.g_small[16 + h4]);
-  exchange<LI2, LI3>(x, bufs, parity, t, bar);
+  gs_stage<F, P, 1>(x, [&](int k) { return T.g_small[64 + 4 * h4 + (k >> 1)]; });
+  gs_stage<F, P, 2>(x, [&](int k) { return T.g_small[32 + 2 * h4 + (k >> 2)]; });
+  gs_stage<F, P, 4>(x, [&](int) { return T.g_small[16 + h4]; });
+  exchange<P, B, LI2, LI3>(x, bufs, parity, t, bar);
   // I3: distances 64, 128, 256
   const int b9 = t >> 6;
-#pragma unroll
-  for (int k = 0; k < 8; k += 2) F::gs(x[k], x[k + 1], T.g_small[8 + 4 * b9 + (k >> 1)]);
-#pragma unroll
-  for (int k = 0; k < 8; ++k)
-    if (!(k & 2)) F::gs(x[k], x[k + 2], T.g_small[4 + 2 * b9 + (k >> 2)]);
-#pragma unroll
-  for (int k = 0; k < 4; ++k) F::gs(x[k], x[k + 4], T.g_small[2 + b9]);
-  exchange<LI3, LF1>(x, bufs, parity, t, bar);
+  gs_stage<F, P, 1>(x, [&](int k) { return T.g_small[8 + 4 * b9 + (k >> 1)]; });
+  gs_stage<F, P, 2>(x, [&](int k) { return T.g_small[4 + 2 * b9 + (k >> 2)]; });
+  gs_stage<F, P, 4>(x, [&](int) { return T.g_small[2 + b9]; });
+  exchange<P, B, LI3, LF1>(x, bufs, parity, t, bar);
   // I4: distance 512
-#pragma unroll
-  for (int k = 0; k < 4; ++k) F::gs(x[k], x[k + 4], T.g_small[1]);
+  gs_stage<F, P, 4>(x, [&](int) { return T.g_small[1]; });
 }
 
 }  // namespace dev
