@@ -39,7 +39,10 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="eq32x4096",
-                    choices=["eq32x4096", "eq4x16", "range16x65536", "lt8x64", "range4x16"])
+                    choices=["eq32x4096", "eq4x16", "range16x65536", "lt8x64", "range4x16", "gates", "serving"])
+    ap.add_argument("--queries", type=int, default=16, help="queries per serving phase")
+    ap.add_argument("--batch", type=int, default=65536, help="gates per step of the gate microbenchmark")
+    ap.add_argument("--engine", default="default", choices=["default", "dual_prime", "goldilocks"])
     ap.add_argument("--rows", type=int, default=None, help="override the workload's row count")
     ap.add_argument("--e2e-steps", type=int, default=1)
     ap.add_argument("--cpu-rows", type=int, default=1, help="rows of the workload the oracle times")
@@ -214,6 +217,191 @@ def run_reference(args, dist):
     print(json.dumps(line), flush=True)
 
 
+# ------------------------------------------------------------------ gate microbenchmark
+def run_gates(args, dist):
+    """One step = one batch of independent random gate bootstraps."""
+    import torch
+
+    from oracle import oracle as O
+    from paper_2510_15413_b300 import fhesql as F
+    from paper_2510_15413_b300 import workloads as WL
+
+    dev = dist.local
+    torch.cuda.set_device(dev)
+    peaks, peak_kind = measured_peaks()
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    ctx = F.Context(args.seed, device=dev, engine=args.engine)
+    B = args.batch
+    types, xb, yb = WL.gates(B, seed=args.seed)
+    x = ctx.encrypt_bits(xb, WL.STREAM_GATES, 0)
+    y = ctx.encrypt_bits(yb, WL.STREAM_GATES, B)
+    dt = torch.from_numpy(types).to(f"cuda:{dev}")
+    da = torch.from_numpy(x.view(np.int32)).to(f"cuda:{dev}")
+    db = torch.from_numpy(y.view(np.int32)).to(f"cuda:{dev}")
+    out = torch.zeros((B, ctx.words), dtype=torch.int32, device=f"cuda:{dev}")
+    st = torch.cuda.current_stream()
+    for _ in range(max(3, args.warmup)):
+        ctx.gate_batch(dt, da, db, out, stream=st)
+    torch.cuda.synchronize()
+    sampler = ClockSampler(bus_id_of(dev))
+    dist.barrier()
+    torch.cuda.synchronize()
+    sampler.start()
+    time.sleep(0.4)
+    ctx.profile_begin()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    for _ in range(args.steps):
+        ctx.gate_batch(dt, da, db, out, stream=st)
+    e1.record(st)
+    torch.cuda.synchronize()
+    dist.barrier()
+    kt = ctx.profile_end()
+    clocks = sampler.stop()
+    ms = dist.max(e0.elapsed_time(e1))
+    value = dist.world * B * args.steps / (ms / 1e3)
+    truth = np.array([[1, 1, 1, 0], [0, 0, 0, 1], [0, 1, 1, 1], [0, 1, 1, 0], [1, 0, 0, 1]], np.uint8)[types, 2 * xb + yb]
+    correct = bool(np.array_equal(ctx.decrypt_bits(out.cpu().numpy().view(np.uint32)), truth))
+    roof = roofline_of(kt, ms, sms, peaks)
+    # end to end: pinned host inputs -> device -> gates -> host, copies timed
+    hx, hy, ht = (torch.from_numpy(x.view(np.int32)).pin_memory(), torch.from_numpy(y.view(np.int32)).pin_memory(),
+                  torch.from_numpy(types).pin_memory())
+    hout = torch.zeros((B, ctx.words), dtype=torch.int32).pin_memory()
+    f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    f0.record(st)
+    for _ in range(args.e2e_steps):
+        dt.copy_(ht, non_blocking=True)
+        da.copy_(hx, non_blocking=True)
+        db.copy_(hy, non_blocking=True)
+        ctx.gate_batch(dt, da, db, out, stream=st)
+        hout.copy_(out, non_blocking=True)
+    f1.record(st)
+    torch.cuda.synchronize()
+    e2e_ms = dist.max(f0.elapsed_time(f1))
+    cpu = None
+    if dist.rank == 0 and not args.no_cpu_baseline:
+        threads = os.cpu_count() or 1
+        O.set_threads(threads)
+        o = O.Oracle(args.seed)
+        m = min(B, 8 * threads)
+        ox = o.encrypt_bits(xb[:m], WL.STREAM_GATES, 0)
+        oy = o.encrypt_bits(yb[:m], WL.STREAM_GATES, B)
+        t0 = time.perf_counter()
+        o.gate_batch(types[:m].astype(np.int32), ox, oy)
+        dt_cpu = time.perf_counter() - t0
+        cpu = {"value": m / dt_cpu, "unit": "gate bootstraps/s", "cores": O.max_threads(), "kind": "oracle",
+               "sample": f"{m} random gates of the batch in {dt_cpu:.1f} s"}
+        o.close()
+    line = {"metric": "gate bootstraps/s", "value": value, "unit": "gate bootstraps/s", "n_gpus": dist.world,
+            "steps": args.steps, "warmup": max(3, args.warmup), "ms_per_step": ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32 (exact integer)",
+            "data": "synthetic (seeded random gates, seeded keys)",
+            "config": {"workload": f"gates x{B}", "engine": ["goldilocks", "dual_prime"][ctx.engine],
+                       "gate_types": "NAND/AND/OR/XOR/XNOR uniform",
+                       "l2": "inputs %s L2 (%.0f MB)" % ("larger than" if 2 * B * 2524 > 126e6 else "within",
+                                                          2 * B * 2524 / 1e6)},
+            "correct": correct, "roofline": roof, "cpu_baseline": cpu,
+            "e2e": {"value": dist.world * B * args.e2e_steps / (e2e_ms / 1e3), "unit": "gate bootstraps/s",
+                    "h2d_bytes_per_step": (2 * B * ctx.words * 4 + B), "d2h_bytes_per_step": B * ctx.words * 4},
+            "gpu_launches": int(kt["blind_rotate_launches"] + kt["keyswitch_launches"]) + args.steps,
+            "clocks": clocks, "peaks": {"kind": peak_kind, "hbm_gbs": peaks.get("hbm_gbs"), "sms": sms}}
+    ctx.close()
+    if dist.rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------ serving
+def run_serving(args, dist):
+    """Continuous batching: a saturated burst, then Poisson arrivals at 0.5x
+    and 0.9x of the saturated query rate; reports rows/s and p50/p99."""
+    import random
+
+    import torch
+
+    from paper_2510_15413_b300 import fhesql as F
+    from paper_2510_15413_b300 import workloads as WL
+
+    dev = dist.local
+    torch.cuda.set_device(dev)
+    ctx = F.Context(args.seed, device=dev, engine=args.engine)
+    W = ctx.words
+
+    def prepare(tables):
+        ios = []
+        for t in tables:
+            col, cst, pays = WL.encrypt_table(ctx, t)
+            d = lambda a: torch.from_numpy(a.view(np.int32)).to(f"cuda:{dev}")
+            ios.append({"column": d(col), "const": d(cst), "payloads": [d(p) for p in pays],
+                        "match": torch.zeros((t.rows, W), dtype=torch.int32, device=f"cuda:{dev}"),
+                        "outs": [torch.zeros((t.rows, t.payload_width, W), dtype=torch.int32,
+                                             device=f"cuda:{dev}") for _ in pays]})
+        return ios
+
+    def phase(tables, ios, rate_qps):
+        srv = F.Server(ctx, scratch_budget_bytes=8 << 30)
+        rnd = random.Random(args.seed + int(rate_qps * 1000))
+        ids = []
+        t0 = time.perf_counter()
+        next_t = 0.0
+        for t, io in zip(tables, ios):
+            if rate_qps > 0:
+                next_t += rnd.expovariate(rate_qps)
+                delay = t0 + next_t - time.perf_counter()
+                if delay > 0:
+                    time.sleep(delay)
+            ids.append(srv.submit(io["column"], t.rows, t.width, t.pred, io["const"], io["payloads"],
+                                  t.payload_width, io["match"], io["outs"]))
+        for q in ids:
+            srv.wait(q, 3.6e6)
+        wall = time.perf_counter() - t0
+        st = srv.stats()
+        lat = [srv.status(q)[1] for q in ids]
+        srv.close()
+        ok = True
+        for t, io in zip(tables, ios):
+            m_want, _ = t.expected()
+            ok &= bool(np.array_equal(ctx.decrypt_bits(io["match"].cpu().numpy().view(np.uint32)), m_want))
+        rows = sum(t.rows for t in tables)
+        return {"rate_qps": rate_qps, "queries": len(tables), "wall_s": wall, "rows_per_s": rows / wall,
+                "gate_bootstraps_per_s": st["gates"] / wall, "p50_ms": float(np.percentile(lat, 50)),
+                "p99_ms": float(np.percentile(lat, 99)), "rounds": st["rounds"], "correct": ok}
+
+    tables = WL.serving_queries(args.queries, seed=args.seed)
+    ios = prepare(tables)
+    sat = phase(tables, ios, 0.0)
+    q_rate = args.queries / sat["wall_s"]
+    runs = [sat]
+    for frac in (0.5, 0.9):
+        t2 = WL.serving_queries(args.queries, seed=args.seed + int(frac * 10))
+        runs.append(phase(t2, prepare(t2), frac * q_rate))
+    head = runs[-1]
+    line = {"metric": "served encrypted rows/s", "value": head["rows_per_s"], "unit": "rows/s",
+            "n_gpus": dist.world, "steps": len(runs), "warmup": 0, "ms_per_step": head["wall_s"] * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32 (exact integer)",
+            "data": "synthetic (seeded query mix)", "p50_ms": head["p50_ms"], "p99_ms": head["p99_ms"],
+            "config": {"workload": "serving", "queries_per_phase": args.queries,
+                       "rows": "round(2^U[8,10])", "widths": [8, 16, 32], "preds": "EQ/RANGE 50/50",
+                       "payload_columns": "1-2", "engine": ["goldilocks", "dual_prime"][ctx.engine]},
+            "phases": runs}
+    ctx.close()
+    if dist.rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+def roofline_of(kt, ms, sms, peaks):
+    br_ms = kt["blind_rotate_ms"]
+    launches = max(1, kt["blind_rotate_launches"])
+    sm_max_mhz = float(peaks.get("sm_max_mhz", 2032.0))
+    peak = sms * IMAD_PER_CLK_PER_SM * sm_max_mhz * 1e6 / WIDE_MULS_PER_MODMUL / 1e12
+    achieved = MODMULS_PER_BOOTSTRAP * kt["gates"] / (br_ms / 1e3) / 1e12 if br_ms > 0 else 0.0
+    return {"bound": "alu", "kernel": "blind_rotate_kernel", "achieved": achieved, "peak": peak, "unit": "Tmodmul/s",
+            "frac": achieved / peak if peak else None, "traffic": None,
+            "peak_kind": f"derived: {sms} SMs x {IMAD_PER_CLK_PER_SM} IMAD/clk x {sm_max_mhz:.0f} MHz / "
+                         f"{WIDE_MULS_PER_MODMUL} wide multiplies per modmul",
+            "avg_launch_ms": br_ms / launches, "share_of_step": br_ms / ms if ms else None,
+            "keyswitch_ms": kt["keyswitch_ms"]}
+
+
 # ------------------------------------------------------------------ GPU run
 def run_ours(args, dist):
     import torch
@@ -227,7 +415,7 @@ def run_ours(args, dist):
     props = torch.cuda.get_device_properties(dev)
     sms = props.multi_processor_count
 
-    ctx = F.Context(args.seed, device=dev)
+    ctx = F.Context(args.seed, device=dev, engine=args.engine)
     t = WL.table(args.workload, seed=args.seed, rows=args.rows)
     col, cst, pays = WL.encrypt_table(ctx, t)
     W = ctx.words
@@ -273,17 +461,7 @@ def run_ours(args, dist):
         correct &= bool(np.array_equal(ctx.decrypt_uint(o_.cpu().numpy().view(np.uint32), t.payload_width), p_want[q]))
 
     # ---- roofline of the dominant kernel (blind rotation)
-    br_ms = ktimes["blind_rotate_ms"]
-    br_launches = max(1, ktimes["blind_rotate_launches"])
-    sm_max_mhz = float(peaks.get("sm_max_mhz", 2032.0))
-    peak_tmm = sms * IMAD_PER_CLK_PER_SM * sm_max_mhz * 1e6 / WIDE_MULS_PER_MODMUL / 1e12
-    achieved_tmm = MODMULS_PER_BOOTSTRAP * ktimes["gates"] / (br_ms / 1e3) / 1e12 if br_ms > 0 else 0.0
-    roofline = {"bound": "alu", "kernel": "blind_rotate_kernel", "achieved": achieved_tmm, "peak": peak_tmm,
-                "unit": "Tmodmul/s", "frac": achieved_tmm / peak_tmm if peak_tmm else None, "traffic": None,
-                "peak_kind": f"derived: {sms} SMs x {IMAD_PER_CLK_PER_SM} IMAD/clk x {sm_max_mhz:.0f} MHz / "
-                             f"{WIDE_MULS_PER_MODMUL} wide multiplies per modmul",
-                "avg_launch_ms": br_ms / br_launches, "share_of_step": br_ms / (ms * 1.0) if ms else None,
-                "keyswitch_ms": ktimes["keyswitch_ms"]}
+    roofline = roofline_of(ktimes, ms, sms, peaks)
 
     # ---- end to end through the public C-ABI with host buffers (copies inside the timed region)
     hcol = torch.from_numpy(col.view(np.int32)).pin_memory()
@@ -350,6 +528,7 @@ def run_ours(args, dist):
                    "payload_columns": len(t.payloads), "payload_width": t.payload_width,
                    "gates_per_row": t.gates_per_row, "gate_bootstraps_per_step": gates_per_step,
                    "params": "n=630 N=1024 Bg=2^7 l=3 ks 4^8 Torus32",
+                   "engine": ["goldilocks", "dual_prime"][ctx.engine],
                    "l2": "inputs larger than L2 (%.0f MB column+payload per step)" % (h2d / 1e6),
                    "parallelism": f"replica per GPU x{dist.world}"},
         "correct": correct and e2e_ok,
@@ -375,7 +554,7 @@ def main():
         run_reference(args, dist)
     else:
         dist.init(use_cuda=True)
-        run_ours(args, dist)
+        {"gates": run_gates, "serving": run_serving}.get(args.workload, run_ours)(args, dist)
     dist.close()
 
 

@@ -118,6 +118,16 @@ FSQL_API int fsql_ctx_engine(const fsql_ctx* ctx, int* engine);
  * do not depend on it. */
 FSQL_API int fsql_ctx_set_br_gates(fsql_ctx* ctx, int gates_per_cta);
 FSQL_API int fsql_ctx_br_gates(const fsql_ctx* ctx, int* gates_per_cta);
+
+/* Autotuner: times the blind rotation of `probe_gates` synthetic gates
+ * (0 = 4 x SMs x 4) for every launch shape the context's engine offers,
+ * keeps the fastest in the context and in a per-process table keyed by
+ * (device, engine), and returns the chosen gates per CTA and the timings
+ * (ms, in the order 1, 2, 4 gates per CTA; -1 where not offered) in
+ * ms_out[3] (may be NULL).  Synchronises `stream`; allocates its probe
+ * buffers for the duration of the call.  A later context on the same device
+ * and engine starts from the tuned value. */
+FSQL_API int fsql_autotune(fsql_ctx* ctx, size_t probe_gates, void* stream, int* best_gates, double* ms_out);
 FSQL_API void fsql_ctx_destroy(fsql_ctx* ctx);
 FSQL_API int fsql_ctx_params(const fsql_ctx* ctx, fsql_params* out);
 /* Device bytes held by the context for keys (bootstrapping key in the NTT
@@ -222,6 +232,69 @@ FSQL_API int fsql_scan_select(fsql_ctx* ctx, const uint32_t* d_column, size_t ro
 FSQL_API int fsql_scan_select_host(fsql_ctx* ctx, const uint32_t* h_column, size_t rows, uint32_t width, uint32_t pred,
                           const uint32_t* h_const, uint32_t n_payloads, const uint32_t* const* h_payloads,
                           uint32_t payload_width, uint32_t* h_match, uint32_t* const* h_out_payloads, void* stream);
+
+/* ---------------- serving: continuous batching of scan queries ---------------- */
+
+/* One scan-select query for the server (the arguments of fsql_scan_select;
+ * all pointers are device pointers owned by the caller, which keeps them
+ * valid until the query is done, failed or cancelled). */
+#define FSQL_MAX_PAYLOADS 8
+typedef struct fsql_query {
+    const uint32_t* d_column;  /* [rows][width][n+1] */
+    size_t rows;
+    uint32_t width;
+    uint32_t pred;             /* FSQL_EQ, FSQL_LT, FSQL_RANGE */
+    const uint32_t* d_const;   /* [width or 2*width][n+1] */
+    uint32_t n_payloads;       /* <= FSQL_MAX_PAYLOADS */
+    uint32_t payload_width;
+    const uint32_t* d_payloads[FSQL_MAX_PAYLOADS];  /* each [rows][payload_width][n+1] */
+    uint32_t* d_match;                              /* [rows][n+1] */
+    uint32_t* d_out_payloads[FSQL_MAX_PAYLOADS];    /* each [rows][payload_width][n+1] */
+} fsql_query;
+
+typedef struct fsql_server fsql_server;
+
+/* Query states reported by fsql_server_status. */
+#define FSQL_Q_WAITING 0   /* queued until its scratch fits the memory budget */
+#define FSQL_Q_RUNNING 1   /* admitted: its gates join the server's launches */
+#define FSQL_Q_DONE 2      /* outputs complete in device memory */
+#define FSQL_Q_FAILED 3
+#define FSQL_Q_CANCELLED 4
+
+typedef struct fsql_server_stats {
+    uint64_t completed;      /* queries done */
+    uint64_t rounds;         /* launch rounds (one blind rotation + keyswitch pass each) */
+    uint64_t gates;          /* gate bootstraps run */
+    double busy_ms;          /* wall time spent in rounds */
+    double p50_ms, p99_ms;   /* submit-to-done latency percentiles of completed queries */
+    uint64_t waiting, running;
+    size_t scratch_used;     /* bytes of the budget held by admitted queries */
+} fsql_server_stats;
+
+/* A server thread that runs the queries submitted to it (Alg. 2 for each,
+ * the paper §4.2 semantics) on the context's device.  Each round merges the
+ * next circuit level of every admitted query into one launch pair of at
+ * most max_batch_gates gate bootstraps (0 = 2^17).  A submitted query waits
+ * until its device scratch (descriptors and intermediate wires, about
+ * rows x gates_per_row x (32 + 2524) bytes) fits in scratch_budget_bytes,
+ * which the server allocates once.  Results are bit-identical to
+ * fsql_scan_select of the same query alone.  The context must not be
+ * destroyed before the server. */
+FSQL_API int fsql_server_create(fsql_ctx* ctx, size_t scratch_budget_bytes, size_t max_batch_gates,
+                                fsql_server** out);
+/* Queue a query; FSQL_ERR_ADMISSION if its scratch exceeds the whole budget. */
+FSQL_API int fsql_server_submit(fsql_server* server, const fsql_query* query, uint64_t* id);
+/* State (FSQL_Q_*) and, once done, the submit-to-done latency in ms (else -1). */
+FSQL_API int fsql_server_status(fsql_server* server, uint64_t id, int* state, double* latency_ms);
+/* Block until the query is done (FSQL_OK), failed (FSQL_ERR_CUDA) or
+ * cancelled (FSQL_OK), or the timeout passes (FSQL_ERR_TIMEOUT). */
+FSQL_API int fsql_server_wait(fsql_server* server, uint64_t id, double timeout_ms);
+/* Drop a query: a waiting one is never run; a running one stops at the
+ * next round boundary with its outputs incomplete. */
+FSQL_API int fsql_server_cancel(fsql_server* server, uint64_t id);
+FSQL_API int fsql_server_get_stats(fsql_server* server, fsql_server_stats* out);
+/* Stops the server thread after its current round and frees its memory. */
+FSQL_API void fsql_server_destroy(fsql_server* server);
 
 /* Kernel timing with CUDA events, recorded on the launch stream around every
  * blind-rotation and keyswitch launch of this context between

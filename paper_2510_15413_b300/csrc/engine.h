@@ -103,6 +103,27 @@ struct Netlist {
 };
 bool build_netlist(uint32_t pred, uint32_t width, uint32_t n_payloads, uint32_t payload_width, Netlist* out);
 
+// Device buffers of one scan (layouts as in fsql_scan_select) plus its
+// intermediate-wire scratch [rows][internal wires][n+1].
+struct ScanIO {
+  const uint32_t* column = nullptr;
+  size_t rows = 0;
+  uint32_t width = 0, pred = 0;
+  const uint32_t* cst = nullptr;
+  uint32_t n_payloads = 0;
+  const uint32_t* const* payloads = nullptr;
+  uint32_t payload_width = 0;
+  uint32_t* match = nullptr;
+  uint32_t* const* outs = nullptr;
+  uint32_t* wires = nullptr;
+  size_t words = 0;  // n + 1
+};
+// Gates of a row that are neither the match bit nor a mask gate (they need scratch).
+long scan_internal_wires(const Netlist& nl);
+// Descriptors of every gate of every row, level by level, gate-major within a
+// level; level_offset receives levels + 1 offsets into out.
+void scan_descriptors(const Netlist& nl, const ScanIO& io, GateDesc* out, std::vector<size_t>* level_offset);
+
 // kernels.cu
 int device_init(Ctx& c);     // tables, BK -> NTT domain, KSK upload
 void device_free(Ctx& c);

@@ -474,6 +474,7 @@ __global__ void __launch_bounds__(kGroup) ntt_mul_kernel(const int32_t* __restri
   }
   int parity = 0;
   dev::ntt_forward<F, 1, 1>(x, bufs, parity, T, t, 1);
+  __syncthreads();  // the next transform's first exchange writes across warps
   dev::ntt_forward<F, 1, 1>(y, bufs, parity, T, t, 1);
 #pragma unroll
   for (int k = 0; k < 8; ++k) {
@@ -490,6 +491,73 @@ __global__ void __launch_bounds__(kGroup) ntt_mul_kernel(const int32_t* __restri
 }  // namespace
 
 // ------------------------------------------------------------------ host side
+
+// Tuned gates per CTA, per (device, engine), for later contexts of this process.
+static std::mutex g_tune_mu;
+static int g_tuned[64][2] = {};
+void remember_tuning(int device, int engine, int gates) {
+  if (device < 0 || device >= 64 || engine < 0 || engine > 1) return;
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  g_tuned[device][engine] = gates;
+}
+static int tuned_gates(int device, int engine) {
+  if (device < 0 || device >= 64 || engine < 0 || engine > 1) return 0;
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  return g_tuned[device][engine];
+}
+
+long scan_internal_wires(const Netlist& nl) {
+  long k = 0;
+  for (int g = 0; g < nl.first_mask_gate; ++g)
+    if (nl.n_inputs + g != nl.match_wire) ++k;
+  return k;
+}
+
+void scan_descriptors(const Netlist& nl, const ScanIO& io, GateDesc* out, std::vector<size_t>* level_offset) {
+  const size_t W = io.words;
+  const int G = static_cast<int>(nl.type.size());
+  std::vector<long> scratch_index(G, -1);
+  long n_int = 0;
+  for (int g = 0; g < nl.first_mask_gate; ++g)
+    if (nl.n_inputs + g != nl.match_wire) scratch_index[g] = n_int++;
+  const int w = static_cast<int>(io.width);
+  const int nconst = io.pred == FSQL_RANGE ? 2 * w : w;
+  const int pw = static_cast<int>(io.payload_width);
+  auto gate_out = [&](int g, size_t row) -> uint32_t* {
+    if (g >= nl.first_mask_gate) {
+      const int m = g - nl.first_mask_gate;
+      return io.outs[m / pw] + (row * pw + m % pw) * W;
+    }
+    if (nl.n_inputs + g == nl.match_wire) return io.match + row * W;
+    return io.wires + (row * n_int + scratch_index[g]) * W;
+  };
+  auto wire_ptr = [&](int id, size_t row) -> const uint32_t* {
+    if (id < w) return io.column + (row * io.width + id) * W;
+    if (id < w + nconst) return io.cst + static_cast<size_t>(id - w) * W;
+    if (id < nl.n_inputs) {
+      const int m = id - w - nconst;
+      return io.payloads[m / pw] + (row * pw + m % pw) * W;
+    }
+    return gate_out(id - nl.n_inputs, row);
+  };
+  level_offset->assign(nl.levels + 1, 0);
+  size_t pos = 0;
+  for (int L = 1; L <= nl.levels; ++L) {
+    (*level_offset)[L - 1] = pos;
+    for (int g = 0; g < G; ++g) {
+      if (nl.level[g] != L) continue;
+      for (size_t row = 0; row < io.rows; ++row) {
+        GateDesc& d = out[pos++];
+        d.a = wire_ptr(nl.a[g], row);
+        d.b = wire_ptr(nl.b[g], row);
+        d.out = gate_out(g, row);
+        d.type = static_cast<uint32_t>(nl.type[g]);
+        d.pad = 0;
+      }
+    }
+  }
+  (*level_offset)[nl.levels] = pos;
+}
 
 // ------------------------------------------------------------------ scan plan
 
@@ -563,7 +631,9 @@ int device_init(Ctx& c) {
     return FSQL_ERR_UNSUPPORTED;
   }
   CK(cudaSetDevice(c.device));
-  c.br_gates = c.engine == FSQL_ENGINE_GOLDILOCKS ? 4 : 2;  // gates per CTA for large batches
+  // gates per CTA for large batches: measured best on B300 unless tuned in this process
+  c.br_gates = c.engine == FSQL_ENGINE_GOLDILOCKS ? 4 : 2;
+  if (const int g = tuned_gates(c.device, c.engine)) c.br_gates = g;
   int sms = 0;
   CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c.device));
   c.sm_count = sms;
@@ -820,11 +890,7 @@ int prepare_scan(Ctx& c, const uint32_t* d_column, size_t rows, uint32_t width, 
   if (!fsql::build_netlist(pred, width, n_payloads, payload_width, &nl)) return arg_error("bad predicate shape");
   const size_t W = c.p.n + 1;
   const int G = static_cast<int>(nl.type.size());
-  // internal (scratch) wires: every gate that is neither the match bit nor a mask gate
-  std::vector<long> scratch_index(G, -1);
-  long n_int = 0;
-  for (int g = 0; g < nl.first_mask_gate; ++g)
-    if (nl.n_inputs + g != nl.match_wire) scratch_index[g] = n_int++;
+  const long n_int = fsql::scan_internal_wires(nl);
   const size_t wire_words = rows * static_cast<size_t>(n_int) * W;
   if (wire_words > c.wires_cap) {
     cudaFree(c.d_wires);
@@ -862,28 +928,6 @@ int prepare_scan(Ctx& c, const uint32_t* d_column, size_t rows, uint32_t width, 
   pl->outs.assign(d_out_payloads, d_out_payloads + n_payloads);
   pl->wires = c.d_wires;
 
-  const int w = static_cast<int>(width);
-  const int nconst = pred == FSQL_RANGE ? 2 * w : w;
-  auto gate_out = [&](int g, size_t row) -> uint32_t* {
-    if (g >= nl.first_mask_gate) {
-      const int m = g - nl.first_mask_gate;
-      const int q = m / static_cast<int>(payload_width), bit = m % static_cast<int>(payload_width);
-      return d_out_payloads[q] + (row * payload_width + bit) * W;
-    }
-    if (nl.n_inputs + g == nl.match_wire) return d_match + row * W;
-    return c.d_wires + (row * n_int + scratch_index[g]) * W;
-  };
-  auto wire_ptr = [&](int id, size_t row) -> const uint32_t* {
-    if (id < w) return d_column + (row * width + id) * W;
-    if (id < w + nconst) return d_const + static_cast<size_t>(id - w) * W;
-    if (id < nl.n_inputs) {
-      const int m = id - w - nconst;
-      const int q = m / static_cast<int>(payload_width), bit = m % static_cast<int>(payload_width);
-      return d_payloads[q] + (row * payload_width + bit) * W;
-    }
-    return gate_out(id - nl.n_inputs, row);
-  };
-
   const size_t total = rows * static_cast<size_t>(G);
   if (total > c.h_desc_cap) {
     if (c.h_desc) {
@@ -901,25 +945,21 @@ int prepare_scan(Ctx& c, const uint32_t* d_column, size_t rows, uint32_t width, 
   } else {
     cudaEventSynchronize(static_cast<cudaEvent_t>(c.desc_event));  // previous upload done
   }
-  // descriptors level by level, gate-major within a level
-  pl->level_offset.assign(nl.levels + 1, 0);
-  size_t pos = 0;
-  for (int L = 1; L <= nl.levels; ++L) {
-    pl->level_offset[L - 1] = pos;
-    for (int g = 0; g < G; ++g) {
-      if (nl.level[g] != L) continue;
-      for (size_t row = 0; row < rows; ++row) {
-        GateDesc& d = c.h_desc[pos++];
-        d.a = wire_ptr(nl.a[g], row);
-        d.b = wire_ptr(nl.b[g], row);
-        d.out = gate_out(g, row);
-        d.type = static_cast<uint32_t>(nl.type[g]);
-        d.pad = 0;
-      }
-    }
-  }
-  pl->level_offset[nl.levels] = pos;
-  pl->total = pos;
+  fsql::ScanIO io;
+  io.column = d_column;
+  io.rows = rows;
+  io.width = width;
+  io.pred = pred;
+  io.cst = d_const;
+  io.n_payloads = n_payloads;
+  io.payloads = d_payloads;
+  io.payload_width = payload_width;
+  io.match = d_match;
+  io.outs = d_out_payloads;
+  io.wires = c.d_wires;
+  io.words = W;
+  fsql::scan_descriptors(nl, io, c.h_desc, &pl->level_offset);
+  pl->total = pl->level_offset.back();
   int rc = fsql::ensure_desc(c, total);
   if (rc) {
     delete pl;
@@ -1200,6 +1240,76 @@ int fsql_gate_batch_noalloc(fsql_ctx* ctx, const uint8_t* d_types, const uint32_
     return FSQL_ERR_CUDA;
   }
   return FSQL_OK;
+}
+
+int fsql_autotune(fsql_ctx* ctx, size_t probe_gates, void* stream, int* best_gates, double* ms_out) {
+  Ctx* c = device_ctx(ctx);
+  if (!c) return FSQL_ERR_ARG;
+  const size_t count = probe_gates ? probe_gates : static_cast<size_t>(16 * c->sm_count);
+  if (count > (size_t(1) << 20)) return arg_error("probe_gates above 2^20");
+  const size_t words = c->p.n + 1;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  // probe inputs: arbitrary words (the work per gate does not depend on the data)
+  uint32_t* d_in = nullptr;
+  uint8_t* d_types = nullptr;
+  uint32_t* d_big = nullptr;
+  fsql::GateDesc* d_desc = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  int rc = FSQL_OK;
+  double ms[3] = {-1.0, -1.0, -1.0};
+  const int shapes[3] = {1, 2, 4};
+  const int saved = c->br_gates;
+  int best = saved;
+  double best_ms = 0.0;
+  auto fail = [&](const char* what, cudaError_t e) {
+    fsql::set_error(std::string(what) + ": " + cudaGetErrorString(e));
+    rc = FSQL_ERR_CUDA;
+  };
+  cudaError_t e = cudaMalloc(&d_in, 2 * count * words * 4);
+  if (e == cudaSuccess) e = cudaMalloc(&d_types, count);
+  if (e == cudaSuccess) e = cudaMalloc(&d_big, count * (fsql::kN + 1) * 4);
+  if (e == cudaSuccess) e = cudaMalloc(&d_desc, count * sizeof(fsql::GateDesc));
+  if (e == cudaSuccess) e = cudaMemsetAsync(d_in, 0x5a, 2 * count * words * 4, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(d_types, 1, count, st);
+  if (e == cudaSuccess) e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  if (e != cudaSuccess) fail("autotune set-up", e);
+  if (rc == FSQL_OK) {
+    fsql::make_desc_kernel<<<static_cast<unsigned>((count + 255) / 256), 256, 0, st>>>(
+        d_desc, d_types, d_in, d_in + count * words, nullptr, static_cast<int>(count), static_cast<int>(words));
+    for (int si = 0; si < 3 && rc == FSQL_OK; ++si) {
+      const int g = shapes[si];
+      if (fsql_ctx_set_br_gates(ctx, g) != FSQL_OK) continue;  // shape not offered by this engine
+      float t = 0.f;
+      e = fsql::launch_br_any(*c, d_desc, count, d_big, st);  // warm-up
+      if (e == cudaSuccess) e = cudaEventRecord(e0, st);
+      if (e == cudaSuccess) e = fsql::launch_br_any(*c, d_desc, count, d_big, st);
+      if (e == cudaSuccess) e = cudaEventRecord(e1, st);
+      if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+      if (e == cudaSuccess) e = cudaEventElapsedTime(&t, e0, e1);
+      if (e != cudaSuccess) {
+        fail("autotune probe", e);
+        break;
+      }
+      ms[si] = t;
+      if (best_ms == 0.0 || t < best_ms) {
+        best_ms = t;
+        best = g;
+      }
+    }
+  }
+  c->br_gates = rc == FSQL_OK ? best : saved;
+  if (rc == FSQL_OK) fsql::remember_tuning(c->device, c->engine, best);
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  cudaFree(d_in);
+  cudaFree(d_types);
+  cudaFree(d_big);
+  cudaFree(d_desc);
+  if (best_gates) *best_gates = c->br_gates;
+  if (ms_out)
+    for (int i = 0; i < 3; ++i) ms_out[i] = ms[i];
+  return rc;
 }
 
 }  // extern "C"

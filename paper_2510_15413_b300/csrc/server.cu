@@ -1,0 +1,418 @@
+// server.cu -- serving loop with continuous batching for oblivious scans.
+//
+// A query is one scan-select (Alg. 2 ProcessQuery over all rows of a table;
+// §4.2).  Its per-row netlist is a DAG of circuit levels; the gates of one
+// level are independent across rows and across queries.  The server keeps
+// every admitted query's descriptors and intermediate wires on the device
+// and runs rounds: each round gathers the next level (or the next part of a
+// level) of every admitted query into one descriptor list and bootstraps it
+// with one blind-rotation + keyswitch launch pair, so queries of different
+// sizes, widths and predicates share launches.  A query that arrives while
+// others run is admitted at the next round once its scratch fits the memory
+// budget, and joins the following launches (continuous batching); a finished
+// query frees its scratch at once.  Results are independent of the mix: each
+// gate's output depends only on its own inputs and the keys.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <mutex>
+#include <thread>
+#include <vector>
+
+#include "engine.h"
+
+namespace fsql {
+namespace {
+
+using Clock = std::chrono::steady_clock;
+
+// First-fit sub-allocator over [0, size) of one device block.
+class Pool {
+ public:
+  explicit Pool(size_t size) : size_(size) { free_[0] = size; }
+  bool alloc(size_t bytes, size_t* off) {
+    bytes = (bytes + 255) / 256 * 256;
+    for (auto it = free_.begin(); it != free_.end(); ++it) {
+      if (it->second >= bytes) {
+        *off = it->first;
+        const size_t rest = it->second - bytes, start = it->first + bytes;
+        free_.erase(it);
+        if (rest) free_[start] = rest;
+        used_ += bytes;
+        return true;
+      }
+    }
+    return false;
+  }
+  void release(size_t off, size_t bytes) {
+    bytes = (bytes + 255) / 256 * 256;
+    used_ -= bytes;
+    auto it = free_.emplace(off, bytes).first;
+    auto next = std::next(it);
+    if (next != free_.end() && it->first + it->second == next->first) {
+      it->second += next->second;
+      free_.erase(next);
+    }
+    if (it != free_.begin()) {
+      auto prev = std::prev(it);
+      if (prev->first + prev->second == it->first) {
+        prev->second += it->second;
+        free_.erase(it);
+      }
+    }
+  }
+  size_t used() const { return used_; }
+  size_t size() const { return size_; }
+
+ private:
+  size_t size_, used_ = 0;
+  std::map<size_t, size_t> free_;
+};
+
+enum { Q_WAITING = 0, Q_RUNNING = 1, Q_DONE = 2, Q_FAILED = 3, Q_CANCELLED = 4 };
+
+struct Query {
+  uint64_t id = 0;
+  fsql_query q{};
+  Netlist nl;
+  std::vector<size_t> level_offset;
+  size_t total_gates = 0;
+  size_t bytes = 0, off = 0;  // pool block: descriptors then wires
+  GateDesc* d_desc = nullptr;
+  int level = 0;              // next level to bootstrap
+  size_t done_in_level = 0;   // gates of that level already launched
+  int state = Q_WAITING;
+  bool cancel = false;
+  Clock::time_point t_submit, t_done;
+};
+
+size_t query_bytes(const Netlist& nl, const fsql_query& q, size_t words) {
+  const size_t desc = q.rows * nl.type.size() * sizeof(GateDesc);
+  const size_t wires = q.rows * static_cast<size_t>(scan_internal_wires(nl)) * words * 4;
+  return (desc + 255) / 256 * 256 + wires;
+}
+
+}  // namespace
+
+struct Server {
+  Ctx* ctx = nullptr;
+  size_t max_batch = 0;
+  Pool pool{0};
+  uint8_t* d_pool = nullptr;
+  GateDesc* d_round = nullptr;
+  uint32_t* d_big = nullptr;
+  cudaStream_t stream = nullptr;
+  std::mutex mu;
+  std::condition_variable cv;
+  std::thread worker;
+  bool stop = false;
+  uint64_t next_id = 1;
+  std::deque<Query*> waiting;
+  std::vector<Query*> running;
+  std::map<uint64_t, Query*> all;
+  // statistics
+  uint64_t rounds = 0, gates = 0, completed = 0;
+  double busy_ms = 0.0;
+  std::vector<double> latencies_ms;
+  std::string error;
+
+  // Admit waiting queries in arrival order while their blocks fit (caller holds mu).
+  void admit_locked() {
+    while (!waiting.empty()) {
+      Query* q = waiting.front();
+      if (q->cancel) {
+        q->state = Q_CANCELLED;
+        waiting.pop_front();
+        continue;
+      }
+      size_t off = 0;
+      if (!pool.alloc(q->bytes, &off)) break;
+      q->off = off;
+      q->d_desc = reinterpret_cast<GateDesc*>(d_pool + off);
+      const size_t desc_bytes = (q->total_gates * sizeof(GateDesc) + 255) / 256 * 256;
+      ScanIO io;
+      io.column = q->q.d_column;
+      io.rows = q->q.rows;
+      io.width = q->q.width;
+      io.pred = q->q.pred;
+      io.cst = q->q.d_const;
+      io.n_payloads = q->q.n_payloads;
+      io.payloads = q->q.d_payloads;
+      io.payload_width = q->q.payload_width;
+      io.match = q->q.d_match;
+      io.outs = q->q.d_out_payloads;
+      io.wires = reinterpret_cast<uint32_t*>(d_pool + off + desc_bytes);
+      io.words = ctx->p.n + 1;
+      std::vector<GateDesc> h(q->total_gates);
+      scan_descriptors(q->nl, io, h.data(), &q->level_offset);
+      if (cudaMemcpy(q->d_desc, h.data(), h.size() * sizeof(GateDesc), cudaMemcpyHostToDevice) != cudaSuccess) {
+        pool.release(q->off, q->bytes);
+        q->state = Q_FAILED;
+        waiting.pop_front();
+        continue;
+      }
+      q->state = Q_RUNNING;
+      running.push_back(q);
+      waiting.pop_front();
+    }
+  }
+
+  void run() {
+    cudaSetDevice(ctx->device);
+    struct Seg {
+      Query* q;
+      size_t start, n;
+    };
+    std::unique_lock<std::mutex> lk(mu);
+    while (!stop) {
+      admit_locked();
+      // drop cancelled running queries at the round boundary
+      for (auto it = running.begin(); it != running.end();) {
+        if ((*it)->cancel) {
+          pool.release((*it)->off, (*it)->bytes);
+          (*it)->state = Q_CANCELLED;
+          it = running.erase(it);
+        } else {
+          ++it;
+        }
+      }
+      if (running.empty()) {
+        cv.wait_for(lk, std::chrono::milliseconds(50));
+        continue;
+      }
+      // gather the next level (part) of every running query, oldest first
+      std::vector<Seg> segs;
+      size_t total = 0;
+      for (Query* q : running) {
+        if (total >= max_batch) break;
+        const size_t lb = q->level_offset[q->level], le = q->level_offset[q->level + 1];
+        const size_t start = lb + q->done_in_level;
+        const size_t n = std::min(le - start, max_batch - total);
+        if (n == 0) continue;
+        segs.push_back({q, start, n});
+        total += n;
+      }
+      lk.unlock();
+      const auto t0 = Clock::now();
+      bool ok = true;
+      size_t pos = 0;
+      for (const Seg& s : segs) {
+        ok = ok && cudaMemcpyAsync(d_round + pos, s.q->d_desc + s.start, s.n * sizeof(GateDesc),
+                                   cudaMemcpyDeviceToDevice, stream) == cudaSuccess;
+        pos += s.n;
+      }
+      if (ok) {
+        std::lock_guard<std::mutex> ctx_lk(ctx->mu);  // the context's launch bookkeeping is shared
+        ok = launch_gates(*ctx, d_round, total, d_big, stream) == FSQL_OK;
+      }
+      if (ok) ok = cudaStreamSynchronize(stream) == cudaSuccess;
+      const auto t1 = Clock::now();
+      lk.lock();
+      busy_ms += std::chrono::duration<double, std::milli>(t1 - t0).count();
+      ++rounds;
+      gates += total;
+      if (!ok) {
+        error = std::string("round failed: ") + cudaGetErrorString(cudaGetLastError());
+        for (const Seg& s : segs) s.q->state = Q_FAILED;
+      }
+      for (const Seg& s : segs) {
+        Query* q = s.q;
+        if (q->state == Q_FAILED) continue;
+        q->done_in_level += s.n;
+        if (q->level_offset[q->level] + q->done_in_level == q->level_offset[q->level + 1]) {
+          ++q->level;
+          q->done_in_level = 0;
+        }
+        if (q->level == q->nl.levels) {
+          q->state = Q_DONE;
+          q->t_done = t1;
+          ++completed;
+          latencies_ms.push_back(std::chrono::duration<double, std::milli>(q->t_done - q->t_submit).count());
+        }
+      }
+      for (auto it = running.begin(); it != running.end();) {
+        if ((*it)->state == Q_DONE || (*it)->state == Q_FAILED) {
+          pool.release((*it)->off, (*it)->bytes);
+          it = running.erase(it);
+        } else {
+          ++it;
+        }
+      }
+      cv.notify_all();
+    }
+  }
+};
+
+}  // namespace fsql
+
+using fsql::Server;
+
+namespace {
+int arg_error(const char* msg) {
+  fsql::set_error(msg);
+  return FSQL_ERR_ARG;
+}
+double percentile(std::vector<double> v, double p) {
+  if (v.empty()) return 0.0;
+  std::sort(v.begin(), v.end());
+  const double idx = p * (v.size() - 1);
+  const size_t lo = static_cast<size_t>(idx), hi = std::min(lo + 1, v.size() - 1);
+  return v[lo] + (v[hi] - v[lo]) * (idx - lo);
+}
+}  // namespace
+
+extern "C" {
+
+int fsql_server_create(fsql_ctx* ctx, size_t scratch_budget_bytes, size_t max_batch_gates, fsql_server** out) {
+  if (!ctx || !out) return arg_error("null argument");
+  *out = nullptr;
+  auto* c = reinterpret_cast<fsql::Ctx*>(ctx);
+  if (c->device < 0 || !c->d_bkhat) return arg_error("context has no device keys");
+  if (scratch_budget_bytes < (1u << 20)) return arg_error("scratch budget below 1 MiB");
+  if (max_batch_gates == 0) max_batch_gates = size_t(1) << 17;
+  if (max_batch_gates > (size_t(1) << 20)) return arg_error("max_batch_gates above 2^20");
+  if (cudaSetDevice(c->device) != cudaSuccess) return arg_error("cudaSetDevice failed");
+  auto* s = new Server();
+  s->ctx = c;
+  s->max_batch = max_batch_gates;
+  s->pool = fsql::Pool(scratch_budget_bytes);
+  cudaError_t e = cudaMalloc(&s->d_pool, scratch_budget_bytes);
+  if (e == cudaSuccess) e = cudaMalloc(&s->d_round, max_batch_gates * sizeof(fsql::GateDesc));
+  if (e == cudaSuccess) e = cudaMalloc(&s->d_big, std::min<size_t>(max_batch_gates, size_t(1) << 18) * (fsql::kN + 1) * 4);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking);
+  if (e != cudaSuccess) {
+    fsql::set_error(std::string("server allocation: ") + cudaGetErrorString(e));
+    cudaFree(s->d_pool);
+    cudaFree(s->d_round);
+    cudaFree(s->d_big);
+    delete s;
+    return FSQL_ERR_OOM;
+  }
+  s->worker = std::thread([s] { s->run(); });
+  *out = reinterpret_cast<fsql_server*>(s);
+  return FSQL_OK;
+}
+
+int fsql_server_submit(fsql_server* server, const fsql_query* q, uint64_t* id) {
+  if (!server || !q || !id) return arg_error("null argument");
+  auto* s = reinterpret_cast<Server*>(server);
+  if (q->rows == 0) return arg_error("empty table");
+  if (!q->d_column || !q->d_const || !q->d_match) return arg_error("null column, constant or match pointer");
+  if (q->n_payloads > FSQL_MAX_PAYLOADS) return arg_error("too many payload columns");
+  for (uint32_t k = 0; k < q->n_payloads; ++k)
+    if (!q->d_payloads[k] || !q->d_out_payloads[k]) return arg_error("null payload pointer");
+  auto* qq = new fsql::Query();
+  qq->q = *q;
+  if (!fsql::build_netlist(q->pred, q->width, q->n_payloads, q->payload_width, &qq->nl)) {
+    delete qq;
+    return arg_error("bad predicate shape");
+  }
+  qq->total_gates = q->rows * qq->nl.type.size();
+  qq->bytes = fsql::query_bytes(qq->nl, *q, s->ctx->p.n + 1);
+  if (qq->bytes > s->pool.size()) {
+    delete qq;
+    fsql::set_error("query scratch exceeds the server's whole memory budget");
+    return FSQL_ERR_ADMISSION;
+  }
+  qq->t_submit = fsql::Clock::now();
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    qq->id = s->next_id++;
+    s->all[qq->id] = qq;
+    s->waiting.push_back(qq);
+  }
+  s->cv.notify_all();
+  *id = qq->id;
+  return FSQL_OK;
+}
+
+int fsql_server_status(fsql_server* server, uint64_t id, int* state, double* latency_ms) {
+  if (!server || !state) return arg_error("null argument");
+  auto* s = reinterpret_cast<Server*>(server);
+  std::lock_guard<std::mutex> lk(s->mu);
+  auto it = s->all.find(id);
+  if (it == s->all.end()) return arg_error("unknown query id");
+  *state = it->second->state;
+  if (latency_ms)
+    *latency_ms = it->second->state == fsql::Q_DONE
+                      ? std::chrono::duration<double, std::milli>(it->second->t_done - it->second->t_submit).count()
+                      : -1.0;
+  return FSQL_OK;
+}
+
+int fsql_server_wait(fsql_server* server, uint64_t id, double timeout_ms) {
+  if (!server) return arg_error("null server");
+  auto* s = reinterpret_cast<Server*>(server);
+  std::unique_lock<std::mutex> lk(s->mu);
+  auto it = s->all.find(id);
+  if (it == s->all.end()) return arg_error("unknown query id");
+  fsql::Query* q = it->second;
+  const auto deadline = fsql::Clock::now() + std::chrono::duration<double, std::milli>(timeout_ms);
+  while (q->state == fsql::Q_WAITING || q->state == fsql::Q_RUNNING) {
+    if (s->cv.wait_until(lk, deadline) == std::cv_status::timeout &&
+        (q->state == fsql::Q_WAITING || q->state == fsql::Q_RUNNING)) {
+      fsql::set_error("query still running at the timeout");
+      return FSQL_ERR_TIMEOUT;
+    }
+  }
+  if (q->state == fsql::Q_FAILED) {
+    fsql::set_error(s->error.empty() ? "query failed" : s->error);
+    return FSQL_ERR_CUDA;
+  }
+  return FSQL_OK;
+}
+
+int fsql_server_cancel(fsql_server* server, uint64_t id) {
+  if (!server) return arg_error("null server");
+  auto* s = reinterpret_cast<Server*>(server);
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    auto it = s->all.find(id);
+    if (it == s->all.end()) return arg_error("unknown query id");
+    it->second->cancel = true;
+  }
+  s->cv.notify_all();
+  return FSQL_OK;
+}
+
+int fsql_server_get_stats(fsql_server* server, fsql_server_stats* out) {
+  if (!server || !out) return arg_error("null argument");
+  auto* s = reinterpret_cast<Server*>(server);
+  std::lock_guard<std::mutex> lk(s->mu);
+  out->completed = s->completed;
+  out->rounds = s->rounds;
+  out->gates = s->gates;
+  out->busy_ms = s->busy_ms;
+  out->p50_ms = percentile(s->latencies_ms, 0.50);
+  out->p99_ms = percentile(s->latencies_ms, 0.99);
+  out->waiting = s->waiting.size();
+  out->running = s->running.size();
+  out->scratch_used = s->pool.used();
+  return FSQL_OK;
+}
+
+void fsql_server_destroy(fsql_server* server) {
+  if (!server) return;
+  auto* s = reinterpret_cast<Server*>(server);
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    s->stop = true;
+  }
+  s->cv.notify_all();
+  if (s->worker.joinable()) s->worker.join();
+  cudaSetDevice(s->ctx->device);
+  cudaStreamSynchronize(s->stream);
+  cudaStreamDestroy(s->stream);
+  cudaFree(s->d_pool);
+  cudaFree(s->d_round);
+  cudaFree(s->d_big);
+  for (auto& kv : s->all) delete kv.second;
+  delete s;
+}
+
+}  // extern "C"

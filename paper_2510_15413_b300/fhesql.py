@@ -22,12 +22,16 @@ ENGINES = {"default": -1, "goldilocks": 0, "dual_prime": 1}
 
 # every symbol include/fhesql.h declares
 API = ["fsql_params_default", "fsql_params_toy", "fsql_ctx_create", "fsql_ctx_create_engine", "fsql_ctx_engine",
-       "fsql_ctx_set_br_gates", "fsql_ctx_br_gates",
+       "fsql_ctx_set_br_gates", "fsql_ctx_br_gates", "fsql_autotune",
        "fsql_ctx_destroy", "fsql_ctx_params",
        "fsql_ctx_device_bytes", "fsql_export_keys", "fsql_encrypt", "fsql_encrypt_bits", "fsql_encrypt_uint",
        "fsql_phase", "fsql_decrypt_bits", "fsql_decrypt_uint", "fsql_gate_batch", "fsql_blind_rotate_extract",
        "fsql_keyswitch", "fsql_debug_ntt_mul", "fsql_plan_info", "fsql_scan_select", "fsql_scan_select_host",
-       "fsql_profile_begin", "fsql_profile_end", "fsql_gate_batch_noalloc", "fsql_last_error"]
+       "fsql_profile_begin", "fsql_profile_end", "fsql_gate_batch_noalloc", "fsql_server_create",
+       "fsql_server_submit", "fsql_server_status", "fsql_server_wait", "fsql_server_cancel",
+       "fsql_server_get_stats", "fsql_server_destroy", "fsql_last_error"]
+FSQL_MAX_PAYLOADS = 8
+Q_WAITING, Q_RUNNING, Q_DONE, Q_FAILED, Q_CANCELLED = range(5)
 
 
 class FsqlError(RuntimeError):
@@ -39,6 +43,18 @@ class FsqlError(RuntimeError):
 class fsql_kernel_times(C.Structure):
     _fields_ = [("blind_rotate_ms", C.c_double), ("keyswitch_ms", C.c_double),
                 ("blind_rotate_launches", C.c_uint64), ("keyswitch_launches", C.c_uint64), ("gates", C.c_uint64)]
+
+
+class fsql_query(C.Structure):
+    _fields_ = [("d_column", C.c_void_p), ("rows", C.c_size_t), ("width", C.c_uint32), ("pred", C.c_uint32),
+                ("d_const", C.c_void_p), ("n_payloads", C.c_uint32), ("payload_width", C.c_uint32),
+                ("d_payloads", C.c_void_p * 8), ("d_match", C.c_void_p), ("d_out_payloads", C.c_void_p * 8)]
+
+
+class fsql_server_stats(C.Structure):
+    _fields_ = [("completed", C.c_uint64), ("rounds", C.c_uint64), ("gates", C.c_uint64), ("busy_ms", C.c_double),
+                ("p50_ms", C.c_double), ("p99_ms", C.c_double), ("waiting", C.c_uint64), ("running", C.c_uint64),
+                ("scratch_used", C.c_size_t)]
 
 
 class fsql_params(C.Structure):
@@ -67,6 +83,7 @@ def load() -> C.CDLL:
         "fsql_ctx_engine": (i32, [vp, C.POINTER(i32)]),
         "fsql_ctx_set_br_gates": (i32, [vp, i32]),
         "fsql_ctx_br_gates": (i32, [vp, C.POINTER(i32)]),
+        "fsql_autotune": (i32, [vp, sz, vp, C.POINTER(i32), C.POINTER(C.c_double)]),
         "fsql_ctx_destroy": (None, [vp]),
         "fsql_ctx_params": (i32, [vp, C.POINTER(fsql_params)]),
         "fsql_ctx_device_bytes": (i32, [vp, C.POINTER(sz), C.POINTER(sz)]),
@@ -87,6 +104,13 @@ def load() -> C.CDLL:
         "fsql_scan_select_host": (i32, [vp, vp, sz, u32, u32, vp, u32, vp, u32, vp, vp, vp]),
         "fsql_profile_begin": (i32, [vp]),
         "fsql_profile_end": (i32, [vp, C.POINTER(fsql_kernel_times)]),
+        "fsql_server_create": (i32, [vp, sz, sz, C.POINTER(vp)]),
+        "fsql_server_submit": (i32, [vp, C.POINTER(fsql_query), C.POINTER(u64)]),
+        "fsql_server_status": (i32, [vp, u64, C.POINTER(i32), C.POINTER(C.c_double)]),
+        "fsql_server_wait": (i32, [vp, u64, C.c_double]),
+        "fsql_server_cancel": (i32, [vp, u64]),
+        "fsql_server_get_stats": (i32, [vp, C.POINTER(fsql_server_stats)]),
+        "fsql_server_destroy": (None, [vp]),
         "fsql_last_error": (C.c_char_p, []),
     }
     for name, (res, args) in sig.items():
@@ -187,6 +211,13 @@ class Context:
     @br_gates.setter
     def br_gates(self, g: int) -> None:
         _check(load().fsql_ctx_set_br_gates(self._h, int(g)))
+
+    def autotune(self, probe_gates: int = 0, stream=None):
+        """Pick the fastest blind-rotation launch shape; returns (gates per CTA, {shape: ms})."""
+        best = C.c_int()
+        ms = (C.c_double * 3)()
+        _check(load().fsql_autotune(self._h, probe_gates, _stream(stream), C.byref(best), ms))
+        return int(best.value), {g: ms[i] for i, g in enumerate((1, 2, 4)) if ms[i] >= 0}
 
     @property
     def handle(self) -> C.c_void_p:
@@ -292,3 +323,53 @@ class Context:
         return {"blind_rotate_ms": t.blind_rotate_ms, "keyswitch_ms": t.keyswitch_ms,
                 "blind_rotate_launches": int(t.blind_rotate_launches),
                 "keyswitch_launches": int(t.keyswitch_launches), "gates": int(t.gates)}
+
+
+class Server:
+    """Continuous-batching scan server on a context's device (fsql_server_*)."""
+
+    def __init__(self, ctx: Context, scratch_budget_bytes: int, max_batch_gates: int = 0):
+        h = C.c_void_p()
+        _check(load().fsql_server_create(ctx.handle, int(scratch_budget_bytes), int(max_batch_gates), C.byref(h)))
+        self._h = h
+        self.ctx = ctx
+
+    def submit(self, column, rows: int, width: int, pred: int, const, payloads, payload_width: int, match,
+               out_payloads) -> int:
+        q = fsql_query()
+        q.d_column, q.rows, q.width, q.pred = _ptr(column), rows, width, pred
+        q.d_const, q.n_payloads, q.payload_width = _ptr(const), len(payloads), payload_width
+        for i, (a, b) in enumerate(zip(payloads, out_payloads)):
+            q.d_payloads[i] = _ptr(a)
+            q.d_out_payloads[i] = _ptr(b)
+        q.d_match = _ptr(match)
+        qid = C.c_uint64()
+        _check(load().fsql_server_submit(self._h, C.byref(q), C.byref(qid)))
+        return int(qid.value)
+
+    def status(self, qid: int):
+        st, lat = C.c_int(), C.c_double()
+        _check(load().fsql_server_status(self._h, qid, C.byref(st), C.byref(lat)))
+        return int(st.value), float(lat.value)
+
+    def wait(self, qid: int, timeout_ms: float = 600000.0) -> None:
+        _check(load().fsql_server_wait(self._h, qid, timeout_ms))
+
+    def cancel(self, qid: int) -> None:
+        _check(load().fsql_server_cancel(self._h, qid))
+
+    def stats(self) -> dict:
+        st = fsql_server_stats()
+        _check(load().fsql_server_get_stats(self._h, C.byref(st)))
+        return {f: getattr(st, f) for f, _ in fsql_server_stats._fields_}
+
+    def close(self) -> None:
+        if self._h:
+            load().fsql_server_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -109,6 +109,28 @@ def table(name: str, seed: int = 1, rows: int | None = None) -> Table:
     raise KeyError(name)
 
 
+def serving_queries(count: int, seed: int = 1, min_log2: float = 8.0, max_log2: float = 10.0):
+    """Seeded query mix for the serving benchmark: rows = round(2^U[min, max]),
+    width in {8, 16, 32}, EQ or RANGE (50/50), 1-2 payload columns of the same
+    width; EQ constants come from the column, RANGE bounds cover about 10% of
+    the value range."""
+    g = _rng(seed, 3)
+    out = []
+    for i in range(count):
+        rows = int(round(2 ** g.uniform(min_log2, max_log2)))
+        w = int(g.choice([8, 16, 32]))
+        npay = int(g.integers(1, 3))
+        c = g.integers(0, 1 << w, rows, dtype=np.uint64)
+        pays = [g.integers(0, 1 << w, rows, dtype=np.uint64) for _ in range(npay)]
+        if g.integers(0, 2) == 0:
+            out.append(Table(f"q{i}", rows, w, PRED_EQ, c, pays, w, (int(c[int(g.integers(0, rows))]),)))
+        else:
+            span = max(1, (1 << w) // 10)
+            lo = int(g.integers(0, (1 << w) - span + 1))
+            out.append(Table(f"q{i}", rows, w, PRED_RANGE, c, pays, w, (lo, lo + span)))
+    return out
+
+
 def gates(batch: int, seed: int = 1):
     """(types uint8 [B], x bits [B], y bits [B]) for the gate microbenchmark."""
     g = _rng(seed, 2)

@@ -218,3 +218,17 @@ def test_scan_eq32x4096_full_size_sampled_rows(env):
     om, (oout,) = o.scan(sub.pred, sub.width, ocol, ocst, [opay], sub.payload_width)
     assert np.array_equal(match.reshape(t.rows, -1)[rows], om)
     assert np.array_equal(outs[0].reshape(t.rows, t.payload_width, -1)[rows], oout)
+
+
+def test_autotune_picks_a_shape_and_keeps_results(env):
+    ctx, _ = env
+    types, xb, yb = WL.gates(40, seed=9)
+    x = ctx.encrypt_bits(xb, WL.STREAM_GATES, 0)
+    y = ctx.encrypt_bits(yb, WL.STREAM_GATES, 40)
+    a = torch.zeros((40, 631), dtype=torch.int32, device="cuda")
+    b = torch.zeros((40, 631), dtype=torch.int32, device="cuda")
+    ctx.gate_batch(dev(types), dev(x.view(np.int32)), dev(y.view(np.int32)), a)
+    best, ms = ctx.autotune(probe_gates=1184)
+    assert best in ms and ctx.br_gates == best and all(v > 0 for v in ms.values())
+    ctx.gate_batch(dev(types), dev(x.view(np.int32)), dev(y.view(np.int32)), b)
+    assert np.array_equal(host(a), host(b))
