@@ -262,7 +262,7 @@ def run_gates(args, dist):
     value = dist.world * B * args.steps / (ms / 1e3)
     truth = np.array([[1, 1, 1, 0], [0, 0, 0, 1], [0, 1, 1, 1], [0, 1, 1, 0], [1, 0, 0, 1]], np.uint8)[types, 2 * xb + yb]
     correct = bool(np.array_equal(ctx.decrypt_bits(out.cpu().numpy().view(np.uint32)), truth))
-    roof = roofline_of(kt, ms, sms, peaks)
+    roof = roofline_of(kt, ms, sms, peaks, f"gates{B}")
     # end to end: pinned host inputs -> device -> gates -> host, copies timed
     hx, hy, ht = (torch.from_numpy(x.view(np.int32)).pin_memory(), torch.from_numpy(y.view(np.int32)).pin_memory(),
                   torch.from_numpy(types).pin_memory())
@@ -388,14 +388,44 @@ def run_serving(args, dist):
         print(json.dumps(line), flush=True)
 
 
-def roofline_of(kt, ms, sms, peaks):
+def kernel_source_hash() -> str:
+    """sha256 of the blind-rotation kernel's sources (ntt.cuh, kernels.cu)."""
+    import hashlib
+
+    h = hashlib.sha256()
+    for f in ("ntt.cuh", "kernels.cu"):
+        with open(os.path.join(ROOT, "paper_2510_15413_b300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
+def measured_traffic(workload: str):
+    """Per-launch DRAM bytes of the blind rotation from the committed ncu
+    summary of this workload, if it was taken on the current kernel sources."""
+    path = os.path.join(ROOT, "profiles", f"blind_rotate_{workload}_dram.md")
+    try:
+        fields = {}
+        with open(path) as f:
+            for line in f:
+                if ":" in line and line.startswith("- "):
+                    k, v = line[2:].split(":", 1)
+                    fields[k.strip()] = v.strip()
+        if fields.get("kernel_source_sha256") != kernel_source_hash():
+            return None
+        return float(fields["dram_bytes_per_launch"])
+    except Exception:
+        return None
+
+
+def roofline_of(kt, ms, sms, peaks, workload=None):
     br_ms = kt["blind_rotate_ms"]
     launches = max(1, kt["blind_rotate_launches"])
     sm_max_mhz = float(peaks.get("sm_max_mhz", 2032.0))
     peak = sms * IMAD_PER_CLK_PER_SM * sm_max_mhz * 1e6 / WIDE_MULS_PER_MODMUL / 1e12
     achieved = MODMULS_PER_BOOTSTRAP * kt["gates"] / (br_ms / 1e3) / 1e12 if br_ms > 0 else 0.0
     return {"bound": "alu", "kernel": "blind_rotate_kernel", "achieved": achieved, "peak": peak, "unit": "Tmodmul/s",
-            "frac": achieved / peak if peak else None, "traffic": None,
+            "frac": achieved / peak if peak else None,
+            "traffic": measured_traffic(workload) if workload else None, "traffic_unit": "DRAM bytes per launch",
             "peak_kind": f"derived: {sms} SMs x {IMAD_PER_CLK_PER_SM} IMAD/clk x {sm_max_mhz:.0f} MHz / "
                          f"{WIDE_MULS_PER_MODMUL} wide multiplies per modmul",
             "avg_launch_ms": br_ms / launches, "share_of_step": br_ms / ms if ms else None,
@@ -461,7 +491,7 @@ def run_ours(args, dist):
         correct &= bool(np.array_equal(ctx.decrypt_uint(o_.cpu().numpy().view(np.uint32), t.payload_width), p_want[q]))
 
     # ---- roofline of the dominant kernel (blind rotation)
-    roofline = roofline_of(ktimes, ms, sms, peaks)
+    roofline = roofline_of(ktimes, ms, sms, peaks, args.workload)
 
     # ---- end to end through the public C-ABI with host buffers (copies inside the timed region)
     hcol = torch.from_numpy(col.view(np.int32)).pin_memory()
