@@ -48,6 +48,8 @@ def parse():
     ap.add_argument("--cpu-rows", type=int, default=1, help="rows of the workload the oracle times")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-per-gate", action="store_true", help="skip the per-gate-launch baseline")
+    ap.add_argument("--verify-rows", type=int, default=0,
+                    help="rows of the timed scan the CPU oracle recomputes word for word (first, matching, last...)")
     ap.add_argument("--seed", type=int, default=1)
     return ap.parse_args()
 
@@ -189,6 +191,42 @@ def oracle_rate(table, seed: int, rows: int):
     gates = rows * table.gates_per_row
     o.close()
     return gates / dt, O.max_threads(), dt, gates
+
+
+def verify_rows_with_oracle(table, seed, k, match, outs):
+    """Recompute k rows (first, a matching one, last, then evenly spaced) with
+    the CPU oracle from its own encryptions and compare every output word."""
+    from oracle import oracle as O
+    from paper_2510_15413_b300 import workloads as WL
+
+    O.set_threads(os.cpu_count() or 1)
+    o = O.Oracle(seed)
+    m_want, _ = table.expected()
+    cand = [0, int(np.argmax(m_want)) if m_want.any() else 1, table.rows - 1]
+    cand += [int(r) for r in np.linspace(0, table.rows - 1, max(k, 3)).astype(int)]
+    rows = []
+    for r in cand:
+        if r not in rows:
+            rows.append(r)
+        if len(rows) == k:
+            break
+    rows = sorted(rows)
+    w, pw = table.width, table.payload_width
+    col = np.concatenate([o.encrypt_bits(table.column_bits().reshape(table.rows, w)[r], WL.STREAM_COLUMN, r * w)
+                          for r in rows])
+    cst = o.encrypt_bits(table.const_bits(), WL.STREAM_CONST, 0)
+    pays = [np.concatenate([o.encrypt_bits(table.payload_bits(q).reshape(table.rows, pw)[r], WL.STREAM_PAYLOAD,
+                                           q * table.rows * pw + r * pw) for r in rows])
+            for q in range(len(table.payloads))]
+    t0 = time.perf_counter()
+    om, oouts = o.scan(table.pred, w, col, cst, pays, pw)
+    dt = time.perf_counter() - t0
+    o.close()
+    gm = match.cpu().numpy().view(np.uint32)[rows]
+    same = bool(np.array_equal(gm, om))
+    for q, out in enumerate(outs):
+        same &= bool(np.array_equal(out.cpu().numpy().view(np.uint32)[rows], oouts[q]))
+    return {"rows": [int(r) for r in rows], "words_equal": same, "oracle_seconds": dt}
 
 
 def run_reference(args, dist):
@@ -494,26 +532,35 @@ def run_ours(args, dist):
     roofline = roofline_of(ktimes, ms, sms, peaks, args.workload)
 
     # ---- end to end through the public C-ABI with host buffers (copies inside the timed region)
-    hcol = torch.from_numpy(col.view(np.int32)).pin_memory()
-    hcst = torch.from_numpy(cst.view(np.int32)).pin_memory()
-    hpay = [torch.from_numpy(p.view(np.int32)).pin_memory() for p in pays]
-    hmatch = torch.zeros((t.rows, W), dtype=torch.int32).pin_memory()
-    houts = [torch.zeros((t.rows, t.payload_width, W), dtype=torch.int32).pin_memory() for _ in pays]
-    h2d = (hcol.numel() + hcst.numel() + sum(p.numel() for p in hpay)) * 4
-    d2h = (hmatch.numel() + sum(o.numel() for o in houts)) * 4
-    ctx.scan_select_host(hcol, t.rows, t.width, t.pred, hcst, hpay, t.payload_width, hmatch, houts, stream=st)
-    dist.barrier()
-    torch.cuda.synchronize()
-    f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    f0.record(st)
-    for _ in range(args.e2e_steps):
+    h2d = (col.size + cst.size + sum(p.size for p in pays)) * 4
+    d2h = (t.rows * W + len(pays) * t.rows * t.payload_width * W) * 4
+    e2e = None
+    if args.e2e_steps > 0:
+        hcol = torch.from_numpy(col.view(np.int32)).pin_memory()
+        hcst = torch.from_numpy(cst.view(np.int32)).pin_memory()
+        hpay = [torch.from_numpy(p.view(np.int32)).pin_memory() for p in pays]
+        hmatch = torch.zeros((t.rows, W), dtype=torch.int32).pin_memory()
+        houts = [torch.zeros((t.rows, t.payload_width, W), dtype=torch.int32).pin_memory() for _ in pays]
         ctx.scan_select_host(hcol, t.rows, t.width, t.pred, hcst, hpay, t.payload_width, hmatch, houts, stream=st)
-    f1.record(st)
-    torch.cuda.synchronize()
-    dist.barrier()
-    e2e_ms = dist.max(f0.elapsed_time(f1))
-    e2e_value = dist.world * gates_per_step * args.e2e_steps / (e2e_ms / 1e3)
-    e2e_ok = bool(np.array_equal(ctx.decrypt_bits(hmatch.numpy().view(np.uint32)), m_want))
+        dist.barrier()
+        torch.cuda.synchronize()
+        f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        f0.record(st)
+        for _ in range(args.e2e_steps):
+            ctx.scan_select_host(hcol, t.rows, t.width, t.pred, hcst, hpay, t.payload_width, hmatch, houts,
+                                 stream=st)
+        f1.record(st)
+        torch.cuda.synchronize()
+        dist.barrier()
+        e2e_ms = dist.max(f0.elapsed_time(f1))
+        e2e = {"value": dist.world * gates_per_step * args.e2e_steps / (e2e_ms / 1e3), "unit": "gate bootstraps/s",
+               "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
+        correct &= bool(np.array_equal(ctx.decrypt_bits(hmatch.numpy().view(np.uint32)), m_want))
+
+    # ---- oracle recomputation of sampled rows of the timed scan
+    verified = None
+    if args.verify_rows > 0 and dist.rank == 0:
+        verified = verify_rows_with_oracle(t, args.seed, args.verify_rows, match, outs)
 
     # ---- per-gate launch baseline and batched rate on the 16-row table
     small = None
@@ -561,11 +608,11 @@ def run_ours(args, dist):
                    "engine": ["goldilocks", "dual_prime"][ctx.engine],
                    "l2": "inputs larger than L2 (%.0f MB column+payload per step)" % (h2d / 1e6),
                    "parallelism": f"replica per GPU x{dist.world}"},
-        "correct": correct and e2e_ok,
+        "correct": correct,
+        "oracle_rows": verified,
         "roofline": roofline,
         "cpu_baseline": cpu,
-        "e2e": {"value": e2e_value, "unit": "gate bootstraps/s", "h2d_bytes_per_step": h2d,
-                "d2h_bytes_per_step": d2h},
+        "e2e": e2e,
         "gpu_launches": int(ktimes["blind_rotate_launches"] + ktimes["keyswitch_launches"]),
         "clocks": clocks,
         "per_gate_baseline": small,
