@@ -113,7 +113,7 @@ FSQL_API int fsql_ctx_create_engine(const fsql_params* params, uint64_t seed, in
                                     fsql_ctx** out);
 FSQL_API int fsql_ctx_engine(const fsql_ctx* ctx, int* engine);
 /* Launch shape of the blind rotation for large batches: gates per CTA, each
- * gate 128 threads (1, 2 or 4 for the Goldilocks engine, 1 or 2 for the
+ * gate 128 threads (1, 2 or 4 for the Goldilocks engine, 1 to 4 for the
  * dual-prime engine; batches under two gates per SM always use 1).  Results
  * do not depend on it. */
 FSQL_API int fsql_ctx_set_br_gates(fsql_ctx* ctx, int gates_per_cta);
@@ -123,8 +123,8 @@ FSQL_API int fsql_ctx_br_gates(const fsql_ctx* ctx, int* gates_per_cta);
  * (0 = 4 x SMs x 4) for every launch shape the context's engine offers,
  * keeps the fastest in the context and in a per-process table keyed by
  * (device, engine), and returns the chosen gates per CTA and the timings
- * (ms, in the order 1, 2, 4 gates per CTA; -1 where not offered) in
- * ms_out[3] (may be NULL).  Synchronises `stream`; allocates its probe
+ * (ms, in the order 1, 2, 3, 4 gates per CTA; -1 where not offered) in
+ * ms_out[4] (may be NULL).  Synchronises `stream`; allocates its probe
  * buffers for the duration of the call.  A later context on the same device
  * and engine starts from the tuned value. */
 FSQL_API int fsql_autotune(fsql_ctx* ctx, size_t probe_gates, void* stream, int* best_gates, double* ms_out);

@@ -56,7 +56,7 @@ struct Ctx {
   uint64_t seed = 0;
   int device = -1;
   int engine = FSQL_ENGINE_DUAL_PRIME;
-  int br_gates = 2;              // gates per blind-rotation CTA for large batches (1 or 2)
+  int br_gates = 3;              // gates per blind-rotation CTA for large batches
   // host-side secrets and standard-domain keys (client side)
   std::vector<uint8_t> s;    // LWE key [n]
   std::vector<uint8_t> S;    // GLWE key [N]

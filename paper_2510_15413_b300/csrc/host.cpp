@@ -289,7 +289,7 @@ int fsql_ctx_create_engine(const fsql_params* params, uint64_t seed, int device,
     c->seed = seed;
     c->device = device;
     c->engine = engine;
-    c->br_gates = engine == FSQL_ENGINE_GOLDILOCKS ? 4 : 2;
+    c->br_gates = engine == FSQL_ENGINE_GOLDILOCKS ? 4 : 3;
     fsql::keygen(*c);
     if (device >= 0) {
       const int rc = fsql::device_init(*c);
@@ -313,8 +313,8 @@ int fsql_ctx_set_br_gates(fsql_ctx* ctx, int gates_per_cta) {
   Ctx* c = reinterpret_cast<Ctx*>(ctx);
   const bool ok = c->engine == FSQL_ENGINE_GOLDILOCKS
                       ? (gates_per_cta == 1 || gates_per_cta == 2 || gates_per_cta == 4)
-                      : (gates_per_cta == 1 || gates_per_cta == 2);
-  if (!ok) return arg_error("gates per CTA: 1, 2 or 4 (Goldilocks engine), 1 or 2 (dual-prime engine)");
+                      : (gates_per_cta >= 1 && gates_per_cta <= 4);
+  if (!ok) return arg_error("gates per CTA: 1, 2 or 4 (Goldilocks engine), 1 to 4 (dual-prime engine)");
   c->br_gates = gates_per_cta;
   return FSQL_OK;
 }

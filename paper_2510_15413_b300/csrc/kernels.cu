@@ -44,18 +44,24 @@ template <int P>
 __host__ __device__ constexpr int xbuf_polys() {
   return P > 2 ? P : 2;
 }
-// Per gate: two exchange buffers, the accumulator, the switched mask.
-template <int P>
+// Per gate: NB exchange buffers, the accumulator, the switched mask.
+template <int P, int NB = 2>
 __host__ __device__ constexpr int gate_bytes() {
-  return 2 * xbuf_polys<P>() * kN * 8 + kGateAcc + kGateAbar + 16;
+  return NB * xbuf_polys<P>() * kN * 8 + kGateAcc + kGateAbar + 16;
 }
 template <class F>
 __host__ __device__ constexpr int tab_bytes() {
   return (sizeof(typename F::Tables) + 127) / 128 * 128;
 }
+// Exchange buffers per gate: two (one barrier per exchange) when they fit,
+// one for 3 or more gates per CTA.
+template <int G>
+__host__ __device__ constexpr int xbufs_for() {
+  return G >= 3 ? 1 : 2;
+}
 template <class F, int G, int P>
 __host__ __device__ constexpr int br_smem() {
-  return tab_bytes<F>() + kStages * P * kChunkU64 * 8 + G * gate_bytes<P>();
+  return tab_bytes<F>() + kStages * P * kChunkU64 * 8 + G * gate_bytes<P, xbufs_for<G>()>();
 }
 
 constexpr int kKsGates = 16;                     // gates per keyswitch CTA
@@ -272,8 +278,9 @@ __global__ void __launch_bounds__(G * kGroup, 1)
   constexpr int kStepsPerCmux = kRows / kPolys;
   constexpr int kStepU64 = kPolys * kChunkU64;
   constexpr int kBufPolys = xbuf_polys<kPolys>();
-  constexpr int kGateXbuf = 2 * kBufPolys * kN * 8;
-  constexpr int kGateBytes = gate_bytes<kPolys>();
+  constexpr int kNB = xbufs_for<G>();
+  constexpr int kGateXbuf = kNB * kBufPolys * kN * 8;
+  constexpr int kGateBytes = gate_bytes<kPolys, kNB>();
   extern __shared__ __align__(128) uint8_t smem[];
   typename F::Tables& T = *reinterpret_cast<typename F::Tables*>(smem);
   uint64_t* stage = reinterpret_cast<uint64_t*>(smem + kTabBytes);
@@ -362,7 +369,7 @@ __global__ void __launch_bounds__(G * kGroup, 1)
               x[p][q] = F::from_digit((v >> shift) & dmask, dhalf);
             }
           }
-          dev::ntt_forward<F, kPolys, kBufPolys>(x, xbufs, parity, T, t, bar);
+          dev::ntt_forward<F, kPolys, kBufPolys, kNB>(x, xbufs, parity, T, t, bar);
           const uint64_t* ch = stage + (k % kStages) * kStepU64;
 #pragma unroll
           for (int q = 0; q < 8; ++q) {
@@ -381,7 +388,7 @@ __global__ void __launch_bounds__(G * kGroup, 1)
           y[0][q] = F::acc0(acc[q]);
           y[1][q] = F::acc1(acc[q]);
         }
-        dev::ntt_inverse<F, 2, kBufPolys>(y, xbufs, parity, T, t, bar);
+        dev::ntt_inverse<F, 2, kBufPolys, kNB>(y, xbufs, parity, T, t, bar);
 #pragma unroll
         for (int c = 0; c < 2; ++c)
 #pragma unroll
@@ -632,7 +639,7 @@ int device_init(Ctx& c) {
   }
   CK(cudaSetDevice(c.device));
   // gates per CTA for large batches: measured best on B300 unless tuned in this process
-  c.br_gates = c.engine == FSQL_ENGINE_GOLDILOCKS ? 4 : 2;
+  c.br_gates = c.engine == FSQL_ENGINE_GOLDILOCKS ? 4 : 3;
   if (const int g = tuned_gates(c.device, c.engine)) c.br_gates = g;
   int sms = 0;
   CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c.device));
@@ -728,9 +735,10 @@ static cudaError_t launch_br_engine(int sm_count, const GateDesc* d_desc, size_t
 }
 
 // Launch shapes measured best on B300 per engine: the 64-bit prime is ALU
-// bound and wants more resident gates (one gadget row per step, up to 4
-// gates per CTA); the two-prime engine is latency bound and wants more
-// independent work per thread (two rows per step, up to 2 gates per CTA).
+// bound and wants more resident gates (one gadget row per step, 4 gates per
+// CTA); the two-prime engine is latency bound and wants independent work per
+// thread (two rows per step) and resident warps (3 gates per CTA: 158
+// registers, one exchange buffer per gate so that 3 fit in shared memory).
 // Batches smaller than two gates per SM always use one gate per CTA.
 static cudaError_t launch_br_any(Ctx& c, const GateDesc* d_desc, size_t count, uint32_t* d_big, cudaStream_t st) {
   const int n = static_cast<int>(c.p.n), bg = static_cast<int>(c.p.bg_bits);
@@ -746,6 +754,10 @@ static cudaError_t launch_br_any(Ctx& c, const GateDesc* d_desc, size_t count, u
   using F = dev::DualPrime;
   if (small || c.br_gates == 1)
     return launch_br_engine<F, 1, 2>(c.sm_count, d_desc, count, c.d_bkhat, c.d_tables, n, bg, d_big, st);
+  if (c.br_gates == 3)
+    return launch_br_engine<F, 3, 2>(c.sm_count, d_desc, count, c.d_bkhat, c.d_tables, n, bg, d_big, st);
+  if (c.br_gates == 4)
+    return launch_br_engine<F, 4, 2>(c.sm_count, d_desc, count, c.d_bkhat, c.d_tables, n, bg, d_big, st);
   return launch_br_engine<F, 2, 2>(c.sm_count, d_desc, count, c.d_bkhat, c.d_tables, n, bg, d_big, st);
 }
 
@@ -1256,8 +1268,8 @@ int fsql_autotune(fsql_ctx* ctx, size_t probe_gates, void* stream, int* best_gat
   fsql::GateDesc* d_desc = nullptr;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   int rc = FSQL_OK;
-  double ms[3] = {-1.0, -1.0, -1.0};
-  const int shapes[3] = {1, 2, 4};
+  double ms[4] = {-1.0, -1.0, -1.0, -1.0};
+  const int shapes[4] = {1, 2, 3, 4};
   const int saved = c->br_gates;
   int best = saved;
   double best_ms = 0.0;
@@ -1277,7 +1289,7 @@ int fsql_autotune(fsql_ctx* ctx, size_t probe_gates, void* stream, int* best_gat
   if (rc == FSQL_OK) {
     fsql::make_desc_kernel<<<static_cast<unsigned>((count + 255) / 256), 256, 0, st>>>(
         d_desc, d_types, d_in, d_in + count * words, nullptr, static_cast<int>(count), static_cast<int>(words));
-    for (int si = 0; si < 3 && rc == FSQL_OK; ++si) {
+    for (int si = 0; si < 4 && rc == FSQL_OK; ++si) {
       const int g = shapes[si];
       if (fsql_ctx_set_br_gates(ctx, g) != FSQL_OK) continue;  // shape not offered by this engine
       float t = 0.f;
@@ -1308,7 +1320,7 @@ int fsql_autotune(fsql_ctx* ctx, size_t probe_gates, void* stream, int* best_gat
   cudaFree(d_desc);
   if (best_gates) *best_gates = c->br_gates;
   if (ms_out)
-    for (int i = 0; i < 3; ++i) ms_out[i] = ms[i];
+    for (int i = 0; i < 4; ++i) ms_out[i] = ms[i];
   return rc;
 }
 

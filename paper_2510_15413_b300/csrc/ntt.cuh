@@ -260,9 +260,10 @@ struct LI2 { static __device__ __forceinline__ int at(int t, int k) { return 64 
 struct LI3 { static __device__ __forceinline__ int at(int t, int k) { return 512 * (t >> 6) + 64 * k + (t & 63); } };
 
 // Move the P x 1024 values of P polynomials from layout S to layout D
-// through one of the group's two exchange buffers.  Each buffer holds B >= P
-// polynomials (B is the same for every exchange of a kernel, so buffer 0 and
-// buffer 1 never overlap).  Consecutive exchanges alternate buffers.
+// through the group's exchange buffers: NB = 2 buffers used alternately, or
+// NB = 1 buffer (less shared memory, one more barrier per inverse).  Each
+// buffer holds B >= P polynomials (B is the same for every exchange of a
+// kernel, so two buffers never overlap).
 //
 // Warp-local exchanges.  In layouts F2, F3, F4 (= I1) and I2 the 32 threads
 // of warp w hold exactly the elements [256 w, 256 w + 256); F1 and I3 spread
@@ -275,11 +276,15 @@ struct LI3 { static __device__ __forceinline__ int at(int t, int k) { return 512
 // local, or a named barrier came in between); a spread exchange is always
 // preceded by a group-wide barrier since the last reads of its buffer (the
 // CTA barrier at the start of each step, or the named barrier of I2->I3).
-template <int P, int B, class S, class D, bool kWarpLocal>
+template <int P, int B, int NB, class S, class D, bool kWarpLocal>
 __device__ __forceinline__ void exchange(uint64_t (&x)[P][8], uint64_t* bufs, int& parity, int t, int bar) {
   static_assert(P <= B, "exchange buffer too small");
-  uint64_t* buf = bufs + parity * (B * 1024);
+  uint64_t* buf = bufs + (NB == 2 ? parity : 0) * (B * 1024);
   parity ^= 1;
+  // with one buffer, the previous exchange's reads must be over before these
+  // writes: within the warp for warp-local writes; a spread write follows a
+  // spread read only in the inverse (I3 -> F1), whose caller adds the barrier
+  if (NB == 1) __syncwarp();
 #pragma unroll
   for (int p = 0; p < P; ++p)
 #pragma unroll
@@ -320,50 +325,51 @@ __device__ __forceinline__ void gs_stage(uint64_t (&x)[P][8], TwOf tw) {
 // next exchange uses.  Its first exchange writes across warps, so the caller
 // separates it from the exchanges of an earlier transform by a group-wide
 // barrier.
-template <class F, int P, int B>
+template <class F, int P, int B, int NB = 2>
 __device__ __forceinline__ void ntt_forward(uint64_t (&x)[P][8], uint64_t* bufs, int& parity,
                                             const typename F::Tables& T, int t, int bar) {
   // F1: distances 512, 256, 128 (register bits 2, 1, 0), twiddles uniform
   ct_stage<F, P, 4>(x, [&](int) { return T.f_small[1]; });
   ct_stage<F, P, 2>(x, [&](int k) { return T.f_small[2 + (k >> 2)]; });
   ct_stage<F, P, 1>(x, [&](int k) { return T.f_small[4 + (k >> 1)]; });
-  exchange<P, B, LF1, LF2, false>(x, bufs, parity, t, bar);
+  exchange<P, B, NB, LF1, LF2, false>(x, bufs, parity, t, bar);
   // F2: distances 64, 32, 16
   const int h3 = t >> 4;
   ct_stage<F, P, 4>(x, [&](int) { return T.f_small[8 + h3]; });
   ct_stage<F, P, 2>(x, [&](int k) { return T.f_small[16 + 2 * h3 + (k >> 2)]; });
   ct_stage<F, P, 1>(x, [&](int k) { return T.f_small[32 + 4 * h3 + (k >> 1)]; });
-  exchange<P, B, LF2, LF3, true>(x, bufs, parity, t, bar);
+  exchange<P, B, NB, LF2, LF3, true>(x, bufs, parity, t, bar);
   // F3: distances 8, 4, 2 (per-thread twiddles)
   ct_stage<F, P, 4>(x, [&](int) { return T.f3[0][t]; });
   ct_stage<F, P, 2>(x, [&](int k) { return T.f3[1 + (k >> 2)][t]; });
   ct_stage<F, P, 1>(x, [&](int k) { return T.f3[3 + (k >> 1)][t]; });
-  exchange<P, B, LF3, LF4, true>(x, bufs, parity, t, bar);
+  exchange<P, B, NB, LF3, LF4, true>(x, bufs, parity, t, bar);
   // F4: distance 1
   ct_stage<F, P, 1>(x, [&](int k) { return T.f4[k >> 1][t]; });
 }
 
 // Inverse transform of P polynomials (no 1/N): layout F4 -> layout F1 (natural order).
-template <class F, int P, int B>
+template <class F, int P, int B, int NB = 2>
 __device__ __forceinline__ void ntt_inverse(uint64_t (&x)[P][8], uint64_t* bufs, int& parity,
                                             const typename F::Tables& T, int t, int bar) {
   // I1: distances 1, 2, 4 (per-thread twiddles)
   gs_stage<F, P, 1>(x, [&](int k) { return T.i1[k >> 1][t]; });
   gs_stage<F, P, 2>(x, [&](int k) { return T.i1[4 + (k >> 2)][t]; });
   gs_stage<F, P, 4>(x, [&](int) { return T.i1[6][t]; });
-  exchange<P, B, LF4, LI2, true>(x, bufs, parity, t, bar);
+  exchange<P, B, NB, LF4, LI2, true>(x, bufs, parity, t, bar);
   // I2: distances 8, 16, 32
   const int h4 = t >> 3;
   gs_stage<F, P, 1>(x, [&](int k) { return T.g_small[64 + 4 * h4 + (k >> 1)]; });
   gs_stage<F, P, 2>(x, [&](int k) { return T.g_small[32 + 2 * h4 + (k >> 2)]; });
   gs_stage<F, P, 4>(x, [&](int) { return T.g_small[16 + h4]; });
-  exchange<P, B, LI2, LI3, false>(x, bufs, parity, t, bar);
+  exchange<P, B, NB, LI2, LI3, false>(x, bufs, parity, t, bar);
   // I3: distances 64, 128, 256
   const int b9 = t >> 6;
   gs_stage<F, P, 1>(x, [&](int k) { return T.g_small[8 + 4 * b9 + (k >> 1)]; });
   gs_stage<F, P, 2>(x, [&](int k) { return T.g_small[4 + 2 * b9 + (k >> 2)]; });
   gs_stage<F, P, 4>(x, [&](int) { return T.g_small[2 + b9]; });
-  exchange<P, B, LI3, LF1, false>(x, bufs, parity, t, bar);
+  if (NB == 1) named_sync(bar);  // every thread's I2 -> I3 reads are over (spread write next)
+  exchange<P, B, NB, LI3, LF1, false>(x, bufs, parity, t, bar);
   // I4: distance 512
   gs_stage<F, P, 4>(x, [&](int) { return T.g_small[1]; });
 }

@@ -215,9 +215,9 @@ class Context:
     def autotune(self, probe_gates: int = 0, stream=None):
         """Pick the fastest blind-rotation launch shape; returns (gates per CTA, {shape: ms})."""
         best = C.c_int()
-        ms = (C.c_double * 3)()
+        ms = (C.c_double * 4)()
         _check(load().fsql_autotune(self._h, probe_gates, _stream(stream), C.byref(best), ms))
-        return int(best.value), {g: ms[i] for i, g in enumerate((1, 2, 4)) if ms[i] >= 0}
+        return int(best.value), {g: ms[i] for i, g in enumerate((1, 2, 3, 4)) if ms[i] >= 0}
 
     @property
     def handle(self) -> C.c_void_p:
