@@ -414,12 +414,17 @@ __global__ void __launch_bounds__(G * kGroup, 1)
 // bits, 8 base-4 digits most significant first; digit v at level j selects
 // key row KSK[i][j][v-1]; out = (0, .., 0, b) - sum of the selected rows.
 // Grid: (gate groups of kKsGates, column tiles of kKsCols); each thread owns
-// one output column of every gate of its group.  Output of gate g goes to
-// desc[g].out when desc is given, else to out_contig + g*(n+1).
+// one output column of every gate of its group.  For each position i the
+// thread copies its column of the 3 x 8 nonzero-digit key rows into its own
+// slots of a shared table whose digit-0 rows are zero, so each gate's term is
+// one table load indexed by its digit (no compare or select); only the
+// owning thread reads a slot, so no barrier is needed.  Output of gate g goes
+// to desc[g].out when desc is given, else to out_contig + g*(n+1).
 __global__ void __launch_bounds__(kKsCols)
     keyswitch_kernel(const uint32_t* __restrict__ big, const GateDesc* __restrict__ desc,
                      uint32_t* __restrict__ out_contig, int count, const uint32_t* __restrict__ ksk, int n) {
   __shared__ uint16_t dig[kKsGates][kN];
+  __shared__ uint32_t tbl[kKsT][4][kKsCols];  // [level][digit][column of this tile]
   const int g0 = blockIdx.x * kKsGates;
   const int ng = min(kKsGates, count - g0);
   for (int q = threadIdx.x; q < kKsGates * kN; q += kKsCols) {
@@ -428,28 +433,29 @@ __global__ void __launch_bounds__(kKsCols)
     if (g < ng) v = static_cast<uint16_t>((big[static_cast<size_t>(g0 + g) * (kN + 1) + i] + (1u << 15)) >> 16);
     dig[g][i] = v;
   }
+  const int tc = threadIdx.x;
+#pragma unroll
+  for (int j = 0; j < kKsT; ++j) tbl[j][0][tc] = 0u;
   __syncthreads();
-  const int col = blockIdx.y * kKsCols + threadIdx.x;
+  const int col = blockIdx.y * kKsCols + tc;
   uint32_t acc[kKsGates];
 #pragma unroll
   for (int g = 0; g < kKsGates; ++g) acc[g] = 0u;
   const uint32_t* base = ksk + col;
 #pragma unroll 1
   for (int i = 0; i < kN; ++i) {
-    uint32_t dv[kKsGates];
-#pragma unroll
-    for (int g = 0; g < kKsGates; ++g) dv[g] = dig[g][i];
 #pragma unroll
     for (int j = 0; j < kKsT; ++j) {
       const uint32_t* rows = base + static_cast<size_t>((i * kKsT + j) * kKsDigits) * kKsRowWords;
-      const uint32_t r1 = __ldg(rows), r2 = __ldg(rows + kKsRowWords), r3 = __ldg(rows + 2 * kKsRowWords);
-      const int sh = 14 - 2 * j;
+      tbl[j][1][tc] = __ldg(rows);
+      tbl[j][2][tc] = __ldg(rows + kKsRowWords);
+      tbl[j][3][tc] = __ldg(rows + 2 * kKsRowWords);
+    }
 #pragma unroll
-      for (int g = 0; g < kKsGates; ++g) {
-        const uint32_t d = (dv[g] >> sh) & 3u;
-        const uint32_t sel = d == 1 ? r1 : (d == 2 ? r2 : r3);
-        acc[g] -= d ? sel : 0u;
-      }
+    for (int g = 0; g < kKsGates; ++g) {
+      const uint32_t dv = dig[g][i];
+#pragma unroll
+      for (int j = 0; j < kKsT; ++j) acc[g] -= tbl[j][(dv >> (14 - 2 * j)) & 3u][tc];
     }
   }
   if (col > n) return;
