@@ -39,7 +39,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="eq32x4096",
-                    choices=["eq32x4096", "eq4x16", "range16x65536", "lt8x64", "range4x16", "gates", "serving"])
+                    choices=["eq32x4096", "eq4x16", "range16x65536", "range16x65536maj", "lt8x64", "lt8x64maj", "range4x16",
+                             "range4x16maj", "gates", "serving"])
     ap.add_argument("--queries", type=int, default=16, help="queries per serving phase")
     ap.add_argument("--batch", type=int, default=65536, help="gates per step of the gate microbenchmark")
     ap.add_argument("--engine", default="default", choices=["default", "dual_prime", "goldilocks"])

@@ -64,12 +64,21 @@ extern "C" {
 #define FSQL_ANDYN 7
 #define FSQL_ORNY 8
 #define FSQL_ORYN 9
+/* MAJNYY(a, b, c) = majority of (not a, b, c): one bootstrap of -a + b + c
+ * (three inputs; used only inside scan netlists, not by fsql_gate_batch). */
+#define FSQL_MAJNYY 10
 
 /* Predicates of the WHERE clause (§4.3 B: equality and comparison).
- * EQ: c = k.  LT: c < k (unsigned).  RANGE: lo <= c < hi (unsigned). */
+ * EQ: c = k.  LT: c < k (unsigned).  RANGE: lo <= c < hi (unsigned).
+ * LT and RANGE use an LSB-first ripple comparator of 4w - 3 gates;
+ * LT_MAJ and RANGE_MAJ compute the same predicates with a majority chain of
+ * w gates per comparator (lt_i = MAJ(not c_i, k_i, lt_{i-1})), not in the
+ * paper: different gates, hence different output words, same plaintext. */
 #define FSQL_EQ 0
 #define FSQL_LT 1
 #define FSQL_RANGE 2
+#define FSQL_LT_MAJ 3
+#define FSQL_RANGE_MAJ 4
 
 /* TFHE parameters.  Torus32; GLWE dimension k = 1.  The GPU kernels
  * implement N = 1024, l = 3, 2 <= bg_bits <= 10, ks_base_bits = 2, ks_t = 8
@@ -211,15 +220,18 @@ FSQL_API int fsql_plan_info(uint32_t pred, uint32_t width, uint32_t n_payloads, 
 
 /* Oblivious scan-select (Alg. 2 ProcessQuery over all rows; §4.2).
  * d_column: [rows][width][n+1] encrypted column; d_const: the encrypted
- * constant bits ([width][n+1] for EQ/LT, lo then hi [2*width][n+1] for
- * RANGE); d_payloads: host array of n_payloads device pointers, each
+ * constant bits ([width][n+1] for EQ/LT/LT_MAJ, lo then hi [2*width][n+1]
+ * for RANGE/RANGE_MAJ); d_payloads: host array of n_payloads device pointers, each
  * [rows][payload_width][n+1].  Outputs: d_match [rows][n+1] the encrypted
  * predicate bit of each row; d_out_payloads: host array of n_payloads device
  * pointers [rows][payload_width][n+1] = AND(match, payload bit), i.e. the
  * payload where the row matches and an encryption of 0 elsewhere.  Every row
  * runs the same gates: the work depends only on the sizes.  Outputs may not
  * alias inputs.  per_gate != 0 launches one gate per kernel launch (the plain
- * baseline); otherwise each circuit level runs as batched launches. */
+ * baseline); otherwise each circuit level runs as batched launches, and
+ * the launch sequence of a scan is captured once as a CUDA graph (on a
+ * stream of the context) and replayed on `stream` by later calls with the
+ * same buffers and shape (plain launches while fsql_profile is recording). */
 FSQL_API int fsql_scan_select(fsql_ctx* ctx, const uint32_t* d_column, size_t rows, uint32_t width, uint32_t pred,
                      const uint32_t* d_const, uint32_t n_payloads, const uint32_t* const* d_payloads,
                      uint32_t payload_width, uint32_t* d_match, uint32_t* const* d_out_payloads, int per_gate,

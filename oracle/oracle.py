@@ -13,9 +13,9 @@ import numpy as np
 
 from . import build_oracle
 
-P_EQ, P_LT, P_RANGE = 0, 1, 2
+P_EQ, P_LT, P_RANGE, P_LT_MAJ, P_RANGE_MAJ = 0, 1, 2, 3, 4
 GATES = {"NAND": 0, "AND": 1, "OR": 2, "XOR": 3, "XNOR": 4, "NOR": 5,
-         "ANDNY": 6, "ANDYN": 7, "ORNY": 8, "ORYN": 9}
+         "ANDNY": 6, "ANDYN": 7, "ORNY": 8, "ORYN": 9, "MAJNYY": 10}
 
 
 class Params(C.Structure):
@@ -66,6 +66,11 @@ def lib():
         L.orc_keyswitch.argtypes = [C.c_void_p, u32p, u32p]
         L.orc_gate_lincomb.argtypes = [C.c_int, C.c_int, u32p, u32p, u32p]
         L.orc_gate.argtypes = [C.c_void_p, C.c_int, u32p, u32p, u32p]
+        L.orc_gate3.argtypes = [C.c_void_p, C.c_int, u32p, u32p, u32p, u32p]
+        L.orc_gate_lincomb3.argtypes = [C.c_int, C.c_int, u32p, u32p, u32p, u32p]
+        L.orc_gate_plain3.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int]
+        L.orc_netlist3.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_void_p,
+                                   C.c_void_p, C.c_void_p, C.POINTER(C.c_int32), C.POINTER(C.c_int32)]
         L.orc_gate_batch.argtypes = [C.c_void_p, i32p, u32p, u32p, u32p, C.c_size_t]
         L.orc_not.argtypes = [C.c_int, u32p, u32p]
         L.orc_netlist.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_void_p,
@@ -157,8 +162,24 @@ def netlist(pred: int, w: int, n_payload: int = 0, pw: int = 0):
     return t, a, b, int(m.value), int(ninp.value)
 
 
+def netlist3(pred: int, w: int, n_payload: int = 0, pw: int = 0):
+    """Per-row netlist with third inputs: (types, a, b, c, match_wire, n_inputs); c = -1 for two-input gates."""
+    m, ninp = C.c_int32(), C.c_int32()
+    g = lib().orc_netlist3(pred, w, n_payload, pw, None, None, None, None, C.byref(m), C.byref(ninp))
+    if g < 0:
+        raise ValueError("bad netlist request")
+    t, a, b, c = (np.zeros(g, np.int32) for _ in range(4))
+    lib().orc_netlist3(pred, w, n_payload, pw, t.ctypes.data, a.ctypes.data, b.ctypes.data, c.ctypes.data,
+                       C.byref(m), C.byref(ninp))
+    return t, a, b, c, int(m.value), int(ninp.value)
+
+
+def gate_plain3(gate: int, x: int, y: int, z: int) -> int:
+    return int(lib().orc_gate_plain3(gate, x, y, z))
+
+
 def netlist_eval_plain(pred: int, w: int, n_payload: int, pw: int, inputs):
-    t, _, _, m, ninp = netlist(pred, w, n_payload, pw)
+    t, _, _, _, m, ninp = netlist3(pred, w, n_payload, pw)
     inp = np.ascontiguousarray(inputs, dtype=np.uint8)
     assert inp.size == ninp
     wires = np.zeros(ninp + t.size, np.uint8)
@@ -272,6 +293,13 @@ class Oracle:
         a, b = _u32(a).ravel(), _u32(b).ravel()
         out = np.zeros(self.n + 1, np.uint32)
         if lib().orc_gate(self._h, gate, a, b, out) != 0:
+            raise ValueError("bad gate")
+        return out
+
+    def gate3(self, gate: int, a, b, c):
+        a, b, c = _u32(a).ravel(), _u32(b).ravel(), _u32(c).ravel()
+        out = np.zeros(self.n + 1, np.uint32)
+        if lib().orc_gate3(self._h, gate, a, b, c, out) != 0:
             raise ValueError("bad gate")
         return out
 

@@ -485,7 +485,7 @@ ORC_API void orc_keyswitch(const orc_ctx *c, const uint32_t *big, uint32_t *out)
 }
 
 /* Gate types (numbering fixed by the library's C interface). */
-enum { G_NAND = 0, G_AND, G_OR, G_XOR, G_XNOR, G_NOR, G_ANDNY, G_ANDYN, G_ORNY, G_ORYN, G_COUNT };
+enum { G_NAND = 0, G_AND, G_OR, G_XOR, G_XNOR, G_NOR, G_ANDNY, G_ANDYN, G_ORNY, G_ORYN, G_MAJNYY, G_COUNT };
 
 /* Linear combination before the bootstrap: constant (0, ..., 0, k) plus
  * ca * c1 + cb * c2, all mod q, with q/8 = 2^29.  The sign of the resulting
@@ -513,14 +513,26 @@ ORC_API int orc_gate_lincomb(int type, int n, const uint32_t *c1, const uint32_t
     return 0;
 }
 
+/* Three-input majority with the first input negated, MAJ(not a, b, c): the
+ * sum -c1 + c2 + c3 of three +-q/8 encodings is +-q/8 or +-3q/8 and its
+ * sign is the majority vote (no constant).  Two-input types ignore c3. */
+ORC_API int orc_gate_lincomb3(int type, int n, const uint32_t *c1, const uint32_t *c2, const uint32_t *c3,
+                              uint32_t *out)
+{
+    if (type != G_MAJNYY) return orc_gate_lincomb(type, n, c1, c2, out);
+    for (int x = 0; x <= n; x++) out[x] = c2[x] + c3[x] - c1[x];
+    return 0;
+}
+
 /* One gate bootstrap: lincomb -> blind rotation -> extract -> keyswitch. */
-ORC_API int orc_gate(const orc_ctx *c, int type, const uint32_t *c1, const uint32_t *c2, uint32_t *out)
+ORC_API int orc_gate3(const orc_ctx *c, int type, const uint32_t *c1, const uint32_t *c2, const uint32_t *c3,
+                      uint32_t *out)
 {
     int n = c->p.n, N = c->p.N;
     uint32_t *lin = (uint32_t *)malloc(sizeof(uint32_t) * (n + 1));
     uint32_t *acc = (uint32_t *)malloc(sizeof(uint32_t) * 2 * N);
     uint32_t *big = (uint32_t *)malloc(sizeof(uint32_t) * (N + 1));
-    int rc = orc_gate_lincomb(type, n, c1, c2, lin);
+    int rc = (type == G_MAJNYY && !c3) ? -1 : orc_gate_lincomb3(type, n, c1, c2, c3, lin);
     if (rc == 0) {
         orc_blind_rotate(c, lin, acc);
         orc_sample_extract(N, acc, big);
@@ -530,6 +542,11 @@ ORC_API int orc_gate(const orc_ctx *c, int type, const uint32_t *c1, const uint3
     free(acc);
     free(big);
     return rc;
+}
+
+ORC_API int orc_gate(const orc_ctx *c, int type, const uint32_t *c1, const uint32_t *c2, uint32_t *out)
+{
+    return orc_gate3(c, type, c1, c2, NULL, out);
 }
 
 /* Independent gates, one per thread. */
@@ -556,23 +573,26 @@ ORC_API void orc_not(int n, const uint32_t *in, uint32_t *out)
 /* payload bits (column-major, LSB first), then gate outputs in order.     */
 /* ------------------------------------------------------------------ */
 
-enum { P_EQ = 0, P_LT = 1, P_RANGE = 2 };
+enum { P_EQ = 0, P_LT = 1, P_RANGE = 2, P_LT_MAJ = 3, P_RANGE_MAJ = 4 };
 
 typedef struct {
-    int32_t *type, *a, *b; /* one entry per gate; gate g writes wire first_gate_wire + g */
+    int32_t *type, *a, *b, *c; /* one entry per gate (c = -1: two inputs); gate g writes wire first_gate_wire + g */
     int count, cap, next_wire;
 } netlist;
 
-static int nl_add(netlist *nl, int type, int a, int b)
+static int nl_add3(netlist *nl, int type, int a, int b, int c)
 {
     if (nl->type) {
         nl->type[nl->count] = type;
         nl->a[nl->count] = a;
         nl->b[nl->count] = b;
+        if (nl->c) nl->c[nl->count] = c;
     }
     nl->count++;
     return nl->next_wire++;
 }
+
+static int nl_add(netlist *nl, int type, int a, int b) { return nl_add3(nl, type, a, b, -1); }
 
 /* x_i = XNOR(c_i, k_i); then a pairwise AND tree: each round pairs (2j, 2j+1)
  * in order and moves a trailing odd element to the end of the next round. */
@@ -603,22 +623,36 @@ static int nl_lt(netlist *nl, int cbase, int kbase, int w)
     return lt;
 }
 
+/* Unsigned c < k as a majority chain (c < k over bits 0..i is "not c_i and
+ * k_i", or, when c_i = k_i, the result over bits 0..i-1; with bits this is
+ * the majority of not c_i, k_i and that result):
+ * lt_0 = (not c_0) and k_0;  lt_i = MAJ(not c_i, k_i, lt_{i-1}). */
+static int nl_lt_maj(netlist *nl, int cbase, int kbase, int w)
+{
+    int lt = nl_add(nl, G_ANDNY, cbase, kbase);
+    for (int i = 1; i < w; i++) lt = nl_add3(nl, G_MAJNYY, cbase + i, kbase + i, lt);
+    return lt;
+}
+
 /* Build the per-row netlist.  Returns the number of gates; fills the arrays
- * when non-null (each of capacity >= the count).  *match_wire receives the
- * wire of the match bit; mask gate outputs are the last n_payload*pw wires. */
-ORC_API int orc_netlist(int pred, int w, int n_payload, int pw, int32_t *type, int32_t *a, int32_t *b,
-                        int32_t *match_wire, int32_t *n_inputs)
+ * when non-null (each of capacity >= the count; c may be NULL for the
+ * two-input predicates).  *match_wire receives the wire of the match bit;
+ * mask gate outputs are the last n_payload*pw wires. */
+ORC_API int orc_netlist3(int pred, int w, int n_payload, int pw, int32_t *type, int32_t *a, int32_t *b,
+                         int32_t *c, int32_t *match_wire, int32_t *n_inputs)
 {
     if (w < 1 || w > 64 || pw < 0 || n_payload < 0) return -1;
-    int nconst = pred == P_RANGE ? 2 * w : w;
+    int range = pred == P_RANGE || pred == P_RANGE_MAJ;
+    int nconst = range ? 2 * w : w;
     int ninp = w + nconst + n_payload * pw;
-    netlist nl = {type, a, b, 0, 0, ninp};
+    netlist nl = {type, a, b, c, 0, 0, ninp};
     int m;
     if (pred == P_EQ) m = nl_eq(&nl, 0, w, w);
     else if (pred == P_LT) m = nl_lt(&nl, 0, w, w);
-    else if (pred == P_RANGE) {
-        int ge_lo = nl_lt(&nl, 0, w, w);
-        int lt_hi = nl_lt(&nl, 0, 2 * w, w);
+    else if (pred == P_LT_MAJ) m = nl_lt_maj(&nl, 0, w, w);
+    else if (range) {
+        int ge_lo = pred == P_RANGE ? nl_lt(&nl, 0, w, w) : nl_lt_maj(&nl, 0, w, w);
+        int lt_hi = pred == P_RANGE ? nl_lt(&nl, 0, 2 * w, w) : nl_lt_maj(&nl, 0, 2 * w, w);
         m = nl_add(&nl, G_ANDNY, ge_lo, lt_hi); /* not(c < lo) and (c < hi) */
     } else return -1;
     for (int p = 0; p < n_payload; p++)
@@ -626,6 +660,12 @@ ORC_API int orc_netlist(int pred, int w, int n_payload, int pw, int32_t *type, i
     if (match_wire) *match_wire = m;
     if (n_inputs) *n_inputs = ninp;
     return nl.count;
+}
+
+ORC_API int orc_netlist(int pred, int w, int n_payload, int pw, int32_t *type, int32_t *a, int32_t *b,
+                        int32_t *match_wire, int32_t *n_inputs)
+{
+    return orc_netlist3(pred, w, n_payload, pw, type, a, b, NULL, match_wire, n_inputs);
 }
 
 /* Plaintext evaluation of a gate type on bits (truth-table reference). */
@@ -646,20 +686,29 @@ ORC_API int orc_gate_plain(int type, int x, int y)
     return -1;
 }
 
+ORC_API int orc_gate_plain3(int type, int x, int y, int z)
+{
+    if (type == G_MAJNYY) return ((!x) + y + z) >= 2;
+    return orc_gate_plain(type, x, y);
+}
+
 /* Plaintext evaluation of the netlist on one row's input bits. */
 ORC_API int orc_netlist_eval_plain(int pred, int w, int n_payload, int pw, const uint8_t *inputs, uint8_t *wires_out)
 {
     int32_t m, ninp;
-    int g = orc_netlist(pred, w, n_payload, pw, NULL, NULL, NULL, &m, &ninp);
+    int g = orc_netlist3(pred, w, n_payload, pw, NULL, NULL, NULL, NULL, &m, &ninp);
     if (g < 0) return -1;
     int32_t *t = (int32_t *)malloc(sizeof(int32_t) * g), *a = (int32_t *)malloc(sizeof(int32_t) * g),
-            *b = (int32_t *)malloc(sizeof(int32_t) * g);
-    orc_netlist(pred, w, n_payload, pw, t, a, b, &m, &ninp);
+            *b = (int32_t *)malloc(sizeof(int32_t) * g), *c3 = (int32_t *)malloc(sizeof(int32_t) * g);
+    orc_netlist3(pred, w, n_payload, pw, t, a, b, c3, &m, &ninp);
     for (int i = 0; i < ninp; i++) wires_out[i] = inputs[i];
-    for (int k = 0; k < g; k++) wires_out[ninp + k] = (uint8_t)orc_gate_plain(t[k], wires_out[a[k]], wires_out[b[k]]);
+    for (int k = 0; k < g; k++)
+        wires_out[ninp + k] = (uint8_t)orc_gate_plain3(t[k], wires_out[a[k]], wires_out[b[k]],
+                                                       c3[k] >= 0 ? wires_out[c3[k]] : 0);
     free(t);
     free(a);
     free(b);
+    free(c3);
     return m;
 }
 
@@ -675,20 +724,22 @@ ORC_API int orc_scan(const orc_ctx *c, int pred, int w, const uint32_t *column, 
                      uint32_t *const *out_payloads, long long rows)
 {
     int32_t m, ninp;
-    int g = orc_netlist(pred, w, n_payload, pw, NULL, NULL, NULL, &m, &ninp);
+    int g = orc_netlist3(pred, w, n_payload, pw, NULL, NULL, NULL, NULL, &m, &ninp);
     if (g < 0) return -1;
     int32_t *t = (int32_t *)malloc(sizeof(int32_t) * g), *a = (int32_t *)malloc(sizeof(int32_t) * g),
-            *b = (int32_t *)malloc(sizeof(int32_t) * g), *depth = (int32_t *)malloc(sizeof(int32_t) * (ninp + g));
-    orc_netlist(pred, w, n_payload, pw, t, a, b, &m, &ninp);
+            *b = (int32_t *)malloc(sizeof(int32_t) * g), *c3 = (int32_t *)malloc(sizeof(int32_t) * g),
+            *depth = (int32_t *)malloc(sizeof(int32_t) * (ninp + g));
+    orc_netlist3(pred, w, n_payload, pw, t, a, b, c3, &m, &ninp);
     int maxd = 0;
     for (int i = 0; i < ninp; i++) depth[i] = 0;
     for (int k = 0; k < g; k++) {
-        int da = depth[a[k]], db = depth[b[k]];
-        depth[ninp + k] = 1 + (da > db ? da : db);
+        int d = depth[a[k]] > depth[b[k]] ? depth[a[k]] : depth[b[k]];
+        if (c3[k] >= 0 && depth[c3[k]] > d) d = depth[c3[k]];
+        depth[ninp + k] = 1 + d;
         if (depth[ninp + k] > maxd) maxd = depth[ninp + k];
     }
     size_t W = (size_t)c->p.n + 1, per_row = (size_t)(ninp + g) * W;
-    int nconst = pred == P_RANGE ? 2 * w : w;
+    int nconst = (pred == P_RANGE || pred == P_RANGE_MAJ) ? 2 * w : w;
     uint32_t *wires = (uint32_t *)malloc(sizeof(uint32_t) * per_row * (size_t)(rows > 0 ? rows : 1));
     for (long long row = 0; row < rows; row++) {
         uint32_t *wr = wires + (size_t)row * per_row;
@@ -705,7 +756,8 @@ ORC_API int orc_scan(const orc_ctx *c, int pred, int w, const uint32_t *column, 
             for (int k = 0; k < g; k++) {
                 if (depth[ninp + k] != d) continue;
                 uint32_t *wr = wires + (size_t)row * per_row;
-                bad |= orc_gate(c, t[k], wr + (size_t)a[k] * W, wr + (size_t)b[k] * W, wr + (size_t)(ninp + k) * W) != 0;
+                bad |= orc_gate3(c, t[k], wr + (size_t)a[k] * W, wr + (size_t)b[k] * W,
+                                 c3[k] >= 0 ? wr + (size_t)c3[k] * W : NULL, wr + (size_t)(ninp + k) * W) != 0;
             }
     }
     int first_mask = ninp + g - n_payload * pw;
@@ -720,6 +772,7 @@ ORC_API int orc_scan(const orc_ctx *c, int pred, int w, const uint32_t *column, 
     free(t);
     free(a);
     free(b);
+    free(c3);
     free(depth);
     return bad ? -1 : 0;
 }

@@ -25,10 +25,12 @@ constexpr int kKsDigits = (1 << kKsBaseBits) - 1;  // nonzero digit values
 constexpr int kKsRowWords = 640;  // n+1 padded to a multiple of 4 words (16 B)
 constexpr int kMaxN = 1024;  // largest LWE dimension the kernels take
 
-// One bootstrapped gate: inputs a, b and output pointer, all [n+1] words.
+// One bootstrapped gate: inputs a, b (and c for three-input gates, else
+// null) and output pointer, all [n+1] words.
 struct GateDesc {
   const uint32_t* a;
   const uint32_t* b;
+  const uint32_t* c;
   uint32_t* out;
   uint32_t type;
   uint32_t pad;
@@ -82,6 +84,7 @@ struct Ctx {
   size_t stage_cap = 0;
   Plan* plan = nullptr;
   void* prof = nullptr;          // kernel-timing events while profiling (kernels.cu)
+  void* capture_stream = nullptr;  // cudaStream_t used to capture scan graphs
   int sm_count = 0;
   std::mutex mu;
 };
@@ -97,7 +100,7 @@ struct Netlist {
   int n_inputs = 0;          // column bits, constant bits, payload bits
   int match_wire = -1;
   int first_mask_gate = 0;   // gates [first_mask_gate, count) are the payload masks
-  std::vector<int> type, a, b;  // gate g writes wire n_inputs + g
+  std::vector<int> type, a, b, c;  // gate g writes wire n_inputs + g; c = -1 for two inputs
   std::vector<int> level;       // 1-based level of each gate
   int levels = 0;
 };

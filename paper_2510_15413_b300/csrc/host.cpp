@@ -153,11 +153,13 @@ struct Builder {
   Netlist& nl;
   std::vector<int> wire_level;
   explicit Builder(Netlist& n) : nl(n), wire_level(n.n_inputs, 0) {}
-  int gate(int type, int a, int b) {
-    const int lv = 1 + std::max(wire_level[a], wire_level[b]);
+  int gate(int type, int a, int b, int c = -1) {
+    int lv = 1 + std::max(wire_level[a], wire_level[b]);
+    if (c >= 0) lv = std::max(lv, 1 + wire_level[c]);
     nl.type.push_back(type);
     nl.a.push_back(a);
     nl.b.push_back(b);
+    nl.c.push_back(c);
     nl.level.push_back(lv);
     nl.levels = std::max(nl.levels, lv);
     wire_level.push_back(lv);
@@ -189,25 +191,36 @@ struct Builder {
     }
     return lt;
   }
+  // c < k as a majority chain: less_0 = !c_0 & k_0;
+  // less_i = MAJ(!c_i, k_i, less_{i-1}) (same truth table, one gate per bit).
+  int less_maj(int c0, int k0, int w) {
+    int lt = gate(FSQL_ANDNY, c0, k0);
+    for (int i = 1; i < w; ++i) lt = gate(FSQL_MAJNYY, c0 + i, k0 + i, lt);
+    return lt;
+  }
 };
 
 }  // namespace
 
 bool build_netlist(uint32_t pred, uint32_t width, uint32_t n_payloads, uint32_t payload_width, Netlist* out) {
-  if (width < 1 || width > 64 || pred > FSQL_RANGE || n_payloads > 64 || payload_width > 64) return false;
+  if (width < 1 || width > 64 || pred > FSQL_RANGE_MAJ || n_payloads > 64 || payload_width > 64) return false;
   if (n_payloads > 0 && payload_width == 0) return false;
   Netlist nl;
   const int w = static_cast<int>(width);
-  const int nconst = pred == FSQL_RANGE ? 2 * w : w;
+  const bool range = pred == FSQL_RANGE || pred == FSQL_RANGE_MAJ;
+  const int nconst = range ? 2 * w : w;
   nl.n_inputs = w + nconst + static_cast<int>(n_payloads * payload_width);
   Builder b(nl);
   if (pred == FSQL_EQ) {
     nl.match_wire = b.equal(0, w, w);
   } else if (pred == FSQL_LT) {
     nl.match_wire = b.less(0, w, w);
+  } else if (pred == FSQL_LT_MAJ) {
+    nl.match_wire = b.less_maj(0, w, w);
   } else {
-    const int below_lo = b.less(0, w, w);
-    const int below_hi = b.less(0, 2 * w, w);
+    const bool maj = pred == FSQL_RANGE_MAJ;
+    const int below_lo = maj ? b.less_maj(0, w, w) : b.less(0, w, w);
+    const int below_hi = maj ? b.less_maj(0, 2 * w, w) : b.less(0, 2 * w, w);
     nl.match_wire = b.gate(FSQL_ANDNY, below_lo, below_hi);  // !(c < lo) & (c < hi)
   }
   nl.first_mask_gate = static_cast<int>(nl.type.size());

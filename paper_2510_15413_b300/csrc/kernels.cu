@@ -190,24 +190,26 @@ __device__ __forceinline__ void cp_async_wait() {
   asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
 }
 
-// Gate linear forms on the +-q/8 encoding: out = (0, .., 0, k) + ca*c1 + cb*c2.
+// Gate linear forms on the +-q/8 encoding:
+// out = (0, .., 0, k) + ca*c1 + cb*c2 + cc*c3.
 struct Lin {
   uint32_t k;
-  uint32_t ca, cb;
+  uint32_t ca, cb, cc;
 };
 __device__ __forceinline__ Lin gate_lin(uint32_t type) {
   const uint32_t E = 1u << 29, M = 0xFFFFFFFFu;  // q/8, -1
   switch (type) {
-    case FSQL_NAND: return {E, M, M};
-    case FSQL_AND: return {0u - E, 1u, 1u};
-    case FSQL_OR: return {E, 1u, 1u};
-    case FSQL_XOR: return {2u * E, 2u, 2u};
-    case FSQL_XNOR: return {0u - 2u * E, 0u - 2u, 0u - 2u};
-    case FSQL_NOR: return {0u - E, M, M};
-    case FSQL_ANDNY: return {0u - E, M, 1u};
-    case FSQL_ANDYN: return {0u - E, 1u, M};
-    case FSQL_ORNY: return {E, M, 1u};
-    default: return {E, 1u, M};  // FSQL_ORYN (types are validated on the host)
+    case FSQL_NAND: return {E, M, M, 0u};
+    case FSQL_AND: return {0u - E, 1u, 1u, 0u};
+    case FSQL_OR: return {E, 1u, 1u, 0u};
+    case FSQL_XOR: return {2u * E, 2u, 2u, 0u};
+    case FSQL_XNOR: return {0u - 2u * E, 0u - 2u, 0u - 2u, 0u};
+    case FSQL_NOR: return {0u - E, M, M, 0u};
+    case FSQL_ANDNY: return {0u - E, M, 1u, 0u};
+    case FSQL_ANDYN: return {0u - E, 1u, M, 0u};
+    case FSQL_ORNY: return {E, M, 1u, 0u};
+    case FSQL_MAJNYY: return {0u, M, 1u, 1u};  // majority of (not a, b, c): sign of -a + b + c
+    default: return {E, 1u, M, 0u};  // FSQL_ORYN (other values compute ORYN)
   }
 }
 
@@ -252,6 +254,7 @@ __global__ void make_desc_kernel(GateDesc* __restrict__ desc, const uint8_t* __r
   GateDesc d;
   d.a = a + static_cast<size_t>(g) * words;
   d.b = b + static_cast<size_t>(g) * words;
+  d.c = nullptr;
   d.out = out ? out + static_cast<size_t>(g) * words : nullptr;
   d.type = types[g];
   d.pad = 0;
@@ -312,8 +315,10 @@ __global__ void __launch_bounds__(G * kGroup, 1)
       const GateDesc d = desc[gi];
       const Lin lin = gate_lin(d.type);
       // linear combination and modulus switch q -> 2N (round half up)
+      const uint32_t* c3 = lin.cc ? d.c : nullptr;  // a missing third input counts as zero
       for (int x = t; x <= n; x += kGroup) {
         uint32_t v = lin.ca * d.a[x] + lin.cb * d.b[x];
+        if (c3) v += lin.cc * c3[x];
         if (x == n) v += lin.k;
         const uint32_t ms = ((v + (1u << 20)) >> 21) & (2 * kN - 1);
         if (x < n) abar[x] = static_cast<uint16_t>(ms);
@@ -534,7 +539,7 @@ void scan_descriptors(const Netlist& nl, const ScanIO& io, GateDesc* out, std::v
   for (int g = 0; g < nl.first_mask_gate; ++g)
     if (nl.n_inputs + g != nl.match_wire) scratch_index[g] = n_int++;
   const int w = static_cast<int>(io.width);
-  const int nconst = io.pred == FSQL_RANGE ? 2 * w : w;
+  const int nconst = (io.pred == FSQL_RANGE || io.pred == FSQL_RANGE_MAJ) ? 2 * w : w;
   const int pw = static_cast<int>(io.payload_width);
   auto gate_out = [&](int g, size_t row) -> uint32_t* {
     if (g >= nl.first_mask_gate) {
@@ -563,6 +568,7 @@ void scan_descriptors(const Netlist& nl, const ScanIO& io, GateDesc* out, std::v
         GateDesc& d = out[pos++];
         d.a = wire_ptr(nl.a[g], row);
         d.b = wire_ptr(nl.b[g], row);
+        d.c = nl.c[g] >= 0 ? wire_ptr(nl.c[g], row) : nullptr;
         d.out = gate_out(g, row);
         d.type = static_cast<uint32_t>(nl.type[g]);
         d.pad = 0;
@@ -587,6 +593,15 @@ struct Plan {
   // plan
   std::vector<size_t> level_offset;  // descriptors of level L: [level_offset[L], level_offset[L+1])
   size_t total = 0;
+  // the plan's level launches captured as a CUDA graph (rebuilt if the
+  // context's descriptor or sample buffers move or its launch shape changes)
+  cudaGraphExec_t graph = nullptr;
+  const GateDesc* graph_desc = nullptr;
+  const uint32_t* graph_big = nullptr;
+  int graph_br_gates = 0;
+  ~Plan() {
+    if (graph) cudaGraphExecDestroy(graph);
+  }
 };
 
 
@@ -702,6 +717,8 @@ void device_free(Ctx& c) {
   cudaFree(c.d_stage);
   if (c.h_desc) cudaFreeHost(c.h_desc);
   if (c.desc_event) cudaEventDestroy(static_cast<cudaEvent_t>(c.desc_event));
+  if (c.capture_stream) cudaStreamDestroy(static_cast<cudaStream_t>(c.capture_stream));
+  c.capture_stream = nullptr;
   delete static_cast<Profile*>(c.prof);
   c.prof = nullptr;
   delete c.plan;
@@ -828,7 +845,7 @@ int launch_gates(Ctx& c, const GateDesc* d_desc, size_t count, uint32_t* d_big, 
 // Scratch of fsql_gate_batch_noalloc: the extracted samples between the
 // blind-rotation and keyswitch kernels and the gate descriptors, for at most
 // kNoAllocMaxGates gates.  These arrays live in the library's device image,
-// so every GPU that loads the library holds them (4.0 MiB + 32 KiB) until the
+// so every GPU that loads the library holds them (4.0 MiB + 40 KiB) until the
 // process exits, and every call of the entry point on that GPU reuses them.
 namespace fsql {
 constexpr size_t kNoAllocMaxGates = 1024;
@@ -1000,7 +1017,7 @@ int validate_scan(Ctx* c, const uint32_t* column, size_t rows, uint32_t width, u
   if (rows == 0) return FSQL_OK;
   if (!column || !cst || !match) return arg_error("null column, constant or match pointer");
   if (width < 1 || width > 64) return arg_error("width must be in [1, 64]");
-  if (pred > FSQL_RANGE) return arg_error("unknown predicate");
+  if (pred > FSQL_RANGE_MAJ) return arg_error("unknown predicate");
   if (n_payloads > 64 || (n_payloads && (!payloads || !outs || payload_width < 1 || payload_width > 64)))
     return arg_error("bad payload arguments");
   for (uint32_t q = 0; q < n_payloads; ++q)
@@ -1109,10 +1126,50 @@ int fsql_scan_select(fsql_ctx* ctx, const uint32_t* d_column, size_t rows, uint3
     }
     return FSQL_OK;
   }
-  for (size_t L = 0; L + 1 < pl.level_offset.size(); ++L) {
-    rc = fsql::launch_gates(*c, c->d_desc + pl.level_offset[L], pl.level_offset[L + 1] - pl.level_offset[L],
-                            c->d_big, stream);
-    if (rc) return rc;
+  auto launch_levels = [&](void* st) -> int {
+    for (size_t L = 0; L + 1 < pl.level_offset.size(); ++L) {
+      const int r = fsql::launch_gates(*c, c->d_desc + pl.level_offset[L],
+                                       pl.level_offset[L + 1] - pl.level_offset[L], c->d_big, st);
+      if (r) return r;
+    }
+    return FSQL_OK;
+  };
+  const auto* prof = static_cast<const fsql::Profile*>(c->prof);
+  if (prof && prof->recording) return launch_levels(stream);  // per-launch events need plain launches
+  // CUDA graph of the whole level sequence, captured once per plan on the
+  // context's capture stream and replayed on the caller's stream
+  fsql::Plan& mp = *c->plan;
+  if (!mp.graph || mp.graph_desc != c->d_desc || mp.graph_big != c->d_big || mp.graph_br_gates != c->br_gates) {
+    if (mp.graph) cudaGraphExecDestroy(mp.graph);
+    mp.graph = nullptr;
+    cudaStream_t cs = static_cast<cudaStream_t>(c->capture_stream);
+    if (!cs) {
+      if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) return launch_levels(stream);
+      c->capture_stream = cs;
+    }
+    cudaGraph_t g = nullptr;
+    if (cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return launch_levels(stream);
+    rc = launch_levels(cs);
+    const cudaError_t ec = cudaStreamEndCapture(cs, &g);
+    if (rc || ec != cudaSuccess || !g) {
+      if (g) cudaGraphDestroy(g);
+      cudaGetLastError();
+      return rc ? rc : launch_levels(stream);
+    }
+    const cudaError_t ei = cudaGraphInstantiate(&mp.graph, g, 0);
+    cudaGraphDestroy(g);
+    if (ei != cudaSuccess) {
+      mp.graph = nullptr;
+      cudaGetLastError();
+      return launch_levels(stream);
+    }
+    mp.graph_desc = c->d_desc;
+    mp.graph_big = c->d_big;
+    mp.graph_br_gates = c->br_gates;
+  }
+  if (cudaGraphLaunch(mp.graph, static_cast<cudaStream_t>(stream)) != cudaSuccess) {
+    fsql::set_error("scan graph launch failed");
+    return FSQL_ERR_CUDA;
   }
   return FSQL_OK;
 }
@@ -1128,7 +1185,7 @@ int fsql_scan_select_host(fsql_ctx* ctx, const uint32_t* h_column, size_t rows, 
   if (rows == 0) return FSQL_OK;
   const size_t W = c->p.n + 1;
   const size_t col_w = rows * width * W;
-  const size_t cst_w = (pred == FSQL_RANGE ? 2 : 1) * static_cast<size_t>(width) * W;
+  const size_t cst_w = ((pred == FSQL_RANGE || pred == FSQL_RANGE_MAJ) ? 2 : 1) * static_cast<size_t>(width) * W;
   const size_t pay_w = rows * static_cast<size_t>(payload_width) * W;
   const size_t total = col_w + cst_w + 2 * n_payloads * pay_w + rows * W;
   {

@@ -15,8 +15,9 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libfhesql.so")
 
 FSQL_OK, FSQL_ERR_ARG, FSQL_ERR_OOM, FSQL_ERR_CUDA, FSQL_ERR_TIMEOUT, FSQL_ERR_ADMISSION, FSQL_ERR_UNSUPPORTED = range(7)
-GATES = {"NAND": 0, "AND": 1, "OR": 2, "XOR": 3, "XNOR": 4, "NOR": 5, "ANDNY": 6, "ANDYN": 7, "ORNY": 8, "ORYN": 9}
-FSQL_EQ, FSQL_LT, FSQL_RANGE = 0, 1, 2
+GATES = {"NAND": 0, "AND": 1, "OR": 2, "XOR": 3, "XNOR": 4, "NOR": 5, "ANDNY": 6, "ANDYN": 7, "ORNY": 8, "ORYN": 9,
+         "MAJNYY": 10}
+FSQL_EQ, FSQL_LT, FSQL_RANGE, FSQL_LT_MAJ, FSQL_RANGE_MAJ = 0, 1, 2, 3, 4
 FSQL_ENGINE_DEFAULT, FSQL_ENGINE_GOLDILOCKS, FSQL_ENGINE_DUAL_PRIME = -1, 0, 1
 ENGINES = {"default": -1, "goldilocks": 0, "dual_prime": 1}
 

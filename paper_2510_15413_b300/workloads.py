@@ -24,7 +24,7 @@ from dataclasses import dataclass, field
 import numpy as np
 
 STREAM_COLUMN, STREAM_PAYLOAD, STREAM_CONST, STREAM_GATES = 5, 6, 7, 8
-PRED_EQ, PRED_LT, PRED_RANGE = 0, 1, 2
+PRED_EQ, PRED_LT, PRED_RANGE, PRED_LT_MAJ, PRED_RANGE_MAJ = 0, 1, 2, 3, 4
 MICRO_GATES = (0, 1, 2, 3, 4)  # NAND, AND, OR, XOR, XNOR
 
 
@@ -57,7 +57,7 @@ class Table:
         c = self.column
         if self.pred == PRED_EQ:
             m = c == np.uint64(self.consts[0])
-        elif self.pred == PRED_LT:
+        elif self.pred in (PRED_LT, PRED_LT_MAJ):
             m = c < np.uint64(self.consts[0])
         else:
             m = (c >= np.uint64(self.consts[0])) & (c < np.uint64(self.consts[1]))
@@ -66,7 +66,8 @@ class Table:
     @property
     def gates_per_row(self) -> int:
         w = self.width
-        pred = {PRED_EQ: 2 * w - 1, PRED_LT: 4 * w - 3, PRED_RANGE: 2 * (4 * w - 3) + 1}[self.pred]
+        pred = {PRED_EQ: 2 * w - 1, PRED_LT: 4 * w - 3, PRED_RANGE: 2 * (4 * w - 3) + 1,
+                PRED_LT_MAJ: w, PRED_RANGE_MAJ: 2 * w + 1}[self.pred]
         return pred + len(self.payloads) * self.payload_width
 
 
@@ -75,6 +76,13 @@ def _rng(seed: int, purpose: int) -> np.random.Generator:
 
 
 def table(name: str, seed: int = 1, rows: int | None = None) -> Table:
+    """A named workload table; the suffix "maj" gives the same table with the
+    majority-chain comparator (LT_MAJ / RANGE_MAJ) instead of the ripple one."""
+    if name.endswith("maj"):
+        t = table(name[:-3], seed, rows)
+        t.pred = {PRED_LT: PRED_LT_MAJ, PRED_RANGE: PRED_RANGE_MAJ}[t.pred]
+        t.name = name
+        return t
     g = _rng(seed, 1)
     if name == "eq4x16":
         r = rows or 16

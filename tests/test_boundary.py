@@ -72,16 +72,18 @@ def test_encryption_equals_oracle_encryption():
 
 
 def _oracle_levels(pred, w, npay, pw):
-    t, a, b, m, ninp = O.netlist(pred, w, npay, pw)
+    t, a, b, c, m, ninp = O.netlist3(pred, w, npay, pw)
     depth = [0] * ninp
     for k in range(t.size):
-        depth.append(1 + max(depth[a[k]], depth[b[k]]))
+        depth.append(1 + max(depth[a[k]], depth[b[k]], depth[c[k]] if c[k] >= 0 else 0))
     d = np.array(depth[ninp:])
     return int(t.size), [int((d == L).sum()) for L in range(1, d.max() + 1)]
 
 
 @pytest.mark.parametrize("shape", [(WL.PRED_EQ, 4, 1, 4), (WL.PRED_EQ, 32, 1, 32), (WL.PRED_LT, 8, 1, 8),
-                                   (WL.PRED_RANGE, 16, 2, 16), (WL.PRED_EQ, 1, 0, 0), (WL.PRED_RANGE, 3, 3, 5)])
+                                   (WL.PRED_RANGE, 16, 2, 16), (WL.PRED_EQ, 1, 0, 0), (WL.PRED_RANGE, 3, 3, 5),
+                                   (WL.PRED_LT_MAJ, 8, 1, 8), (WL.PRED_RANGE_MAJ, 16, 2, 16),
+                                   (WL.PRED_RANGE_MAJ, 1, 1, 1)])
 def test_scheduler_levels_equal_oracle_netlist_depths(shape):
     assert F.plan_info(*shape) == _oracle_levels(*shape)
 
@@ -94,6 +96,8 @@ def test_scheduler_known_level_widths():
     assert g * 4096 == 389120 and [4096 * x for x in widths] == [131072, 65536, 32768, 16384, 8192, 4096, 131072]
     g, widths = F.plan_info(WL.PRED_RANGE, 16, 2, 16)
     assert g * 65536 == 10158080 and widths[0] * 65536 == 65536 * 62
+    g, widths = F.plan_info(WL.PRED_RANGE_MAJ, 16, 2, 16)
+    assert g == 65 and WL.table("range16x65536maj").gates_per_row == 65
 
 
 def test_argument_errors_are_codes_not_crashes():

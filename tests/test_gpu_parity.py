@@ -169,7 +169,8 @@ def encrypt_both(ctx, o, t):
     return lib_ct, orc_ct
 
 
-@pytest.mark.parametrize("name,rows", [("eq4x16", 16), ("lt8x64", 5), ("range4x16", 6)])
+@pytest.mark.parametrize("name,rows", [("eq4x16", 16), ("lt8x64", 5), ("range4x16", 6), ("lt8x64maj", 6),
+                                       ("range4x16maj", 7)])
 def test_scan_small_tables_bit_exact(env, name, rows):
     ctx, o = env
     t = WL.table(name, seed=3, rows=rows)
@@ -180,6 +181,26 @@ def test_scan_small_tables_bit_exact(env, name, rows):
     for a, b in zip(outs, oouts):
         assert np.array_equal(a.reshape(b.shape), b)
     check_plaintext(ctx, t, match, outs)
+
+
+def test_scan_graph_replay_is_stable(env):
+    """The second scan on the same buffers replays the captured launch graph."""
+    ctx, _ = env
+    t = WL.table("range4x16maj", seed=5, rows=4)
+    col, cst, pays = WL.encrypt_table(ctx, t)
+    dcol, dcst, dp = dev(col.view(np.int32)), dev(cst.view(np.int32)), [dev(p.view(np.int32)) for p in pays]
+    match = torch.zeros((t.rows, ctx.words), dtype=torch.int32, device="cuda")
+    outs = [torch.zeros((t.rows, t.payload_width, ctx.words), dtype=torch.int32, device="cuda") for _ in pays]
+    results = []
+    for _ in range(3):
+        match.zero_()
+        for o_ in outs:
+            o_.zero_()
+        ctx.scan_select(dcol, t.rows, t.width, t.pred, dcst, dp, t.payload_width, match, outs)
+        results.append((host(match).copy(), [host(o_).copy() for o_ in outs]))
+    for m, o in results[1:]:
+        assert np.array_equal(m, results[0][0]) and all(np.array_equal(a, b) for a, b in zip(o, results[0][1]))
+    check_plaintext(ctx, t, results[0][0].view(np.uint32), [x.view(np.uint32) for x in results[0][1]])
 
 
 def test_scan_per_gate_and_host_paths_equal_batched(env):

@@ -346,19 +346,46 @@ def test_netlist_gate_counts_match_workload_definitions():
             assert int((t == O.GATES["AND"]).sum()) == int(nand)
 
 
-@pytest.mark.parametrize("pred", [O.P_EQ, O.P_LT, O.P_RANGE])
+def test_majority_gate_plain_and_counts():
+    for x in (0, 1):
+        for y in (0, 1):
+            for z in (0, 1):
+                assert O.gate_plain3(O.GATES["MAJNYY"], x, y, z) == int((1 - x) + y + z >= 2)
+    # a w-bit majority comparator is w gates (one ANDNY, w-1 majorities) instead of 4w-3
+    t, a, b, c, m, ninp = O.netlist3(O.P_LT_MAJ, 16)
+    assert t.size == 16 and (t == O.GATES["MAJNYY"]).sum() == 15 and (c >= 0).sum() == 15
+    t, *_ = O.netlist3(O.P_RANGE_MAJ, 16, 2, 16)
+    assert t.size == 16 + 16 + 1 + 32  # vs 155 with ripple comparators
+
+
+@pytest.mark.parametrize("which", ["toy", "real"])
+def test_majority_gate_truth_table_encrypted(which, toy_oracle, real_oracle):
+    o = toy_oracle if which == "toy" else real_oracle
+    combos = [(x, y, z) for x in (0, 1) for y in (0, 1) for z in (0, 1)]
+    if which == "real":
+        combos = combos[::3]
+    cts = o.encrypt_bits(np.array([v for cmb in combos for v in cmb], np.uint8), stream=33).reshape(-1, 3, o.n + 1)
+    for (x, y, z), ct in zip(combos, cts):
+        out = o.gate3(O.GATES["MAJNYY"], ct[0], ct[1], ct[2])
+        assert o.decrypt_bits(out)[0] == int((1 - x) + y + z >= 2)
+        assert abs(abs(int(centered(o.phase(out))[0])) - E8) < (1 << 27)
+
+
+@pytest.mark.parametrize("pred", [O.P_EQ, O.P_LT, O.P_RANGE, O.P_LT_MAJ, O.P_RANGE_MAJ])
 @pytest.mark.parametrize("w", [1, 2, 3, 4])
 def test_netlist_brute_force(pred, w):
+    rng = pred in (O.P_RANGE, O.P_RANGE_MAJ)
     for c in range(1 << w):
         for k in range(1 << w):
-            for k2 in (range(1 << w) if pred == O.P_RANGE else [None]):
+            for k2 in (range(1 << w) if rng else [None]):
                 pay = (c * 5 + 3) % (1 << w)
                 inp = [(c >> i) & 1 for i in range(w)] + [(k >> i) & 1 for i in range(w)]
-                if pred == O.P_RANGE:
+                if rng:
                     inp += [(k2 >> i) & 1 for i in range(w)]
                 inp += [(pay >> i) & 1 for i in range(w)]
                 wires, m = O.netlist_eval_plain(pred, w, 1, w, np.array(inp, np.uint8))
-                want = {O.P_EQ: c == k, O.P_LT: c < k, O.P_RANGE: k <= c < (k2 or 0)}[pred]
+                want = {O.P_EQ: c == k, O.P_LT: c < k, O.P_LT_MAJ: c < k,
+                        O.P_RANGE: rng and k <= c < (k2 or 0), O.P_RANGE_MAJ: rng and k <= c < (k2 or 0)}[pred]
                 assert wires[m] == int(want)
                 out = wires[-w:]
                 assert int(sum(int(out[i]) << i for i in range(w))) == (pay if want else 0)
@@ -367,14 +394,14 @@ def test_netlist_brute_force(pred, w):
 # --------------------------------------------------------------------------
 # the scan end to end (toy parameters) against the plaintext SQL answer
 # --------------------------------------------------------------------------
-@pytest.mark.parametrize("pred", [O.P_EQ, O.P_LT, O.P_RANGE])
+@pytest.mark.parametrize("pred", [O.P_EQ, O.P_LT, O.P_RANGE, O.P_LT_MAJ, O.P_RANGE_MAJ])
 def test_scan_toy_matches_plaintext_sql(pred, toy_oracle):
     o = toy_oracle
     rng = np.random.default_rng(100 + pred)
     w, rows = 4, 16
     c = rng.integers(0, 16, rows)
     pay = rng.integers(0, 16, rows)
-    if pred == O.P_RANGE:
+    if pred in (O.P_RANGE, O.P_RANGE_MAJ):
         lo, hi = 3, 11
         kbits = [(lo >> i) & 1 for i in range(w)] + [(hi >> i) & 1 for i in range(w)]
     else:
@@ -387,9 +414,10 @@ def test_scan_toy_matches_plaintext_sql(pred, toy_oracle):
     mbits = o.decrypt_bits(match)
     obits = o.decrypt_bits(outp.reshape(-1, o.n + 1)).reshape(rows, w)
     for r in range(rows):
-        want = {O.P_EQ: c[r] == k if pred != O.P_RANGE else None,
-                O.P_LT: c[r] < k if pred != O.P_RANGE else None,
-                O.P_RANGE: lo <= c[r] < hi if pred == O.P_RANGE else None}[pred]
+        if pred in (O.P_RANGE, O.P_RANGE_MAJ):
+            want = lo <= c[r] < hi
+        else:
+            want = c[r] == k if pred == O.P_EQ else c[r] < k
         assert mbits[r] == int(want)
         got = int(sum(int(obits[r, i]) << i for i in range(w)))
         assert got == (int(pay[r]) if want else 0)
