@@ -79,6 +79,12 @@ def lib():
         L.orc_netlist_eval_plain.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int, u8p, u8p]
         L.orc_scan.argtypes = [C.c_void_p, C.c_int, C.c_int, u32p, u32p, C.c_int, C.c_int,
                                C.POINTER(C.c_void_p), u32p, C.POINTER(C.c_void_p), C.c_longlong]
+        L.orc_netlist_plain.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int, C.c_uint64, C.c_uint64, C.c_void_p,
+                                        C.c_void_p, C.c_void_p, C.POINTER(C.c_int32), C.c_void_p,
+                                        C.POINTER(C.c_int32)]
+        L.orc_netlist_plain_eval.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int, C.c_uint64, C.c_uint64, u8p, u8p]
+        L.orc_scan_plain.argtypes = [C.c_void_p, C.c_int, C.c_int, u32p, C.c_uint64, C.c_uint64, C.c_int, C.c_int,
+                                     C.POINTER(C.c_void_p), u32p, C.POINTER(C.c_void_p), C.c_longlong]
         L.orc_set_threads.argtypes = [C.c_int]
         L.orc_max_threads.restype = C.c_int
         _lib = L
@@ -185,6 +191,41 @@ def netlist_eval_plain(pred: int, w: int, n_payload: int, pw: int, inputs):
     wires = np.zeros(ninp + t.size, np.uint8)
     lib().orc_netlist_eval_plain(pred, w, n_payload, pw, inp, wires)
     return wires, m
+
+
+LIT_FALSE, LIT_TRUE = -1, -2
+
+
+def _plain_consts(consts):
+    k = [int(v) for v in consts] + [0, 0]
+    return k[0], k[1]
+
+
+def netlist_plain(pred: int, w: int, n_payload: int, pw: int, consts):
+    """Netlist for plaintext query constants (k,) or (lo, hi): (types, a, b,
+    match literal, output literals, n_inputs).  A literal is 2*wire + negated,
+    or LIT_FALSE / LIT_TRUE; wires are column bits, payload bits, gate outputs."""
+    k0, k1 = _plain_consts(consts)
+    m, ninp = C.c_int32(), C.c_int32()
+    g = lib().orc_netlist_plain(pred, w, n_payload, pw, k0, k1, None, None, None, C.byref(m), None, C.byref(ninp))
+    if g < 0:
+        raise ValueError("bad netlist request")
+    t, a, b = (np.zeros(max(g, 1), np.int32) for _ in range(3))
+    ol = np.zeros(max(1, n_payload * pw), np.int32)
+    lib().orc_netlist_plain(pred, w, n_payload, pw, k0, k1, t.ctypes.data, a.ctypes.data, b.ctypes.data,
+                            C.byref(m), ol.ctypes.data, C.byref(ninp))
+    return t[:g], a[:g], b[:g], int(m.value), ol[:n_payload * pw], int(ninp.value)
+
+
+def netlist_plain_eval(pred: int, w: int, n_payload: int, pw: int, consts, inputs):
+    """(match bit, masked payload bits) of one row under plaintext constants."""
+    k0, k1 = _plain_consts(consts)
+    inp = np.ascontiguousarray(inputs, dtype=np.uint8)
+    assert inp.size == w + n_payload * pw
+    out = np.zeros(1 + n_payload * pw, np.uint8)
+    if lib().orc_netlist_plain_eval(pred, w, n_payload, pw, k0, k1, inp, out) < 0:
+        raise ValueError("bad netlist request")
+    return int(out[0]), out[1:]
 
 
 class Oracle:
@@ -330,6 +371,23 @@ class Oracle:
         pin = (C.c_void_p * max(1, len(pays)))(*[p.ctypes.data for p in pays])
         pout = (C.c_void_p * max(1, len(outs)))(*[o.ctypes.data for o in outs])
         rc = lib().orc_scan(self._h, pred, w, column, consts, len(pays), pw, pin, match, pout, rows)
+        if rc != 0:
+            raise ValueError("scan failed")
+        return match, outs
+
+    def scan_plain(self, pred: int, w: int, column, consts, payloads, pw: int):
+        """Scan with plaintext query constants (k,) or (lo, hi): returns
+        (match [rows, n+1], [payload outs [rows, pw, n+1]])."""
+        W = self.n + 1
+        column = _u32(column).reshape(-1, w, W)
+        rows = column.shape[0]
+        k0, k1 = _plain_consts(consts)
+        pays = [_u32(p).reshape(rows, pw, W) for p in payloads]
+        match = np.zeros((rows, W), np.uint32)
+        outs = [np.zeros((rows, pw, W), np.uint32) for _ in pays]
+        pin = (C.c_void_p * max(1, len(pays)))(*[p.ctypes.data for p in pays])
+        pout = (C.c_void_p * max(1, len(outs)))(*[o.ctypes.data for o in outs])
+        rc = lib().orc_scan_plain(self._h, pred, w, column, k0, k1, len(pays), pw, pin, match, pout, rows)
         if rc != 0:
             raise ValueError("scan failed")
         return match, outs

@@ -777,6 +777,210 @@ ORC_API int orc_scan(const orc_ctx *c, int pred, int w, const uint32_t *column, 
     return bad ? -1 : 0;
 }
 
+/* ------------------------------------------------------------------ */
+/* Plaintext query constants (§4.2 lets an operand of a comparison be a    */
+/* plaintext; §6.1 D times trivially encrypted operands).  The server then */
+/* knows every constant bit, so a gate with a known input reduces: XNOR    */
+/* with a known bit is the column bit or its negation (no bootstrap), and  */
+/* a comparator step with known k_i is one AND (k_i = 0) or one OR         */
+/* (k_i = 1) of (not c_i) with the running result, or nothing when that    */
+/* result is already a known bit.  Values are literals: 2*wire + negated,  */
+/* or LIT_FALSE / LIT_TRUE for a known bit.  Every gate still writes a     */
+/* plain (non-negated) wire; negation is folded into the gate type.        */
+/* Wires: column bits 0..w-1, then payload bits, then gate outputs.        */
+/* Outputs that are not gate outputs are materialised without bootstrap:   */
+/* a copy or negation (every word negated) of an input ciphertext, or the  */
+/* trivial ciphertext (0, .., 0, +-q/8) of a known bit.                    */
+/* ------------------------------------------------------------------ */
+
+#define LIT_FALSE (-1)
+#define LIT_TRUE (-2)
+
+static int lit_not(int u)
+{
+    if (u == LIT_FALSE) return LIT_TRUE;
+    if (u == LIT_TRUE) return LIT_FALSE;
+    return u ^ 1;
+}
+
+/* u and v; with two wires the gate type absorbs the negations */
+static int lit_and(netlist *nl, int u, int v)
+{
+    static const int type[4] = {G_AND, G_ANDNY, G_ANDYN, G_NOR}; /* [neg u + 2 neg v] */
+    if (u == LIT_FALSE || v == LIT_FALSE) return LIT_FALSE;
+    if (u == LIT_TRUE) return v;
+    if (v == LIT_TRUE) return u;
+    return 2 * nl_add(nl, type[(u & 1) + 2 * (v & 1)], u >> 1, v >> 1);
+}
+
+/* u or v */
+static int lit_or(netlist *nl, int u, int v)
+{
+    static const int type[4] = {G_OR, G_ORNY, G_ORYN, G_NAND}; /* [neg u + 2 neg v] */
+    if (u == LIT_TRUE || v == LIT_TRUE) return LIT_TRUE;
+    if (u == LIT_FALSE) return v;
+    if (v == LIT_FALSE) return u;
+    return 2 * nl_add(nl, type[(u & 1) + 2 * (v & 1)], u >> 1, v >> 1);
+}
+
+/* c == k: the literal c_i (k_i = 1) or not c_i (k_i = 0) per bit, then the
+ * same pairwise AND tree as the encrypted-constant netlist. */
+static int nlp_eq(netlist *nl, int cbase, int w, uint64_t k)
+{
+    int list[64], m = w;
+    for (int i = 0; i < w; i++) list[i] = 2 * (cbase + i) + (int)(((k >> i) & 1) ^ 1);
+    while (m > 1) {
+        int nm = 0;
+        for (int j = 0; j + 1 < m; j += 2) list[nm++] = lit_and(nl, list[j], list[j + 1]);
+        if (m & 1) list[nm++] = list[m - 1];
+        m = nm;
+    }
+    return list[0];
+}
+
+/* c < k: lt_0 = (not c_0) and k_0; lt_i = MAJ(not c_i, k_i, lt_{i-1}), which
+ * is (not c_i) or lt_{i-1} for k_i = 1 and (not c_i) and lt_{i-1} for k_i = 0
+ * (the ripple form reduces to the same two cases). */
+static int nlp_lt(netlist *nl, int cbase, int w, uint64_t k)
+{
+    int lt = (k & 1) ? 2 * cbase + 1 : LIT_FALSE;
+    for (int i = 1; i < w; i++) {
+        int nc = 2 * (cbase + i) + 1;
+        lt = ((k >> i) & 1) ? lit_or(nl, nc, lt) : lit_and(nl, nc, lt);
+    }
+    return lt;
+}
+
+/* Netlist for plaintext constants k0 (EQ, LT) or lo = k0, hi = k1 (RANGE).
+ * pred: P_EQ, P_LT or P_RANGE (the majority forms are the same here).
+ * Returns the gate count; *match_lit gets the match literal and out_lits
+ * (capacity n_payload*pw, may be NULL) the literal of every masked payload
+ * bit; when the match is a wire, the mask gates are the last n_payload*pw
+ * gates. */
+ORC_API int orc_netlist_plain(int pred, int w, int n_payload, int pw, uint64_t k0, uint64_t k1, int32_t *type,
+                              int32_t *a, int32_t *b, int32_t *match_lit, int32_t *out_lits, int32_t *n_inputs)
+{
+    if (w < 1 || w > 64 || pw < 0 || n_payload < 0) return -1;
+    int ninp = w + n_payload * pw;
+    netlist nl = {type, a, b, NULL, 0, 0, ninp};
+    int m;
+    if (pred == P_EQ) m = nlp_eq(&nl, 0, w, k0);
+    else if (pred == P_LT || pred == P_LT_MAJ) m = nlp_lt(&nl, 0, w, k0);
+    else if (pred == P_RANGE || pred == P_RANGE_MAJ) {
+        int below_lo = nlp_lt(&nl, 0, w, k0);
+        int below_hi = nlp_lt(&nl, 0, w, k1);
+        m = lit_and(&nl, lit_not(below_lo), below_hi);
+    } else return -1;
+    for (int p = 0; p < n_payload; p++)
+        for (int bit = 0; bit < pw; bit++) {
+            int o = lit_and(&nl, m, 2 * (w + p * pw + bit));
+            if (out_lits) out_lits[p * pw + bit] = o;
+        }
+    if (match_lit) *match_lit = m;
+    if (n_inputs) *n_inputs = ninp;
+    return nl.count;
+}
+
+static int lit_value(const uint8_t *wires, int lit)
+{
+    if (lit == LIT_FALSE) return 0;
+    if (lit == LIT_TRUE) return 1;
+    return wires[lit >> 1] ^ (lit & 1);
+}
+
+/* Plaintext evaluation: inputs = column bits then payload bits of one row;
+ * outputs = match bit then the masked payload bits. */
+ORC_API int orc_netlist_plain_eval(int pred, int w, int n_payload, int pw, uint64_t k0, uint64_t k1,
+                                   const uint8_t *inputs, uint8_t *outputs)
+{
+    int32_t m, ninp;
+    int g = orc_netlist_plain(pred, w, n_payload, pw, k0, k1, NULL, NULL, NULL, &m, NULL, &ninp);
+    if (g < 0) return -1;
+    int np = n_payload * pw;
+    int32_t *t = (int32_t *)malloc(sizeof(int32_t) * (g + 1)), *a = (int32_t *)malloc(sizeof(int32_t) * (g + 1)),
+            *b = (int32_t *)malloc(sizeof(int32_t) * (g + 1)), *ol = (int32_t *)malloc(sizeof(int32_t) * (np + 1));
+    uint8_t *wires = (uint8_t *)malloc((size_t)(ninp + g + 1));
+    orc_netlist_plain(pred, w, n_payload, pw, k0, k1, t, a, b, &m, ol, &ninp);
+    for (int i = 0; i < ninp; i++) wires[i] = inputs[i];
+    for (int k = 0; k < g; k++) wires[ninp + k] = (uint8_t)orc_gate_plain(t[k], wires[a[k]], wires[b[k]]);
+    outputs[0] = (uint8_t)lit_value(wires, m);
+    for (int i = 0; i < np; i++) outputs[1 + i] = (uint8_t)lit_value(wires, ol[i]);
+    free(t);
+    free(a);
+    free(b);
+    free(ol);
+    free(wires);
+    return g;
+}
+
+/* ciphertext of a literal: copy, negation, or trivial encryption */
+static void lit_materialise(int n, const uint32_t *wr, size_t W, int lit, uint32_t *out)
+{
+    if (lit == LIT_FALSE || lit == LIT_TRUE) {
+        memset(out, 0, (size_t)n * 4);
+        out[n] = lit == LIT_TRUE ? (uint32_t)1 << 29 : (uint32_t)0 - ((uint32_t)1 << 29);
+    } else if (lit & 1) {
+        orc_not(n, wr + (size_t)(lit >> 1) * W, out);
+    } else {
+        memcpy(out, wr + (size_t)(lit >> 1) * W, W * 4);
+    }
+}
+
+/* The scan with plaintext constants: layouts as orc_scan, without consts. */
+ORC_API int orc_scan_plain(const orc_ctx *c, int pred, int w, const uint32_t *column, uint64_t k0, uint64_t k1,
+                           int n_payload, int pw, const uint32_t *const *payloads, uint32_t *match,
+                           uint32_t *const *out_payloads, long long rows)
+{
+    int32_t m, ninp;
+    int g = orc_netlist_plain(pred, w, n_payload, pw, k0, k1, NULL, NULL, NULL, &m, NULL, &ninp);
+    if (g < 0) return -1;
+    int np = n_payload * pw;
+    int32_t *t = (int32_t *)malloc(sizeof(int32_t) * (g + 1)), *a = (int32_t *)malloc(sizeof(int32_t) * (g + 1)),
+            *b = (int32_t *)malloc(sizeof(int32_t) * (g + 1)), *ol = (int32_t *)malloc(sizeof(int32_t) * (np + 1)),
+            *depth = (int32_t *)malloc(sizeof(int32_t) * (ninp + g + 1));
+    orc_netlist_plain(pred, w, n_payload, pw, k0, k1, t, a, b, &m, ol, &ninp);
+    int maxd = 0;
+    for (int i = 0; i < ninp; i++) depth[i] = 0;
+    for (int k = 0; k < g; k++) {
+        depth[ninp + k] = 1 + (depth[a[k]] > depth[b[k]] ? depth[a[k]] : depth[b[k]]);
+        if (depth[ninp + k] > maxd) maxd = depth[ninp + k];
+    }
+    size_t W = (size_t)c->p.n + 1, per_row = (size_t)(ninp + g) * W;
+    uint32_t *wires = (uint32_t *)malloc(sizeof(uint32_t) * per_row * (size_t)(rows > 0 ? rows : 1));
+    for (long long row = 0; row < rows; row++) {
+        uint32_t *wr = wires + (size_t)row * per_row;
+        for (int i = 0; i < w; i++) memcpy(wr + i * W, column + ((size_t)row * w + i) * W, W * 4);
+        for (int p = 0; p < n_payload; p++)
+            for (int bit = 0; bit < pw; bit++)
+                memcpy(wr + (size_t)(w + p * pw + bit) * W, payloads[p] + ((size_t)row * pw + bit) * W, W * 4);
+    }
+    int bad = 0;
+    for (int d = 1; d <= maxd; d++) {
+#pragma omp parallel for schedule(dynamic, 1) collapse(2) reduction(| : bad)
+        for (long long row = 0; row < rows; row++)
+            for (int k = 0; k < g; k++) {
+                if (depth[ninp + k] != d) continue;
+                uint32_t *wr = wires + (size_t)row * per_row;
+                bad |= orc_gate(c, t[k], wr + (size_t)a[k] * W, wr + (size_t)b[k] * W,
+                                wr + (size_t)(ninp + k) * W) != 0;
+            }
+    }
+    for (long long row = 0; row < rows; row++) {
+        const uint32_t *wr = wires + (size_t)row * per_row;
+        lit_materialise(c->p.n, wr, W, m, match + (size_t)row * W);
+        for (int p = 0; p < n_payload; p++)
+            for (int bit = 0; bit < pw; bit++)
+                lit_materialise(c->p.n, wr, W, ol[p * pw + bit], out_payloads[p] + ((size_t)row * pw + bit) * W);
+    }
+    free(wires);
+    free(t);
+    free(a);
+    free(b);
+    free(ol);
+    free(depth);
+    return bad ? -1 : 0;
+}
+
 ORC_API void orc_set_threads(int k)
 {
 #ifdef _OPENMP

@@ -421,3 +421,89 @@ def test_scan_toy_matches_plaintext_sql(pred, toy_oracle):
         assert mbits[r] == int(want)
         got = int(sum(int(obits[r, i]) << i for i in range(w)))
         assert got == (int(pay[r]) if want else 0)
+
+
+# --------------------------------------------------------------------------
+# plaintext query constants: reduced netlists, copies and trivial outputs
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("pred", [O.P_EQ, O.P_LT, O.P_RANGE])
+@pytest.mark.parametrize("w", [1, 2, 3, 4])
+def test_plain_constant_netlist_brute_force(pred, w):
+    """Every column value x every constant (every lo, hi pair for RANGE):
+    the reduced netlist computes the SQL predicate and the masked payload."""
+    rng = pred == O.P_RANGE
+    for k in range(1 << w):
+        for k2 in (range(1 << w) if rng else [0]):
+            consts = (k, k2) if rng else (k,)
+            for c in range(1 << w):
+                pay = (c * 5 + 3) % (1 << w)
+                inp = [(c >> i) & 1 for i in range(w)] + [(pay >> i) & 1 for i in range(w)]
+                m, out = O.netlist_plain_eval(pred, w, 1, w, consts, np.array(inp, np.uint8))
+                want = {O.P_EQ: c == k, O.P_LT: c < k, O.P_RANGE: k <= c < k2}[pred]
+                assert m == int(want), (consts, c)
+                assert int(sum(int(out[i]) << i for i in range(w))) == (pay if want else 0)
+
+
+def test_plain_constant_gate_counts_closed_form():
+    """EQ: w - 1 ANDs; LT: one gate per bit above the lowest set bit of k
+    (none for k = 0, the predicate is then false); masks add one gate per
+    payload bit unless the match is a known bit."""
+    for w in (1, 5, 16, 32):
+        for k in sorted({0, 1, 2, 6, (1 << w) - 1, 1 << (w - 1)}):
+            if k >= 1 << w:
+                continue
+            t, _, _, m, ol, _ = O.netlist_plain(O.P_EQ, w, 1, w, (k,))
+            assert t.size == (w - 1) + w
+            t, _, _, m, ol, _ = O.netlist_plain(O.P_LT, w, 0, 0, (k,))
+            low = (k & -k).bit_length() - 1
+            assert t.size == (0 if k == 0 else w - 1 - low)
+            assert (m == O.LIT_FALSE) == (k == 0)
+    # k = 0: no gate at all, every output a known bit
+    t, _, _, m, ol, _ = O.netlist_plain(O.P_LT, 8, 2, 8, (0,))
+    assert t.size == 0 and m == O.LIT_FALSE and np.all(ol == O.LIT_FALSE)
+    # RANGE with lo = 0: not(c < 0) is true, so match = (c < hi)
+    t, _, _, m, _, _ = O.netlist_plain(O.P_RANGE, 16, 0, 0, (0, 6554))
+    t2, _, _, m2, _, _ = O.netlist_plain(O.P_LT, 16, 0, 0, (6554,))
+    assert t.size == t2.size and m == m2
+
+
+@pytest.mark.parametrize("pred,consts", [(O.P_EQ, (9,)), (O.P_LT, (11,)), (O.P_RANGE, (3, 12)),
+                                         (O.P_LT, (0,)), (O.P_LT, (8,)), (O.P_RANGE, (0, 16 - 1)),
+                                         (O.P_EQ, (0,))])
+def test_scan_plain_toy_matches_plaintext_sql(pred, consts, toy_oracle):
+    o = toy_oracle
+    rng = np.random.default_rng(200 + pred + sum(consts))
+    w, rows = 4, 16
+    c = rng.integers(0, 16, rows)
+    pay = rng.integers(0, 16, rows)
+    col = o.encrypt_bits(np.array([(v >> i) & 1 for v in c for i in range(w)], np.uint8), stream=5)
+    pct = o.encrypt_bits(np.array([(v >> i) & 1 for v in pay for i in range(w)], np.uint8), stream=9)
+    match, (outp,) = o.scan_plain(pred, w, col, consts, [pct], w)
+    mbits = o.decrypt_bits(match)
+    obits = o.decrypt_bits(outp.reshape(-1, o.n + 1)).reshape(rows, w)
+    for r in range(rows):
+        want = {O.P_EQ: c[r] == consts[0], O.P_LT: c[r] < consts[0],
+                O.P_RANGE: consts[0] <= c[r] < consts[-1]}[pred]
+        assert mbits[r] == int(want)
+        assert int(sum(int(obits[r, i]) << i for i in range(w))) == (int(pay[r]) if want else 0)
+    # outputs that are not gate outputs are exact copies, negations or trivial ciphertexts
+    _, _, _, m, ol, _ = O.netlist_plain(pred, w, 1, w, consts)
+    col3 = col.reshape(rows, w, o.n + 1).astype(np.int64)
+    if m == O.LIT_FALSE:
+        assert np.all(match[:, :o.n] == 0) and np.all(match[:, o.n] == np.uint32((Q - E8) % Q))
+        assert np.all(outp[:, :, :o.n] == 0) and np.all(outp[:, :, o.n] == np.uint32((Q - E8) % Q))
+    elif m >= 0 and (m >> 1) < w:
+        src = col3[:, m >> 1]
+        want = (-src) % Q if m & 1 else src
+        assert np.array_equal(match.astype(np.int64), want)
+
+
+def test_scan_plain_equality_at_real_params(real_oracle):
+    """One 3-bit row at the real parameters, a match and a miss."""
+    o = real_oracle
+    w = 3
+    col = o.encrypt_bits(np.array([1, 0, 1, 0, 1, 1], np.uint8), stream=5)  # rows 5, 6
+    pct = o.encrypt_bits(np.array([1, 1, 0, 0, 1, 1], np.uint8), stream=9)  # payloads 3, 6
+    match, (outp,) = o.scan_plain(O.P_EQ, w, col, (5,), [pct], w)
+    assert list(o.decrypt_bits(match)) == [1, 0]
+    assert list(o.decrypt_bits(outp.reshape(-1, o.n + 1))) == [1, 1, 0, 0, 0, 0]
