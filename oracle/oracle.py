@@ -15,7 +15,7 @@ from . import build_oracle
 
 P_EQ, P_LT, P_RANGE, P_LT_MAJ, P_RANGE_MAJ = 0, 1, 2, 3, 4
 GATES = {"NAND": 0, "AND": 1, "OR": 2, "XOR": 3, "XNOR": 4, "NOR": 5,
-         "ANDNY": 6, "ANDYN": 7, "ORNY": 8, "ORYN": 9, "MAJNYY": 10}
+         "ANDNY": 6, "ANDYN": 7, "ORNY": 8, "ORYN": 9, "MAJNYY": 10, "XOR3": 11, "MAJ": 12}
 
 
 class Params(C.Structure):
@@ -85,6 +85,10 @@ def lib():
         L.orc_netlist_plain_eval.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int, C.c_uint64, C.c_uint64, u8p, u8p]
         L.orc_scan_plain.argtypes = [C.c_void_p, C.c_int, C.c_int, u32p, C.c_uint64, C.c_uint64, C.c_int, C.c_int,
                                      C.POINTER(C.c_void_p), u32p, C.POINTER(C.c_void_p), C.c_longlong]
+        L.orc_sum_netlist.argtypes = [C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                      C.c_void_p, C.POINTER(C.c_int32)]
+        L.orc_sum_eval_plain.argtypes = [C.c_int, C.c_int, C.c_int, u8p, u8p]
+        L.orc_aggregate_sum.argtypes = [C.c_void_p, u32p, C.c_int, C.c_int, C.c_int, u32p]
         L.orc_set_threads.argtypes = [C.c_int]
         L.orc_max_threads.restype = C.c_int
         _lib = L
@@ -226,6 +230,39 @@ def netlist_plain_eval(pred: int, w: int, n_payload: int, pw: int, consts, input
     if lib().orc_netlist_plain_eval(pred, w, n_payload, pw, k0, k1, inp, out) < 0:
         raise ValueError("bad netlist request")
     return int(out[0]), out[1:]
+
+
+def gate_lincomb3(gate: int, n: int, a, b, c):
+    """Linear combination of a three-input (or two-input) gate on [n+1] words."""
+    a, b, c = _u32(a).ravel(), _u32(b).ravel(), _u32(c).ravel()
+    out = np.zeros(n + 1, np.uint32)
+    if lib().orc_gate_lincomb3(gate, n, a, b, c, out) != 0:
+        raise ValueError("bad gate")
+    return out
+
+
+def sum_netlist(rows: int, pw: int, ow: int):
+    """SUM-aggregation circuit: (types, a, b, c, output literals [ow], n_inputs)."""
+    ninp = C.c_int32()
+    g = lib().orc_sum_netlist(rows, pw, ow, None, None, None, None, None, C.byref(ninp))
+    if g < 0:
+        raise ValueError("bad aggregation shape")
+    t, a, b, c = (np.zeros(max(g, 1), np.int32) for _ in range(4))
+    ol = np.zeros(ow, np.int32)
+    lib().orc_sum_netlist(rows, pw, ow, t.ctypes.data, a.ctypes.data, b.ctypes.data, c.ctypes.data, ol.ctypes.data,
+                          C.byref(ninp))
+    return t[:g], a[:g], b[:g], c[:g], ol, int(ninp.value)
+
+
+def sum_eval_plain(rows: int, pw: int, ow: int, values) -> int:
+    """The SUM circuit evaluated on plaintext bits of the given row values."""
+    vals = [int(v) for v in values]
+    assert len(vals) == rows
+    bits = np.array([(v >> j) & 1 for v in vals for j in range(pw)], np.uint8)
+    out = np.zeros(ow, np.uint8)
+    if lib().orc_sum_eval_plain(rows, pw, ow, bits, out) < 0:
+        raise ValueError("bad aggregation shape")
+    return int(sum(int(out[j]) << j for j in range(ow)))
 
 
 class Oracle:
@@ -374,6 +411,15 @@ class Oracle:
         if rc != 0:
             raise ValueError("scan failed")
         return match, outs
+
+    def aggregate_sum(self, values, rows: int, pw: int, ow: int):
+        """Encrypted SUM of rows values of pw bits ([rows, pw, n+1]) mod 2^ow -> [ow, n+1]."""
+        W = self.n + 1
+        vals = _u32(values).reshape(rows * pw * W)
+        out = np.zeros((ow, W), np.uint32)
+        if lib().orc_aggregate_sum(self._h, vals, rows, pw, ow, out) != 0:
+            raise ValueError("aggregation failed")
+        return out
 
     def scan_plain(self, pred: int, w: int, column, consts, payloads, pw: int):
         """Scan with plaintext query constants (k,) or (lo, hi): returns

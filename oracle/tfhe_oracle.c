@@ -485,7 +485,8 @@ ORC_API void orc_keyswitch(const orc_ctx *c, const uint32_t *big, uint32_t *out)
 }
 
 /* Gate types (numbering fixed by the library's C interface). */
-enum { G_NAND = 0, G_AND, G_OR, G_XOR, G_XNOR, G_NOR, G_ANDNY, G_ANDYN, G_ORNY, G_ORYN, G_MAJNYY, G_COUNT };
+enum { G_NAND = 0, G_AND, G_OR, G_XOR, G_XNOR, G_NOR, G_ANDNY, G_ANDYN, G_ORNY, G_ORYN, G_MAJNYY, G_XOR3, G_MAJ,
+       G_COUNT };
 
 /* Linear combination before the bootstrap: constant (0, ..., 0, k) plus
  * ca * c1 + cb * c2, all mod q, with q/8 = 2^29.  The sign of the resulting
@@ -513,16 +514,30 @@ ORC_API int orc_gate_lincomb(int type, int n, const uint32_t *c1, const uint32_t
     return 0;
 }
 
-/* Three-input majority with the first input negated, MAJ(not a, b, c): the
- * sum -c1 + c2 + c3 of three +-q/8 encodings is +-q/8 or +-3q/8 and its
- * sign is the majority vote (no constant).  Two-input types ignore c3. */
+/* Three-input gates (no constant term).  With t of the three inputs true,
+ * c1 + c2 + c3 has phase (2t - 3) q/8:
+ *   MAJ     c1 + c2 + c3: +-q/8 or +-3q/8, positive iff t >= 2;
+ *   MAJNYY  -c1 + c2 + c3: the same vote with the first input negated;
+ *   XOR3    -2 (c1 + c2 + c3) = -(2t - 3) q/4, which is +q/4 for t = 1 and
+ *           (as -3q/4 mod q) for t = 3, -q/4 for t = 0 and t = 2: positive
+ *           iff t is odd (the sum bit of a full adder).
+ * Two-input types ignore c3. */
 ORC_API int orc_gate_lincomb3(int type, int n, const uint32_t *c1, const uint32_t *c2, const uint32_t *c3,
                               uint32_t *out)
 {
-    if (type != G_MAJNYY) return orc_gate_lincomb(type, n, c1, c2, out);
-    for (int x = 0; x <= n; x++) out[x] = c2[x] + c3[x] - c1[x];
+    if (type == G_MAJNYY) {
+        for (int x = 0; x <= n; x++) out[x] = c2[x] + c3[x] - c1[x];
+    } else if (type == G_MAJ) {
+        for (int x = 0; x <= n; x++) out[x] = c1[x] + c2[x] + c3[x];
+    } else if (type == G_XOR3) {
+        for (int x = 0; x <= n; x++) out[x] = (uint32_t)0 - 2u * (c1[x] + c2[x] + c3[x]);
+    } else {
+        return orc_gate_lincomb(type, n, c1, c2, out);
+    }
     return 0;
 }
+
+static int gate_has_three_inputs(int type) { return type == G_MAJNYY || type == G_MAJ || type == G_XOR3; }
 
 /* One gate bootstrap: lincomb -> blind rotation -> extract -> keyswitch. */
 ORC_API int orc_gate3(const orc_ctx *c, int type, const uint32_t *c1, const uint32_t *c2, const uint32_t *c3,
@@ -532,7 +547,7 @@ ORC_API int orc_gate3(const orc_ctx *c, int type, const uint32_t *c1, const uint
     uint32_t *lin = (uint32_t *)malloc(sizeof(uint32_t) * (n + 1));
     uint32_t *acc = (uint32_t *)malloc(sizeof(uint32_t) * 2 * N);
     uint32_t *big = (uint32_t *)malloc(sizeof(uint32_t) * (N + 1));
-    int rc = (type == G_MAJNYY && !c3) ? -1 : orc_gate_lincomb3(type, n, c1, c2, c3, lin);
+    int rc = (gate_has_three_inputs(type) && !c3) ? -1 : orc_gate_lincomb3(type, n, c1, c2, c3, lin);
     if (rc == 0) {
         orc_blind_rotate(c, lin, acc);
         orc_sample_extract(N, acc, big);
@@ -689,6 +704,8 @@ ORC_API int orc_gate_plain(int type, int x, int y)
 ORC_API int orc_gate_plain3(int type, int x, int y, int z)
 {
     if (type == G_MAJNYY) return ((!x) + y + z) >= 2;
+    if (type == G_MAJ) return (x + y + z) >= 2;
+    if (type == G_XOR3) return (x + y + z) & 1;
     return orc_gate_plain(type, x, y);
 }
 
@@ -976,6 +993,152 @@ ORC_API int orc_scan_plain(const orc_ctx *c, int pred, int w, const uint32_t *co
     free(t);
     free(a);
     free(b);
+    free(ol);
+    free(depth);
+    return bad ? -1 : 0;
+}
+
+/* ------------------------------------------------------------------ */
+/* SUM aggregation of the selected rows (§6.1 D, the result_k / result_v  */
+/* sums: the masked values of all rows added homomorphically; rows that  */
+/* do not match contribute zero).                                         */
+/* Each value is rows x pw encrypted bits, LSB first; the sum is taken     */
+/* mod 2^ow.  The circuit is a carry-save (Wallace) tree of full adders:   */
+/* sum bit XOR3(x, y, z) and carry MAJ(x, y, z), one bootstrap each, then  */
+/* one ripple-carry adder.  Canonical form (every choice fixes the words):  */
+/*  - column j (weight 2^j, j < ow) starts as the bits j of rows 0..R-1;  */
+/*  - while some column holds more than 2 wires, one layer: for j = 0..ow-1 */
+/*    take its wires in order in groups of three; each group appends its    */
+/*    XOR3 to the next layer's column j and (if j + 1 < ow) its MAJ to the   */
+/*    next layer's column j + 1; the 0-2 wires left over follow;            */
+/*  - ripple: carry = none; for j = 0..ow-1 the operands are column j's      */
+/*    wires then the carry: none -> output 0; one -> that wire; two ->      */
+/*    XOR and carry AND; three -> XOR3 and carry MAJ (no carry out of the   */
+/*    top column).                                                          */
+/* Wires: input bit (r, j) is r*pw + j; gate outputs follow.  Output j is a */
+/* literal (2*wire, or LIT_FALSE).                                          */
+/* ------------------------------------------------------------------ */
+
+ORC_API int orc_sum_netlist(int rows, int pw, int ow, int32_t *type, int32_t *a, int32_t *b, int32_t *c,
+                            int32_t *out_lits, int32_t *n_inputs)
+{
+    if (rows < 1 || pw < 1 || pw > 64 || ow < 1 || ow > 64) return -1;
+    int ninp = rows * pw, cap = rows + 4;
+    netlist nl = {type, a, b, c, 0, 0, ninp};
+    int *cur = (int *)malloc(sizeof(int) * (size_t)ow * cap), *nxt = (int *)malloc(sizeof(int) * (size_t)ow * cap);
+    int *cn = (int *)calloc((size_t)ow, sizeof(int)), *nn = (int *)calloc((size_t)ow, sizeof(int));
+    for (int j = 0; j < ow && j < pw; j++) {
+        for (int r = 0; r < rows; r++) cur[(size_t)j * cap + r] = r * pw + j;
+        cn[j] = rows;
+    }
+    for (;;) {
+        int widest = 0;
+        for (int j = 0; j < ow; j++)
+            if (cn[j] > widest) widest = cn[j];
+        if (widest <= 2) break;
+        for (int j = 0; j < ow; j++) nn[j] = 0;
+        for (int j = 0; j < ow; j++) {
+            const int *L = cur + (size_t)j * cap;
+            int i = 0;
+            for (; cn[j] - i >= 3; i += 3) {
+                nxt[(size_t)j * cap + nn[j]++] = nl_add3(&nl, G_XOR3, L[i], L[i + 1], L[i + 2]);
+                if (j + 1 < ow) nxt[(size_t)(j + 1) * cap + nn[j + 1]++] = nl_add3(&nl, G_MAJ, L[i], L[i + 1], L[i + 2]);
+            }
+            for (; i < cn[j]; i++) nxt[(size_t)j * cap + nn[j]++] = L[i];
+        }
+        int *t = cur; cur = nxt; nxt = t;
+        int *tn = cn; cn = nn; nn = tn;
+    }
+    int carry = -1;
+    for (int j = 0; j < ow; j++) {
+        int ops[3], k = 0;
+        for (int i = 0; i < cn[j]; i++) ops[k++] = cur[(size_t)j * cap + i];
+        if (carry >= 0) ops[k++] = carry;
+        int lit, top = j + 1 == ow;
+        if (k == 0) {
+            lit = LIT_FALSE;
+            carry = -1;
+        } else if (k == 1) {
+            lit = 2 * ops[0];
+            carry = -1;
+        } else if (k == 2) {
+            lit = 2 * nl_add(&nl, G_XOR, ops[0], ops[1]);
+            carry = top ? -1 : nl_add(&nl, G_AND, ops[0], ops[1]);
+        } else {
+            lit = 2 * nl_add3(&nl, G_XOR3, ops[0], ops[1], ops[2]);
+            carry = top ? -1 : nl_add3(&nl, G_MAJ, ops[0], ops[1], ops[2]);
+        }
+        if (out_lits) out_lits[j] = lit;
+    }
+    free(cur);
+    free(nxt);
+    free(cn);
+    free(nn);
+    if (n_inputs) *n_inputs = ninp;
+    return nl.count;
+}
+
+/* Plaintext evaluation of the SUM circuit: in_bits [rows][pw] -> out_bits [ow]. */
+ORC_API int orc_sum_eval_plain(int rows, int pw, int ow, const uint8_t *in_bits, uint8_t *out_bits)
+{
+    int32_t ninp;
+    int g = orc_sum_netlist(rows, pw, ow, NULL, NULL, NULL, NULL, NULL, &ninp);
+    if (g < 0) return -1;
+    int32_t *t = (int32_t *)malloc(sizeof(int32_t) * (g + 1)), *a = (int32_t *)malloc(sizeof(int32_t) * (g + 1)),
+            *b = (int32_t *)malloc(sizeof(int32_t) * (g + 1)), *c3 = (int32_t *)malloc(sizeof(int32_t) * (g + 1)),
+            *ol = (int32_t *)malloc(sizeof(int32_t) * ow);
+    uint8_t *wires = (uint8_t *)malloc((size_t)(ninp + g + 1));
+    orc_sum_netlist(rows, pw, ow, t, a, b, c3, ol, &ninp);
+    for (int i = 0; i < ninp; i++) wires[i] = in_bits[i];
+    for (int k = 0; k < g; k++)
+        wires[ninp + k] = (uint8_t)orc_gate_plain3(t[k], wires[a[k]], wires[b[k]], c3[k] >= 0 ? wires[c3[k]] : 0);
+    for (int j = 0; j < ow; j++) out_bits[j] = (uint8_t)lit_value(wires, ol[j]);
+    free(t);
+    free(a);
+    free(b);
+    free(c3);
+    free(ol);
+    free(wires);
+    return g;
+}
+
+/* Encrypted SUM: in [rows][pw][n+1] -> out [ow][n+1]; gates run level by
+ * level (a gate's level is one more than its deepest input), side by side. */
+ORC_API int orc_aggregate_sum(const orc_ctx *c, const uint32_t *in, int rows, int pw, int ow, uint32_t *out)
+{
+    int32_t ninp;
+    int g = orc_sum_netlist(rows, pw, ow, NULL, NULL, NULL, NULL, NULL, &ninp);
+    if (g < 0) return -1;
+    int32_t *t = (int32_t *)malloc(sizeof(int32_t) * (g + 1)), *a = (int32_t *)malloc(sizeof(int32_t) * (g + 1)),
+            *b = (int32_t *)malloc(sizeof(int32_t) * (g + 1)), *c3 = (int32_t *)malloc(sizeof(int32_t) * (g + 1)),
+            *ol = (int32_t *)malloc(sizeof(int32_t) * ow), *depth = (int32_t *)malloc(sizeof(int32_t) * (ninp + g + 1));
+    orc_sum_netlist(rows, pw, ow, t, a, b, c3, ol, &ninp);
+    int maxd = 0;
+    for (int i = 0; i < ninp; i++) depth[i] = 0;
+    for (int k = 0; k < g; k++) {
+        int d = depth[a[k]] > depth[b[k]] ? depth[a[k]] : depth[b[k]];
+        if (c3[k] >= 0 && depth[c3[k]] > d) d = depth[c3[k]];
+        depth[ninp + k] = 1 + d;
+        if (depth[ninp + k] > maxd) maxd = depth[ninp + k];
+    }
+    size_t W = (size_t)c->p.n + 1;
+    uint32_t *wires = (uint32_t *)malloc(sizeof(uint32_t) * W * (size_t)(ninp + g + 1));
+    memcpy(wires, in, sizeof(uint32_t) * W * (size_t)ninp);
+    int bad = 0;
+    for (int d = 1; d <= maxd; d++) {
+#pragma omp parallel for schedule(dynamic, 1) reduction(| : bad)
+        for (int k = 0; k < g; k++) {
+            if (depth[ninp + k] != d) continue;
+            bad |= orc_gate3(c, t[k], wires + (size_t)a[k] * W, wires + (size_t)b[k] * W,
+                             c3[k] >= 0 ? wires + (size_t)c3[k] * W : NULL, wires + (size_t)(ninp + k) * W) != 0;
+        }
+    }
+    for (int j = 0; j < ow; j++) lit_materialise(c->p.n, wires, W, ol[j], out + (size_t)j * W);
+    free(wires);
+    free(t);
+    free(a);
+    free(b);
+    free(c3);
     free(ol);
     free(depth);
     return bad ? -1 : 0;

@@ -507,3 +507,102 @@ def test_scan_plain_equality_at_real_params(real_oracle):
     match, (outp,) = o.scan_plain(O.P_EQ, w, col, (5,), [pct], w)
     assert list(o.decrypt_bits(match)) == [1, 0]
     assert list(o.decrypt_bits(outp.reshape(-1, o.n + 1))) == [1, 1, 0, 0, 0, 0]
+
+
+# --------------------------------------------------------------------------
+# SUM aggregation: full-adder gates and the carry-save tree
+# --------------------------------------------------------------------------
+def test_full_adder_gates_plain():
+    for x in (0, 1):
+        for y in (0, 1):
+            for z in (0, 1):
+                assert O.gate_plain3(O.GATES["XOR3"], x, y, z) == (x + y + z) % 2
+                assert O.gate_plain3(O.GATES["MAJ"], x, y, z) == int(x + y + z >= 2)
+
+
+@pytest.mark.parametrize("which", ["toy", "real"])
+@pytest.mark.parametrize("gate", ["XOR3", "MAJ"])
+def test_full_adder_gates_encrypted(which, gate, toy_oracle, real_oracle):
+    """Every input triple (toy) or a spread of them (real parameters): the
+    bootstrapped output decrypts to the truth table at +-q/8."""
+    o = toy_oracle if which == "toy" else real_oracle
+    combos = [(x, y, z) for x in (0, 1) for y in (0, 1) for z in (0, 1)]
+    if which == "real":
+        combos = combos[1::2]
+    cts = o.encrypt_bits(np.array([v for cmb in combos for v in cmb], np.uint8), stream=34).reshape(-1, 3, o.n + 1)
+    for (x, y, z), ct in zip(combos, cts):
+        out = o.gate3(O.GATES[gate], ct[0], ct[1], ct[2])
+        want = (x + y + z) % 2 if gate == "XOR3" else int(x + y + z >= 2)
+        assert o.decrypt_bits(out)[0] == want
+        assert abs(abs(int(centered(o.phase(out))[0])) - E8) < (1 << 27)
+
+
+def test_full_adder_lincomb_phases_closed_form():
+    """Before the bootstrap, the three-input forms put t true inputs at
+    (2t - 3) q/8 (MAJ) and -(2t - 3) q/4 (XOR3), exactly, on noiseless
+    trivial ciphertexts."""
+    n = 4
+    enc = lambda v: np.array([0] * n + [E8 if v else (Q - E8)], np.uint32)
+    for x in (0, 1):
+        for y in (0, 1):
+            for z in (0, 1):
+                t = x + y + z
+                c = [enc(x), enc(y), enc(z)]
+                maj = O.gate_lincomb3(O.GATES["MAJ"], n, *c)
+                xor3 = O.gate_lincomb3(O.GATES["XOR3"], n, *c)
+                assert int(maj[n]) == ((2 * t - 3) * E8) % Q
+                assert int(xor3[n]) == (-(2 * t - 3) * 2 * E8) % Q
+
+
+def test_sum_circuit_exhaustive_small():
+    """Every value combination for tiny tables: the circuit's plaintext
+    evaluation equals the integer sum mod 2^ow."""
+    import itertools
+
+    for rows in (1, 2, 3, 4):
+        for pw in (1, 2):
+            for ow in sorted({1, pw, pw + 1, pw + 3}):
+                for vals in itertools.product(range(1 << pw), repeat=rows):
+                    assert O.sum_eval_plain(rows, pw, ow, vals) == sum(vals) % (1 << ow), (rows, pw, ow, vals)
+
+
+def test_sum_circuit_random_larger():
+    rng = np.random.default_rng(9)
+    for rows, pw, ow in [(5, 3, 6), (7, 4, 7), (16, 8, 12), (33, 5, 11), (100, 16, 23), (9, 4, 3)]:
+        for _ in range(20):
+            vals = [int(v) for v in rng.integers(0, 1 << pw, rows)]
+            assert O.sum_eval_plain(rows, pw, ow, vals) == sum(vals) % (1 << ow)
+    # extreme values: every bit set
+    for rows, pw in [(64, 8), (17, 16)]:
+        ow = pw + 7
+        assert O.sum_eval_plain(rows, pw, ow, [(1 << pw) - 1] * rows) == rows * ((1 << pw) - 1) % (1 << ow)
+
+
+def test_sum_circuit_shape():
+    """Only full adders (XOR3 with MAJ) and half adders (XOR with AND) appear,
+    paired except in the top column, which drops its carry; a single row
+    needs no gate at all (outputs are its bits and known zeros)."""
+    t, a, b, c, ol, ninp = O.sum_netlist(1, 8, 10)
+    assert t.size == 0 and list(ol[:8]) == [2 * j for j in range(8)] and all(ol[8:] == O.LIT_FALSE)
+    t, a, b, c, ol, ninp = O.sum_netlist(4096, 32, 44)
+    kinds = {int(k) for k in np.unique(t)}
+    assert kinds <= {O.GATES["XOR3"], O.GATES["MAJ"], O.GATES["XOR"], O.GATES["AND"]}
+    n_xor3, n_maj = int((t == O.GATES["XOR3"]).sum()), int((t == O.GATES["MAJ"]).sum())
+    n_xor, n_and = int((t == O.GATES["XOR"]).sum()), int((t == O.GATES["AND"]).sum())
+    assert 0 <= n_xor3 - n_maj and 0 <= n_xor - n_and <= 1
+    assert np.all(c[(t == O.GATES["XOR3"]) | (t == O.GATES["MAJ"])] >= 0)
+
+
+def test_aggregate_sum_toy_decrypts_to_sum(toy_oracle):
+    o = toy_oracle
+    rng = np.random.default_rng(12)
+    for rows, pw, ow in [(6, 3, 6), (1, 4, 6), (9, 2, 3)]:
+        vals = rng.integers(0, 1 << pw, rows)
+        bits = np.array([(int(v) >> j) & 1 for v in vals for j in range(pw)], np.uint8)
+        ct = o.encrypt_bits(bits, stream=40 + rows)
+        out = o.aggregate_sum(ct, rows, pw, ow)
+        got = o.decrypt_bits(out)
+        assert int(sum(int(got[j]) << j for j in range(ow))) == int(vals.sum()) % (1 << ow)
+        if rows == 1:  # no gate: copies of the input bits and trivial zeros
+            assert np.array_equal(out[:pw], ct.reshape(pw, -1))
+            assert np.all(out[pw:, :o.n] == 0) and np.all(out[pw:, o.n] == np.uint32(Q - E8))
