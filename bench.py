@@ -40,9 +40,12 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="eq32x4096",
                     choices=["eq32x4096", "eq4x16", "range16x65536", "range16x65536maj", "lt8x64", "lt8x64maj", "range4x16",
-                             "range4x16maj", "gates", "serving"])
+                             "range4x16maj", "eq32x4096plain", "range16x65536plain", "eq4x16plain", "gates",
+                             "serving"])
     ap.add_argument("--queries", type=int, default=16, help="queries per serving phase")
     ap.add_argument("--batch", type=int, default=65536, help="gates per step of the gate microbenchmark")
+    ap.add_argument("--sweep", default="",
+                    help="gate microbenchmark over these batch sizes (comma separated, e.g. 1,16,256,4096,65536,1048576)")
     ap.add_argument("--engine", default="default", choices=["default", "dual_prime", "goldilocks"])
     ap.add_argument("--rows", type=int, default=None, help="override the workload's row count")
     ap.add_argument("--e2e-steps", type=int, default=1)
@@ -168,6 +171,22 @@ class Dist:
             self.pg.destroy_process_group()
 
 
+def gates_per_row(table) -> int:
+    """Gate bootstraps per row of the table's circuit (the library's scheduler)."""
+    from paper_2510_15413_b300 import fhesql as F
+
+    npay = len(table.payloads)
+    if table.plain:
+        return F.plan_info_plain(table.pred, table.width, npay, table.payload_width, table.consts)[0]
+    return F.plan_info(table.pred, table.width, npay, table.payload_width)[0]
+
+
+def oracle_scan(o, table, col, cst, pays):
+    if table.plain:
+        return o.scan_plain(table.pred, table.width, col, table.consts, pays, table.payload_width)
+    return o.scan(table.pred, table.width, col, cst, pays, table.payload_width)
+
+
 # ------------------------------------------------------------------ CPU oracle timing
 def oracle_rate(table, seed: int, rows: int):
     """Time the oracle on `rows` rows of the table (own encryption, untimed);
@@ -187,9 +206,9 @@ def oracle_rate(table, seed: int, rows: int):
                                            q * table.rows * pw + r * pw) for r in idx])
             for q in range(len(table.payloads))]
     t0 = time.perf_counter()
-    o.scan(table.pred, w, col, cst, pays, pw)
+    oracle_scan(o, table, col, cst, pays)
     dt = time.perf_counter() - t0
-    gates = rows * table.gates_per_row
+    gates = rows * gates_per_row(table)
     o.close()
     return gates / dt, O.max_threads(), dt, gates
 
@@ -220,7 +239,7 @@ def verify_rows_with_oracle(table, seed, k, match, outs):
                                            q * table.rows * pw + r * pw) for r in rows])
             for q in range(len(table.payloads))]
     t0 = time.perf_counter()
-    om, oouts = o.scan(table.pred, w, col, cst, pays, pw)
+    om, oouts = oracle_scan(o, table, col, cst, pays)
     dt = time.perf_counter() - t0
     o.close()
     gm = match.cpu().numpy().view(np.uint32)[rows]
@@ -243,13 +262,14 @@ def run_reference(args, dist):
         r, threads, dt, gates = oracle_rate(t, args.seed, args.cpu_rows)
         rates.append(r)
     value = statistics.median(rates)
-    sample = f"{args.cpu_rows} row(s) of {args.workload} = {args.cpu_rows * t.gates_per_row} gate bootstraps per step"
+    gpr = gates_per_row(t)
+    sample = f"{args.cpu_rows} row(s) of {args.workload} = {args.cpu_rows * gpr} gate bootstraps per step"
     line = {"impl": "reference", "metric": "gate bootstraps/s", "value": value, "unit": "gate bootstraps/s",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32/u64 (exact integer)",
-            "data": "synthetic", "rows_per_s": value / t.gates_per_row,
+            "data": "synthetic", "rows_per_s": value / gpr,
             "config": {"workload": args.workload, "rows": t.rows, "width": t.width,
-                       "gates_per_row": t.gates_per_row, "parallelism": "oracle threads over independent gates"},
+                       "gates_per_row": gpr, "parallelism": "oracle threads over independent gates"},
             "cpu_baseline": {"value": value, "unit": "gate bootstraps/s", "cores": threads, "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": value, "unit": "gate bootstraps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -349,6 +369,86 @@ def run_gates(args, dist):
         print(json.dumps(line), flush=True)
 
 
+def run_gate_sweep(args, dist):
+    """Gate microbenchmark over batch sizes: for each B, CUDA-event time of
+    whole batches of B independent random gate bootstraps (inputs resident),
+    every output decrypted against the gate's truth table.  B = 1 is the
+    per-gate launch path; larger B use the batched persistent launches."""
+    import torch
+
+    from paper_2510_15413_b300 import fhesql as F
+    from paper_2510_15413_b300 import workloads as WL
+
+    dev = dist.local
+    torch.cuda.set_device(dev)
+    peaks, peak_kind = measured_peaks()
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    ctx = F.Context(args.seed, device=dev, engine=args.engine)
+    st = torch.cuda.current_stream()
+    truth_tab = np.array([[1, 1, 1, 0], [0, 0, 0, 1], [0, 1, 1, 1], [0, 1, 1, 0], [1, 0, 0, 1]], np.uint8)
+    sizes = [int(v) for v in args.sweep.split(",") if v]
+    sampler = ClockSampler(bus_id_of(dev))
+    sampler.start()
+    points, launches, all_ok = [], 0, True
+    for B in sizes:
+        types, xb, yb = WL.gates(B, seed=args.seed)
+        x = ctx.encrypt_bits(xb, WL.STREAM_GATES, 0)
+        y = ctx.encrypt_bits(yb, WL.STREAM_GATES, B)
+        dt = torch.from_numpy(types).to(f"cuda:{dev}")
+        da = torch.from_numpy(x.view(np.int32)).to(f"cuda:{dev}")
+        db = torch.from_numpy(y.view(np.int32)).to(f"cuda:{dev}")
+        out = torch.zeros((B, ctx.words), dtype=torch.int32, device=f"cuda:{dev}")
+        warm = 3 if B <= (1 << 16) else 1
+        for _ in range(warm):
+            ctx.gate_batch(dt, da, db, out, stream=st)
+        torch.cuda.synchronize()
+        # enough whole batches for about a second of device time (at least one)
+        t_est = time.perf_counter()
+        ctx.gate_batch(dt, da, db, out, stream=st)
+        torch.cuda.synchronize()
+        one = time.perf_counter() - t_est
+        steps = max(1, min(200, int(1.0 / max(one, 1e-6))))
+        dist.barrier()
+        torch.cuda.synchronize()
+        ctx.profile_begin()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        for _ in range(steps):
+            ctx.gate_batch(dt, da, db, out, stream=st)
+        e1.record(st)
+        torch.cuda.synchronize()
+        kt = ctx.profile_end()
+        ms = dist.max(e0.elapsed_time(e1))
+        launches += int(kt["blind_rotate_launches"] + kt["keyswitch_launches"]) + steps
+        ok = bool(np.array_equal(ctx.decrypt_bits(out.cpu().numpy().view(np.uint32)),
+                                 truth_tab[types, 2 * xb + yb]))
+        all_ok &= ok
+        roof = roofline_of(kt, ms, sms, peaks, f"gates{B}")
+        points.append({"batch": B, "gate_bootstraps_per_s": dist.world * B * steps / (ms / 1e3),
+                       "ms_per_batch": ms / steps, "steps": steps, "warmup": warm, "correct": ok,
+                       "br_ms_per_launch": roof["avg_launch_ms"], "frac": roof["frac"]})
+        del dt, da, db, out
+        torch.cuda.empty_cache()
+    clocks = sampler.stop()
+    head = points[-1]
+    line = {"metric": "gate bootstraps/s", "value": head["gate_bootstraps_per_s"], "unit": "gate bootstraps/s",
+            "n_gpus": dist.world, "steps": head["steps"], "warmup": head["warmup"],
+            "ms_per_step": head["ms_per_batch"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "u32 (exact integer)",
+            "data": "synthetic (seeded random gates, seeded keys)",
+            "config": {"workload": "gates sweep " + ",".join(map(str, sizes)),
+                       "engine": ["goldilocks", "dual_prime"][ctx.engine],
+                       "gate_types": "NAND/AND/OR/XOR/XNOR uniform",
+                       "l2": "inputs within L2 below B = 2^14, larger above"},
+            "correct": all_ok, "sweep": points, "gpu_launches": launches, "clocks": clocks,
+            "batched_vs_per_gate": (head["gate_bootstraps_per_s"] / points[0]["gate_bootstraps_per_s"]
+                                    if points[0]["batch"] == 1 else None),
+            "peaks": {"kind": peak_kind, "hbm_gbs": peaks.get("hbm_gbs"), "sms": sms}}
+    ctx.close()
+    if dist.rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 # ------------------------------------------------------------------ serving
 def run_serving(args, dist):
     """Continuous batching: a saturated burst, then Poisson arrivals at 0.5x
@@ -428,13 +528,18 @@ def run_serving(args, dist):
 
 
 def kernel_source_hash() -> str:
-    """sha256 of the blind-rotation kernel's sources (ntt.cuh, kernels.cu)."""
+    """sha256 of the blind-rotation kernel's sources: ntt.cuh and the device
+    part of kernels.cu (everything before its host-side section)."""
     import hashlib
 
     h = hashlib.sha256()
-    for f in ("ntt.cuh", "kernels.cu"):
-        with open(os.path.join(ROOT, "paper_2510_15413_b300", "csrc", f), "rb") as fh:
-            h.update(fh.read())
+    with open(os.path.join(ROOT, "paper_2510_15413_b300", "csrc", "ntt.cuh"), "rb") as fh:
+        h.update(fh.read())
+    with open(os.path.join(ROOT, "paper_2510_15413_b300", "csrc", "kernels.cu"), "rb") as fh:
+        text = fh.read()
+    marker = b"// ------------------------------------------------------------------ host side"
+    assert marker in text, "kernels.cu lost its host-side marker"
+    h.update(text.split(marker)[0])
     return h.hexdigest()
 
 
@@ -496,7 +601,11 @@ def run_ours(args, dist):
     st = torch.cuda.current_stream()
 
     def step():
-        ctx.scan_select(dcol, t.rows, t.width, t.pred, dcst, dpay, t.payload_width, match, outs, stream=st)
+        if t.plain:
+            ctx.scan_select_plain(dcol, t.rows, t.width, t.pred, t.consts, dpay, t.payload_width, match, outs,
+                                  stream=st)
+        else:
+            ctx.scan_select(dcol, t.rows, t.width, t.pred, dcst, dpay, t.payload_width, match, outs, stream=st)
 
     for _ in range(max(3, args.warmup)):
         step()
@@ -519,7 +628,8 @@ def run_ours(args, dist):
     ktimes = ctx.profile_end()
     clocks = sampler.stop()
     ms = dist.max(e0.elapsed_time(e1))
-    gates_per_step = t.rows * t.gates_per_row
+    gpr = gates_per_row(t)
+    gates_per_step = t.rows * gpr
     value = dist.world * gates_per_step * args.steps / (ms / 1e3)
 
     # ---- correctness of the timed outputs (plaintext answer)
@@ -533,7 +643,7 @@ def run_ours(args, dist):
     roofline = roofline_of(ktimes, ms, sms, peaks, args.workload)
 
     # ---- end to end through the public C-ABI with host buffers (copies inside the timed region)
-    h2d = (col.size + cst.size + sum(p.size for p in pays)) * 4
+    h2d = (col.size + (0 if t.plain else cst.size) + sum(p.size for p in pays)) * 4
     d2h = (t.rows * W + len(pays) * t.rows * t.payload_width * W) * 4
     e2e = None
     if args.e2e_steps > 0:
@@ -542,14 +652,28 @@ def run_ours(args, dist):
         hpay = [torch.from_numpy(p.view(np.int32)).pin_memory() for p in pays]
         hmatch = torch.zeros((t.rows, W), dtype=torch.int32).pin_memory()
         houts = [torch.zeros((t.rows, t.payload_width, W), dtype=torch.int32).pin_memory() for _ in pays]
-        ctx.scan_select_host(hcol, t.rows, t.width, t.pred, hcst, hpay, t.payload_width, hmatch, houts, stream=st)
+
+        def e2e_step():
+            if t.plain:  # pinned host -> device, the scan, device -> host, all on the launch stream
+                dcol.copy_(hcol, non_blocking=True)
+                for d_, h_ in zip(dpay, hpay):
+                    d_.copy_(h_, non_blocking=True)
+                ctx.scan_select_plain(dcol, t.rows, t.width, t.pred, t.consts, dpay, t.payload_width, match, outs,
+                                      stream=st)
+                hmatch.copy_(match, non_blocking=True)
+                for h_, d_ in zip(houts, outs):
+                    h_.copy_(d_, non_blocking=True)
+            else:
+                ctx.scan_select_host(hcol, t.rows, t.width, t.pred, hcst, hpay, t.payload_width, hmatch, houts,
+                                     stream=st)
+
+        e2e_step()
         dist.barrier()
         torch.cuda.synchronize()
         f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         f0.record(st)
         for _ in range(args.e2e_steps):
-            ctx.scan_select_host(hcol, t.rows, t.width, t.pred, hcst, hpay, t.payload_width, hmatch, houts,
-                                 stream=st)
+            e2e_step()
         f1.record(st)
         torch.cuda.synchronize()
         dist.barrier()
@@ -584,7 +708,7 @@ def run_ours(args, dist):
             run()
             b.record(st)
             torch.cuda.synchronize()
-            res[mode] = ts.rows * ts.gates_per_row / (a.elapsed_time(b) / 1e3)
+            res[mode] = ts.rows * gates_per_row(ts) / (a.elapsed_time(b) / 1e3)
         small = {"workload": "eq4x16 (16 rows, 176 gate bootstraps)", "batched_gate_bootstraps_per_s": res["batched"],
                  "per_gate_gate_bootstraps_per_s": res["per_gate"],
                  "batched_over_per_gate": res["batched"] / res["per_gate"],
@@ -603,8 +727,9 @@ def run_ours(args, dist):
         "data": "synthetic (seeded tables, seeded keys)",
         "rows_per_s": dist.world * t.rows * args.steps / (ms / 1e3),
         "config": {"workload": args.workload, "rows": t.rows, "width": t.width, "pred": t.pred,
+                   "constants": "plaintext" if t.plain else "encrypted",
                    "payload_columns": len(t.payloads), "payload_width": t.payload_width,
-                   "gates_per_row": t.gates_per_row, "gate_bootstraps_per_step": gates_per_step,
+                   "gates_per_row": gpr, "gate_bootstraps_per_step": gates_per_step,
                    "params": "n=630 N=1024 Bg=2^7 l=3 ks 4^8 Torus32",
                    "engine": ["goldilocks", "dual_prime"][ctx.engine],
                    "l2": "inputs larger than L2 (%.0f MB column+payload per step)" % (h2d / 1e6),
@@ -632,7 +757,10 @@ def main():
         run_reference(args, dist)
     else:
         dist.init(use_cuda=True)
-        {"gates": run_gates, "serving": run_serving}.get(args.workload, run_ours)(args, dist)
+        if args.workload == "gates" and args.sweep:
+            run_gate_sweep(args, dist)
+        else:
+            {"gates": run_gates, "serving": run_serving}.get(args.workload, run_ours)(args, dist)
     dist.close()
 
 

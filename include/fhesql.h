@@ -6,7 +6,7 @@
  * query homomorphically on every encrypted row, collects the encrypted mask
  * bits, and applies them to the selected columns with a homomorphic
  * If-Then-Else so that non-matching rows become encryptions of zero (§4.2;
- * §6 D, eq. (1)-(3)).  The client (Alg. 1) encrypts the query constants and
+ * §6.1 D, eq. (1)-(3)).  The client (Alg. 1) encrypts the query constants and
  * decrypts the result.  FHE is the TFHE scheme the paper cites (§1, §2.2):
  * here one LWE ciphertext per bit, every binary gate one gate bootstrap.
  *
@@ -64,11 +64,17 @@ extern "C" {
 #define FSQL_ANDYN 7
 #define FSQL_ORNY 8
 #define FSQL_ORYN 9
-/* MAJNYY(a, b, c) = majority of (not a, b, c): one bootstrap of -a + b + c
- * (three inputs; used only inside scan netlists, not by fsql_gate_batch). */
+/* Three-input gates, used only inside scan and aggregation circuits (not by
+ * fsql_gate_batch).  MAJNYY(a, b, c) = majority of (not a, b, c): one
+ * bootstrap of -a + b + c.  XOR3(a, b, c) = a xor b xor c: one bootstrap of
+ * -2(a + b + c) (t true inputs give phase -(2t - 3) q/4, positive iff t is
+ * odd).  MAJ(a, b, c) = majority: one bootstrap of a + b + c.  XOR3 and MAJ
+ * are the sum and carry of a full adder. */
 #define FSQL_MAJNYY 10
+#define FSQL_XOR3 11
+#define FSQL_MAJ 12
 
-/* Predicates of the WHERE clause (§4.3 B: equality and comparison).
+/* Predicates of the WHERE clause (§4.2 B: equality and comparison).
  * EQ: c = k.  LT: c < k (unsigned).  RANGE: lo <= c < hi (unsigned).
  * LT and RANGE use an LSB-first ripple comparator of 4w - 3 gates;
  * LT_MAJ and RANGE_MAJ compute the same predicates with a majority chain of
@@ -237,6 +243,55 @@ FSQL_API int fsql_scan_select(fsql_ctx* ctx, const uint32_t* d_column, size_t ro
                      uint32_t payload_width, uint32_t* d_match, uint32_t* const* d_out_payloads, int per_gate,
                      void* stream);
 
+/* Oblivious scan-select with plaintext query constants (§4.2 lets an
+ * operand of the comparison be a plaintext; §6.1 D times trivially
+ * encrypted operands).  consts: HOST array, consts[0] = k for EQ/LT/LT_MAJ,
+ * consts[0] = lo and consts[1] = hi for RANGE/RANGE_MAJ; each must fit in
+ * width bits (else FSQL_ERR_ARG).  The server then knows every constant bit
+ * and reduces the circuit: XNOR with a known bit is the column bit or its
+ * negation (no bootstrap), so EQ takes width-1 AND gates per row; a
+ * comparator step with known k_i is one AND or OR gate, or none while the
+ * running result is a known bit (LT and LT_MAJ give the same circuit).
+ * Outputs that no gate writes are copies or negations (every word negated)
+ * of input ciphertexts, or the trivial ciphertext (0, .., 0, +-q/8) of a
+ * known bit.  The gates, hence the work, depend on the constant's bits: the
+ * constant is not hidden from the server in this variant.  Other arguments,
+ * layouts and the graph replay are those of fsql_scan_select. */
+FSQL_API int fsql_scan_select_plain(fsql_ctx* ctx, const uint32_t* d_column, size_t rows, uint32_t width,
+                                    uint32_t pred, const uint64_t* consts, uint32_t n_payloads,
+                                    const uint32_t* const* d_payloads, uint32_t payload_width, uint32_t* d_match,
+                                    uint32_t* const* d_out_payloads, int per_gate, void* stream);
+
+/* fsql_plan_info for the plaintext-constant circuit of consts (host array as
+ * in fsql_scan_select_plain); *literal_outputs (if non-null) receives the
+ * outputs per row that no gate writes. */
+FSQL_API int fsql_plan_info_plain(uint32_t pred, uint32_t width, uint32_t n_payloads, uint32_t payload_width,
+                                  const uint64_t* consts, uint32_t* gates_per_row, uint32_t* levels,
+                                  uint32_t* level_widths, uint32_t max_levels, uint32_t* literal_outputs);
+
+/* SUM aggregation of selected rows (§6.1 D: the masked values of a scan
+ * summed homomorphically into one value; rows that do not match were masked
+ * to zero).  d_values: [rows][width][n+1] encrypted unsigned values (LSB
+ * first), e.g. one d_out_payloads column of fsql_scan_select; d_out:
+ * [out_width][n+1] receives the encrypted sum mod 2^out_width (out_width >=
+ * width + ceil(log2 rows) keeps it exact).  Circuit: a carry-save tree of
+ * full adders (XOR3 sum, MAJ carry; one bootstrap each) reduces every bit
+ * column to at most two wires, then one ripple-carry adder; per layer, each
+ * column's wires are taken in order in groups of three, sums stay in the
+ * column and carries move to the next (dropped above out_width), with the
+ * 0-2 leftover wires after them.  About 2 rows x width bootstraps; depth
+ * about log_1.5(rows) + out_width levels.  Outputs that are inputs or known
+ * zeros (one row, high bits) are copies or trivial ciphertexts.  The
+ * context keeps the circuit's scratch (intermediate wires, descriptors) per
+ * argument set and replays its launches as a CUDA graph.  Limits: rows <=
+ * 2^22, 1 <= width, out_width <= 64.  d_out may not alias d_values. */
+FSQL_API int fsql_aggregate_sum(fsql_ctx* ctx, const uint32_t* d_values, size_t rows, uint32_t width,
+                                uint32_t out_width, uint32_t* d_out, void* stream);
+
+/* Gate count and level count of the SUM circuit for (rows, width, out_width). */
+FSQL_API int fsql_sum_plan_info(size_t rows, uint32_t width, uint32_t out_width, uint32_t* gates, uint32_t* levels,
+                                uint32_t* literal_outputs);
+
 /* The same scan from host buffers (layouts as above, h_payloads / h_out_payloads
  * are arrays of host pointers): copies inputs to the device, runs the batched
  * scan, copies the outputs back and synchronises `stream` before returning.
@@ -247,21 +302,25 @@ FSQL_API int fsql_scan_select_host(fsql_ctx* ctx, const uint32_t* h_column, size
 
 /* ---------------- serving: continuous batching of scan queries ---------------- */
 
-/* One scan-select query for the server (the arguments of fsql_scan_select;
- * all pointers are device pointers owned by the caller, which keeps them
- * valid until the query is done, failed or cancelled). */
+/* One scan-select query for the server (the arguments of fsql_scan_select,
+ * or of fsql_scan_select_plain when plain != 0; all pointers are device
+ * pointers owned by the caller, which keeps them valid until the query is
+ * done, failed or cancelled). */
 #define FSQL_MAX_PAYLOADS 8
 typedef struct fsql_query {
     const uint32_t* d_column;  /* [rows][width][n+1] */
     size_t rows;
     uint32_t width;
-    uint32_t pred;             /* FSQL_EQ, FSQL_LT, FSQL_RANGE */
-    const uint32_t* d_const;   /* [width or 2*width][n+1] */
+    uint32_t pred;             /* FSQL_EQ, FSQL_LT, FSQL_RANGE, FSQL_LT_MAJ, FSQL_RANGE_MAJ */
+    const uint32_t* d_const;   /* [width or 2*width][n+1]; unused (may be null) when plain */
     uint32_t n_payloads;       /* <= FSQL_MAX_PAYLOADS */
     uint32_t payload_width;
     const uint32_t* d_payloads[FSQL_MAX_PAYLOADS];  /* each [rows][payload_width][n+1] */
     uint32_t* d_match;                              /* [rows][n+1] */
     uint32_t* d_out_payloads[FSQL_MAX_PAYLOADS];    /* each [rows][payload_width][n+1] */
+    uint32_t plain;            /* nonzero: the constants are the plaintexts consts[] */
+    uint32_t pad;
+    uint64_t consts[2];        /* k, or lo and hi, each within width bits */
 } fsql_query;
 
 typedef struct fsql_server fsql_server;
@@ -284,7 +343,7 @@ typedef struct fsql_server_stats {
 } fsql_server_stats;
 
 /* A server thread that runs the queries submitted to it (Alg. 2 for each,
- * the paper §4.2 semantics) on the context's device.  Each round merges the
+ * §4.2 semantics) on the context's device.  Each round merges the
  * next circuit level of every admitted query into one launch pair of at
  * most max_batch_gates gate bootstraps (0 = 2^17).  A submitted query waits
  * until its device scratch (descriptors and intermediate wires, about

@@ -9,7 +9,7 @@
  * What it computes (every output word is a fixed function of seed and inputs):
  *   - the scan of Alg. 2 (ProcessQuery): per row, evaluate the WHERE
  *     predicate homomorphically into one encrypted mask bit, then apply the
- *     mask to the selected payload columns with If-Then-Else (§4.2, §6 D,
+ *     mask to the selected payload columns with If-Then-Else (§4.2, §6.1 D,
  *     eq. (1)-(3)); for one-bit payloads cmux(m, v, 0) is AND(m, v);
  *   - every binary gate is a TFHE gate bootstrap (the TFHE construction the
  *     paper cites in §1 and §2.2): linear combination, modulus switch, blind

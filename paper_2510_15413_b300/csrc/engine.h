@@ -51,6 +51,18 @@ struct NttTablesT {
   uint64_t pad;
 };
 
+// How a scan output that no gate writes is produced (plaintext constants):
+// a copy or a negation (every word negated) of an input or intermediate
+// ciphertext, or the trivial ciphertext (0, .., 0, -q/8 or +q/8) of a known bit.
+enum : uint32_t { kOutCopy = 0, kOutNegate = 1, kOutFalse = 2, kOutTrue = 3 };
+
+struct OutDesc {
+  const uint32_t* src;  // [n+1] words; null for kOutFalse / kOutTrue
+  uint32_t* dst;        // [n+1] words
+  uint32_t mode;
+  uint32_t pad;
+};
+
 struct Plan;  // scan plan (kernels.cu)
 
 struct Ctx {
@@ -82,7 +94,10 @@ struct Ctx {
   void* desc_event = nullptr;    // cudaEvent_t guarding h_desc reuse
   uint32_t* d_stage = nullptr;   // device staging for the host-buffer scan
   size_t stage_cap = 0;
+  OutDesc* d_lits = nullptr;     // scan outputs no gate writes (plaintext constants)
+  size_t lits_cap = 0;
   Plan* plan = nullptr;
+  Plan* agg_plan = nullptr;      // SUM aggregation plan (owns its buffers)
   void* prof = nullptr;          // kernel-timing events while profiling (kernels.cu)
   void* capture_stream = nullptr;  // cudaStream_t used to capture scan graphs
   int sm_count = 0;
@@ -98,13 +113,29 @@ uint32_t encode_bit(bool b);
 // Per-row netlist of a predicate (circuit scheduler, host side).
 struct Netlist {
   int n_inputs = 0;          // column bits, constant bits, payload bits
-  int match_wire = -1;
+  int n_const = 0;           // constant-ciphertext inputs (none with plaintext constants)
+  int match_wire = -1;       // -1: no gate writes the match bit (see literal_outs)
   int first_mask_gate = 0;   // gates [first_mask_gate, count) are the payload masks
   std::vector<int> type, a, b, c;  // gate g writes wire n_inputs + g; c = -1 for two inputs
   std::vector<int> level;       // 1-based level of each gate
   int levels = 0;
+  // outputs that no gate writes: target -1 is the match bit, m >= 0 the
+  // m-th masked payload bit; wire -1 for a known bit
+  struct LiteralOut {
+    int target;
+    int wire;
+    uint32_t mode;
+  };
+  std::vector<LiteralOut> literal_outs;
 };
 bool build_netlist(uint32_t pred, uint32_t width, uint32_t n_payloads, uint32_t payload_width, Netlist* out);
+// The SUM-aggregation circuit over rows x width input bits (input bit (r, j)
+// is wire r * width + j); every output bit j is a literal output with target j.
+bool build_sum_netlist(size_t rows, uint32_t width, uint32_t out_width, Netlist* out);
+// The netlist for plaintext constants k0 (EQ, LT) or lo = k0, hi = k1 (RANGE):
+// gates with a known input are reduced away (see host.cpp).
+bool build_netlist_plain(uint32_t pred, uint32_t width, uint32_t n_payloads, uint32_t payload_width, uint64_t k0,
+                         uint64_t k1, Netlist* out);
 
 // Device buffers of one scan (layouts as in fsql_scan_select) plus its
 // intermediate-wire scratch [rows][internal wires][n+1].
@@ -126,6 +157,8 @@ long scan_internal_wires(const Netlist& nl);
 // Descriptors of every gate of every row, level by level, gate-major within a
 // level; level_offset receives levels + 1 offsets into out.
 void scan_descriptors(const Netlist& nl, const ScanIO& io, GateDesc* out, std::vector<size_t>* level_offset);
+// Descriptors of the outputs no gate writes, every row.
+void scan_literals(const Netlist& nl, const ScanIO& io, std::vector<OutDesc>* out);
 
 // kernels.cu
 int device_init(Ctx& c);     // tables, BK -> NTT domain, KSK upload
@@ -134,5 +167,8 @@ int launch_gates(Ctx& c, const GateDesc* d_desc, size_t count, uint32_t* d_big, 
 int launch_blind_rotate(Ctx& c, const GateDesc* d_desc, size_t count, uint32_t* d_big, void* stream);
 int launch_keyswitch(Ctx& c, const uint32_t* d_big, const GateDesc* d_desc, uint32_t* d_out_contig,
                      size_t count, void* stream);
+
+// plain.cu
+int launch_literals(const OutDesc* d_lits, size_t count, int n, void* stream);
 
 }  // namespace fsql

@@ -1,7 +1,7 @@
 // host.cpp -- client-side half of the library: parameters, seeded key
 // generation (KeyGen of §2.2), encryption and decryption (Alg. 1 EncryptQuery /
 // Decrypt), and the circuit scheduler that lowers a WHERE predicate to levels
-// of bootstrapped gates (Alg. 2 EvaluateHomomorphicTree, §4.3 B).
+// of bootstrapped gates (Alg. 2 EvaluateHomomorphicTree, §4.2 B).
 //
 // Randomness is SplitMix64 (Steele, Lea & Flood, OOPSLA 2014) used as a
 // counter-addressed generator: value #k of a generator started at state x is
@@ -200,7 +200,186 @@ struct Builder {
   }
 };
 
+// Values of the plaintext-constant netlist: a wire, possibly negated, or a
+// bit the server already knows.
+struct Lit {
+  int wire = -1;      // -1: known bit
+  bool flip = false;  // wire: negated; known bit: its value
+  static Lit known(bool v) {
+    Lit l;
+    l.flip = v;
+    return l;
+  }
+  static Lit of(int w, bool negated) {
+    Lit l;
+    l.wire = w;
+    l.flip = negated;
+    return l;
+  }
+  bool is_known() const { return wire < 0; }
+  Lit operator!() const {
+    Lit l = *this;
+    l.flip = !l.flip;
+    return l;
+  }
+};
+
+// Boolean algebra on literals over a Builder: a known operand decides the
+// result or drops out; two wires make one gate whose type absorbs the
+// negations, so every gate output is a plain wire.
+struct LitBuilder {
+  Builder& b;
+  explicit LitBuilder(Builder& bb) : b(bb) {}
+  Lit both(Lit x, Lit y) {
+    if (x.is_known()) return x.flip ? y : Lit::known(false);
+    if (y.is_known()) return y.flip ? x : Lit::known(false);
+    int type = FSQL_AND;
+    if (x.flip && y.flip) type = FSQL_NOR;      // !x & !y
+    else if (x.flip) type = FSQL_ANDNY;         // !x & y
+    else if (y.flip) type = FSQL_ANDYN;         // x & !y
+    return Lit::of(b.gate(type, x.wire, y.wire), false);
+  }
+  Lit either(Lit x, Lit y) {
+    if (x.is_known()) return x.flip ? Lit::known(true) : y;
+    if (y.is_known()) return y.flip ? Lit::known(true) : x;
+    int type = FSQL_OR;
+    if (x.flip && y.flip) type = FSQL_NAND;     // !x | !y
+    else if (x.flip) type = FSQL_ORNY;          // !x | y
+    else if (y.flip) type = FSQL_ORYN;          // x | !y
+    return Lit::of(b.gate(type, x.wire, y.wire), false);
+  }
+  // c == k with k known: bit i is c_i or !c_i; then the same neighbour-pairing
+  // AND reduction as the encrypted-constant circuit.
+  Lit equal(int c0, int w, uint64_t k) {
+    std::vector<Lit> cur;
+    for (int i = 0; i < w; ++i) cur.push_back(Lit::of(c0 + i, ((k >> i) & 1) == 0));
+    while (cur.size() > 1) {
+      std::vector<Lit> next;
+      size_t i = 0;
+      for (; i + 1 < cur.size(); i += 2) next.push_back(both(cur[i], cur[i + 1]));
+      if (i < cur.size()) next.push_back(cur[i]);
+      cur.swap(next);
+    }
+    return cur[0];
+  }
+  // c < k with k known: less_i = MAJ(!c_i, k_i, less_{i-1}) is
+  // !c_i | less_{i-1} when k_i = 1 and !c_i & less_{i-1} when k_i = 0
+  // (less_{-1} = false).
+  Lit less(int c0, int w, uint64_t k) {
+    Lit lt = Lit::known(false);
+    for (int i = 0; i < w; ++i) {
+      const Lit not_c = Lit::of(c0 + i, true);
+      lt = ((k >> i) & 1) ? either(not_c, lt) : both(not_c, lt);
+    }
+    return lt;
+  }
+};
+
 }  // namespace
+
+bool build_netlist_plain(uint32_t pred, uint32_t width, uint32_t n_payloads, uint32_t payload_width, uint64_t k0,
+                         uint64_t k1, Netlist* out) {
+  if (width < 1 || width > 64 || pred > FSQL_RANGE_MAJ || n_payloads > 64 || payload_width > 64) return false;
+  if (n_payloads > 0 && payload_width == 0) return false;
+  Netlist nl;
+  const int w = static_cast<int>(width);
+  nl.n_const = 0;
+  nl.n_inputs = w + static_cast<int>(n_payloads * payload_width);
+  Builder b(nl);
+  LitBuilder lb(b);
+  Lit match;
+  if (pred == FSQL_EQ) {
+    match = lb.equal(0, w, k0);
+  } else if (pred == FSQL_LT || pred == FSQL_LT_MAJ) {
+    match = lb.less(0, w, k0);
+  } else {
+    const Lit below_lo = lb.less(0, w, k0);
+    const Lit below_hi = lb.less(0, w, k1);
+    match = lb.both(!below_lo, below_hi);  // !(c < lo) & (c < hi)
+  }
+  const bool match_is_gate = !match.is_known() && !match.flip && match.wire >= nl.n_inputs;
+  nl.match_wire = match_is_gate ? match.wire : -1;
+  if (!match_is_gate) {
+    const uint32_t mode = match.is_known() ? (match.flip ? kOutTrue : kOutFalse) : (match.flip ? kOutNegate : kOutCopy);
+    nl.literal_outs.push_back({-1, match.wire, mode});
+  }
+  nl.first_mask_gate = static_cast<int>(nl.type.size());
+  // cmux(m, v, 0) = m AND v per payload bit; with a known m it is v or 0
+  int m_index = 0;
+  for (uint32_t q = 0; q < n_payloads; ++q)
+    for (uint32_t bit = 0; bit < payload_width; ++bit, ++m_index) {
+      const Lit v = Lit::of(w + static_cast<int>(q * payload_width + bit), false);
+      const Lit o = lb.both(match, v);
+      if (o.is_known()) nl.literal_outs.push_back({m_index, -1, o.flip ? kOutTrue : kOutFalse});
+      else if (o.wire < nl.n_inputs) nl.literal_outs.push_back({m_index, o.wire, o.flip ? kOutNegate : kOutCopy});
+    }
+  *out = std::move(nl);
+  return true;
+}
+
+// SUM of `rows` values of `width` bits mod 2^out_width as a carry-save tree.
+// Bit columns hold the wires of weight 2^j; a layer turns each group of three
+// wires of a column (in order) into a full adder whose sum stays in the
+// column and whose carry joins the next column of the next layer (columns
+// are visited low to high, so a column's next list is: carries from below,
+// its own sums, its 0-2 leftover wires).  When no column has more than two
+// wires, a ripple-carry adder finishes: per column its wires plus the
+// incoming carry, 0 operands -> known 0, 1 -> that wire, 2 -> half adder
+// (XOR, AND), 3 -> full adder (XOR3, MAJ); the top column drops its carry.
+// Every output is a literal output (copy of a wire, or known 0).
+bool build_sum_netlist(size_t rows, uint32_t width, uint32_t out_width, Netlist* out) {
+  if (width < 1 || width > 64 || out_width < 1 || out_width > 64 || rows > (size_t(1) << 22) ||
+      rows * width > (size_t(1) << 24))
+    return false;
+  Netlist nl;
+  const int w = static_cast<int>(width), ow = static_cast<int>(out_width);
+  nl.n_inputs = static_cast<int>(rows * width);
+  nl.n_const = 0;
+  nl.match_wire = -1;
+  Builder b(nl);
+  std::vector<std::vector<int>> column(ow);
+  for (int j = 0; j < std::min(w, ow); ++j)
+    for (size_t r = 0; r < rows; ++r) column[j].push_back(static_cast<int>(r * width) + j);
+  auto crowded = [&]() {
+    for (const auto& c : column)
+      if (c.size() > 2) return true;
+    return false;
+  };
+  while (crowded()) {
+    std::vector<std::vector<int>> next(ow);
+    for (int j = 0; j < ow; ++j) {
+      const std::vector<int>& wires = column[j];
+      size_t i = 0;
+      for (; i + 3 <= wires.size(); i += 3) {
+        next[j].push_back(b.gate(FSQL_XOR3, wires[i], wires[i + 1], wires[i + 2]));
+        if (j + 1 < ow) next[j + 1].push_back(b.gate(FSQL_MAJ, wires[i], wires[i + 1], wires[i + 2]));
+      }
+      next[j].insert(next[j].end(), wires.begin() + static_cast<long>(i), wires.end());
+    }
+    column.swap(next);
+  }
+  int carry = -1;
+  for (int j = 0; j < ow; ++j) {
+    std::vector<int> ops = column[j];
+    if (carry >= 0) ops.push_back(carry);
+    const bool top = j + 1 == ow;
+    carry = -1;
+    int result = -1;
+    if (ops.size() == 1) {
+      result = ops[0];
+    } else if (ops.size() == 2) {
+      result = b.gate(FSQL_XOR, ops[0], ops[1]);
+      if (!top) carry = b.gate(FSQL_AND, ops[0], ops[1]);
+    } else if (ops.size() == 3) {
+      result = b.gate(FSQL_XOR3, ops[0], ops[1], ops[2]);
+      if (!top) carry = b.gate(FSQL_MAJ, ops[0], ops[1], ops[2]);
+    }
+    nl.literal_outs.push_back({j, result, result < 0 ? kOutFalse : kOutCopy});
+  }
+  nl.first_mask_gate = static_cast<int>(nl.type.size());
+  *out = std::move(nl);
+  return true;
+}
 
 bool build_netlist(uint32_t pred, uint32_t width, uint32_t n_payloads, uint32_t payload_width, Netlist* out) {
   if (width < 1 || width > 64 || pred > FSQL_RANGE_MAJ || n_payloads > 64 || payload_width > 64) return false;
@@ -209,6 +388,7 @@ bool build_netlist(uint32_t pred, uint32_t width, uint32_t n_payloads, uint32_t 
   const int w = static_cast<int>(width);
   const bool range = pred == FSQL_RANGE || pred == FSQL_RANGE_MAJ;
   const int nconst = range ? 2 * w : w;
+  nl.n_const = nconst;
   nl.n_inputs = w + nconst + static_cast<int>(n_payloads * payload_width);
   Builder b(nl);
   if (pred == FSQL_EQ) {
@@ -466,6 +646,41 @@ int fsql_plan_info(uint32_t pred, uint32_t width, uint32_t n_payloads, uint32_t 
       for (int lv : nl.level)
         if (static_cast<uint32_t>(lv) <= max_levels) level_widths[lv - 1]++;
     }
+    return FSQL_OK;
+  });
+}
+
+int fsql_sum_plan_info(size_t rows, uint32_t width, uint32_t out_width, uint32_t* gates, uint32_t* levels,
+                       uint32_t* literal_outputs) {
+  return guarded([&]() -> int {
+    fsql::Netlist nl;
+    if (!fsql::build_sum_netlist(rows, width, out_width, &nl)) return arg_error("bad aggregation shape");
+    if (gates) *gates = static_cast<uint32_t>(nl.type.size());
+    if (levels) *levels = static_cast<uint32_t>(nl.levels);
+    if (literal_outputs) *literal_outputs = static_cast<uint32_t>(nl.literal_outs.size());
+    return FSQL_OK;
+  });
+}
+
+int fsql_plan_info_plain(uint32_t pred, uint32_t width, uint32_t n_payloads, uint32_t payload_width,
+                         const uint64_t* consts, uint32_t* gates_per_row, uint32_t* levels, uint32_t* level_widths,
+                         uint32_t max_levels, uint32_t* literal_outputs) {
+  return guarded([&]() -> int {
+    if (!consts) return arg_error("null constants");
+    const bool range = pred == FSQL_RANGE || pred == FSQL_RANGE_MAJ;
+    const uint64_t k0 = consts[0], k1 = range ? consts[1] : 0;
+    if (width >= 1 && width < 64 && (k0 >> width || k1 >> width)) return arg_error("constant wider than the column");
+    fsql::Netlist nl;
+    if (!fsql::build_netlist_plain(pred, width, n_payloads, payload_width, k0, k1, &nl))
+      return arg_error("bad predicate shape");
+    if (gates_per_row) *gates_per_row = static_cast<uint32_t>(nl.type.size());
+    if (levels) *levels = static_cast<uint32_t>(nl.levels);
+    if (level_widths) {
+      for (uint32_t k = 0; k < max_levels; ++k) level_widths[k] = 0;
+      for (int lv : nl.level)
+        if (static_cast<uint32_t>(lv) <= max_levels) level_widths[lv - 1]++;
+    }
+    if (literal_outputs) *literal_outputs = static_cast<uint32_t>(nl.literal_outs.size());
     return FSQL_OK;
   });
 }

@@ -209,6 +209,8 @@ __device__ __forceinline__ Lin gate_lin(uint32_t type) {
     case FSQL_ANDYN: return {0u - E, 1u, M, 0u};
     case FSQL_ORNY: return {E, M, 1u, 0u};
     case FSQL_MAJNYY: return {0u, M, 1u, 1u};  // majority of (not a, b, c): sign of -a + b + c
+    case FSQL_XOR3: return {0u, 0u - 2u, 0u - 2u, 0u - 2u};  // parity of (a, b, c): sign of -2(a + b + c)
+    case FSQL_MAJ: return {0u, 1u, 1u, 1u};  // majority of (a, b, c): sign of a + b + c
     default: return {E, 1u, M, 0u};  // FSQL_ORYN (other values compute ORYN)
   }
 }
@@ -539,7 +541,7 @@ void scan_descriptors(const Netlist& nl, const ScanIO& io, GateDesc* out, std::v
   for (int g = 0; g < nl.first_mask_gate; ++g)
     if (nl.n_inputs + g != nl.match_wire) scratch_index[g] = n_int++;
   const int w = static_cast<int>(io.width);
-  const int nconst = (io.pred == FSQL_RANGE || io.pred == FSQL_RANGE_MAJ) ? 2 * w : w;
+  const int nconst = nl.n_const;
   const int pw = static_cast<int>(io.payload_width);
   auto gate_out = [&](int g, size_t row) -> uint32_t* {
     if (g >= nl.first_mask_gate) {
@@ -578,6 +580,39 @@ void scan_descriptors(const Netlist& nl, const ScanIO& io, GateDesc* out, std::v
   (*level_offset)[nl.levels] = pos;
 }
 
+void scan_literals(const Netlist& nl, const ScanIO& io, std::vector<OutDesc>* out) {
+  out->clear();
+  if (nl.literal_outs.empty()) return;
+  const size_t W = io.words;
+  const int w = static_cast<int>(io.width);
+  const int pw = static_cast<int>(io.payload_width);
+  std::vector<long> scratch_index(nl.type.size(), -1);
+  long n_int = 0;
+  for (int g = 0; g < nl.first_mask_gate; ++g)
+    if (nl.n_inputs + g != nl.match_wire) scratch_index[g] = n_int++;
+  auto wire_ptr = [&](int id, size_t row) -> const uint32_t* {
+    if (id < 0) return nullptr;
+    if (id < w) return io.column + (row * io.width + id) * W;
+    if (id < w + nl.n_const) return io.cst + static_cast<size_t>(id - w) * W;
+    if (id < nl.n_inputs) {
+      const int m = id - w - nl.n_const;
+      return io.payloads[m / pw] + (row * pw + m % pw) * W;
+    }
+    // an intermediate gate output (the mask gates and the match gate are never literal sources)
+    return io.wires + (row * n_int + scratch_index[id - nl.n_inputs]) * W;
+  };
+  out->reserve(io.rows * nl.literal_outs.size());
+  for (size_t row = 0; row < io.rows; ++row)
+    for (const auto& l : nl.literal_outs) {
+      OutDesc d;
+      d.src = wire_ptr(l.wire, row);
+      d.dst = l.target < 0 ? io.match + row * W : io.outs[l.target / pw] + (row * pw + l.target % pw) * W;
+      d.mode = l.mode;
+      d.pad = 0;
+      out->push_back(d);
+    }
+}
+
 // ------------------------------------------------------------------ scan plan
 
 struct Plan {
@@ -590,17 +625,31 @@ struct Plan {
   uint32_t* match = nullptr;
   std::vector<uint32_t*> outs;
   uint32_t* wires = nullptr;
+  bool plain = false;  // plaintext constants k0 (and k1 for RANGE)
+  uint64_t k0 = 0, k1 = 0;
   // plan
   std::vector<size_t> level_offset;  // descriptors of level L: [level_offset[L], level_offset[L+1])
   size_t total = 0;
+  size_t n_lits = 0;  // outputs no gate writes, descriptors in Ctx::d_lits
   // the plan's level launches captured as a CUDA graph (rebuilt if the
   // context's descriptor or sample buffers move or its launch shape changes)
   cudaGraphExec_t graph = nullptr;
   const GateDesc* graph_desc = nullptr;
   const uint32_t* graph_big = nullptr;
+  const OutDesc* graph_lits = nullptr;
   int graph_br_gates = 0;
+  // SUM aggregation plans: key and the buffers they own
+  const uint32_t* agg_in = nullptr;
+  uint32_t* agg_out = nullptr;
+  uint32_t agg_width = 0, agg_out_width = 0;
+  GateDesc* own_desc = nullptr;
+  OutDesc* own_lits = nullptr;
+  uint32_t* own_wires = nullptr;
   ~Plan() {
     if (graph) cudaGraphExecDestroy(graph);
+    cudaFree(own_desc);
+    cudaFree(own_lits);
+    cudaFree(own_wires);
   }
 };
 
@@ -717,12 +766,17 @@ void device_free(Ctx& c) {
   cudaFree(c.d_stage);
   if (c.h_desc) cudaFreeHost(c.h_desc);
   if (c.desc_event) cudaEventDestroy(static_cast<cudaEvent_t>(c.desc_event));
+  cudaFree(c.d_lits);
+  c.d_lits = nullptr;
+  c.lits_cap = 0;
   if (c.capture_stream) cudaStreamDestroy(static_cast<cudaStream_t>(c.capture_stream));
   c.capture_stream = nullptr;
   delete static_cast<Profile*>(c.prof);
   c.prof = nullptr;
   delete c.plan;
   c.plan = nullptr;
+  delete c.agg_plan;
+  c.agg_plan = nullptr;
   c.d_bkhat = nullptr;
   c.d_ksk = nullptr;
   c.d_tables = nullptr;
@@ -917,12 +971,17 @@ Ctx* device_ctx(fsql_ctx* ctx) {
 
 int check_types_host(size_t count) { return count > (size_t(1) << 31) ? arg_error("too many gates") : FSQL_OK; }
 
-// Build (or reuse) the descriptor plan of a scan and upload it to c.d_desc.
+// Build (or reuse) the descriptor plan of a scan and upload it to c.d_desc
+// (and the outputs no gate writes to c.d_lits).  plain: the constants are the
+// plaintext values k0 (and k1), d_const is unused.
 int prepare_scan(Ctx& c, const uint32_t* d_column, size_t rows, uint32_t width, uint32_t pred,
                  const uint32_t* d_const, uint32_t n_payloads, const uint32_t* const* d_payloads,
-                 uint32_t payload_width, uint32_t* d_match, uint32_t* const* d_out_payloads, void* stream) {
+                 uint32_t payload_width, uint32_t* d_match, uint32_t* const* d_out_payloads, void* stream,
+                 bool plain = false, uint64_t k0 = 0, uint64_t k1 = 0) {
   fsql::Netlist nl;
-  if (!fsql::build_netlist(pred, width, n_payloads, payload_width, &nl)) return arg_error("bad predicate shape");
+  const bool ok = plain ? fsql::build_netlist_plain(pred, width, n_payloads, payload_width, k0, k1, &nl)
+                        : fsql::build_netlist(pred, width, n_payloads, payload_width, &nl);
+  if (!ok) return arg_error("bad predicate shape");
   const size_t W = c.p.n + 1;
   const int G = static_cast<int>(nl.type.size());
   const long n_int = fsql::scan_internal_wires(nl);
@@ -943,7 +1002,7 @@ int prepare_scan(Ctx& c, const uint32_t* d_column, size_t rows, uint32_t width, 
   fsql::Plan* pl = c.plan;
   bool same = pl && pl->column == d_column && pl->rows == rows && pl->width == width && pl->pred == pred &&
               pl->n_payloads == n_payloads && pl->payload_width == payload_width && pl->cst == d_const &&
-              pl->match == d_match && pl->wires == c.d_wires;
+              pl->match == d_match && pl->wires == c.d_wires && pl->plain == plain && pl->k0 == k0 && pl->k1 == k1;
   for (uint32_t q = 0; same && q < n_payloads; ++q)
     same = pl->payloads[q] == d_payloads[q] && pl->outs[q] == d_out_payloads[q];
   if (same) return FSQL_OK;
@@ -962,6 +1021,9 @@ int prepare_scan(Ctx& c, const uint32_t* d_column, size_t rows, uint32_t width, 
   pl->match = d_match;
   pl->outs.assign(d_out_payloads, d_out_payloads + n_payloads);
   pl->wires = c.d_wires;
+  pl->plain = plain;
+  pl->k0 = k0;
+  pl->k1 = k1;
 
   const size_t total = rows * static_cast<size_t>(G);
   if (total > c.h_desc_cap) {
@@ -1001,6 +1063,29 @@ int prepare_scan(Ctx& c, const uint32_t* d_column, size_t rows, uint32_t width, 
     return rc;
   }
   cudaStream_t st = static_cast<cudaStream_t>(stream);
+  std::vector<fsql::OutDesc> lits;
+  fsql::scan_literals(nl, io, &lits);
+  pl->n_lits = lits.size();
+  if (!lits.empty()) {
+    if (lits.size() > c.lits_cap) {
+      cudaFree(c.d_lits);
+      c.d_lits = nullptr;
+      c.lits_cap = 0;
+      if (cudaMalloc(&c.d_lits, lits.size() * sizeof(fsql::OutDesc)) != cudaSuccess) {
+        fsql::set_error("scan literal descriptor allocation failed");
+        delete pl;
+        return FSQL_ERR_OOM;
+      }
+      c.lits_cap = lits.size();
+    }
+    // pageable source: the copy is staged before cudaMemcpyAsync returns
+    if (cudaMemcpyAsync(c.d_lits, lits.data(), lits.size() * sizeof(fsql::OutDesc), cudaMemcpyHostToDevice, st) !=
+        cudaSuccess) {
+      fsql::set_error("literal descriptor upload failed");
+      delete pl;
+      return FSQL_ERR_CUDA;
+    }
+  }
   if (cudaMemcpyAsync(c.d_desc, c.h_desc, total * sizeof(GateDesc), cudaMemcpyHostToDevice, st) != cudaSuccess ||
       cudaEventRecord(static_cast<cudaEvent_t>(c.desc_event), st) != cudaSuccess) {
     fsql::set_error("descriptor upload failed");
@@ -1008,6 +1093,79 @@ int prepare_scan(Ctx& c, const uint32_t* d_column, size_t rows, uint32_t width, 
     return FSQL_ERR_CUDA;
   }
   c.plan = pl;
+  return FSQL_OK;
+}
+
+// Build (or reuse) the SUM-aggregation plan for these arguments: the
+// circuit's descriptors, output descriptors and intermediate wires live in
+// buffers the plan owns.
+int prepare_sum(Ctx& c, const uint32_t* d_in, size_t rows, uint32_t width, uint32_t out_width, uint32_t* d_out,
+                void* stream) {
+  fsql::Plan* pl = c.agg_plan;
+  if (pl && pl->agg_in == d_in && pl->rows == rows && pl->agg_width == width && pl->agg_out_width == out_width &&
+      pl->agg_out == d_out)
+    return FSQL_OK;
+  delete c.agg_plan;
+  c.agg_plan = nullptr;
+  fsql::Netlist nl;
+  if (!fsql::build_sum_netlist(rows, width, out_width, &nl)) return arg_error("bad aggregation shape");
+  const size_t W = c.p.n + 1, G = nl.type.size();
+  pl = new fsql::Plan();
+  pl->agg_in = d_in;
+  pl->rows = rows;
+  pl->agg_width = width;
+  pl->agg_out_width = out_width;
+  pl->agg_out = d_out;
+  if ((G && (cudaMalloc(&pl->own_desc, G * sizeof(fsql::GateDesc)) != cudaSuccess ||
+             cudaMalloc(&pl->own_wires, G * W * 4) != cudaSuccess)) ||
+      cudaMalloc(&pl->own_lits, nl.literal_outs.size() * sizeof(fsql::OutDesc)) != cudaSuccess) {
+    delete pl;
+    fsql::set_error("aggregation scratch allocation failed");
+    return FSQL_ERR_OOM;
+  }
+  auto wire_ptr = [&](int id) -> const uint32_t* {
+    if (id < nl.n_inputs) return d_in + static_cast<size_t>(id) * W;  // input bit (r, j) = r * width + j
+    return pl->own_wires + static_cast<size_t>(id - nl.n_inputs) * W;
+  };
+  std::vector<fsql::GateDesc> desc(G);
+  pl->level_offset.assign(nl.levels + 1, 0);
+  size_t pos = 0;
+  for (int L = 1; L <= nl.levels; ++L) {
+    pl->level_offset[L - 1] = pos;
+    for (size_t g = 0; g < G; ++g) {
+      if (nl.level[g] != L) continue;
+      fsql::GateDesc& d = desc[pos++];
+      d.a = wire_ptr(nl.a[g]);
+      d.b = wire_ptr(nl.b[g]);
+      d.c = nl.c[g] >= 0 ? wire_ptr(nl.c[g]) : nullptr;
+      d.out = pl->own_wires + g * W;
+      d.type = static_cast<uint32_t>(nl.type[g]);
+      d.pad = 0;
+    }
+  }
+  pl->level_offset[nl.levels] = pos;
+  pl->total = pos;
+  std::vector<fsql::OutDesc> lits;
+  for (const auto& l : nl.literal_outs) {
+    fsql::OutDesc d;
+    d.src = l.wire >= 0 ? wire_ptr(l.wire) : nullptr;
+    d.dst = d_out + static_cast<size_t>(l.target) * W;
+    d.mode = l.mode;
+    d.pad = 0;
+    lits.push_back(d);
+  }
+  pl->n_lits = lits.size();
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  // pageable sources: each copy is staged before cudaMemcpyAsync returns
+  if ((G && cudaMemcpyAsync(pl->own_desc, desc.data(), G * sizeof(fsql::GateDesc), cudaMemcpyHostToDevice, st) !=
+                cudaSuccess) ||
+      cudaMemcpyAsync(pl->own_lits, lits.data(), lits.size() * sizeof(fsql::OutDesc), cudaMemcpyHostToDevice, st) !=
+          cudaSuccess) {
+    delete pl;
+    fsql::set_error("aggregation descriptor upload failed");
+    return FSQL_ERR_CUDA;
+  }
+  c.agg_plan = pl;
   return FSQL_OK;
 }
 
@@ -1024,6 +1182,73 @@ int validate_scan(Ctx* c, const uint32_t* column, size_t rows, uint32_t width, u
     if (!payloads[q] || !outs[q]) return arg_error("null payload pointer");
   if (rows > (size_t(1) << 26)) return arg_error("too many rows");
   (void)c;
+  return FSQL_OK;
+}
+
+// Run the prepared plan: every level's gates (batched, or one gate per
+// launch), then the outputs no gate writes.  The batched sequence is
+// captured once per plan as a CUDA graph on the context's capture stream and
+// replayed on the caller's stream.  Called with c->mu held.
+int execute_plan(Ctx* c, fsql::Plan& pl, const fsql::GateDesc* d_desc, const fsql::OutDesc* d_lits, int per_gate,
+                 void* stream) {
+  const int n = static_cast<int>(c->p.n);
+  size_t widest = 0;
+  for (size_t L = 0; L + 1 < pl.level_offset.size(); ++L)
+    widest = std::max(widest, pl.level_offset[L + 1] - pl.level_offset[L]);
+  int rc = fsql::ensure_big(*c, per_gate ? 1 : std::min(widest, fsql::kMaxChunk));
+  if (rc) return rc;
+  if (per_gate) {
+    for (size_t g = 0; g < pl.total; ++g) {
+      rc = fsql::launch_gates(*c, d_desc + g, 1, c->d_big, stream);
+      if (rc) return rc;
+    }
+    return fsql::launch_literals(d_lits, pl.n_lits, n, stream);
+  }
+  auto launch_all = [&](void* st) -> int {
+    for (size_t L = 0; L + 1 < pl.level_offset.size(); ++L) {
+      const int r = fsql::launch_gates(*c, d_desc + pl.level_offset[L],
+                                       pl.level_offset[L + 1] - pl.level_offset[L], c->d_big, st);
+      if (r) return r;
+    }
+    return fsql::launch_literals(d_lits, pl.n_lits, n, st);
+  };
+  const auto* prof = static_cast<const fsql::Profile*>(c->prof);
+  if (prof && prof->recording) return launch_all(stream);  // per-launch events need plain launches
+  fsql::Plan& mp = pl;
+  if (!mp.graph || mp.graph_desc != d_desc || mp.graph_big != c->d_big || mp.graph_lits != d_lits ||
+      mp.graph_br_gates != c->br_gates) {
+    if (mp.graph) cudaGraphExecDestroy(mp.graph);
+    mp.graph = nullptr;
+    cudaStream_t cs = static_cast<cudaStream_t>(c->capture_stream);
+    if (!cs) {
+      if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) return launch_all(stream);
+      c->capture_stream = cs;
+    }
+    cudaGraph_t g = nullptr;
+    if (cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return launch_all(stream);
+    rc = launch_all(cs);
+    const cudaError_t ec = cudaStreamEndCapture(cs, &g);
+    if (rc || ec != cudaSuccess || !g) {
+      if (g) cudaGraphDestroy(g);
+      cudaGetLastError();
+      return rc ? rc : launch_all(stream);
+    }
+    const cudaError_t ei = cudaGraphInstantiate(&mp.graph, g, 0);
+    cudaGraphDestroy(g);
+    if (ei != cudaSuccess) {
+      mp.graph = nullptr;
+      cudaGetLastError();
+      return launch_all(stream);
+    }
+    mp.graph_desc = d_desc;
+    mp.graph_big = c->d_big;
+    mp.graph_lits = d_lits;
+    mp.graph_br_gates = c->br_gates;
+  }
+  if (cudaGraphLaunch(mp.graph, static_cast<cudaStream_t>(stream)) != cudaSuccess) {
+    fsql::set_error("scan graph launch failed");
+    return FSQL_ERR_CUDA;
+  }
   return FSQL_OK;
 }
 
@@ -1113,65 +1338,40 @@ int fsql_scan_select(fsql_ctx* ctx, const uint32_t* d_column, size_t rows, uint3
   int rc = prepare_scan(*c, d_column, rows, width, pred, d_const, n_payloads, d_payloads, payload_width, d_match,
                         d_out_payloads, stream);
   if (rc) return rc;
-  const fsql::Plan& pl = *c->plan;
-  size_t widest = 0;
-  for (size_t L = 0; L + 1 < pl.level_offset.size(); ++L)
-    widest = std::max(widest, pl.level_offset[L + 1] - pl.level_offset[L]);
-  rc = fsql::ensure_big(*c, per_gate ? 1 : std::min(widest, fsql::kMaxChunk));
+  return execute_plan(c, *c->plan, c->d_desc, c->d_lits, per_gate, stream);
+}
+
+int fsql_aggregate_sum(fsql_ctx* ctx, const uint32_t* d_values, size_t rows, uint32_t width, uint32_t out_width,
+                       uint32_t* d_out, void* stream) {
+  Ctx* c = device_ctx(ctx);
+  if (!c) return FSQL_ERR_ARG;
+  if ((rows && !d_values) || !d_out) return arg_error("null values or output pointer");
+  std::lock_guard<std::mutex> lk(c->mu);
+  int rc = prepare_sum(*c, d_values, rows, width, out_width, d_out, stream);
   if (rc) return rc;
-  if (per_gate) {
-    for (size_t g = 0; g < pl.total; ++g) {
-      rc = fsql::launch_gates(*c, c->d_desc + g, 1, c->d_big, stream);
-      if (rc) return rc;
-    }
-    return FSQL_OK;
-  }
-  auto launch_levels = [&](void* st) -> int {
-    for (size_t L = 0; L + 1 < pl.level_offset.size(); ++L) {
-      const int r = fsql::launch_gates(*c, c->d_desc + pl.level_offset[L],
-                                       pl.level_offset[L + 1] - pl.level_offset[L], c->d_big, st);
-      if (r) return r;
-    }
-    return FSQL_OK;
-  };
-  const auto* prof = static_cast<const fsql::Profile*>(c->prof);
-  if (prof && prof->recording) return launch_levels(stream);  // per-launch events need plain launches
-  // CUDA graph of the whole level sequence, captured once per plan on the
-  // context's capture stream and replayed on the caller's stream
-  fsql::Plan& mp = *c->plan;
-  if (!mp.graph || mp.graph_desc != c->d_desc || mp.graph_big != c->d_big || mp.graph_br_gates != c->br_gates) {
-    if (mp.graph) cudaGraphExecDestroy(mp.graph);
-    mp.graph = nullptr;
-    cudaStream_t cs = static_cast<cudaStream_t>(c->capture_stream);
-    if (!cs) {
-      if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) return launch_levels(stream);
-      c->capture_stream = cs;
-    }
-    cudaGraph_t g = nullptr;
-    if (cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return launch_levels(stream);
-    rc = launch_levels(cs);
-    const cudaError_t ec = cudaStreamEndCapture(cs, &g);
-    if (rc || ec != cudaSuccess || !g) {
-      if (g) cudaGraphDestroy(g);
-      cudaGetLastError();
-      return rc ? rc : launch_levels(stream);
-    }
-    const cudaError_t ei = cudaGraphInstantiate(&mp.graph, g, 0);
-    cudaGraphDestroy(g);
-    if (ei != cudaSuccess) {
-      mp.graph = nullptr;
-      cudaGetLastError();
-      return launch_levels(stream);
-    }
-    mp.graph_desc = c->d_desc;
-    mp.graph_big = c->d_big;
-    mp.graph_br_gates = c->br_gates;
-  }
-  if (cudaGraphLaunch(mp.graph, static_cast<cudaStream_t>(stream)) != cudaSuccess) {
-    fsql::set_error("scan graph launch failed");
-    return FSQL_ERR_CUDA;
-  }
-  return FSQL_OK;
+  return execute_plan(c, *c->agg_plan, c->agg_plan->own_desc, c->agg_plan->own_lits, 0, stream);
+}
+
+int fsql_scan_select_plain(fsql_ctx* ctx, const uint32_t* d_column, size_t rows, uint32_t width, uint32_t pred,
+                           const uint64_t* consts, uint32_t n_payloads, const uint32_t* const* d_payloads,
+                           uint32_t payload_width, uint32_t* d_match, uint32_t* const* d_out_payloads, int per_gate,
+                           void* stream) {
+  Ctx* c = device_ctx(ctx);
+  if (!c) return FSQL_ERR_ARG;
+  if (!consts) return arg_error("null constants");
+  // the constant pointer is host memory here; only its presence is checked by validate_scan
+  if (int rc = validate_scan(c, d_column, rows, width, pred, d_column, n_payloads, d_payloads, payload_width,
+                             d_match, d_out_payloads))
+    return rc;
+  const bool range = pred == FSQL_RANGE || pred == FSQL_RANGE_MAJ;
+  const uint64_t k0 = consts[0], k1 = range ? consts[1] : 0;
+  if (width < 64 && (k0 >> width || k1 >> width)) return arg_error("constant wider than the column");
+  if (rows == 0) return FSQL_OK;
+  std::lock_guard<std::mutex> lk(c->mu);
+  int rc = prepare_scan(*c, d_column, rows, width, pred, nullptr, n_payloads, d_payloads, payload_width, d_match,
+                        d_out_payloads, stream, true, k0, k1);
+  if (rc) return rc;
+  return execute_plan(c, *c->plan, c->d_desc, c->d_lits, per_gate, stream);
 }
 
 int fsql_scan_select_host(fsql_ctx* ctx, const uint32_t* h_column, size_t rows, uint32_t width, uint32_t pred,

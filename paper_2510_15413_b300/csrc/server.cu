@@ -82,8 +82,10 @@ struct Query {
   Netlist nl;
   std::vector<size_t> level_offset;
   size_t total_gates = 0;
-  size_t bytes = 0, off = 0;  // pool block: descriptors then wires
+  size_t bytes = 0, off = 0;  // pool block: gate descriptors, output descriptors, wires
   GateDesc* d_desc = nullptr;
+  OutDesc* d_lits = nullptr;  // outputs no gate writes (plaintext constants)
+  size_t n_lits = 0;
   int level = 0;              // next level to bootstrap
   size_t done_in_level = 0;   // gates of that level already launched
   int state = Q_WAITING;
@@ -91,10 +93,13 @@ struct Query {
   Clock::time_point t_submit, t_done;
 };
 
+size_t round256(size_t b) { return (b + 255) / 256 * 256; }
+
 size_t query_bytes(const Netlist& nl, const fsql_query& q, size_t words) {
   const size_t desc = q.rows * nl.type.size() * sizeof(GateDesc);
+  const size_t lits = q.rows * nl.literal_outs.size() * sizeof(OutDesc);
   const size_t wires = q.rows * static_cast<size_t>(scan_internal_wires(nl)) * words * 4;
-  return (desc + 255) / 256 * 256 + wires;
+  return round256(desc) + round256(lits) + wires;
 }
 
 }  // namespace
@@ -134,7 +139,9 @@ struct Server {
       if (!pool.alloc(q->bytes, &off)) break;
       q->off = off;
       q->d_desc = reinterpret_cast<GateDesc*>(d_pool + off);
-      const size_t desc_bytes = (q->total_gates * sizeof(GateDesc) + 255) / 256 * 256;
+      const size_t desc_bytes = round256(q->total_gates * sizeof(GateDesc));
+      const size_t lit_bytes = round256(q->q.rows * q->nl.literal_outs.size() * sizeof(OutDesc));
+      q->d_lits = reinterpret_cast<OutDesc*>(d_pool + off + desc_bytes);
       ScanIO io;
       io.column = q->q.d_column;
       io.rows = q->q.rows;
@@ -146,11 +153,16 @@ struct Server {
       io.payload_width = q->q.payload_width;
       io.match = q->q.d_match;
       io.outs = q->q.d_out_payloads;
-      io.wires = reinterpret_cast<uint32_t*>(d_pool + off + desc_bytes);
+      io.wires = reinterpret_cast<uint32_t*>(d_pool + off + desc_bytes + lit_bytes);
       io.words = ctx->p.n + 1;
       std::vector<GateDesc> h(q->total_gates);
       scan_descriptors(q->nl, io, h.data(), &q->level_offset);
-      if (cudaMemcpy(q->d_desc, h.data(), h.size() * sizeof(GateDesc), cudaMemcpyHostToDevice) != cudaSuccess) {
+      std::vector<OutDesc> hl;
+      scan_literals(q->nl, io, &hl);
+      q->n_lits = hl.size();
+      if (cudaMemcpy(q->d_desc, h.data(), h.size() * sizeof(GateDesc), cudaMemcpyHostToDevice) != cudaSuccess ||
+          (!hl.empty() &&
+           cudaMemcpy(q->d_lits, hl.data(), hl.size() * sizeof(OutDesc), cudaMemcpyHostToDevice) != cudaSuccess)) {
         pool.release(q->off, q->bytes);
         q->state = Q_FAILED;
         waiting.pop_front();
@@ -159,6 +171,32 @@ struct Server {
       q->state = Q_RUNNING;
       running.push_back(q);
       waiting.pop_front();
+    }
+  }
+
+  // A query whose gates are all done: write the outputs no gate writes, then
+  // mark it done (caller holds mu; the literal kernel is short).
+  void finish_locked(Query* q) {
+    if (q->n_lits && (launch_literals(q->d_lits, q->n_lits, static_cast<int>(ctx->p.n), stream) != FSQL_OK ||
+                      cudaStreamSynchronize(stream) != cudaSuccess)) {
+      error = "literal outputs failed";
+      q->state = Q_FAILED;
+      return;
+    }
+    q->state = Q_DONE;
+    q->t_done = Clock::now();
+    ++completed;
+    latencies_ms.push_back(std::chrono::duration<double, std::milli>(q->t_done - q->t_submit).count());
+  }
+
+  void release_finished_locked() {
+    for (auto it = running.begin(); it != running.end();) {
+      if ((*it)->state == Q_DONE || (*it)->state == Q_FAILED) {
+        pool.release((*it)->off, (*it)->bytes);
+        it = running.erase(it);
+      } else {
+        ++it;
+      }
     }
   }
 
@@ -180,6 +218,17 @@ struct Server {
         } else {
           ++it;
         }
+      }
+      // queries with no gate left (a plaintext constant can leave none at all)
+      bool finished = false;
+      for (Query* q : running)
+        if (q->state == Q_RUNNING && q->level == q->nl.levels) {
+          finish_locked(q);
+          finished = true;
+        }
+      if (finished) {
+        release_finished_locked();
+        cv.notify_all();
       }
       if (running.empty()) {
         cv.wait_for(lk, std::chrono::milliseconds(50));
@@ -228,21 +277,9 @@ struct Server {
           ++q->level;
           q->done_in_level = 0;
         }
-        if (q->level == q->nl.levels) {
-          q->state = Q_DONE;
-          q->t_done = t1;
-          ++completed;
-          latencies_ms.push_back(std::chrono::duration<double, std::milli>(q->t_done - q->t_submit).count());
-        }
+        if (q->level == q->nl.levels) finish_locked(q);
       }
-      for (auto it = running.begin(); it != running.end();) {
-        if ((*it)->state == Q_DONE || (*it)->state == Q_FAILED) {
-          pool.release((*it)->off, (*it)->bytes);
-          it = running.erase(it);
-        } else {
-          ++it;
-        }
-      }
+      release_finished_locked();
       cv.notify_all();
     }
   }
@@ -302,13 +339,22 @@ int fsql_server_submit(fsql_server* server, const fsql_query* q, uint64_t* id) {
   if (!server || !q || !id) return arg_error("null argument");
   auto* s = reinterpret_cast<Server*>(server);
   if (q->rows == 0) return arg_error("empty table");
-  if (!q->d_column || !q->d_const || !q->d_match) return arg_error("null column, constant or match pointer");
+  if (!q->d_column || (!q->d_const && !q->plain) || !q->d_match)
+    return arg_error("null column, constant or match pointer");
   if (q->n_payloads > FSQL_MAX_PAYLOADS) return arg_error("too many payload columns");
   for (uint32_t k = 0; k < q->n_payloads; ++k)
     if (!q->d_payloads[k] || !q->d_out_payloads[k]) return arg_error("null payload pointer");
   auto* qq = new fsql::Query();
   qq->q = *q;
-  if (!fsql::build_netlist(q->pred, q->width, q->n_payloads, q->payload_width, &qq->nl)) {
+  const bool range = q->pred == FSQL_RANGE || q->pred == FSQL_RANGE_MAJ;
+  if (q->plain && q->width < 64 && (q->consts[0] >> q->width || (range && q->consts[1] >> q->width))) {
+    delete qq;
+    return arg_error("constant wider than the column");
+  }
+  const bool built = q->plain ? fsql::build_netlist_plain(q->pred, q->width, q->n_payloads, q->payload_width,
+                                                          q->consts[0], range ? q->consts[1] : 0, &qq->nl)
+                              : fsql::build_netlist(q->pred, q->width, q->n_payloads, q->payload_width, &qq->nl);
+  if (!built) {
     delete qq;
     return arg_error("bad predicate shape");
   }

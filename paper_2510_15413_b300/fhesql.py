@@ -16,7 +16,7 @@ LIB_PATH = os.path.join(HERE, "libfhesql.so")
 
 FSQL_OK, FSQL_ERR_ARG, FSQL_ERR_OOM, FSQL_ERR_CUDA, FSQL_ERR_TIMEOUT, FSQL_ERR_ADMISSION, FSQL_ERR_UNSUPPORTED = range(7)
 GATES = {"NAND": 0, "AND": 1, "OR": 2, "XOR": 3, "XNOR": 4, "NOR": 5, "ANDNY": 6, "ANDYN": 7, "ORNY": 8, "ORYN": 9,
-         "MAJNYY": 10}
+         "MAJNYY": 10, "XOR3": 11, "MAJ": 12}
 FSQL_EQ, FSQL_LT, FSQL_RANGE, FSQL_LT_MAJ, FSQL_RANGE_MAJ = 0, 1, 2, 3, 4
 FSQL_ENGINE_DEFAULT, FSQL_ENGINE_GOLDILOCKS, FSQL_ENGINE_DUAL_PRIME = -1, 0, 1
 ENGINES = {"default": -1, "goldilocks": 0, "dual_prime": 1}
@@ -28,6 +28,7 @@ API = ["fsql_params_default", "fsql_params_toy", "fsql_ctx_create", "fsql_ctx_cr
        "fsql_ctx_device_bytes", "fsql_export_keys", "fsql_encrypt", "fsql_encrypt_bits", "fsql_encrypt_uint",
        "fsql_phase", "fsql_decrypt_bits", "fsql_decrypt_uint", "fsql_gate_batch", "fsql_blind_rotate_extract",
        "fsql_keyswitch", "fsql_debug_ntt_mul", "fsql_plan_info", "fsql_scan_select", "fsql_scan_select_host",
+       "fsql_scan_select_plain", "fsql_plan_info_plain", "fsql_aggregate_sum", "fsql_sum_plan_info",
        "fsql_profile_begin", "fsql_profile_end", "fsql_gate_batch_noalloc", "fsql_server_create",
        "fsql_server_submit", "fsql_server_status", "fsql_server_wait", "fsql_server_cancel",
        "fsql_server_get_stats", "fsql_server_destroy", "fsql_last_error"]
@@ -49,7 +50,8 @@ class fsql_kernel_times(C.Structure):
 class fsql_query(C.Structure):
     _fields_ = [("d_column", C.c_void_p), ("rows", C.c_size_t), ("width", C.c_uint32), ("pred", C.c_uint32),
                 ("d_const", C.c_void_p), ("n_payloads", C.c_uint32), ("payload_width", C.c_uint32),
-                ("d_payloads", C.c_void_p * 8), ("d_match", C.c_void_p), ("d_out_payloads", C.c_void_p * 8)]
+                ("d_payloads", C.c_void_p * 8), ("d_match", C.c_void_p), ("d_out_payloads", C.c_void_p * 8),
+                ("plain", C.c_uint32), ("pad", C.c_uint32), ("consts", C.c_uint64 * 2)]
 
 
 class fsql_server_stats(C.Structure):
@@ -103,6 +105,11 @@ def load() -> C.CDLL:
         "fsql_plan_info": (i32, [u32, u32, u32, u32, C.POINTER(u32), C.POINTER(u32), vp, u32]),
         "fsql_scan_select": (i32, [vp, vp, sz, u32, u32, vp, u32, vp, u32, vp, vp, i32, vp]),
         "fsql_scan_select_host": (i32, [vp, vp, sz, u32, u32, vp, u32, vp, u32, vp, vp, vp]),
+        "fsql_scan_select_plain": (i32, [vp, vp, sz, u32, u32, vp, u32, vp, u32, vp, vp, i32, vp]),
+        "fsql_aggregate_sum": (i32, [vp, vp, sz, u32, u32, vp, vp]),
+        "fsql_sum_plan_info": (i32, [sz, u32, u32, C.POINTER(u32), C.POINTER(u32), C.POINTER(u32)]),
+        "fsql_plan_info_plain": (i32, [u32, u32, u32, u32, vp, C.POINTER(u32), C.POINTER(u32), vp, u32,
+                                       C.POINTER(u32)]),
         "fsql_profile_begin": (i32, [vp]),
         "fsql_profile_end": (i32, [vp, C.POINTER(fsql_kernel_times)]),
         "fsql_server_create": (i32, [vp, sz, sz, C.POINTER(vp)]),
@@ -172,6 +179,28 @@ def plan_info(pred: int, width: int, n_payloads: int, payload_width: int, max_le
     _check(load().fsql_plan_info(pred, width, n_payloads, payload_width, C.byref(g), C.byref(lv),
                                  widths.ctypes.data, max_levels))
     return int(g.value), [int(x) for x in widths[: lv.value]]
+
+
+def sum_plan_info(rows: int, width: int, out_width: int):
+    """(gates, levels, literal outputs) of the SUM-aggregation circuit."""
+    g, lv, lit = C.c_uint32(), C.c_uint32(), C.c_uint32()
+    _check(load().fsql_sum_plan_info(rows, width, out_width, C.byref(g), C.byref(lv), C.byref(lit)))
+    return int(g.value), int(lv.value), int(lit.value)
+
+
+def _consts_array(consts):
+    k = [int(v) for v in consts] + [0, 0]
+    return (C.c_uint64 * 2)(k[0], k[1])
+
+
+def plan_info_plain(pred: int, width: int, n_payloads: int, payload_width: int, consts, max_levels: int = 256):
+    """(gates per row, level widths, outputs per row no gate writes) of the
+    plaintext-constant circuit for consts = (k,) or (lo, hi)."""
+    g, lv, lit = C.c_uint32(), C.c_uint32(), C.c_uint32()
+    widths = np.zeros(max_levels, np.uint32)
+    _check(load().fsql_plan_info_plain(pred, width, n_payloads, payload_width, _consts_array(consts), C.byref(g),
+                                       C.byref(lv), widths.ctypes.data, max_levels, C.byref(lit)))
+    return int(g.value), [int(x) for x in widths[: lv.value]], int(lit.value)
 
 
 class Context:
@@ -307,6 +336,20 @@ class Context:
         _check(load().fsql_scan_select(self._h, _ptr(column), rows, width, pred, _ptr(const), k, pin,
                                        payload_width, _ptr(match), pout, int(bool(per_gate)), _stream(stream)))
 
+    def aggregate_sum(self, values, rows: int, width: int, out_width: int, out, stream=None) -> None:
+        """fsql_aggregate_sum: values [rows, width, n+1] -> out [out_width, n+1], sum mod 2^out_width."""
+        _check(load().fsql_aggregate_sum(self._h, _ptr(values), rows, width, out_width, _ptr(out), _stream(stream)))
+
+    def scan_select_plain(self, column, rows: int, width: int, pred: int, consts, payloads, payload_width: int,
+                          match, out_payloads, per_gate: bool = False, stream=None) -> None:
+        """fsql_scan_select_plain: consts = (k,) or (lo, hi) as plaintext integers."""
+        k = len(payloads)
+        pin = (C.c_void_p * max(1, k))(*[_ptr(p) for p in payloads])
+        pout = (C.c_void_p * max(1, k))(*[_ptr(p) for p in out_payloads])
+        _check(load().fsql_scan_select_plain(self._h, _ptr(column), rows, width, pred, _consts_array(consts), k,
+                                             pin, payload_width, _ptr(match), pout, int(bool(per_gate)),
+                                             _stream(stream)))
+
     def scan_select_host(self, column, rows: int, width: int, pred: int, const, payloads, payload_width: int,
                          match, out_payloads, stream=None) -> None:
         k = len(payloads)
@@ -336,10 +379,15 @@ class Server:
         self.ctx = ctx
 
     def submit(self, column, rows: int, width: int, pred: int, const, payloads, payload_width: int, match,
-               out_payloads) -> int:
+               out_payloads, plain_consts=None) -> int:
+        """Queue a scan; const is the encrypted constant (device), or None with
+        plain_consts = (k,) or (lo, hi) for plaintext constants."""
         q = fsql_query()
         q.d_column, q.rows, q.width, q.pred = _ptr(column), rows, width, pred
         q.d_const, q.n_payloads, q.payload_width = _ptr(const), len(payloads), payload_width
+        if plain_consts is not None:
+            k = [int(v) for v in plain_consts] + [0, 0]
+            q.plain, q.consts[0], q.consts[1] = 1, k[0], k[1]
         for i, (a, b) in enumerate(zip(payloads, out_payloads)):
             q.d_payloads[i] = _ptr(a)
             q.d_out_payloads[i] = _ptr(b)

@@ -1,6 +1,6 @@
 """Seeded synthetic workloads (plaintext side only; no homomorphic arithmetic).
 
-The paper measures on u32 key/value tables it does not publish (§6 D); these
+The paper measures on u32 key/value tables it does not publish (§6.1 D); these
 generators stand in for them with the shapes of the benchmark workloads:
 
   eq4x16        16 rows, one 4-bit column c ~ U[0,16), one 4-bit payload,
@@ -9,6 +9,8 @@ generators stand in for them with the shapes of the benchmark workloads:
                 WHERE c = k with k drawn from the column (about one match)
   range16x65536 65536 rows, one uint16 column (uniform), two uint16 payloads,
                 WHERE lo <= c < hi with hi - lo = 6554 (10% selectivity)
+  <name>maj     the same table with the majority-chain comparator
+  <name>plain   the same table with the query constants given as plaintexts
   gates(B)      B independent gates: random bit pairs, gate type uniform in
                 {NAND, AND, OR, XOR, XNOR}
 
@@ -38,6 +40,7 @@ class Table:
     payloads: list = field(default_factory=list)  # list of uint64 [rows]
     payload_width: int = 0
     consts: tuple = ()                 # (k,) or (lo, hi)
+    plain: bool = False                # constants given to the server as plaintexts
 
     def const_bits(self) -> np.ndarray:
         bits = []
@@ -65,6 +68,11 @@ class Table:
 
     @property
     def gates_per_row(self) -> int:
+        """Bootstraps per row with encrypted constants (with plaintext
+        constants the count depends on the constant's bits; the library's
+        plan_info_plain gives it)."""
+        if self.plain:
+            raise ValueError("gate count of a plaintext-constant scan depends on the constants")
         w = self.width
         pred = {PRED_EQ: 2 * w - 1, PRED_LT: 4 * w - 3, PRED_RANGE: 2 * (4 * w - 3) + 1,
                 PRED_LT_MAJ: w, PRED_RANGE_MAJ: 2 * w + 1}[self.pred]
@@ -77,7 +85,13 @@ def _rng(seed: int, purpose: int) -> np.random.Generator:
 
 def table(name: str, seed: int = 1, rows: int | None = None) -> Table:
     """A named workload table; the suffix "maj" gives the same table with the
-    majority-chain comparator (LT_MAJ / RANGE_MAJ) instead of the ripple one."""
+    majority-chain comparator (LT_MAJ / RANGE_MAJ) instead of the ripple one,
+    the suffix "plain" the same table with plaintext query constants."""
+    if name.endswith("plain"):
+        t = table(name[:-5], seed, rows)
+        t.plain = True
+        t.name = name
+        return t
     if name.endswith("maj"):
         t = table(name[:-3], seed, rows)
         t.pred = {PRED_LT: PRED_LT_MAJ, PRED_RANGE: PRED_RANGE_MAJ}[t.pred]

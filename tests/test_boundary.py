@@ -130,3 +130,60 @@ def test_workload_tables_plaintext_semantics():
     assert WL.table("eq4x16").gates_per_row * 16 == 176
     types, x, y = WL.gates(1000)
     assert set(np.unique(types)) == {0, 1, 2, 3, 4}
+
+
+def _oracle_plain_plan(pred, w, npay, pw, consts):
+    t, a, b, m, ol, ninp = O.netlist_plain(pred, w, npay, pw, consts)
+    depth = [0] * ninp
+    for k in range(t.size):
+        depth.append(1 + max(depth[a[k]], depth[b[k]]))
+    d = np.array(depth[ninp:], dtype=int)
+    widths = [int((d == L).sum()) for L in range(1, (d.max() if d.size else 0) + 1)]
+    # outputs that are not a gate's own plain output
+    lits = [m] + list(ol)
+    n_lit = sum(1 for x in lits if not (x >= 0 and (x >> 1) >= ninp and not x & 1))
+    return int(t.size), widths, n_lit
+
+
+@pytest.mark.parametrize("pred", [WL.PRED_EQ, WL.PRED_LT, WL.PRED_RANGE, WL.PRED_LT_MAJ])
+@pytest.mark.parametrize("w", [1, 3, 4, 16])
+def test_plain_scheduler_equals_oracle_netlist(pred, w):
+    """The library's plaintext-constant circuits (gate count, level widths,
+    outputs without a gate) equal the oracle's for many constants."""
+    rng = np.random.default_rng(w * 10 + pred)
+    top = 1 << w
+    ks = sorted({0, 1, top - 1, top >> 1, *[int(v) for v in rng.integers(0, top, 6)]})
+    for k in ks:
+        for k2 in (ks if pred == WL.PRED_RANGE else [0]):
+            consts = (k, k2) if pred == WL.PRED_RANGE else (k,)
+            assert F.plan_info_plain(pred, w, 2, 3, consts) == _oracle_plain_plan(pred, w, 2, 3, consts), consts
+
+
+def test_plain_scheduler_counts_and_errors():
+    g, widths, lits = F.plan_info_plain(WL.PRED_EQ, 32, 1, 32, (123456789,))
+    assert g == 31 + 32 and widths[-1] == 32 and lits == 0
+    g, widths, lits = F.plan_info_plain(WL.PRED_LT, 8, 2, 8, (0,))
+    assert g == 0 and widths == [] and lits == 1 + 16
+    with pytest.raises(F.FsqlError):
+        F.plan_info_plain(WL.PRED_LT, 8, 1, 8, (256,))  # wider than the column
+    assert WL.table("eq32x4096plain").plain and WL.table("eq32x4096plain").consts == WL.table("eq32x4096").consts
+
+
+@pytest.mark.parametrize("rows,width,out_width", [(1, 4, 6), (2, 1, 1), (3, 2, 4), (6, 3, 6), (16, 4, 8), (33, 5, 11),
+                                                  (100, 16, 23), (4096, 32, 44), (9, 4, 3)])
+def test_sum_circuit_equals_oracle_circuit(rows, width, out_width):
+    """The library's SUM-aggregation circuit has the oracle's gate count,
+    depth and number of outputs for every shape tried."""
+    t, a, b, c, ol, ninp = O.sum_netlist(rows, width, out_width)
+    depth = [0] * ninp
+    for k in range(t.size):
+        depth.append(1 + max(depth[a[k]], depth[b[k]], depth[c[k]] if c[k] >= 0 else 0))
+    levels = max(depth[ninp:]) if t.size else 0
+    assert F.sum_plan_info(rows, width, out_width) == (int(t.size), levels, out_width)
+
+
+def test_sum_circuit_limits():
+    assert F.sum_plan_info(0, 8, 5) == (0, 0, 5)  # empty table: every output bit a known zero
+    for bad in [(4, 0, 4), (4, 8, 0), (4, 8, 65), (1 << 23, 1, 8)]:
+        with pytest.raises(F.FsqlError):
+            F.sum_plan_info(*bad)

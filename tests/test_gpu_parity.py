@@ -216,6 +216,127 @@ def test_scan_per_gate_and_host_paths_equal_batched(env):
     assert np.array_equal(m1, m3) and all(np.array_equal(a, b) for a, b in zip(o1, o3))
 
 
+def run_scan_plain(ctx, t, col, pays, per_gate=False):
+    W = ctx.words
+    dcol = dev(col.view(np.int32))
+    dp = [dev(p.view(np.int32)) for p in pays]
+    match = torch.full((t.rows, W), 7, dtype=torch.int32, device="cuda")  # stale words must be overwritten
+    outs = [torch.full((t.rows, t.payload_width, W), 7, dtype=torch.int32, device="cuda") for _ in pays]
+    ctx.scan_select_plain(dcol, t.rows, t.width, t.pred, t.consts, dp, t.payload_width, match, outs,
+                          per_gate=per_gate)
+    return host(match).view(np.uint32), [host(x).view(np.uint32) for x in outs]
+
+
+# plaintext constants: ordinary constants and the degenerate ones (no gate at
+# all, a negated column bit as the match, lo = 0, the largest constants)
+@pytest.mark.parametrize("name,rows,consts", [
+    ("eq4x16plain", 16, None), ("lt8x64plain", 6, None), ("range4x16plain", 7, None),
+    ("lt8x64plain", 5, (0,)), ("lt8x64plain", 5, (128,)), ("lt8x64plain", 5, (255,)),
+    ("range4x16plain", 6, (0, 9)), ("range4x16plain", 6, (15, 3)), ("eq4x16plain", 5, (15,)),
+])
+def test_scan_plain_constants_bit_exact(env, name, rows, consts):
+    ctx, o = env
+    t = WL.table(name, seed=6, rows=rows)
+    if consts is not None:
+        t.consts = consts
+    (col, _, pays), (ocol, _, opays) = encrypt_both(ctx, o, t)
+    match, outs = run_scan_plain(ctx, t, col, pays)
+    om, oouts = o.scan_plain(t.pred, t.width, ocol, t.consts, opays, t.payload_width)
+    assert np.array_equal(match.reshape(om.shape), om)
+    for a, b in zip(outs, oouts):
+        assert np.array_equal(a.reshape(b.shape), b)
+    check_plaintext(ctx, t, match, outs)
+
+
+def test_scan_plain_per_gate_equals_batched_and_replays(env):
+    ctx, _ = env
+    t = WL.table("range4x16plain", seed=7, rows=5)
+    col, _, pays = WL.encrypt_table(ctx, t)
+    m1, o1 = run_scan_plain(ctx, t, col, pays)
+    m2, o2 = run_scan_plain(ctx, t, col, pays, per_gate=True)
+    m3, o3 = run_scan_plain(ctx, t, col, pays)
+    for m, o_ in ((m2, o2), (m3, o3)):
+        assert np.array_equal(m, m1) and all(np.array_equal(a, b) for a, b in zip(o_, o1))
+
+
+def test_scan_plain_eq32x4096_full_size_sampled_rows(env):
+    """Plaintext-constant equality at the benchmark size: every row decrypted
+    against the SQL answer, the matching row and the last row recomputed by
+    the oracle word for word."""
+    ctx, o = env
+    t = WL.table("eq32x4096plain", seed=1)
+    col, _, pays = WL.encrypt_table(ctx, t)
+    match, outs = run_scan_plain(ctx, t, col, pays)
+    check_plaintext(ctx, t, match, outs)
+    m_want, _ = t.expected()
+    rows = sorted({int(np.argmax(m_want)), t.rows - 1})
+    ocol = np.concatenate([o.encrypt_bits(t.column_bits().reshape(t.rows, t.width)[r], WL.STREAM_COLUMN,
+                                          r * t.width) for r in rows])
+    opay = np.concatenate([o.encrypt_bits(t.payload_bits(0).reshape(t.rows, t.payload_width)[r],
+                                          WL.STREAM_PAYLOAD, r * t.payload_width) for r in rows])
+    om, (oout,) = o.scan_plain(t.pred, t.width, ocol, t.consts, [opay], t.payload_width)
+    assert np.array_equal(match.reshape(t.rows, -1)[rows], om)
+    assert np.array_equal(outs[0].reshape(t.rows, t.payload_width, -1)[rows], oout)
+
+
+# ---------------------------------------------------------------- SUM aggregation
+@pytest.mark.parametrize("rows,width,out_width", [(6, 3, 6), (1, 4, 6), (24, 8, 13), (9, 4, 3)])
+def test_aggregate_sum_bit_exact(env, rows, width, out_width):
+    ctx, o = env
+    rng = np.random.default_rng(rows * 7 + width)
+    vals = rng.integers(0, 1 << width, rows)
+    bits = np.array([(int(v) >> j) & 1 for v in vals for j in range(width)], np.uint8)
+    ct = both_encrypt_bits(ctx, o, bits, 41)
+    out = torch.full((out_width, ctx.words), 7, dtype=torch.int32, device="cuda")
+    ctx.aggregate_sum(dev(ct.view(np.int32)), rows, width, out_width, out)
+    got = host(out).view(np.uint32)
+    assert np.array_equal(got, o.aggregate_sum(ct, rows, width, out_width))
+    dec = ctx.decrypt_bits(got)
+    assert int(sum(int(dec[j]) << j for j in range(out_width))) == int(vals.sum()) % (1 << out_width)
+
+
+def test_aggregate_sum_empty_and_replay(env):
+    ctx, _ = env
+    out = torch.full((5, ctx.words), 7, dtype=torch.int32, device="cuda")
+    ctx.aggregate_sum(None, 0, 8, 5, out)  # no rows: the sum is a known zero
+    got = host(out).view(np.uint32)
+    assert np.all(got[:, :-1] == 0) and np.all(got[:, -1] == np.uint32((1 << 32) - (1 << 29)))
+    # the same arguments twice: the second call replays the plan and gives the same words
+    rng = np.random.default_rng(3)
+    vals = rng.integers(0, 16, 10)
+    ct = ctx.encrypt_bits(np.array([(int(v) >> j) & 1 for v in vals for j in range(4)], np.uint8), 42, 0)
+    dct = dev(ct.view(np.int32))
+    res = []
+    for _ in range(2):
+        o_ = torch.zeros((8, ctx.words), dtype=torch.int32, device="cuda")
+        ctx.aggregate_sum(dct, 10, 4, 8, o_)
+        res.append(host(o_))
+    assert np.array_equal(res[0], res[1])
+
+
+def test_scan_then_sum_full_size(env):
+    """SUM over the masked payload of the full-size equality scan (4096 rows,
+    262,080 more bootstraps): the decrypted sum is the SQL answer, and the
+    oracle's own evaluation of the same circuit on a 24-row slice of the
+    masked column gives the same words as the library's."""
+    ctx, o = env
+    t = WL.table("eq32x4096", seed=1)
+    col, cst, pays = WL.encrypt_table(ctx, t)
+    match, outs = run_scan(ctx, t, col, cst, pays)
+    masked = dev(outs[0].view(np.int32))
+    ow = 44
+    out = torch.zeros((ow, ctx.words), dtype=torch.int32, device="cuda")
+    ctx.aggregate_sum(masked, t.rows, 32, ow, out)
+    dec = ctx.decrypt_bits(host(out).view(np.uint32))
+    _, (p_want,) = t.expected()
+    assert int(sum(int(dec[j]) << j for j in range(ow))) == int(p_want.astype(object).sum()) % (1 << ow)
+    # oracle on a slice: rows 0..23 of the masked column, an 8-bit slice of each value
+    sl = outs[0].reshape(t.rows, 32, -1)[:24, :8].copy()
+    out2 = torch.zeros((13, ctx.words), dtype=torch.int32, device="cuda")
+    ctx.aggregate_sum(dev(sl.view(np.int32)), 24, 8, 13, out2)
+    assert np.array_equal(host(out2).view(np.uint32), o.aggregate_sum(sl, 24, 8, 13))
+
+
 def test_scan_eq32x4096_full_size_sampled_rows(env):
     """The benchmark workload at full size, in the benchmark's launch
     configuration; the oracle recomputes whole sampled rows (the matching row

@@ -93,3 +93,42 @@ def test_cancel_waiting_query(ctx):
     srv.wait(b, 300000)
     assert srv.status(a)[0] == F.Q_DONE and srv.status(b)[0] == F.Q_CANCELLED
     srv.close()
+
+
+def test_served_plain_constant_queries_equal_solo(ctx):
+    """Plaintext-constant queries (including one with no gate at all and one
+    whose match is a negated column bit) served next to an encrypted one."""
+    specs = [("eq4x16plain", 1, None), ("lt8x64plain", 2, (0,)), ("lt8x64plain", 3, (128,)),
+             ("range4x16plain", 4, None), ("eq4x16", 5, None)]
+    tables = []
+    for name, seed, consts in specs:
+        t = WL.table(name, seed=seed, rows=6)
+        if consts is not None:
+            t.consts = consts
+        tables.append(t)
+    ios = [prepare(ctx, t) for t in tables]
+    srv = F.Server(ctx, scratch_budget_bytes=2 << 20, max_batch_gates=64)
+    ids = [srv.submit(io["column"], t.rows, t.width, t.pred, None if t.plain else io["const"], io["payloads"],
+                      t.payload_width, io["match"], io["outs"], plain_consts=t.consts if t.plain else None)
+           for t, io in zip(tables, ios)]
+    for qid in ids:
+        srv.wait(qid, 300000)
+        assert srv.status(qid)[0] == F.Q_DONE
+    srv.close()
+    W = ctx.words
+    for t, io in zip(tables, ios):
+        m = torch.zeros((t.rows, W), dtype=torch.int32, device="cuda")
+        o = [torch.zeros((t.rows, t.payload_width, W), dtype=torch.int32, device="cuda") for _ in io["payloads"]]
+        if t.plain:
+            ctx.scan_select_plain(io["column"], t.rows, t.width, t.pred, t.consts, io["payloads"], t.payload_width,
+                                  m, o)
+        else:
+            ctx.scan_select(io["column"], t.rows, t.width, t.pred, io["const"], io["payloads"], t.payload_width, m, o)
+        torch.cuda.synchronize()
+        assert np.array_equal(io["match"].cpu().numpy(), m.cpu().numpy())
+        for a, b in zip(io["outs"], o):
+            assert np.array_equal(a.cpu().numpy(), b.cpu().numpy())
+        m_want, p_want = t.expected()
+        assert np.array_equal(ctx.decrypt_bits(m.cpu().numpy().view(np.uint32)), m_want)
+        for q, b in enumerate(o):
+            assert np.array_equal(ctx.decrypt_uint(b.cpu().numpy().view(np.uint32), t.payload_width), p_want[q])
