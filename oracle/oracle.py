@@ -89,6 +89,10 @@ def lib():
                                       C.c_void_p, C.POINTER(C.c_int32)]
         L.orc_sum_eval_plain.argtypes = [C.c_int, C.c_int, C.c_int, u8p, u8p]
         L.orc_aggregate_sum.argtypes = [C.c_void_p, u32p, C.c_int, C.c_int, C.c_int, u32p]
+        L.orc_extreme_netlist.argtypes = [C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p,
+                                          C.c_void_p, C.c_void_p, C.POINTER(C.c_int32)]
+        L.orc_extreme_eval_plain.argtypes = [C.c_int, C.c_int, C.c_int, u8p, u8p]
+        L.orc_aggregate_extreme.argtypes = [C.c_void_p, C.c_int, u32p, C.c_void_p, C.c_int, C.c_int, u32p]
         L.orc_set_threads.argtypes = [C.c_int]
         L.orc_max_threads.restype = C.c_int
         _lib = L
@@ -265,6 +269,31 @@ def sum_eval_plain(rows: int, pw: int, ow: int, values) -> int:
     return int(sum(int(out[j]) << j for j in range(ow)))
 
 
+def extreme_netlist(is_min: bool, rows: int, w: int):
+    """MAX (is_min False) or MIN circuit: (types, a, b, c, output literals [w], n_inputs)."""
+    ninp = C.c_int32()
+    g = lib().orc_extreme_netlist(int(is_min), rows, w, None, None, None, None, None, C.byref(ninp))
+    if g < 0:
+        raise ValueError("bad aggregation shape")
+    t, a, b, c = (np.zeros(max(g, 1), np.int32) for _ in range(4))
+    ol = np.zeros(w, np.int32)
+    lib().orc_extreme_netlist(int(is_min), rows, w, t.ctypes.data, a.ctypes.data, b.ctypes.data, c.ctypes.data,
+                              ol.ctypes.data, C.byref(ninp))
+    return t[:g], a[:g], b[:g], c[:g], ol, int(ninp.value)
+
+
+def extreme_eval_plain(is_min: bool, w: int, values, match=None) -> int:
+    """The MAX / MIN circuit on plaintext row values (and match bits for MIN)."""
+    vals = [int(v) for v in values]
+    bits = [(v >> j) & 1 for v in vals for j in range(w)]
+    if is_min:
+        bits += [int(m) for m in match]
+    out = np.zeros(w, np.uint8)
+    if lib().orc_extreme_eval_plain(int(is_min), len(vals), w, np.array(bits, np.uint8), out) < 0:
+        raise ValueError("bad aggregation shape")
+    return int(sum(int(out[j]) << j for j in range(w)))
+
+
 class Oracle:
     """Keys for one seed plus the TFHE operations, all on the CPU."""
 
@@ -418,6 +447,18 @@ class Oracle:
         vals = _u32(values).reshape(rows * pw * W)
         out = np.zeros((ow, W), np.uint32)
         if lib().orc_aggregate_sum(self._h, vals, rows, pw, ow, out) != 0:
+            raise ValueError("aggregation failed")
+        return out
+
+    def aggregate_extreme(self, is_min: bool, values, rows: int, w: int, match=None):
+        """Encrypted MAX / MIN of rows values [rows, w, n+1] (MIN: match bits [rows, n+1]) -> [w, n+1]."""
+        W = self.n + 1
+        vals = _u32(values).reshape(max(rows * w * W, 1)) if rows else np.zeros(1, np.uint32)
+        m = _u32(match).reshape(rows * W) if (is_min and rows) else None
+        out = np.zeros((w, W), np.uint32)
+        rc = lib().orc_aggregate_extreme(self._h, int(is_min), vals, m.ctypes.data if m is not None else None,
+                                         rows, w, out)
+        if rc != 0:
             raise ValueError("aggregation failed")
         return out
 

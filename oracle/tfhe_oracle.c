@@ -1144,6 +1144,134 @@ ORC_API int orc_aggregate_sum(const orc_ctx *c, const uint32_t *in, int rows, in
     return bad ? -1 : 0;
 }
 
+/* ------------------------------------------------------------------ */
+/* MAX and MIN of the selected rows (§4.2 B lists max(a, b) and min(a, b) */
+/* among the operators of the homomorphic expression tree).  Unsigned      */
+/* values of w bits, LSB first.  Pairwise: s = [a < b] by the majority     */
+/* comparator (s_0 = ANDNY(a_0, b_0), s_i = MAJNYY(a_i, b_i, s_{i-1})), then */
+/* per bit a multiplexer OR(AND(s, x), ANDNY(s, y)) = s ? x : y, with      */
+/* (x, y) = (b, a) for max and (a, b) for min.  Rows reduce as a tournament */
+/* in the order of the equality AND tree: each round pairs (2i, 2i+1) and   */
+/* moves an unpaired last value to the end of the next round.  MAX takes    */
+/* the masked values as they are (a row that does not match is 0, the      */
+/* identity of max over unsigned values); MIN first replaces every bit of  */
+/* a row that does not match by 1, u_j = ORYN(v_j, m) = v_j or not m, so   */
+/* such rows become 2^w - 1, the identity of min.  No rows: MAX is 0, MIN  */
+/* is 2^w - 1 (known bits).  Wires: value bit (r, j) is r*w + j; for MIN    */
+/* the match bit of row r is rows*w + r; gate outputs follow.              */
+/* ------------------------------------------------------------------ */
+
+static void nl_extreme_pair(netlist *nl, int is_min, const int *a, const int *b, int w, int *out)
+{
+    int s = nl_add(nl, G_ANDNY, a[0], b[0]); /* s = [a < b] */
+    for (int i = 1; i < w; i++) s = nl_add3(nl, G_MAJNYY, a[i], b[i], s);
+    for (int j = 0; j < w; j++) {
+        int x = is_min ? a[j] : b[j], y = is_min ? b[j] : a[j];
+        int tx = nl_add(nl, G_AND, s, x);
+        int ty = nl_add(nl, G_ANDNY, s, y);
+        out[j] = nl_add(nl, G_OR, tx, ty);
+    }
+}
+
+ORC_API int orc_extreme_netlist(int is_min, int rows, int w, int32_t *type, int32_t *a, int32_t *b, int32_t *c,
+                                int32_t *out_lits, int32_t *n_inputs)
+{
+    if (rows < 0 || w < 1 || w > 64) return -1;
+    int ninp = rows * w + (is_min ? rows : 0);
+    netlist nl = {type, a, b, c, 0, 0, ninp};
+    int *cur = (int *)malloc(sizeof(int) * (size_t)(rows > 0 ? rows : 1) * w);
+    int *nxt = (int *)malloc(sizeof(int) * (size_t)(rows > 0 ? rows : 1) * w);
+    for (int r = 0; r < rows; r++)
+        for (int j = 0; j < w; j++)
+            cur[(size_t)r * w + j] = is_min ? nl_add(&nl, G_ORYN, r * w + j, rows * w + r) : r * w + j;
+    int m = rows;
+    while (m > 1) {
+        int nm = 0;
+        for (int i = 0; i + 1 < m; i += 2, nm++)
+            nl_extreme_pair(&nl, is_min, cur + (size_t)i * w, cur + (size_t)(i + 1) * w, w, nxt + (size_t)nm * w);
+        if (m & 1) {
+            memcpy(nxt + (size_t)nm * w, cur + (size_t)(m - 1) * w, sizeof(int) * w);
+            nm++;
+        }
+        int *t = cur; cur = nxt; nxt = t;
+        m = nm;
+    }
+    if (out_lits)
+        for (int j = 0; j < w; j++) out_lits[j] = rows > 0 ? 2 * cur[j] : (is_min ? LIT_TRUE : LIT_FALSE);
+    free(cur);
+    free(nxt);
+    if (n_inputs) *n_inputs = ninp;
+    return nl.count;
+}
+
+/* Plaintext evaluation: values [rows] (w bits each), match bits [rows] (MIN only). */
+ORC_API int orc_extreme_eval_plain(int is_min, int rows, int w, const uint8_t *in_bits, uint8_t *out_bits)
+{
+    int32_t ninp;
+    int g = orc_extreme_netlist(is_min, rows, w, NULL, NULL, NULL, NULL, NULL, &ninp);
+    if (g < 0) return -1;
+    int32_t *t = (int32_t *)malloc(sizeof(int32_t) * (g + 1)), *a = (int32_t *)malloc(sizeof(int32_t) * (g + 1)),
+            *b = (int32_t *)malloc(sizeof(int32_t) * (g + 1)), *c3 = (int32_t *)malloc(sizeof(int32_t) * (g + 1)),
+            *ol = (int32_t *)malloc(sizeof(int32_t) * w);
+    uint8_t *wires = (uint8_t *)malloc((size_t)(ninp + g + 1));
+    orc_extreme_netlist(is_min, rows, w, t, a, b, c3, ol, &ninp);
+    for (int i = 0; i < ninp; i++) wires[i] = in_bits[i];
+    for (int k = 0; k < g; k++)
+        wires[ninp + k] = (uint8_t)orc_gate_plain3(t[k], wires[a[k]], wires[b[k]], c3[k] >= 0 ? wires[c3[k]] : 0);
+    for (int j = 0; j < w; j++) out_bits[j] = (uint8_t)lit_value(wires, ol[j]);
+    free(t);
+    free(a);
+    free(b);
+    free(c3);
+    free(ol);
+    free(wires);
+    return g;
+}
+
+/* Encrypted MAX / MIN: values [rows][w][n+1], match [rows][n+1] (MIN only,
+ * else NULL) -> out [w][n+1]; gates level by level as orc_aggregate_sum. */
+ORC_API int orc_aggregate_extreme(const orc_ctx *c, int is_min, const uint32_t *values, const uint32_t *match,
+                                  int rows, int w, uint32_t *out)
+{
+    int32_t ninp;
+    int g = orc_extreme_netlist(is_min, rows, w, NULL, NULL, NULL, NULL, NULL, &ninp);
+    if (g < 0 || (is_min && rows > 0 && !match)) return -1;
+    int32_t *t = (int32_t *)malloc(sizeof(int32_t) * (g + 1)), *a = (int32_t *)malloc(sizeof(int32_t) * (g + 1)),
+            *b = (int32_t *)malloc(sizeof(int32_t) * (g + 1)), *c3 = (int32_t *)malloc(sizeof(int32_t) * (g + 1)),
+            *ol = (int32_t *)malloc(sizeof(int32_t) * w), *depth = (int32_t *)malloc(sizeof(int32_t) * (ninp + g + 1));
+    orc_extreme_netlist(is_min, rows, w, t, a, b, c3, ol, &ninp);
+    int maxd = 0;
+    for (int i = 0; i < ninp; i++) depth[i] = 0;
+    for (int k = 0; k < g; k++) {
+        int d = depth[a[k]] > depth[b[k]] ? depth[a[k]] : depth[b[k]];
+        if (c3[k] >= 0 && depth[c3[k]] > d) d = depth[c3[k]];
+        depth[ninp + k] = 1 + d;
+        if (depth[ninp + k] > maxd) maxd = depth[ninp + k];
+    }
+    size_t W = (size_t)c->p.n + 1;
+    uint32_t *wires = (uint32_t *)malloc(sizeof(uint32_t) * W * (size_t)(ninp + g + 1));
+    memcpy(wires, values, sizeof(uint32_t) * W * (size_t)rows * w);
+    if (is_min && rows > 0) memcpy(wires + W * (size_t)rows * w, match, sizeof(uint32_t) * W * (size_t)rows);
+    int bad = 0;
+    for (int d = 1; d <= maxd; d++) {
+#pragma omp parallel for schedule(dynamic, 1) reduction(| : bad)
+        for (int k = 0; k < g; k++) {
+            if (depth[ninp + k] != d) continue;
+            bad |= orc_gate3(c, t[k], wires + (size_t)a[k] * W, wires + (size_t)b[k] * W,
+                             c3[k] >= 0 ? wires + (size_t)c3[k] * W : NULL, wires + (size_t)(ninp + k) * W) != 0;
+        }
+    }
+    for (int j = 0; j < w; j++) lit_materialise(c->p.n, wires, W, ol[j], out + (size_t)j * W);
+    free(wires);
+    free(t);
+    free(a);
+    free(b);
+    free(c3);
+    free(ol);
+    free(depth);
+    return bad ? -1 : 0;
+}
+
 ORC_API void orc_set_threads(int k)
 {
 #ifdef _OPENMP

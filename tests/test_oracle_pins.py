@@ -606,3 +606,50 @@ def test_aggregate_sum_toy_decrypts_to_sum(toy_oracle):
         if rows == 1:  # no gate: copies of the input bits and trivial zeros
             assert np.array_equal(out[:pw], ct.reshape(pw, -1))
             assert np.all(out[pw:, :o.n] == 0) and np.all(out[pw:, o.n] == np.uint32(Q - E8))
+
+
+# --------------------------------------------------------------------------
+# MAX / MIN of the selected rows: comparator + multiplexer tournament
+# --------------------------------------------------------------------------
+def test_extreme_circuits_exhaustive_small():
+    """Every value (and match) combination for tiny tables: MAX is the
+    largest masked value (0 for no rows), MIN the smallest selected value
+    (2^w - 1 when nothing is selected)."""
+    import itertools
+
+    for w in (1, 2, 3):
+        for rows in range(0, 5):
+            for vals in itertools.product(range(1 << w), repeat=rows):
+                assert O.extreme_eval_plain(False, w, vals) == (max(vals) if vals else 0)
+                for m in itertools.product((0, 1), repeat=rows):
+                    sel = [v for v, mm in zip(vals, m) if mm]
+                    assert O.extreme_eval_plain(True, w, vals, m) == (min(sel) if sel else (1 << w) - 1)
+
+
+def test_extreme_circuits_random_and_counts():
+    rng = np.random.default_rng(21)
+    for rows, w in [(7, 8), (33, 5), (100, 16), (64, 32)]:
+        for _ in range(10):
+            vals = [int(v) for v in rng.integers(0, 1 << w, rows, dtype=np.uint64)]
+            m = [int(v) for v in rng.integers(0, 2, rows)]
+            sel = [v for v, mm in zip(vals, m) if mm]
+            assert O.extreme_eval_plain(False, w, vals) == max(vals)
+            assert O.extreme_eval_plain(True, w, vals, m) == (min(sel) if sel else (1 << w) - 1)
+        # (rows - 1) pairwise steps of w comparator gates and 3w multiplexer gates; MIN adds w per row
+        assert O.extreme_netlist(False, rows, w)[0].size == 4 * w * (rows - 1)
+        assert O.extreme_netlist(True, rows, w)[0].size == 4 * w * (rows - 1) + w * rows
+
+
+def test_aggregate_extreme_toy_decrypts(toy_oracle):
+    o = toy_oracle
+    rng = np.random.default_rng(22)
+    rows, w = 5, 3
+    vals = rng.integers(0, 8, rows)
+    m = np.array([1, 0, 1, 1, 0], np.uint8)
+    ct = o.encrypt_bits(np.array([(int(v) >> j) & 1 for v in vals for j in range(w)], np.uint8), stream=50)
+    mct = o.encrypt_bits(m, stream=51)
+    dec = lambda out: int(sum(int(b) << j for j, b in enumerate(o.decrypt_bits(out))))
+    assert dec(o.aggregate_extreme(False, ct, rows, w)) == int(vals.max())
+    assert dec(o.aggregate_extreme(True, ct, rows, w, mct)) == int(vals[m == 1].min())
+    one = o.aggregate_extreme(False, ct[:w], 1, w)  # one row: its own ciphertexts
+    assert np.array_equal(one, ct[:w].reshape(w, -1))
