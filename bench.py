@@ -40,7 +40,8 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="eq32x4096",
                     choices=["eq32x4096", "eq4x16", "range16x65536", "range16x65536maj", "lt8x64", "lt8x64maj", "range4x16",
-                             "range4x16maj", "eq32x4096plain", "range16x65536plain", "eq4x16plain", "gates",
+                             "range4x16maj", "eq32x4096plain", "range16x65536plain", "eq4x16plain", "eq32x4096sum",
+                             "eq32x4096plainsum", "gates",
                              "serving"])
     ap.add_argument("--queries", type=int, default=16, help="queries per serving phase")
     ap.add_argument("--batch", type=int, default=65536, help="gates per step of the gate microbenchmark")
@@ -600,12 +601,17 @@ def run_ours(args, dist):
     outs = [torch.zeros((t.rows, t.payload_width, W), dtype=torch.int32, device=f"cuda:{dev}") for _ in pays]
     st = torch.cuda.current_stream()
 
+    sums = [torch.zeros((t.sum_width, W), dtype=torch.int32, device=f"cuda:{dev}") for _ in pays] \
+        if t.aggregate else []
+
     def step():
         if t.plain:
             ctx.scan_select_plain(dcol, t.rows, t.width, t.pred, t.consts, dpay, t.payload_width, match, outs,
                                   stream=st)
         else:
             ctx.scan_select(dcol, t.rows, t.width, t.pred, dcst, dpay, t.payload_width, match, outs, stream=st)
+        for o_, s_ in zip(outs, sums):
+            ctx.aggregate_sum(o_, t.rows, t.payload_width, t.sum_width, s_, stream=st)
 
     for _ in range(max(3, args.warmup)):
         step()
@@ -629,7 +635,8 @@ def run_ours(args, dist):
     clocks = sampler.stop()
     ms = dist.max(e0.elapsed_time(e1))
     gpr = gates_per_row(t)
-    gates_per_step = t.rows * gpr
+    sum_gates = len(sums) * F.sum_plan_info(t.rows, t.payload_width, t.sum_width)[0] if t.aggregate else 0
+    gates_per_step = t.rows * gpr + sum_gates
     value = dist.world * gates_per_step * args.steps / (ms / 1e3)
 
     # ---- correctness of the timed outputs (plaintext answer)
@@ -638,13 +645,17 @@ def run_ours(args, dist):
     correct = bool(np.array_equal(got_m, m_want))
     for q, o_ in enumerate(outs):
         correct &= bool(np.array_equal(ctx.decrypt_uint(o_.cpu().numpy().view(np.uint32), t.payload_width), p_want[q]))
+    for q, s_ in enumerate(sums):
+        bits = ctx.decrypt_bits(s_.cpu().numpy().view(np.uint32))
+        got_sum = sum(int(b) << j for j, b in enumerate(bits))
+        correct &= got_sum == int(p_want[q].astype(object).sum()) % (1 << t.sum_width)
 
     # ---- roofline of the dominant kernel (blind rotation)
     roofline = roofline_of(ktimes, ms, sms, peaks, args.workload)
 
     # ---- end to end through the public C-ABI with host buffers (copies inside the timed region)
     h2d = (col.size + (0 if t.plain else cst.size) + sum(p.size for p in pays)) * 4
-    d2h = (t.rows * W + len(pays) * t.rows * t.payload_width * W) * 4
+    d2h = (t.rows * W + len(pays) * t.rows * t.payload_width * W + len(sums) * t.sum_width * W) * 4
     e2e = None
     if args.e2e_steps > 0:
         hcol = torch.from_numpy(col.view(np.int32)).pin_memory()
@@ -653,15 +664,20 @@ def run_ours(args, dist):
         hmatch = torch.zeros((t.rows, W), dtype=torch.int32).pin_memory()
         houts = [torch.zeros((t.rows, t.payload_width, W), dtype=torch.int32).pin_memory() for _ in pays]
 
+        hsums = [torch.zeros((t.sum_width, W), dtype=torch.int32).pin_memory() for _ in sums]
+
         def e2e_step():
-            if t.plain:  # pinned host -> device, the scan, device -> host, all on the launch stream
+            if t.plain or t.aggregate:  # pinned host -> device, the step, device -> host, on the launch stream
                 dcol.copy_(hcol, non_blocking=True)
+                if not t.plain:
+                    dcst.copy_(hcst, non_blocking=True)
                 for d_, h_ in zip(dpay, hpay):
                     d_.copy_(h_, non_blocking=True)
-                ctx.scan_select_plain(dcol, t.rows, t.width, t.pred, t.consts, dpay, t.payload_width, match, outs,
-                                      stream=st)
+                step()
                 hmatch.copy_(match, non_blocking=True)
                 for h_, d_ in zip(houts, outs):
+                    h_.copy_(d_, non_blocking=True)
+                for h_, d_ in zip(hsums, sums):
                     h_.copy_(d_, non_blocking=True)
             else:
                 ctx.scan_select_host(hcol, t.rows, t.width, t.pred, hcst, hpay, t.payload_width, hmatch, houts,
@@ -730,6 +746,7 @@ def run_ours(args, dist):
                    "constants": "plaintext" if t.plain else "encrypted",
                    "payload_columns": len(t.payloads), "payload_width": t.payload_width,
                    "gates_per_row": gpr, "gate_bootstraps_per_step": gates_per_step,
+                   "sum_gate_bootstraps_per_step": sum_gates,
                    "params": "n=630 N=1024 Bg=2^7 l=3 ks 4^8 Torus32",
                    "engine": ["goldilocks", "dual_prime"][ctx.engine],
                    "l2": "inputs larger than L2 (%.0f MB column+payload per step)" % (h2d / 1e6),

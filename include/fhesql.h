@@ -284,9 +284,30 @@ FSQL_API int fsql_plan_info_plain(uint32_t pred, uint32_t width, uint32_t n_payl
  * zeros (one row, high bits) are copies or trivial ciphertexts.  The
  * context keeps the circuit's scratch (intermediate wires, descriptors) per
  * argument set and replays its launches as a CUDA graph.  Limits: rows <=
- * 2^22, 1 <= width, out_width <= 64.  d_out may not alias d_values. */
+ * 2^22, rows x width <= 2^24, 1 <= width, out_width <= 64.  d_out may not
+ * alias d_values. */
 FSQL_API int fsql_aggregate_sum(fsql_ctx* ctx, const uint32_t* d_values, size_t rows, uint32_t width,
                                 uint32_t out_width, uint32_t* d_out, void* stream);
+
+/* MAX and MIN of selected rows (§4.2 B lists max(a, b) and min(a, b)
+ * among the operators of the homomorphic expression tree).  d_values:
+ * [rows][width][n+1] unsigned values (LSB first); d_out: [width][n+1].
+ * MAX takes masked values as they are (an unselected row masked to 0 cannot
+ * win); MIN also takes d_match [rows][n+1], the rows' encrypted match bits,
+ * and first sets every bit of an unselected row to 1 (ORYN(v, m)).  Circuit:
+ * a tournament pairing neighbours (an unpaired last value moves on); each
+ * pair costs width gates of a majority comparator s = [a < b] and 3 width
+ * gates of multiplexers OR(AND(s, x), ANDNY(s, y)).  MAX: 4 width (rows-1)
+ * bootstraps; MIN: width more per row.  No rows: MAX = 0, MIN = 2^width - 1
+ * as trivial ciphertexts.  Plans, scratch and graph replay as
+ * fsql_aggregate_sum (one aggregation plan per context is kept).  Limits:
+ * rows <= 2^22, rows x width <= 2^24, 1 <= width <= 64. */
+FSQL_API int fsql_aggregate_max(fsql_ctx* ctx, const uint32_t* d_values, size_t rows, uint32_t width,
+                                uint32_t* d_out, void* stream);
+FSQL_API int fsql_aggregate_min(fsql_ctx* ctx, const uint32_t* d_values, const uint32_t* d_match, size_t rows,
+                                uint32_t width, uint32_t* d_out, void* stream);
+/* Gate and level counts of the MAX (is_min = 0) or MIN circuit. */
+FSQL_API int fsql_extreme_plan_info(int is_min, size_t rows, uint32_t width, uint32_t* gates, uint32_t* levels);
 
 /* Gate count and level count of the SUM circuit for (rows, width, out_width). */
 FSQL_API int fsql_sum_plan_info(size_t rows, uint32_t width, uint32_t out_width, uint32_t* gates, uint32_t* levels,

@@ -132,6 +132,8 @@ bool build_netlist(uint32_t pred, uint32_t width, uint32_t n_payloads, uint32_t 
 // The SUM-aggregation circuit over rows x width input bits (input bit (r, j)
 // is wire r * width + j); every output bit j is a literal output with target j.
 bool build_sum_netlist(size_t rows, uint32_t width, uint32_t out_width, Netlist* out);
+// MAX / MIN over `rows` values (MIN's match bit of row r is wire rows * width + r).
+bool build_extreme_netlist(bool is_min, size_t rows, uint32_t width, Netlist* out);
 // The netlist for plaintext constants k0 (EQ, LT) or lo = k0, hi = k1 (RANGE):
 // gates with a known input are reduced away (see host.cpp).
 bool build_netlist_plain(uint32_t pred, uint32_t width, uint32_t n_payloads, uint32_t payload_width, uint64_t k0,

@@ -381,6 +381,57 @@ bool build_sum_netlist(size_t rows, uint32_t width, uint32_t out_width, Netlist*
   return true;
 }
 
+// MAX (is_min false) or MIN of `rows` unsigned values of `width` bits.
+// Pairwise step: s = [a < b] from the majority comparator (ANDNY on bit 0,
+// MAJNYY above), then per bit the multiplexer s ? x : y as
+// OR(AND(s, x), ANDNY(s, y)), x = b, y = a for max and x = a, y = b for min.
+// Values meet in a tournament paired like the equality AND tree
+// (neighbours (0,1), (2,3), ..., an unpaired last value moves on).  MIN
+// first sets every bit of a row that does not match to 1 (ORYN(v, m)), so
+// such rows cannot win.  No rows: MAX is 0 and MIN is all ones (known bits).
+// Inputs: value bit (r, j) = wire r * width + j; MIN's match bit of row r
+// is wire rows * width + r.  Output bit j is a literal output with target j.
+bool build_extreme_netlist(bool is_min, size_t rows, uint32_t width, Netlist* out) {
+  if (width < 1 || width > 64 || rows > (size_t(1) << 22) || rows * width > (size_t(1) << 24)) return false;
+  Netlist nl;
+  const int w = static_cast<int>(width), R = static_cast<int>(rows);
+  nl.n_inputs = R * w + (is_min ? R : 0);
+  nl.n_const = 0;
+  nl.match_wire = -1;
+  Builder b(nl);
+  std::vector<std::vector<int>> vals(rows, std::vector<int>(w));
+  for (int r = 0; r < R; ++r)
+    for (int j = 0; j < w; ++j)
+      vals[r][j] = is_min ? b.gate(FSQL_ORYN, r * w + j, R * w + r) : r * w + j;
+  while (vals.size() > 1) {
+    std::vector<std::vector<int>> next;
+    size_t i = 0;
+    for (; i + 1 < vals.size(); i += 2) {
+      const std::vector<int>& lo = vals[i];
+      const std::vector<int>& hi = vals[i + 1];
+      int s = b.gate(FSQL_ANDNY, lo[0], hi[0]);  // [lo < hi]
+      for (int j = 1; j < w; ++j) s = b.gate(FSQL_MAJNYY, lo[j], hi[j], s);
+      std::vector<int> pick(w);
+      for (int j = 0; j < w; ++j) {
+        const int when_less = is_min ? lo[j] : hi[j], otherwise = is_min ? hi[j] : lo[j];
+        const int taken = b.gate(FSQL_AND, s, when_less);
+        const int kept = b.gate(FSQL_ANDNY, s, otherwise);
+        pick[j] = b.gate(FSQL_OR, taken, kept);
+      }
+      next.push_back(std::move(pick));
+    }
+    if (i < vals.size()) next.push_back(std::move(vals[i]));
+    vals.swap(next);
+  }
+  for (int j = 0; j < w; ++j) {
+    if (R > 0) nl.literal_outs.push_back({j, vals[0][j], kOutCopy});
+    else nl.literal_outs.push_back({j, -1, is_min ? kOutTrue : kOutFalse});
+  }
+  nl.first_mask_gate = static_cast<int>(nl.type.size());
+  *out = std::move(nl);
+  return true;
+}
+
 bool build_netlist(uint32_t pred, uint32_t width, uint32_t n_payloads, uint32_t payload_width, Netlist* out) {
   if (width < 1 || width > 64 || pred > FSQL_RANGE_MAJ || n_payloads > 64 || payload_width > 64) return false;
   if (n_payloads > 0 && payload_width == 0) return false;
@@ -658,6 +709,16 @@ int fsql_sum_plan_info(size_t rows, uint32_t width, uint32_t out_width, uint32_t
     if (gates) *gates = static_cast<uint32_t>(nl.type.size());
     if (levels) *levels = static_cast<uint32_t>(nl.levels);
     if (literal_outputs) *literal_outputs = static_cast<uint32_t>(nl.literal_outs.size());
+    return FSQL_OK;
+  });
+}
+
+int fsql_extreme_plan_info(int is_min, size_t rows, uint32_t width, uint32_t* gates, uint32_t* levels) {
+  return guarded([&]() -> int {
+    fsql::Netlist nl;
+    if (!fsql::build_extreme_netlist(is_min != 0, rows, width, &nl)) return arg_error("bad aggregation shape");
+    if (gates) *gates = static_cast<uint32_t>(nl.type.size());
+    if (levels) *levels = static_cast<uint32_t>(nl.levels);
     return FSQL_OK;
   });
 }

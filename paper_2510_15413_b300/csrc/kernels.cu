@@ -638,8 +638,10 @@ struct Plan {
   const uint32_t* graph_big = nullptr;
   const OutDesc* graph_lits = nullptr;
   int graph_br_gates = 0;
-  // SUM aggregation plans: key and the buffers they own
+  // aggregation plans (SUM, MAX, MIN): key and the buffers they own
+  int agg_kind = -1;
   const uint32_t* agg_in = nullptr;
+  const uint32_t* agg_match = nullptr;
   uint32_t* agg_out = nullptr;
   uint32_t agg_width = 0, agg_out_width = 0;
   GateDesc* own_desc = nullptr;
@@ -1096,22 +1098,29 @@ int prepare_scan(Ctx& c, const uint32_t* d_column, size_t rows, uint32_t width, 
   return FSQL_OK;
 }
 
-// Build (or reuse) the SUM-aggregation plan for these arguments: the
-// circuit's descriptors, output descriptors and intermediate wires live in
-// buffers the plan owns.
-int prepare_sum(Ctx& c, const uint32_t* d_in, size_t rows, uint32_t width, uint32_t out_width, uint32_t* d_out,
-                void* stream) {
+enum { kAggSum = 0, kAggMax = 1, kAggMin = 2 };
+
+// Build (or reuse) the aggregation plan (SUM, MAX or MIN) for these
+// arguments: the circuit's descriptors, output descriptors and intermediate
+// wires live in buffers the plan owns.  d_match: MIN's match bits.
+int prepare_aggregate(Ctx& c, int kind, const uint32_t* d_in, const uint32_t* d_match, size_t rows, uint32_t width,
+                      uint32_t out_width, uint32_t* d_out, void* stream) {
   fsql::Plan* pl = c.agg_plan;
-  if (pl && pl->agg_in == d_in && pl->rows == rows && pl->agg_width == width && pl->agg_out_width == out_width &&
-      pl->agg_out == d_out)
+  if (pl && pl->agg_kind == kind && pl->agg_in == d_in && pl->agg_match == d_match && pl->rows == rows &&
+      pl->agg_width == width && pl->agg_out_width == out_width && pl->agg_out == d_out)
     return FSQL_OK;
   delete c.agg_plan;
   c.agg_plan = nullptr;
   fsql::Netlist nl;
-  if (!fsql::build_sum_netlist(rows, width, out_width, &nl)) return arg_error("bad aggregation shape");
+  const bool ok = kind == kAggSum ? fsql::build_sum_netlist(rows, width, out_width, &nl)
+                                  : fsql::build_extreme_netlist(kind == kAggMin, rows, width, &nl);
+  if (!ok) return arg_error("bad aggregation shape");
   const size_t W = c.p.n + 1, G = nl.type.size();
+  const int value_wires = static_cast<int>(rows * width);
   pl = new fsql::Plan();
+  pl->agg_kind = kind;
   pl->agg_in = d_in;
+  pl->agg_match = d_match;
   pl->rows = rows;
   pl->agg_width = width;
   pl->agg_out_width = out_width;
@@ -1124,7 +1133,8 @@ int prepare_sum(Ctx& c, const uint32_t* d_in, size_t rows, uint32_t width, uint3
     return FSQL_ERR_OOM;
   }
   auto wire_ptr = [&](int id) -> const uint32_t* {
-    if (id < nl.n_inputs) return d_in + static_cast<size_t>(id) * W;  // input bit (r, j) = r * width + j
+    if (id < value_wires) return d_in + static_cast<size_t>(id) * W;  // value bit (r, j) = r * width + j
+    if (id < nl.n_inputs) return d_match + static_cast<size_t>(id - value_wires) * W;  // MIN: match bit of row r
     return pl->own_wires + static_cast<size_t>(id - nl.n_inputs) * W;
   };
   std::vector<fsql::GateDesc> desc(G);
@@ -1347,7 +1357,29 @@ int fsql_aggregate_sum(fsql_ctx* ctx, const uint32_t* d_values, size_t rows, uin
   if (!c) return FSQL_ERR_ARG;
   if ((rows && !d_values) || !d_out) return arg_error("null values or output pointer");
   std::lock_guard<std::mutex> lk(c->mu);
-  int rc = prepare_sum(*c, d_values, rows, width, out_width, d_out, stream);
+  int rc = prepare_aggregate(*c, kAggSum, d_values, nullptr, rows, width, out_width, d_out, stream);
+  if (rc) return rc;
+  return execute_plan(c, *c->agg_plan, c->agg_plan->own_desc, c->agg_plan->own_lits, 0, stream);
+}
+
+int fsql_aggregate_max(fsql_ctx* ctx, const uint32_t* d_values, size_t rows, uint32_t width, uint32_t* d_out,
+                       void* stream) {
+  Ctx* c = device_ctx(ctx);
+  if (!c) return FSQL_ERR_ARG;
+  if ((rows && !d_values) || !d_out) return arg_error("null values or output pointer");
+  std::lock_guard<std::mutex> lk(c->mu);
+  int rc = prepare_aggregate(*c, kAggMax, d_values, nullptr, rows, width, width, d_out, stream);
+  if (rc) return rc;
+  return execute_plan(c, *c->agg_plan, c->agg_plan->own_desc, c->agg_plan->own_lits, 0, stream);
+}
+
+int fsql_aggregate_min(fsql_ctx* ctx, const uint32_t* d_values, const uint32_t* d_match, size_t rows,
+                       uint32_t width, uint32_t* d_out, void* stream) {
+  Ctx* c = device_ctx(ctx);
+  if (!c) return FSQL_ERR_ARG;
+  if ((rows && (!d_values || !d_match)) || !d_out) return arg_error("null values, match or output pointer");
+  std::lock_guard<std::mutex> lk(c->mu);
+  int rc = prepare_aggregate(*c, kAggMin, d_values, d_match, rows, width, width, d_out, stream);
   if (rc) return rc;
   return execute_plan(c, *c->agg_plan, c->agg_plan->own_desc, c->agg_plan->own_lits, 0, stream);
 }

@@ -29,6 +29,7 @@ API = ["fsql_params_default", "fsql_params_toy", "fsql_ctx_create", "fsql_ctx_cr
        "fsql_phase", "fsql_decrypt_bits", "fsql_decrypt_uint", "fsql_gate_batch", "fsql_blind_rotate_extract",
        "fsql_keyswitch", "fsql_debug_ntt_mul", "fsql_plan_info", "fsql_scan_select", "fsql_scan_select_host",
        "fsql_scan_select_plain", "fsql_plan_info_plain", "fsql_aggregate_sum", "fsql_sum_plan_info",
+       "fsql_aggregate_max", "fsql_aggregate_min", "fsql_extreme_plan_info",
        "fsql_profile_begin", "fsql_profile_end", "fsql_gate_batch_noalloc", "fsql_server_create",
        "fsql_server_submit", "fsql_server_status", "fsql_server_wait", "fsql_server_cancel",
        "fsql_server_get_stats", "fsql_server_destroy", "fsql_last_error"]
@@ -107,6 +108,9 @@ def load() -> C.CDLL:
         "fsql_scan_select_host": (i32, [vp, vp, sz, u32, u32, vp, u32, vp, u32, vp, vp, vp]),
         "fsql_scan_select_plain": (i32, [vp, vp, sz, u32, u32, vp, u32, vp, u32, vp, vp, i32, vp]),
         "fsql_aggregate_sum": (i32, [vp, vp, sz, u32, u32, vp, vp]),
+        "fsql_aggregate_max": (i32, [vp, vp, sz, u32, vp, vp]),
+        "fsql_aggregate_min": (i32, [vp, vp, vp, sz, u32, vp, vp]),
+        "fsql_extreme_plan_info": (i32, [i32, sz, u32, C.POINTER(u32), C.POINTER(u32)]),
         "fsql_sum_plan_info": (i32, [sz, u32, u32, C.POINTER(u32), C.POINTER(u32), C.POINTER(u32)]),
         "fsql_plan_info_plain": (i32, [u32, u32, u32, u32, vp, C.POINTER(u32), C.POINTER(u32), vp, u32,
                                        C.POINTER(u32)]),
@@ -186,6 +190,13 @@ def sum_plan_info(rows: int, width: int, out_width: int):
     g, lv, lit = C.c_uint32(), C.c_uint32(), C.c_uint32()
     _check(load().fsql_sum_plan_info(rows, width, out_width, C.byref(g), C.byref(lv), C.byref(lit)))
     return int(g.value), int(lv.value), int(lit.value)
+
+
+def extreme_plan_info(is_min: bool, rows: int, width: int):
+    """(gates, levels) of the MAX (is_min False) or MIN circuit."""
+    g, lv = C.c_uint32(), C.c_uint32()
+    _check(load().fsql_extreme_plan_info(int(bool(is_min)), rows, width, C.byref(g), C.byref(lv)))
+    return int(g.value), int(lv.value)
 
 
 def _consts_array(consts):
@@ -339,6 +350,15 @@ class Context:
     def aggregate_sum(self, values, rows: int, width: int, out_width: int, out, stream=None) -> None:
         """fsql_aggregate_sum: values [rows, width, n+1] -> out [out_width, n+1], sum mod 2^out_width."""
         _check(load().fsql_aggregate_sum(self._h, _ptr(values), rows, width, out_width, _ptr(out), _stream(stream)))
+
+    def aggregate_max(self, values, rows: int, width: int, out, stream=None) -> None:
+        """fsql_aggregate_max: values [rows, width, n+1] -> out [width, n+1]."""
+        _check(load().fsql_aggregate_max(self._h, _ptr(values), rows, width, _ptr(out), _stream(stream)))
+
+    def aggregate_min(self, values, match, rows: int, width: int, out, stream=None) -> None:
+        """fsql_aggregate_min: values [rows, width, n+1], match [rows, n+1] -> out [width, n+1]."""
+        _check(load().fsql_aggregate_min(self._h, _ptr(values), _ptr(match), rows, width, _ptr(out),
+                                         _stream(stream)))
 
     def scan_select_plain(self, column, rows: int, width: int, pred: int, consts, payloads, payload_width: int,
                           match, out_payloads, per_gate: bool = False, stream=None) -> None:

@@ -11,6 +11,7 @@ generators stand in for them with the shapes of the benchmark workloads:
                 WHERE lo <= c < hi with hi - lo = 6554 (10% selectivity)
   <name>maj     the same table with the majority-chain comparator
   <name>plain   the same table with the query constants given as plaintexts
+  <name>sum     the same scan followed by the SUM of each masked payload column
   gates(B)      B independent gates: random bit pairs, gate type uniform in
                 {NAND, AND, OR, XOR, XNOR}
 
@@ -41,6 +42,12 @@ class Table:
     payload_width: int = 0
     consts: tuple = ()                 # (k,) or (lo, hi)
     plain: bool = False                # constants given to the server as plaintexts
+    aggregate: bool = False            # SUM of each masked payload column after the scan
+
+    @property
+    def sum_width(self) -> int:
+        """Output bits of an exact SUM of one payload column over all rows."""
+        return self.payload_width + max(1, (self.rows - 1).bit_length())
 
     def const_bits(self) -> np.ndarray:
         bits = []
@@ -86,7 +93,13 @@ def _rng(seed: int, purpose: int) -> np.random.Generator:
 def table(name: str, seed: int = 1, rows: int | None = None) -> Table:
     """A named workload table; the suffix "maj" gives the same table with the
     majority-chain comparator (LT_MAJ / RANGE_MAJ) instead of the ripple one,
-    the suffix "plain" the same table with plaintext query constants."""
+    the suffix "plain" the same table with plaintext query constants, the
+    suffix "sum" the same scan followed by a SUM of its masked payloads."""
+    if name.endswith("sum"):
+        t = table(name[:-3], seed, rows)
+        t.aggregate = True
+        t.name = name
+        return t
     if name.endswith("plain"):
         t = table(name[:-5], seed, rows)
         t.plain = True

@@ -187,3 +187,14 @@ def test_sum_circuit_limits():
     for bad in [(4, 0, 4), (4, 8, 0), (4, 8, 65), (1 << 23, 1, 8)]:
         with pytest.raises(F.FsqlError):
             F.sum_plan_info(*bad)
+
+
+@pytest.mark.parametrize("is_min", [False, True])
+@pytest.mark.parametrize("rows,width", [(0, 4), (1, 4), (2, 3), (5, 3), (7, 8), (64, 32), (4096, 32)])
+def test_extreme_circuits_equal_oracle_circuits(is_min, rows, width):
+    t, a, b, c, ol, ninp = O.extreme_netlist(is_min, rows, width)
+    depth = [0] * ninp
+    for k in range(t.size):
+        depth.append(1 + max(depth[a[k]], depth[b[k]], depth[c[k]] if c[k] >= 0 else 0))
+    levels = max(depth[ninp:]) if t.size else 0
+    assert F.extreme_plan_info(is_min, rows, width) == (int(t.size), levels)

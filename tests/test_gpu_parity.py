@@ -337,6 +337,58 @@ def test_scan_then_sum_full_size(env):
     assert np.array_equal(host(out2).view(np.uint32), o.aggregate_sum(sl, 24, 8, 13))
 
 
+# ---------------------------------------------------------------- MAX / MIN aggregation
+@pytest.mark.parametrize("rows,width", [(5, 3), (1, 4), (8, 6), (0, 3)])
+def test_aggregate_max_min_bit_exact(env, rows, width):
+    ctx, o = env
+    rng = np.random.default_rng(rows * 11 + width)
+    vals = rng.integers(0, 1 << width, rows)
+    m = (rng.integers(0, 2, rows) if rows else np.zeros(0, int)).astype(np.uint8)
+    if rows > 1:
+        m[0] = 1
+    W = ctx.words
+    bits = np.array([(int(v) >> j) & 1 for v in vals for j in range(width)], np.uint8)
+    ct = both_encrypt_bits(ctx, o, bits, 43) if rows else np.zeros((0, W), np.uint32)
+    mct = both_encrypt_bits(ctx, o, m, 44) if rows else np.zeros((0, W), np.uint32)
+    dct = dev(ct.view(np.int32)) if rows else None
+    dm = dev(mct.view(np.int32)) if rows else None
+    for is_min in (False, True):
+        out = torch.full((width, W), 7, dtype=torch.int32, device="cuda")
+        if is_min:
+            ctx.aggregate_min(dct, dm, rows, width, out)
+        else:
+            ctx.aggregate_max(dct, rows, width, out)
+        got = host(out).view(np.uint32)
+        want = o.aggregate_extreme(is_min, ct, rows, width, mct if is_min else None)
+        assert np.array_equal(got, want), is_min
+        dec = ctx.decrypt_bits(got)
+        value = int(sum(int(dec[j]) << j for j in range(width)))
+        sel = [int(v) for v, mm in zip(vals, m) if mm]
+        assert value == ((min(sel) if sel else (1 << width) - 1) if is_min else (int(vals.max()) if rows else 0))
+
+
+def test_scan_then_max_min_full_size(env):
+    """MAX and MIN over the full-size equality scan's payload (4096 rows,
+    524,160 and 655,232 bootstraps): decrypted results equal the SQL
+    answers.  Default engine only: 1.2 M bootstraps take minutes on the
+    64-bit-prime engine, whose gates the small-table tests cover."""
+    ctx, _ = env
+    if ctx.engine != F.FSQL_ENGINE_DUAL_PRIME:
+        pytest.skip("full-size MAX/MIN runs on the default engine")
+    t = WL.table("eq32x4096", seed=1)
+    col, cst, pays = WL.encrypt_table(ctx, t)
+    match, outs = run_scan(ctx, t, col, cst, pays)
+    masked, dmatch = dev(outs[0].view(np.int32)), dev(match.view(np.int32))
+    m_want, (p_want,) = t.expected()
+    raw = t.payloads[0]
+    dec = lambda out: int(sum(int(b) << j for j, b in enumerate(ctx.decrypt_bits(host(out).view(np.uint32)))))
+    out = torch.zeros((32, ctx.words), dtype=torch.int32, device="cuda")
+    ctx.aggregate_max(masked, t.rows, 32, out)
+    assert dec(out) == int(p_want.max())
+    ctx.aggregate_min(masked, dmatch, t.rows, 32, out)
+    assert dec(out) == int(raw[m_want == 1].min())
+
+
 def test_scan_eq32x4096_full_size_sampled_rows(env):
     """The benchmark workload at full size, in the benchmark's launch
     configuration; the oracle recomputes whole sampled rows (the matching row
