@@ -529,8 +529,9 @@ def run_serving(args, dist):
 
 
 def kernel_source_hash() -> str:
-    """sha256 of the blind-rotation kernel's sources: ntt.cuh and the device
-    part of kernels.cu (everything before its host-side section)."""
+    """sha256 of the blind-rotation kernel's sources: ntt.cuh and kernels.cu
+    up to the end of the blind rotation's device code (twiddle tables, gate
+    linear forms, the kernel itself)."""
     import hashlib
 
     h = hashlib.sha256()
@@ -538,8 +539,8 @@ def kernel_source_hash() -> str:
         h.update(fh.read())
     with open(os.path.join(ROOT, "paper_2510_15413_b300", "csrc", "kernels.cu"), "rb") as fh:
         text = fh.read()
-    marker = b"// ------------------------------------------------------------------ host side"
-    assert marker in text, "kernels.cu lost its host-side marker"
+    marker = b"// ---------------------------------------------------------------- end of the blind rotation's device code"
+    assert marker in text, "kernels.cu lost its end-of-blind-rotation marker"
     h.update(text.split(marker)[0])
     return h.hexdigest()
 

@@ -133,6 +133,11 @@ FSQL_API int fsql_ctx_engine(const fsql_ctx* ctx, int* engine);
  * do not depend on it. */
 FSQL_API int fsql_ctx_set_br_gates(fsql_ctx* ctx, int gates_per_cta);
 FSQL_API int fsql_ctx_br_gates(const fsql_ctx* ctx, int* gates_per_cta);
+/* Latency mode for batches smaller than two gates per SM (two-prime engine;
+ * on by default): one gate per CTA of three 128-thread groups that run the
+ * three gadget-row steps of every CMux side by side, instead of one gate per
+ * 128-thread CTA.  The output words are the same either way. */
+FSQL_API int fsql_ctx_set_latency_mode(fsql_ctx* ctx, int on);
 
 /* Autotuner: times the blind rotation of `probe_gates` synthetic gates
  * (0 = 4 x SMs x 4) for every launch shape the context's engine offers,

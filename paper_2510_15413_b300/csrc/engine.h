@@ -71,6 +71,7 @@ struct Ctx {
   int device = -1;
   int engine = FSQL_ENGINE_DUAL_PRIME;
   int br_gates = 3;              // gates per blind-rotation CTA for large batches
+  bool latency_mode = true;      // small batches: one gate per CTA of three groups (two-prime engine)
   // host-side secrets and standard-domain keys (client side)
   std::vector<uint8_t> s;    // LWE key [n]
   std::vector<uint8_t> S;    // GLWE key [N]
@@ -79,6 +80,7 @@ struct Ctx {
   // device-resident keys
   uint64_t* d_bkhat = nullptr;   // [n][2l][32][32][2] u64, NTT domain, times N^-1
   uint32_t* d_ksk = nullptr;     // [N][t][digits][kKsRowWords]
+  uint32_t* d_ks_part = nullptr; // keyswitch partial sums of small batches [16][128][kKsRowWords]
   void* d_tables = nullptr;      // NttTablesT of the engine
   std::vector<uint8_t> tables;   // host copy
   size_t key_bytes = 0;

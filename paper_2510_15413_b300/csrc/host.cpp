@@ -563,6 +563,12 @@ int fsql_ctx_set_br_gates(fsql_ctx* ctx, int gates_per_cta) {
   return FSQL_OK;
 }
 
+int fsql_ctx_set_latency_mode(fsql_ctx* ctx, int on) {
+  if (!ctx) return arg_error("null context");
+  reinterpret_cast<Ctx*>(ctx)->latency_mode = on != 0;
+  return FSQL_OK;
+}
+
 int fsql_ctx_br_gates(const fsql_ctx* ctx, int* gates_per_cta) {
   if (!ctx || !gates_per_cta) return arg_error("null argument");
   *gates_per_cta = reinterpret_cast<const Ctx*>(ctx)->br_gates;

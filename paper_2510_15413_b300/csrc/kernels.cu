@@ -417,6 +417,144 @@ __global__ void __launch_bounds__(G * kGroup, 1)
   }
 }
 
+// ---------------------------------------------------------------- end of the blind rotation's device code
+
+// Latency mode of the blind rotation (batches smaller than two gates per
+// SM, where one 128-thread group per gate leaves the SMs mostly idle and a
+// gate's 630 CMux steps are a sequential chain).  One gate per CTA of three
+// 128-thread groups: in every CMux, group s takes gadget rows 2s and 2s+1
+// (the three steps of the throughput kernel run side by side), stages its
+// two key rows with cp.async, transforms its two digit polynomials and
+// multiply-accumulates them; the groups' reduced sums (each in [0, 2p))
+// meet in shared memory, and groups 0 and 1 each add the three partials of
+// one output polynomial (below 6p, two folds to [0, 2p)), run its inverse
+// transform and add it into ACC.  The arithmetic is the throughput
+// kernel's, so the words are the same.  Two-prime engine only.
+constexpr int kLatGroups = kRows / 2;  // three groups of two gadget rows
+
+template <class F>
+__host__ __device__ constexpr int lat_smem() {
+  return tab_bytes<F>() + kLatGroups * 2 * kChunkU64 * 8 + kLatGroups * 2 * kN * 8 + kGateAcc + kGateAbar + 16;
+}
+
+template <class F>
+__global__ void __launch_bounds__(kLatGroups * kGroup, 1)
+    blind_rotate_latency_kernel(const GateDesc* __restrict__ desc, int count, const uint64_t* __restrict__ bkhat,
+                                const void* __restrict__ gtab, int n, int bg_bits, uint32_t* __restrict__ big) {
+  static_assert(F::kEngine == FSQL_ENGINE_DUAL_PRIME, "latency mode is built for the two-prime engine");
+  constexpr int kThreads = kLatGroups * kGroup;
+  extern __shared__ __align__(128) uint8_t smem[];
+  typename F::Tables& T = *reinterpret_cast<typename F::Tables*>(smem);
+  uint64_t* stage = reinterpret_cast<uint64_t*>(smem + tab_bytes<F>());  // [group][2 rows][kChunkU64]
+  uint64_t* xb_all = stage + kLatGroups * 2 * kChunkU64;                   // [group][2 polys][N]
+  uint32_t* acc_poly = reinterpret_cast<uint32_t*>(xb_all + kLatGroups * 2 * kN);  // [2][N]
+  uint16_t* abar = reinterpret_cast<uint16_t*>(acc_poly + 2 * kN);                 // [n]
+  uint32_t* bbar_slot = reinterpret_cast<uint32_t*>(abar + kMaxN);
+  const int grp = threadIdx.x / kGroup, t = threadIdx.x % kGroup;
+  const int bar = 1 + grp;
+  uint64_t* xbufs = xb_all + grp * 2 * kN;
+  uint64_t* my_stage = stage + grp * 2 * kChunkU64;
+
+  load_tables(T, gtab);
+  uint32_t off = 1u << (31 - bg_bits * kL);
+  for (int j = 1; j <= kL; ++j) off += (1u << (bg_bits - 1)) << (32 - bg_bits * j);
+  const uint32_t dmask = (1u << bg_bits) - 1, dhalf = 1u << (bg_bits - 1);
+  // rows 2 grp and 2 grp + 1 belong to polynomials (2 grp) / l and (2 grp + 1) / l
+  const int row0 = 2 * grp, row1 = 2 * grp + 1;
+  const int u0 = row0 / kL, u1 = row1 / kL;
+  const int shift0 = 32 - bg_bits * (row0 % kL + 1), shift1 = 32 - bg_bits * (row1 % kL + 1);
+
+  for (int gi = blockIdx.x; gi < count; gi += gridDim.x) {
+    __syncthreads();  // tables loaded; the previous gate is extracted
+    const GateDesc d = desc[gi];
+    const Lin lin = gate_lin(d.type);
+    const uint32_t* c3 = lin.cc ? d.c : nullptr;
+    for (int x = threadIdx.x; x <= n; x += kThreads) {
+      uint32_t v = lin.ca * d.a[x] + lin.cb * d.b[x];
+      if (c3) v += lin.cc * c3[x];
+      if (x == n) v += lin.k;
+      const uint32_t ms = ((v + (1u << 20)) >> 21) & (2 * kN - 1);
+      if (x < n) abar[x] = static_cast<uint16_t>(ms);
+      else *bbar_slot = ms;
+    }
+    __syncthreads();
+    {
+      const uint32_t e = (2 * kN - *bbar_slot) & (2 * kN - 1);
+      for (int c = threadIdx.x; c < kN; c += kThreads) {
+        acc_poly[c] = 0u;
+        const uint32_t idx = (static_cast<uint32_t>(c) - e) & (2 * kN - 1);
+        acc_poly[kN + c] = idx < static_cast<uint32_t>(kN) ? (1u << 29) : (0u - (1u << 29));
+      }
+    }
+    int parity = 0;
+    for (int i = 0; i < n; ++i) {
+      __syncthreads();  // ACC of the previous CMux complete; its stage and partials consumed
+      {
+        const uint4* src = reinterpret_cast<const uint4*>(bkhat + static_cast<size_t>(i * kRows + row0) * kChunkU64);
+        uint4* dst = reinterpret_cast<uint4*>(my_stage);
+        for (int q = t; q < 2 * kChunkU64 * 8 / 16; q += kGroup) cp_async16(dst + q, src + q);
+        cp_async_commit();
+      }
+      const uint32_t a_i = abar[i];
+      uint64_t x[2][8];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const uint32_t c = t + 128 * q;
+        const uint32_t idx = (c - a_i) & (2 * kN - 1);
+        uint32_t v[2];
+#pragma unroll
+        for (int r = 0; r < 2; ++r) {
+          const uint32_t* Pu = acc_poly + (r == 0 ? u0 : u1) * kN;
+          const uint32_t rot = idx < static_cast<uint32_t>(kN) ? Pu[idx] : 0u - Pu[idx - kN];
+          v[r] = rot - Pu[c] + off;
+        }
+        x[0][q] = F::from_digit((v[0] >> shift0) & dmask, dhalf);
+        x[1][q] = F::from_digit((v[1] >> shift1) & dmask, dhalf);
+      }
+      dev::ntt_forward<F, 2, 2, 1>(x, xbufs, parity, T, t, bar);
+      cp_async_wait<0>();
+      dev::named_sync(bar);  // the group's key rows are visible to all its threads
+      typename F::Acc acc[8];
+#pragma unroll
+      for (int q = 0; q < 8; ++q)
+#pragma unroll
+        for (int p = 0; p < 2; ++p) {
+          const ulonglong2 w = *reinterpret_cast<const ulonglong2*>(my_stage + p * kChunkU64 + (q * kGroup + t) * 2);
+          F::mac(acc[q], x[p][q], w, p == 0);
+        }
+      dev::named_sync(bar);  // the group is done reading its key rows: reuse them for the partial sums
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        my_stage[8 * t + q] = F::acc0(acc[q]);       // output polynomial 0, forward-output slot 8t + q
+        my_stage[kN + 8 * t + q] = F::acc1(acc[q]);  // output polynomial 1
+      }
+      __syncthreads();  // every group's partial sums written
+      if (grp < 2) {
+        uint64_t y[1][8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          uint32_t s1 = 0, s2 = 0;
+#pragma unroll
+          for (int g = 0; g < kLatGroups; ++g) {
+            const uint64_t v = stage[g * 2 * kChunkU64 + grp * kN + 8 * t + q];
+            s1 += dev::lo32(v);
+            s2 += dev::hi32(v);
+          }
+          y[0][q] = dev::pack(dev::fold(dev::fold(s1, 4 * dev::kP1), 2 * dev::kP1),
+                              dev::fold(dev::fold(s2, 4 * dev::kP2), 2 * dev::kP2));
+        }
+        dev::ntt_inverse<F, 1, 2, 1>(y, xbufs, parity, T, t, bar);
+#pragma unroll
+        for (int q = 0; q < 8; ++q) acc_poly[grp * kN + t + 128 * q] += F::to_torus(y[0][q]);
+      }
+    }
+    __syncthreads();
+    uint32_t* out = big + static_cast<size_t>(gi) * (kN + 1);
+    for (int c = threadIdx.x; c < kN; c += kThreads) out[c] = c == 0 ? acc_poly[0] : 0u - acc_poly[kN - c];
+    if (threadIdx.x == 0) out[kN] = acc_poly[kN];
+  }
+}
+
 // Keyswitch N -> n (see file comment).  Rounding: a + 2^15, keep the top 16
 // bits, 8 base-4 digits most significant first; digit v at level j selects
 // key row KSK[i][j][v-1]; out = (0, .., 0, b) - sum of the selected rows.
@@ -472,6 +610,74 @@ __global__ void __launch_bounds__(kKsCols)
     uint32_t* out = desc ? desc[g0 + g].out : out_contig + static_cast<size_t>(g0 + g) * (n + 1);
     const uint32_t body = col == n ? big[static_cast<size_t>(g0 + g) * (kN + 1) + kN] : 0u;
     out[col] = acc[g] + body;
+  }
+}
+
+// Keyswitch of small batches (latency): the 1024 input positions are split
+// over `splits` CTAs per (gate group, column tile); CTA s sums the key rows
+// of positions [s 1024/splits, (s+1) 1024/splits) into its own partial
+// (part[s][gate][column], kKsPartGates gates per split) and
+// keyswitch_reduce_kernel adds the partials and the body.  Addition mod 2^32
+// is associative, so the words equal the single-pass kernel's.
+constexpr int kKsPartGates = 128;  // largest batch that takes the split path
+constexpr int kKsMaxSplits = 16;
+
+__global__ void __launch_bounds__(kKsCols)
+    keyswitch_part_kernel(const uint32_t* __restrict__ big, int count, const uint32_t* __restrict__ ksk, int splits,
+                          uint32_t* __restrict__ part) {
+  __shared__ uint16_t dig[kKsGates][kN / 2];
+  __shared__ uint32_t tbl[kKsT][4][kKsCols];
+  const int g0 = blockIdx.x * kKsGates;
+  const int ng = min(kKsGates, count - g0);
+  const int span = kN / splits, i0 = blockIdx.z * span;
+  for (int q = threadIdx.x; q < kKsGates * span; q += kKsCols) {
+    const int g = q / span, i = q % span;
+    uint16_t v = 0;
+    if (g < ng) v = static_cast<uint16_t>((big[static_cast<size_t>(g0 + g) * (kN + 1) + i0 + i] + (1u << 15)) >> 16);
+    dig[g][i] = v;
+  }
+  const int tc = threadIdx.x;
+#pragma unroll
+  for (int j = 0; j < kKsT; ++j) tbl[j][0][tc] = 0u;
+  __syncthreads();
+  const int col = blockIdx.y * kKsCols + tc;
+  uint32_t acc[kKsGates];
+#pragma unroll
+  for (int g = 0; g < kKsGates; ++g) acc[g] = 0u;
+  const uint32_t* base = ksk + col;
+#pragma unroll 1
+  for (int i = 0; i < span; ++i) {
+#pragma unroll
+    for (int j = 0; j < kKsT; ++j) {
+      const uint32_t* rows = base + static_cast<size_t>(((i0 + i) * kKsT + j) * kKsDigits) * kKsRowWords;
+      tbl[j][1][tc] = __ldg(rows);
+      tbl[j][2][tc] = __ldg(rows + kKsRowWords);
+      tbl[j][3][tc] = __ldg(rows + 2 * kKsRowWords);
+    }
+#pragma unroll
+    for (int g = 0; g < kKsGates; ++g) {
+      const uint32_t dv = dig[g][i];
+#pragma unroll
+      for (int j = 0; j < kKsT; ++j) acc[g] -= tbl[j][(dv >> (14 - 2 * j)) & 3u][tc];
+    }
+  }
+#pragma unroll
+  for (int g = 0; g < kKsGates; ++g) {
+    if (g >= ng) break;
+    part[(static_cast<size_t>(blockIdx.z) * kKsPartGates + g0 + g) * kKsRowWords + col] = acc[g];
+  }
+}
+
+// One CTA per gate: out = (0, .., 0, b') + the sum of the splits' partials.
+__global__ void __launch_bounds__(kKsCols)
+    keyswitch_reduce_kernel(const uint32_t* __restrict__ part, int splits, const uint32_t* __restrict__ big,
+                            const GateDesc* __restrict__ desc, uint32_t* __restrict__ out_contig, int n) {
+  const int g = blockIdx.x;
+  uint32_t* out = desc ? desc[g].out : out_contig + static_cast<size_t>(g) * (n + 1);
+  for (int col = threadIdx.x; col <= n; col += kKsCols) {
+    uint32_t v = col == n ? big[static_cast<size_t>(g) * (kN + 1) + kN] : 0u;
+    for (int s = 0; s < splits; ++s) v += part[(static_cast<size_t>(s) * kKsPartGates + g) * kKsRowWords + col];
+    out[col] = v;
   }
 }
 
@@ -637,7 +843,7 @@ struct Plan {
   const GateDesc* graph_desc = nullptr;
   const uint32_t* graph_big = nullptr;
   const OutDesc* graph_lits = nullptr;
-  int graph_br_gates = 0;
+  int graph_br_gates = 0;  // launch shape: 2 x gates per CTA + latency mode
   // aggregation plans (SUM, MAX, MIN): key and the buffers they own
   int agg_kind = -1;
   const uint32_t* agg_in = nullptr;
@@ -725,6 +931,7 @@ int device_init(Ctx& c) {
   CK(cudaMalloc(&c.d_tables, c.tables.size()));
   CK(cudaMalloc(&c.d_bkhat, bkhat_words * 8));
   CK(cudaMalloc(&c.d_ksk, ksk_words * 4));
+  CK(cudaMalloc(&c.d_ks_part, static_cast<size_t>(kKsMaxSplits) * kKsPartGates * kKsRowWords * 4));
   c.key_bytes = bkhat_words * 8 + ksk_words * 4 + c.tables.size();
   CK(cudaMemcpy(c.d_tables, c.tables.data(), c.tables.size(), cudaMemcpyHostToDevice));
 
@@ -768,6 +975,8 @@ void device_free(Ctx& c) {
   cudaFree(c.d_stage);
   if (c.h_desc) cudaFreeHost(c.h_desc);
   if (c.desc_event) cudaEventDestroy(static_cast<cudaEvent_t>(c.desc_event));
+  cudaFree(c.d_ks_part);
+  c.d_ks_part = nullptr;
   cudaFree(c.d_lits);
   c.d_lits = nullptr;
   c.lits_cap = 0;
@@ -813,6 +1022,27 @@ static cudaError_t launch_br_engine(int sm_count, const GateDesc* d_desc, size_t
   return cudaGetLastError();
 }
 
+// Latency mode (two-prime engine): one gate per CTA of three groups.
+template <class F>
+static cudaError_t launch_br_latency(int sm_count, const GateDesc* d_desc, size_t count, const uint64_t* bkhat,
+                                     const void* tables, int n, int bg_bits, uint32_t* d_big, cudaStream_t st) {
+  static_assert(lat_smem<F>() <= 227 * 1024, "latency-mode shared memory over budget");
+  static bool attr_set[64] = {};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+  if (!attr_set[dev]) {
+    const cudaError_t e = cudaFuncSetAttribute(blind_rotate_latency_kernel<F>,
+                                               cudaFuncAttributeMaxDynamicSharedMemorySize, lat_smem<F>());
+    if (e != cudaSuccess) return e;
+    attr_set[dev] = true;
+  }
+  const int grid = static_cast<int>(std::min<size_t>(count, static_cast<size_t>(sm_count)));
+  blind_rotate_latency_kernel<F><<<grid, kLatGroups * kGroup, lat_smem<F>(), st>>>(d_desc, static_cast<int>(count),
+                                                                                    bkhat, tables, n, bg_bits, d_big);
+  return cudaGetLastError();
+}
+
 // Launch shapes measured best on B300 per engine: the 64-bit prime is ALU
 // bound and wants more resident gates (one gadget row per step, 4 gates per
 // CTA); the two-prime engine is latency bound and wants independent work per
@@ -831,6 +1061,8 @@ static cudaError_t launch_br_any(Ctx& c, const GateDesc* d_desc, size_t count, u
     return launch_br_engine<F, 4, 1>(c.sm_count, d_desc, count, c.d_bkhat, c.d_tables, n, bg, d_big, st);
   }
   using F = dev::DualPrime;
+  if (small && c.latency_mode)
+    return launch_br_latency<F>(c.sm_count, d_desc, count, c.d_bkhat, c.d_tables, n, bg, d_big, st);
   if (small || c.br_gates == 1)
     return launch_br_engine<F, 1, 2>(c.sm_count, d_desc, count, c.d_bkhat, c.d_tables, n, bg, d_big, st);
   if (c.br_gates == 3)
@@ -851,10 +1083,23 @@ int launch_blind_rotate(Ctx& c, const GateDesc* d_desc, size_t count, uint32_t* 
 int launch_keyswitch(Ctx& c, const uint32_t* d_big, const GateDesc* d_desc, uint32_t* d_out_contig, size_t count,
                      void* stream) {
   if (count == 0) return FSQL_OK;
-  const dim3 grid(static_cast<unsigned>((count + kKsGates - 1) / kKsGates), kKsTiles);
+  const unsigned groups = static_cast<unsigned>((count + kKsGates - 1) / kKsGates);
   LaunchTimer tm(c, static_cast<cudaStream_t>(stream));
-  keyswitch_kernel<<<grid, kKsCols, 0, static_cast<cudaStream_t>(stream)>>>(
-      d_big, d_desc, d_out_contig, static_cast<int>(count), c.d_ksk, static_cast<int>(c.p.n));
+  // splits so that a small batch still fills about two CTAs per SM
+  int splits = 1;
+  while (c.d_ks_part && count <= static_cast<size_t>(kKsPartGates) && splits < kKsMaxSplits &&
+         groups * kKsTiles * splits < static_cast<unsigned>(2 * c.sm_count))
+    splits *= 2;
+  if (splits > 1) {
+    keyswitch_part_kernel<<<dim3(groups, kKsTiles, splits), kKsCols, 0, static_cast<cudaStream_t>(stream)>>>(
+        d_big, static_cast<int>(count), c.d_ksk, splits, c.d_ks_part);
+    CK(cudaGetLastError());
+    keyswitch_reduce_kernel<<<static_cast<unsigned>(count), kKsCols, 0, static_cast<cudaStream_t>(stream)>>>(
+        c.d_ks_part, splits, d_big, d_desc, d_out_contig, static_cast<int>(c.p.n));
+  } else {
+    keyswitch_kernel<<<dim3(groups, kKsTiles), kKsCols, 0, static_cast<cudaStream_t>(stream)>>>(
+        d_big, d_desc, d_out_contig, static_cast<int>(count), c.d_ksk, static_cast<int>(c.p.n));
+  }
   CK(cudaGetLastError());
   tm.done(false, count);
   return FSQL_OK;
@@ -1226,7 +1471,7 @@ int execute_plan(Ctx* c, fsql::Plan& pl, const fsql::GateDesc* d_desc, const fsq
   if (prof && prof->recording) return launch_all(stream);  // per-launch events need plain launches
   fsql::Plan& mp = pl;
   if (!mp.graph || mp.graph_desc != d_desc || mp.graph_big != c->d_big || mp.graph_lits != d_lits ||
-      mp.graph_br_gates != c->br_gates) {
+      mp.graph_br_gates != 2 * c->br_gates + (c->latency_mode ? 1 : 0)) {
     if (mp.graph) cudaGraphExecDestroy(mp.graph);
     mp.graph = nullptr;
     cudaStream_t cs = static_cast<cudaStream_t>(c->capture_stream);
@@ -1253,7 +1498,7 @@ int execute_plan(Ctx* c, fsql::Plan& pl, const fsql::GateDesc* d_desc, const fsq
     mp.graph_desc = d_desc;
     mp.graph_big = c->d_big;
     mp.graph_lits = d_lits;
-    mp.graph_br_gates = c->br_gates;
+    mp.graph_br_gates = 2 * c->br_gates + (c->latency_mode ? 1 : 0);
   }
   if (cudaGraphLaunch(mp.graph, static_cast<cudaStream_t>(stream)) != cudaSuccess) {
     fsql::set_error("scan graph launch failed");

@@ -23,7 +23,7 @@ ENGINES = {"default": -1, "goldilocks": 0, "dual_prime": 1}
 
 # every symbol include/fhesql.h declares
 API = ["fsql_params_default", "fsql_params_toy", "fsql_ctx_create", "fsql_ctx_create_engine", "fsql_ctx_engine",
-       "fsql_ctx_set_br_gates", "fsql_ctx_br_gates", "fsql_autotune",
+       "fsql_ctx_set_br_gates", "fsql_ctx_br_gates", "fsql_ctx_set_latency_mode", "fsql_autotune",
        "fsql_ctx_destroy", "fsql_ctx_params",
        "fsql_ctx_device_bytes", "fsql_export_keys", "fsql_encrypt", "fsql_encrypt_bits", "fsql_encrypt_uint",
        "fsql_phase", "fsql_decrypt_bits", "fsql_decrypt_uint", "fsql_gate_batch", "fsql_blind_rotate_extract",
@@ -86,6 +86,7 @@ def load() -> C.CDLL:
         "fsql_ctx_create_engine": (i32, [C.POINTER(fsql_params), u64, i32, i32, C.POINTER(vp)]),
         "fsql_ctx_engine": (i32, [vp, C.POINTER(i32)]),
         "fsql_ctx_set_br_gates": (i32, [vp, i32]),
+        "fsql_ctx_set_latency_mode": (i32, [vp, i32]),
         "fsql_ctx_br_gates": (i32, [vp, C.POINTER(i32)]),
         "fsql_autotune": (i32, [vp, sz, vp, C.POINTER(i32), C.POINTER(C.c_double)]),
         "fsql_ctx_destroy": (None, [vp]),
@@ -252,6 +253,10 @@ class Context:
     @br_gates.setter
     def br_gates(self, g: int) -> None:
         _check(load().fsql_ctx_set_br_gates(self._h, int(g)))
+
+    def set_latency_mode(self, on: bool) -> None:
+        """Small batches on one gate per CTA of three groups (default on)."""
+        _check(load().fsql_ctx_set_latency_mode(self._h, int(bool(on))))
 
     def autotune(self, probe_gates: int = 0, stream=None):
         """Pick the fastest blind-rotation launch shape; returns (gates per CTA, {shape: ms})."""

@@ -279,6 +279,27 @@ def test_scan_plain_eq32x4096_full_size_sampled_rows(env):
     assert np.array_equal(outs[0].reshape(t.rows, t.payload_width, -1)[rows], oout)
 
 
+def test_latency_mode_equals_group_mode_and_oracle(env):
+    """Small batches: the latency-mode kernel (one gate per CTA of three
+    groups) and the one-group-per-gate kernel give the oracle's words."""
+    ctx, o = env
+    rng = np.random.default_rng(17)
+    for count in (1, 5, 150, 295):
+        types = rng.integers(0, 10, count).astype(np.uint8)
+        a = both_encrypt_bits(ctx, o, rng.integers(0, 2, count).astype(np.uint8), 60)
+        b = both_encrypt_bits(ctx, o, rng.integers(0, 2, count).astype(np.uint8), 61)
+        res = []
+        for on in (True, False):
+            ctx.set_latency_mode(on)
+            out = torch.zeros((count, ctx.words), dtype=torch.int32, device="cuda")
+            ctx.gate_batch(dev(types), dev(a.view(np.int32)), dev(b.view(np.int32)), out)
+            res.append(host(out).view(np.uint32))
+        ctx.set_latency_mode(True)
+        assert np.array_equal(res[0], res[1]), count
+        k = min(count, 4)
+        assert np.array_equal(res[0][:k], o.gate_batch(types[:k].astype(np.int32), a[:k], b[:k]))
+
+
 # ---------------------------------------------------------------- SUM aggregation
 @pytest.mark.parametrize("rows,width,out_width", [(6, 3, 6), (1, 4, 6), (24, 8, 13), (9, 4, 3)])
 def test_aggregate_sum_bit_exact(env, rows, width, out_width):
