@@ -93,6 +93,11 @@ def lib():
                                           C.c_void_p, C.c_void_p, C.POINTER(C.c_int32)]
         L.orc_extreme_eval_plain.argtypes = [C.c_int, C.c_int, C.c_int, u8p, u8p]
         L.orc_aggregate_extreme.argtypes = [C.c_void_p, C.c_int, u32p, C.c_void_p, C.c_int, C.c_int, u32p]
+        L.orc_encrypt_big_bits.argtypes = [C.c_void_p, u8p, C.c_size_t, C.c_uint64, C.c_uint64, u32p]
+        L.orc_decrypt_big_bits.argtypes = [C.c_void_p, u32p, C.c_size_t, u8p]
+        L.orc_gate3_ks_first.argtypes = [C.c_void_p, C.c_int, u32p, u32p, C.c_void_p, u32p]
+        L.orc_scan_ks_first.argtypes = [C.c_void_p, C.c_int, C.c_int, u32p, u32p, C.c_int, C.c_int,
+                                        C.POINTER(C.c_void_p), u32p, C.POINTER(C.c_void_p), C.c_longlong]
         L.orc_set_threads.argtypes = [C.c_int]
         L.orc_max_threads.restype = C.c_int
         _lib = L
@@ -461,6 +466,42 @@ class Oracle:
         if rc != 0:
             raise ValueError("aggregation failed")
         return out
+
+    # ---- keyswitch-first order: ciphertexts of N + 1 words under the N-bit key
+    def encrypt_big_bits(self, bits, stream: int, first_index: int = 0):
+        bits = np.ascontiguousarray(bits, dtype=np.uint8).ravel()
+        out = np.zeros((bits.size, self.N + 1), np.uint32)
+        lib().orc_encrypt_big_bits(self._h, bits, bits.size, stream, first_index, out)
+        return out
+
+    def decrypt_big_bits(self, ct):
+        ct = _u32(ct).reshape(-1, self.N + 1)
+        out = np.zeros(ct.shape[0], np.uint8)
+        lib().orc_decrypt_big_bits(self._h, ct.ravel(), ct.shape[0], out)
+        return out
+
+    def gate3_ks_first(self, gate: int, a, b, c=None):
+        a, b = _u32(a).ravel(), _u32(b).ravel()
+        cc = _u32(c).ravel() if c is not None else None
+        out = np.zeros(self.N + 1, np.uint32)
+        if lib().orc_gate3_ks_first(self._h, gate, a, b, cc.ctypes.data if cc is not None else None, out) != 0:
+            raise ValueError("bad gate")
+        return out
+
+    def scan_ks_first(self, pred: int, w: int, column, consts, payloads, pw: int):
+        """orc_scan in keyswitch-first order: every ciphertext [N+1] words."""
+        W = self.N + 1
+        column = _u32(column).reshape(-1, w, W)
+        rows = column.shape[0]
+        consts = _u32(consts).reshape(-1, W)
+        pays = [_u32(p).reshape(rows, pw, W) for p in payloads]
+        match = np.zeros((rows, W), np.uint32)
+        outs = [np.zeros((rows, pw, W), np.uint32) for _ in pays]
+        pin = (C.c_void_p * max(1, len(pays)))(*[p.ctypes.data for p in pays])
+        pout = (C.c_void_p * max(1, len(outs)))(*[o.ctypes.data for o in outs])
+        if lib().orc_scan_ks_first(self._h, pred, w, column, consts, len(pays), pw, pin, match, pout, rows) != 0:
+            raise ValueError("scan failed")
+        return match, outs
 
     def scan_plain(self, pred: int, w: int, column, consts, payloads, pw: int):
         """Scan with plaintext query constants (k,) or (lo, hi): returns

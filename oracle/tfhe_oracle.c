@@ -1272,6 +1272,115 @@ ORC_API int orc_aggregate_extreme(const orc_ctx *c, int is_min, const uint32_t *
     return bad ? -1 : 0;
 }
 
+/* ------------------------------------------------------------------ */
+/* Keyswitch-first order (the order of TFHE-rs, which the paper uses,     */
+/* §2.2): ciphertexts live under the N-bit key (the GLWE key read as an   */
+/* LWE key), each gate forms its linear combination on N + 1 words,       */
+/* keyswitches that single result to the n-bit key, and bootstraps it; the */
+/* extracted sample is the gate's output, under the N-bit key again.      */
+/* Fresh ciphertexts under the N-bit key use the GLWE noise; ciphertext c */
+/* of a stream draws words c (N + 2) .. c (N + 2) + N + 1.                */
+/* ------------------------------------------------------------------ */
+
+ORC_API void orc_encrypt_big_bits(const orc_ctx *c, const uint8_t *bits, size_t count, uint64_t stream,
+                                  uint64_t first_index, uint32_t *out)
+{
+    int N = c->p.N;
+#pragma omp parallel for schedule(static)
+    for (long long k = 0; k < (long long)count; k++)
+        lwe_encrypt(c->S, N, bits[k] ? (1u << 29) : (uint32_t)(0u - (1u << 29)), c->p.glwe_sigma, c->seed, stream,
+                    (first_index + (uint64_t)k) * (N + 2), out + (size_t)k * (N + 1));
+}
+
+ORC_API void orc_decrypt_big_bits(const orc_ctx *c, const uint32_t *ct, size_t count, uint8_t *out)
+{
+    for (size_t k = 0; k < count; k++)
+        out[k] = (int32_t)lwe_phase(ct + k * (c->p.N + 1), c->S, c->p.N) > 0;
+}
+
+/* One keyswitch-first gate: lincomb on N + 1 words -> keyswitch -> blind
+ * rotation (which modulus-switches its input) -> sample extraction. */
+ORC_API int orc_gate3_ks_first(const orc_ctx *c, int type, const uint32_t *c1, const uint32_t *c2,
+                               const uint32_t *c3, uint32_t *out)
+{
+    int n = c->p.n, N = c->p.N;
+    uint32_t *lin = (uint32_t *)malloc(sizeof(uint32_t) * (N + 1));
+    uint32_t *small = (uint32_t *)malloc(sizeof(uint32_t) * (n + 1));
+    uint32_t *acc = (uint32_t *)malloc(sizeof(uint32_t) * 2 * N);
+    int rc = (gate_has_three_inputs(type) && !c3) ? -1 : orc_gate_lincomb3(type, N, c1, c2, c3, lin);
+    if (rc == 0) {
+        orc_keyswitch(c, lin, small);
+        orc_blind_rotate(c, small, acc);
+        orc_sample_extract(N, acc, out);
+    }
+    free(lin);
+    free(small);
+    free(acc);
+    return rc;
+}
+
+/* The scan in keyswitch-first order: orc_scan's netlists and layouts with
+ * every ciphertext N + 1 words (column, constants, payloads, outputs). */
+ORC_API int orc_scan_ks_first(const orc_ctx *c, int pred, int w, const uint32_t *column, const uint32_t *consts,
+                              int n_payload, int pw, const uint32_t *const *payloads, uint32_t *match,
+                              uint32_t *const *out_payloads, long long rows)
+{
+    int32_t m, ninp;
+    int g = orc_netlist3(pred, w, n_payload, pw, NULL, NULL, NULL, NULL, &m, &ninp);
+    if (g < 0) return -1;
+    int32_t *t = (int32_t *)malloc(sizeof(int32_t) * g), *a = (int32_t *)malloc(sizeof(int32_t) * g),
+            *b = (int32_t *)malloc(sizeof(int32_t) * g), *c3 = (int32_t *)malloc(sizeof(int32_t) * g),
+            *depth = (int32_t *)malloc(sizeof(int32_t) * (ninp + g));
+    orc_netlist3(pred, w, n_payload, pw, t, a, b, c3, &m, &ninp);
+    int maxd = 0;
+    for (int i = 0; i < ninp; i++) depth[i] = 0;
+    for (int k = 0; k < g; k++) {
+        int d = depth[a[k]] > depth[b[k]] ? depth[a[k]] : depth[b[k]];
+        if (c3[k] >= 0 && depth[c3[k]] > d) d = depth[c3[k]];
+        depth[ninp + k] = 1 + d;
+        if (depth[ninp + k] > maxd) maxd = depth[ninp + k];
+    }
+    size_t W = (size_t)c->p.N + 1, per_row = (size_t)(ninp + g) * W;
+    int nconst = (pred == P_RANGE || pred == P_RANGE_MAJ) ? 2 * w : w;
+    uint32_t *wires = (uint32_t *)malloc(sizeof(uint32_t) * per_row * (size_t)(rows > 0 ? rows : 1));
+    for (long long row = 0; row < rows; row++) {
+        uint32_t *wr = wires + (size_t)row * per_row;
+        for (int i = 0; i < w; i++) memcpy(wr + i * W, column + ((size_t)row * w + i) * W, W * 4);
+        for (int i = 0; i < nconst; i++) memcpy(wr + (w + i) * W, consts + (size_t)i * W, W * 4);
+        for (int p = 0; p < n_payload; p++)
+            for (int bit = 0; bit < pw; bit++)
+                memcpy(wr + (size_t)(w + nconst + p * pw + bit) * W, payloads[p] + ((size_t)row * pw + bit) * W, W * 4);
+    }
+    int bad = 0;
+    for (int d = 1; d <= maxd; d++) {
+#pragma omp parallel for schedule(dynamic, 1) collapse(2) reduction(| : bad)
+        for (long long row = 0; row < rows; row++)
+            for (int k = 0; k < g; k++) {
+                if (depth[ninp + k] != d) continue;
+                uint32_t *wr = wires + (size_t)row * per_row;
+                bad |= orc_gate3_ks_first(c, t[k], wr + (size_t)a[k] * W, wr + (size_t)b[k] * W,
+                                          c3[k] >= 0 ? wr + (size_t)c3[k] * W : NULL,
+                                          wr + (size_t)(ninp + k) * W) != 0;
+            }
+    }
+    int first_mask = ninp + g - n_payload * pw;
+    for (long long row = 0; row < rows; row++) {
+        uint32_t *wr = wires + (size_t)row * per_row;
+        memcpy(match + (size_t)row * W, wr + (size_t)m * W, W * 4);
+        for (int p = 0; p < n_payload; p++)
+            for (int bit = 0; bit < pw; bit++)
+                memcpy(out_payloads[p] + ((size_t)row * pw + bit) * W, wr + (size_t)(first_mask + p * pw + bit) * W,
+                       W * 4);
+    }
+    free(wires);
+    free(t);
+    free(a);
+    free(b);
+    free(c3);
+    free(depth);
+    return bad ? -1 : 0;
+}
+
 ORC_API void orc_set_threads(int k)
 {
 #ifdef _OPENMP

@@ -653,3 +653,89 @@ def test_aggregate_extreme_toy_decrypts(toy_oracle):
     assert dec(o.aggregate_extreme(True, ct, rows, w, mct)) == int(vals[m == 1].min())
     one = o.aggregate_extreme(False, ct[:w], 1, w)  # one row: its own ciphertexts
     assert np.array_equal(one, ct[:w].reshape(w, -1))
+
+
+# --------------------------------------------------------------------------
+# keyswitch-first order: ciphertexts under the N-bit key
+# --------------------------------------------------------------------------
+def test_big_key_encryption_noise_and_phase(real_oracle):
+    """Fresh N-bit-key ciphertexts: phase = +-q/8 + e with e of the GLWE
+    noise (sigma 2^-25, i.e. 2^7 in torus units), exactly b - <a, S>."""
+    o = real_oracle
+    rng = np.random.default_rng(31)
+    bits = rng.integers(0, 2, 2000).astype(np.uint8)
+    ct = o.encrypt_big_bits(bits, 70)
+    assert ct.shape == (2000, o.N + 1)
+    S = o.glwe_key().astype(np.int64)
+    ph = (ct[:, o.N].astype(np.int64) - (ct[:, :o.N].astype(np.int64) * S).sum(axis=1)) % Q
+    assert np.array_equal(ph.astype(np.uint32), o.phase_big(ct))
+    e = centered(ph - np.where(bits == 1, E8, Q - E8))
+    assert abs(e.mean()) < 10 and 110 < e.std() < 146
+    assert np.array_equal(o.decrypt_big_bits(ct), bits)
+    # the same (stream, index) gives the same ciphertext
+    assert np.array_equal(o.encrypt_big_bits(bits[5:9], 70, 5), ct[5:9])
+
+
+@pytest.mark.parametrize("which", ["toy", "real"])
+def test_ks_first_gates_truth_tables(which, toy_oracle, real_oracle):
+    """Every two-input gate on every input pair and the three-input gates on
+    every triple (a spread of them at real parameters): the keyswitch-first
+    gate decrypts to the truth table with phase near +-q/8."""
+    o = toy_oracle if which == "toy" else real_oracle
+    pairs = [(x, y) for x in (0, 1) for y in (0, 1)]
+    cts = o.encrypt_big_bits(np.array([1, 0, 1, 1, 0], np.uint8), 71)
+    bit_ct = {0: cts[1], 1: cts[0]}
+    bit_ct2 = {0: cts[4], 1: cts[2]}
+    gates2 = [g for g in range(10)] if which == "toy" else [0, 3, 4, 6, 9]
+    for g in gates2:
+        for x, y in pairs:
+            out = o.gate3_ks_first(g, bit_ct[x], bit_ct2[y])
+            assert o.decrypt_big_bits(out)[0] == O.gate_plain(g, x, y), (g, x, y)
+            assert abs(abs(int(centered(o.phase_big(out))[0])) - E8) < (1 << 27)
+    triples = [(x, y, z) for x in (0, 1) for y in (0, 1) for z in (0, 1)]
+    if which == "real":
+        triples = triples[::3]
+    third = {0: o.encrypt_big_bits(np.array([0], np.uint8), 72)[0], 1: o.encrypt_big_bits(np.array([1], np.uint8), 72, 1)[0]}
+    for g in (O.GATES["MAJNYY"], O.GATES["XOR3"], O.GATES["MAJ"]):
+        for x, y, z in triples:
+            out = o.gate3_ks_first(g, bit_ct[x], bit_ct2[y], third[z])
+            assert o.decrypt_big_bits(out)[0] == O.gate_plain3(g, x, y, z), (g, x, y, z)
+
+
+def test_ks_first_identity_gate_is_bootstrap_of_keyswitch(real_oracle):
+    """AND with a noiseless trivial true input is the identity on the linear
+    combination, so the keyswitch-first gate must equal keyswitch, blind
+    rotation and extraction of the input itself."""
+    o = real_oracle
+    x = o.encrypt_big_bits(np.array([1, 0], np.uint8), 73)
+    T = np.zeros(o.N + 1, np.uint32)
+    T[o.N] = E8
+    for k in range(2):
+        got = o.gate3_ks_first(O.GATES["AND"], x[k], T)
+        want = o.sample_extract(o.blind_rotate(o.keyswitch(x[k])))
+        assert np.array_equal(got, want)
+
+
+@pytest.mark.parametrize("pred", [O.P_EQ, O.P_RANGE_MAJ])
+def test_scan_ks_first_toy_matches_plaintext_sql(pred, toy_oracle):
+    o = toy_oracle
+    rng = np.random.default_rng(300 + pred)
+    w, rows = 4, 12
+    c = rng.integers(0, 16, rows)
+    pay = rng.integers(0, 16, rows)
+    if pred == O.P_RANGE_MAJ:
+        lo, hi = 3, 11
+        kbits = [(lo >> i) & 1 for i in range(w)] + [(hi >> i) & 1 for i in range(w)]
+    else:
+        k = int(c[3])
+        kbits = [(k >> i) & 1 for i in range(w)]
+    col = o.encrypt_big_bits(np.array([(v >> i) & 1 for v in c for i in range(w)], np.uint8), 5)
+    pct = o.encrypt_big_bits(np.array([(v >> i) & 1 for v in pay for i in range(w)], np.uint8), 6)
+    kct = o.encrypt_big_bits(np.array(kbits, np.uint8), 7)
+    match, (outp,) = o.scan_ks_first(pred, w, col, kct, [pct], w)
+    mbits = o.decrypt_big_bits(match)
+    obits = o.decrypt_big_bits(outp.reshape(-1, o.N + 1)).reshape(rows, w)
+    for r in range(rows):
+        want = (lo <= c[r] < hi) if pred == O.P_RANGE_MAJ else c[r] == k
+        assert mbits[r] == int(want)
+        assert int(sum(int(obits[r, i]) << i for i in range(w))) == (int(pay[r]) if want else 0)
