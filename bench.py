@@ -41,7 +41,7 @@ def parse():
     ap.add_argument("--workload", default="eq32x4096",
                     choices=["eq32x4096", "eq4x16", "range16x65536", "range16x65536maj", "lt8x64", "lt8x64maj", "range4x16",
                              "range4x16maj", "eq32x4096plain", "range16x65536plain", "eq4x16plain", "eq32x4096sum",
-                             "eq32x4096plainsum", "gates",
+                             "eq32x4096plainsum", "eq32x4096ksfirst", "gates",
                              "serving"])
     ap.add_argument("--queries", type=int, default=16, help="queries per serving phase")
     ap.add_argument("--batch", type=int, default=65536, help="gates per step of the gate microbenchmark")
@@ -183,6 +183,8 @@ def gates_per_row(table) -> int:
 
 
 def oracle_scan(o, table, col, cst, pays):
+    if table.ks_first:
+        return o.scan_ks_first(table.pred, table.width, col, cst, pays, table.payload_width)
     if table.plain:
         return o.scan_plain(table.pred, table.width, col, table.consts, pays, table.payload_width)
     return o.scan(table.pred, table.width, col, cst, pays, table.payload_width)
@@ -200,10 +202,11 @@ def oracle_rate(table, seed: int, rows: int):
     o = O.Oracle(seed)
     idx = list(range(rows))
     w, pw = table.width, table.payload_width
-    col = np.concatenate([o.encrypt_bits(table.column_bits().reshape(table.rows, w)[r], WL.STREAM_COLUMN, r * w)
+    enc = o.encrypt_big_bits if table.ks_first else o.encrypt_bits
+    col = np.concatenate([enc(table.column_bits().reshape(table.rows, w)[r], WL.STREAM_COLUMN, r * w)
                           for r in idx])
-    cst = o.encrypt_bits(table.const_bits(), WL.STREAM_CONST, 0)
-    pays = [np.concatenate([o.encrypt_bits(table.payload_bits(q).reshape(table.rows, pw)[r], WL.STREAM_PAYLOAD,
+    cst = enc(table.const_bits(), WL.STREAM_CONST, 0)
+    pays = [np.concatenate([enc(table.payload_bits(q).reshape(table.rows, pw)[r], WL.STREAM_PAYLOAD,
                                            q * table.rows * pw + r * pw) for r in idx])
             for q in range(len(table.payloads))]
     t0 = time.perf_counter()
@@ -233,10 +236,11 @@ def verify_rows_with_oracle(table, seed, k, match, outs):
             break
     rows = sorted(rows)
     w, pw = table.width, table.payload_width
-    col = np.concatenate([o.encrypt_bits(table.column_bits().reshape(table.rows, w)[r], WL.STREAM_COLUMN, r * w)
+    enc = o.encrypt_big_bits if table.ks_first else o.encrypt_bits
+    col = np.concatenate([enc(table.column_bits().reshape(table.rows, w)[r], WL.STREAM_COLUMN, r * w)
                           for r in rows])
-    cst = o.encrypt_bits(table.const_bits(), WL.STREAM_CONST, 0)
-    pays = [np.concatenate([o.encrypt_bits(table.payload_bits(q).reshape(table.rows, pw)[r], WL.STREAM_PAYLOAD,
+    cst = enc(table.const_bits(), WL.STREAM_CONST, 0)
+    pays = [np.concatenate([enc(table.payload_bits(q).reshape(table.rows, pw)[r], WL.STREAM_PAYLOAD,
                                            q * table.rows * pw + r * pw) for r in rows])
             for q in range(len(table.payloads))]
     t0 = time.perf_counter()
@@ -594,7 +598,13 @@ def run_ours(args, dist):
     ctx = F.Context(args.seed, device=dev, engine=args.engine)
     t = WL.table(args.workload, seed=args.seed, rows=args.rows)
     col, cst, pays = WL.encrypt_table(ctx, t)
-    W = ctx.words
+    W = ctx.big_words if t.ks_first else ctx.words
+    dec_bits = ctx.decrypt_big_bits if t.ks_first else ctx.decrypt_bits
+
+    def dec_uint(ct, width):
+        bits = dec_bits(ct.reshape(-1, W)).reshape(-1, width).astype(np.uint64)
+        return (bits << np.arange(width, dtype=np.uint64)).sum(axis=1)
+
     dcol = torch.from_numpy(col.view(np.int32)).to(f"cuda:{dev}")
     dcst = torch.from_numpy(cst.view(np.int32)).to(f"cuda:{dev}")
     dpay = [torch.from_numpy(p.view(np.int32)).to(f"cuda:{dev}") for p in pays]
@@ -609,6 +619,9 @@ def run_ours(args, dist):
         if t.plain:
             ctx.scan_select_plain(dcol, t.rows, t.width, t.pred, t.consts, dpay, t.payload_width, match, outs,
                                   stream=st)
+        elif t.ks_first:
+            ctx.scan_select_ks_first(dcol, t.rows, t.width, t.pred, dcst, dpay, t.payload_width, match, outs,
+                                     stream=st)
         else:
             ctx.scan_select(dcol, t.rows, t.width, t.pred, dcst, dpay, t.payload_width, match, outs, stream=st)
         for o_, s_ in zip(outs, sums):
@@ -642,12 +655,12 @@ def run_ours(args, dist):
 
     # ---- correctness of the timed outputs (plaintext answer)
     m_want, p_want = t.expected()
-    got_m = ctx.decrypt_bits(match.cpu().numpy().view(np.uint32))
+    got_m = dec_bits(match.cpu().numpy().view(np.uint32))
     correct = bool(np.array_equal(got_m, m_want))
     for q, o_ in enumerate(outs):
-        correct &= bool(np.array_equal(ctx.decrypt_uint(o_.cpu().numpy().view(np.uint32), t.payload_width), p_want[q]))
+        correct &= bool(np.array_equal(dec_uint(o_.cpu().numpy().view(np.uint32), t.payload_width), p_want[q]))
     for q, s_ in enumerate(sums):
-        bits = ctx.decrypt_bits(s_.cpu().numpy().view(np.uint32))
+        bits = dec_bits(s_.cpu().numpy().view(np.uint32))
         got_sum = sum(int(b) << j for j, b in enumerate(bits))
         correct &= got_sum == int(p_want[q].astype(object).sum()) % (1 << t.sum_width)
 
@@ -668,7 +681,7 @@ def run_ours(args, dist):
         hsums = [torch.zeros((t.sum_width, W), dtype=torch.int32).pin_memory() for _ in sums]
 
         def e2e_step():
-            if t.plain or t.aggregate:  # pinned host -> device, the step, device -> host, on the launch stream
+            if t.plain or t.aggregate or t.ks_first:  # pinned host -> device, the step, device -> host
                 dcol.copy_(hcol, non_blocking=True)
                 if not t.plain:
                     dcst.copy_(hcst, non_blocking=True)
@@ -697,7 +710,7 @@ def run_ours(args, dist):
         e2e_ms = dist.max(f0.elapsed_time(f1))
         e2e = {"value": dist.world * gates_per_step * args.e2e_steps / (e2e_ms / 1e3), "unit": "gate bootstraps/s",
                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
-        correct &= bool(np.array_equal(ctx.decrypt_bits(hmatch.numpy().view(np.uint32)), m_want))
+        correct &= bool(np.array_equal(dec_bits(hmatch.numpy().view(np.uint32)), m_want))
 
     # ---- oracle recomputation of sampled rows of the timed scan
     verified = None
@@ -712,8 +725,8 @@ def run_ours(args, dist):
         s_dcol = torch.from_numpy(scol.view(np.int32)).cuda()
         s_dcst = torch.from_numpy(scst.view(np.int32)).cuda()
         s_dpay = [torch.from_numpy(p.view(np.int32)).cuda() for p in spay]
-        s_match = torch.zeros((ts.rows, W), dtype=torch.int32, device="cuda")
-        s_outs = [torch.zeros((ts.rows, ts.payload_width, W), dtype=torch.int32, device="cuda") for _ in spay]
+        s_match = torch.zeros((ts.rows, ctx.words), dtype=torch.int32, device="cuda")
+        s_outs = [torch.zeros((ts.rows, ts.payload_width, ctx.words), dtype=torch.int32, device="cuda") for _ in spay]
         res = {}
         for mode in ("batched", "per_gate"):
             run = lambda: ctx.scan_select(s_dcol, ts.rows, ts.width, ts.pred, s_dcst, s_dpay, ts.payload_width,
@@ -745,6 +758,7 @@ def run_ours(args, dist):
         "rows_per_s": dist.world * t.rows * args.steps / (ms / 1e3),
         "config": {"workload": args.workload, "rows": t.rows, "width": t.width, "pred": t.pred,
                    "constants": "plaintext" if t.plain else "encrypted",
+                   "order": "keyswitch first (N+1-word ciphertexts)" if t.ks_first else "keyswitch after bootstrap",
                    "payload_columns": len(t.payloads), "payload_width": t.payload_width,
                    "gates_per_row": gpr, "gate_bootstraps_per_step": gates_per_step,
                    "sum_gate_bootstraps_per_step": sum_gates,

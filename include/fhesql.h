@@ -181,6 +181,15 @@ FSQL_API int fsql_decrypt_bits(const fsql_ctx* ctx, const uint32_t* ct, size_t c
 /* Decrypt [rows][width][n+1] into unsigned values. */
 FSQL_API int fsql_decrypt_uint(const fsql_ctx* ctx, const uint32_t* ct, size_t rows, uint32_t width, uint64_t* out);
 
+/* Keyswitch-first order (the order of TFHE-rs, which the paper uses, §2.2):
+ * ciphertexts of N + 1 words under the N-bit key (the GLWE key read as an
+ * LWE key), fresh ones with the GLWE noise; ciphertext c of a stream draws
+ * words c (N + 2) .. c (N + 2) + N + 1.  Layouts as fsql_encrypt_bits /
+ * fsql_decrypt_bits with N + 1 words per ciphertext. */
+FSQL_API int fsql_encrypt_big_bits(const fsql_ctx* ctx, const uint8_t* bits, size_t count, uint64_t stream,
+                                   uint64_t first_index, uint32_t* out);
+FSQL_API int fsql_decrypt_big_bits(const fsql_ctx* ctx, const uint32_t* ct, size_t count, uint8_t* out);
+
 /* ---------------- server side (device memory, asynchronous on `stream`) ---------------- */
 
 /* Gate bootstraps of `count` independent gates: out[g] = gate types[g] of
@@ -317,6 +326,22 @@ FSQL_API int fsql_extreme_plan_info(int is_min, size_t rows, uint32_t width, uin
 /* Gate count and level count of the SUM circuit for (rows, width, out_width). */
 FSQL_API int fsql_sum_plan_info(size_t rows, uint32_t width, uint32_t out_width, uint32_t* gates, uint32_t* levels,
                                 uint32_t* literal_outputs);
+
+/* Gates and scans in keyswitch-first order: every input and output is
+ * N + 1 words under the N-bit key.  A gate forms its linear combination on
+ * N + 1 words, keyswitches that one result to the n-bit key (the keyswitch
+ * before the bootstrap instead of after it), bootstraps it and writes the
+ * extracted sample.  Trades larger ciphertexts (4100 B instead of 2524 B per
+ * bit) for keyswitching once per gate of the combination rather than once
+ * per stored output.  Arguments otherwise as fsql_gate_batch and
+ * fsql_scan_select (encrypted constants; d_const [width or 2 width][N+1]). */
+FSQL_API int fsql_gate_batch_ks_first(fsql_ctx* ctx, const uint8_t* d_types, const uint32_t* d_a,
+                                      const uint32_t* d_b, uint32_t* d_out, size_t count, void* stream);
+FSQL_API int fsql_scan_select_ks_first(fsql_ctx* ctx, const uint32_t* d_column, size_t rows, uint32_t width,
+                                       uint32_t pred, const uint32_t* d_const, uint32_t n_payloads,
+                                       const uint32_t* const* d_payloads, uint32_t payload_width,
+                                       uint32_t* d_match, uint32_t* const* d_out_payloads, int per_gate,
+                                       void* stream);
 
 /* The same scan from host buffers (layouts as above, h_payloads / h_out_payloads
  * are arrays of host pointers): copies inputs to the device, runs the batched

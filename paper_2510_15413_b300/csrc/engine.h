@@ -81,6 +81,12 @@ struct Ctx {
   uint64_t* d_bkhat = nullptr;   // [n][2l][32][32][2] u64, NTT domain, times N^-1
   uint32_t* d_ksk = nullptr;     // [N][t][digits][kKsRowWords]
   uint32_t* d_ks_part = nullptr; // keyswitch partial sums of small batches [16][128][kKsRowWords]
+  // keyswitch-first order: keyswitched samples [cap][n+1], their blind-rotation
+  // descriptors [cap], the trivial true ciphertext [n+1]
+  uint32_t* d_ks_small = nullptr;
+  GateDesc* d_ks_desc = nullptr;
+  uint32_t* d_true = nullptr;
+  size_t ks_small_cap = 0;
   void* d_tables = nullptr;      // NttTablesT of the engine
   std::vector<uint8_t> tables;   // host copy
   size_t key_bytes = 0;

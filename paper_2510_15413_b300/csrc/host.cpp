@@ -639,6 +639,36 @@ int fsql_encrypt_bits(const fsql_ctx* ctx, const uint8_t* bits, size_t count, ui
   });
 }
 
+int fsql_encrypt_big_bits(const fsql_ctx* ctx, const uint8_t* bits, size_t count, uint64_t stream,
+                          uint64_t first_index, uint32_t* out) {
+  return guarded([&]() -> int {
+    if (!ctx || (count && (!bits || !out))) return arg_error("null argument");
+    const Ctx* c = reinterpret_cast<const Ctx*>(ctx);
+    const uint32_t N = c->p.N;
+    const fsql::Stream st(c->seed, stream);
+    fsql::parallel_for(count, [&](size_t k) {
+      fsql::lwe_sample(st, (first_index + k) * (N + 2), c->S.data(), N, fsql::encode_bit(bits[k] != 0),
+                       c->p.glwe_sigma, out + k * (N + 1));
+    });
+    return FSQL_OK;
+  });
+}
+
+int fsql_decrypt_big_bits(const fsql_ctx* ctx, const uint32_t* ct, size_t count, uint8_t* out) {
+  return guarded([&]() -> int {
+    if (!ctx || (count && (!ct || !out))) return arg_error("null argument");
+    const Ctx* c = reinterpret_cast<const Ctx*>(ctx);
+    const uint32_t N = c->p.N;
+    for (size_t k = 0; k < count; ++k) {
+      const uint32_t* row = ct + k * (N + 1);
+      uint32_t dot = 0;
+      for (uint32_t x = 0; x < N; ++x) dot += c->S[x] ? row[x] : 0u;
+      out[k] = static_cast<int32_t>(row[N] - dot) > 0 ? 1 : 0;
+    }
+    return FSQL_OK;
+  });
+}
+
 int fsql_encrypt_uint(const fsql_ctx* ctx, const uint64_t* values, size_t rows, uint32_t width, uint64_t stream,
                       uint64_t first_index, uint32_t* out) {
   return guarded([&]() -> int {

@@ -681,6 +681,93 @@ __global__ void __launch_bounds__(kKsCols)
   }
 }
 
+// Keyswitch-first order (ciphertexts of N + 1 words under the N-bit key):
+// the gate's linear combination is formed on the fly from its N + 1-word
+// inputs while digits are extracted, and the single keyswitched result goes
+// to out_contig[g] (n + 1 words), the blind rotation's input.
+__global__ void __launch_bounds__(kKsCols)
+    keyswitch_lincomb_kernel(const GateDesc* __restrict__ desc, int count, const uint32_t* __restrict__ ksk, int n,
+                             uint32_t* __restrict__ out_contig) {
+  __shared__ uint16_t dig[kKsGates][kN];
+  __shared__ uint32_t tbl[kKsT][4][kKsCols];
+  const int g0 = blockIdx.x * kKsGates;
+  const int ng = min(kKsGates, count - g0);
+  for (int q = threadIdx.x; q < kKsGates * kN; q += kKsCols) {
+    const int g = q / kN, i = q % kN;
+    uint32_t v = 0;
+    if (g < ng) {
+      const GateDesc d = desc[g0 + g];
+      const Lin lin = gate_lin(d.type);
+      v = lin.ca * d.a[i] + lin.cb * d.b[i];
+      if (lin.cc && d.c) v += lin.cc * d.c[i];
+    }
+    dig[g][i] = static_cast<uint16_t>((v + (1u << 15)) >> 16);
+  }
+  const int tc = threadIdx.x;
+#pragma unroll
+  for (int j = 0; j < kKsT; ++j) tbl[j][0][tc] = 0u;
+  __syncthreads();
+  const int col = blockIdx.y * kKsCols + tc;
+  uint32_t acc[kKsGates];
+#pragma unroll
+  for (int g = 0; g < kKsGates; ++g) acc[g] = 0u;
+  const uint32_t* base = ksk + col;
+#pragma unroll 1
+  for (int i = 0; i < kN; ++i) {
+#pragma unroll
+    for (int j = 0; j < kKsT; ++j) {
+      const uint32_t* rows = base + static_cast<size_t>((i * kKsT + j) * kKsDigits) * kKsRowWords;
+      tbl[j][1][tc] = __ldg(rows);
+      tbl[j][2][tc] = __ldg(rows + kKsRowWords);
+      tbl[j][3][tc] = __ldg(rows + 2 * kKsRowWords);
+    }
+#pragma unroll
+    for (int g = 0; g < kKsGates; ++g) {
+      const uint32_t dv = dig[g][i];
+#pragma unroll
+      for (int j = 0; j < kKsT; ++j) acc[g] -= tbl[j][(dv >> (14 - 2 * j)) & 3u][tc];
+    }
+  }
+  if (col > n) return;
+#pragma unroll
+  for (int g = 0; g < kKsGates; ++g) {
+    if (g >= ng) break;
+    uint32_t body = 0u;  // the linear combination's body word
+    if (col == n) {
+      const GateDesc d = desc[g0 + g];
+      const Lin lin = gate_lin(d.type);
+      body = lin.ca * d.a[kN] + lin.cb * d.b[kN] + lin.k;
+      if (lin.cc && d.c) body += lin.cc * d.c[kN];
+    }
+    out_contig[static_cast<size_t>(g0 + g) * (n + 1) + col] = acc[g] + body;
+  }
+}
+
+// Blind-rotation descriptors of the keyswitched samples: AND with the
+// noiseless trivial true (0, .., 0, q/8) is the identity on the linear
+// combination (-q/8 + x + q/8 = x), so the bootstrap sees x unchanged.
+__global__ void identity_desc_kernel(GateDesc* __restrict__ desc, int count, const uint32_t* __restrict__ small,
+                                     const uint32_t* __restrict__ trivial_true, int words) {
+  const int g = blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= count) return;
+  GateDesc d;
+  d.a = small + static_cast<size_t>(g) * words;
+  d.b = trivial_true;
+  d.c = nullptr;
+  d.out = nullptr;
+  d.type = FSQL_AND;
+  d.pad = 0;
+  desc[g] = d;
+}
+
+// Extracted samples (N + 1 words) to the gates' outputs.
+__global__ void copy_out_kernel(const GateDesc* __restrict__ desc, const uint32_t* __restrict__ big, int count) {
+  for (int g = blockIdx.x; g < count; g += gridDim.x) {
+    uint32_t* out = desc[g].out;
+    for (int x = threadIdx.x; x <= kN; x += blockDim.x) out[x] = big[static_cast<size_t>(g) * (kN + 1) + x];
+  }
+}
+
 // Exact negacyclic product through the device NTT (test hook), 128 threads.
 template <class F>
 __global__ void __launch_bounds__(kGroup) ntt_mul_kernel(const int32_t* __restrict__ digits,
@@ -832,6 +919,7 @@ struct Plan {
   std::vector<uint32_t*> outs;
   uint32_t* wires = nullptr;
   bool plain = false;  // plaintext constants k0 (and k1 for RANGE)
+  bool ks_first = false;  // keyswitch-first order: every ciphertext N + 1 words
   uint64_t k0 = 0, k1 = 0;
   // plan
   std::vector<size_t> level_offset;  // descriptors of level L: [level_offset[L], level_offset[L+1])
@@ -977,6 +1065,13 @@ void device_free(Ctx& c) {
   if (c.desc_event) cudaEventDestroy(static_cast<cudaEvent_t>(c.desc_event));
   cudaFree(c.d_ks_part);
   c.d_ks_part = nullptr;
+  cudaFree(c.d_ks_small);
+  cudaFree(c.d_ks_desc);
+  cudaFree(c.d_true);
+  c.d_ks_small = nullptr;
+  c.d_ks_desc = nullptr;
+  c.d_true = nullptr;
+  c.ks_small_cap = 0;
   cudaFree(c.d_lits);
   c.d_lits = nullptr;
   c.lits_cap = 0;
@@ -1140,6 +1235,63 @@ int launch_gates(Ctx& c, const GateDesc* d_desc, size_t count, uint32_t* d_big, 
   return FSQL_OK;
 }
 
+// Scratch of the keyswitch-first order for up to `count` gates per launch:
+// the keyswitched samples, their blind-rotation descriptors (built once for
+// the whole capacity) and the trivial true ciphertext.
+static int ensure_ks_first(Ctx& c, size_t count) {
+  if (count <= c.ks_small_cap) return FSQL_OK;
+  cudaFree(c.d_ks_small);
+  cudaFree(c.d_ks_desc);
+  c.d_ks_small = nullptr;
+  c.d_ks_desc = nullptr;
+  c.ks_small_cap = 0;
+  const size_t words = c.p.n + 1;
+  CK(cudaMalloc(&c.d_ks_small, count * words * 4));
+  CK(cudaMalloc(&c.d_ks_desc, count * sizeof(GateDesc)));
+  if (!c.d_true) {
+    CK(cudaMalloc(&c.d_true, words * 4));
+    std::vector<uint32_t> t(words, 0u);
+    t[words - 1] = 1u << 29;
+    CK(cudaMemcpy(c.d_true, t.data(), words * 4, cudaMemcpyHostToDevice));
+  }
+  identity_desc_kernel<<<static_cast<unsigned>((count + 255) / 256), 256>>>(c.d_ks_desc, static_cast<int>(count),
+                                                                            c.d_ks_small, c.d_true,
+                                                                            static_cast<int>(words));
+  CK(cudaGetLastError());
+  CK(cudaDeviceSynchronize());
+  c.ks_small_cap = count;
+  return FSQL_OK;
+}
+
+// Gates in keyswitch-first order: inputs and outputs N + 1 words.  Per chunk:
+// lincomb + keyswitch, bootstrap of the keyswitched samples, copy of the
+// extracted samples to the outputs.  ensure_ks_first and ensure_big must
+// cover min(count, kMaxChunk) gates.
+int launch_gates_ks_first(Ctx& c, const GateDesc* d_desc, size_t count, uint32_t* d_big, void* stream) {
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  for (size_t off = 0; off < count; off += kMaxChunk) {
+    const size_t cnt = std::min(kMaxChunk, count - off);
+    if (cnt > c.ks_small_cap) {
+      set_error("keyswitch-first scratch too small");
+      return FSQL_ERR_ARG;
+    }
+    {
+      LaunchTimer tm(c, st);
+      keyswitch_lincomb_kernel<<<dim3(static_cast<unsigned>((cnt + kKsGates - 1) / kKsGates), kKsTiles), kKsCols, 0,
+                                 st>>>(d_desc + off, static_cast<int>(cnt), c.d_ksk, static_cast<int>(c.p.n),
+                                       c.d_ks_small);
+      CK(cudaGetLastError());
+      tm.done(false, cnt);
+    }
+    int rc = launch_blind_rotate(c, c.d_ks_desc, cnt, d_big, stream);
+    if (rc) return rc;
+    copy_out_kernel<<<static_cast<unsigned>(std::min<size_t>(cnt, 16 * static_cast<size_t>(c.sm_count))), 256, 0,
+                      st>>>(d_desc + off, d_big, static_cast<int>(cnt));
+    CK(cudaGetLastError());
+  }
+  return FSQL_OK;
+}
+
 }  // namespace fsql
 
 // ------------------------------------------------------------------ no-allocation gate path
@@ -1224,12 +1376,12 @@ int check_types_host(size_t count) { return count > (size_t(1) << 31) ? arg_erro
 int prepare_scan(Ctx& c, const uint32_t* d_column, size_t rows, uint32_t width, uint32_t pred,
                  const uint32_t* d_const, uint32_t n_payloads, const uint32_t* const* d_payloads,
                  uint32_t payload_width, uint32_t* d_match, uint32_t* const* d_out_payloads, void* stream,
-                 bool plain = false, uint64_t k0 = 0, uint64_t k1 = 0) {
+                 bool plain = false, uint64_t k0 = 0, uint64_t k1 = 0, bool ks_first = false) {
   fsql::Netlist nl;
   const bool ok = plain ? fsql::build_netlist_plain(pred, width, n_payloads, payload_width, k0, k1, &nl)
                         : fsql::build_netlist(pred, width, n_payloads, payload_width, &nl);
   if (!ok) return arg_error("bad predicate shape");
-  const size_t W = c.p.n + 1;
+  const size_t W = ks_first ? static_cast<size_t>(c.p.N) + 1 : c.p.n + 1;
   const int G = static_cast<int>(nl.type.size());
   const long n_int = fsql::scan_internal_wires(nl);
   const size_t wire_words = rows * static_cast<size_t>(n_int) * W;
@@ -1249,7 +1401,7 @@ int prepare_scan(Ctx& c, const uint32_t* d_column, size_t rows, uint32_t width, 
   fsql::Plan* pl = c.plan;
   bool same = pl && pl->column == d_column && pl->rows == rows && pl->width == width && pl->pred == pred &&
               pl->n_payloads == n_payloads && pl->payload_width == payload_width && pl->cst == d_const &&
-              pl->match == d_match && pl->wires == c.d_wires && pl->plain == plain && pl->k0 == k0 && pl->k1 == k1;
+              pl->match == d_match && pl->wires == c.d_wires && pl->plain == plain && pl->k0 == k0 && pl->k1 == k1 && pl->ks_first == ks_first;
   for (uint32_t q = 0; same && q < n_payloads; ++q)
     same = pl->payloads[q] == d_payloads[q] && pl->outs[q] == d_out_payloads[q];
   if (same) return FSQL_OK;
@@ -1271,6 +1423,7 @@ int prepare_scan(Ctx& c, const uint32_t* d_column, size_t rows, uint32_t width, 
   pl->plain = plain;
   pl->k0 = k0;
   pl->k1 = k1;
+  pl->ks_first = ks_first;
 
   const size_t total = rows * static_cast<size_t>(G);
   if (total > c.h_desc_cap) {
@@ -1450,19 +1603,24 @@ int execute_plan(Ctx* c, fsql::Plan& pl, const fsql::GateDesc* d_desc, const fsq
   size_t widest = 0;
   for (size_t L = 0; L + 1 < pl.level_offset.size(); ++L)
     widest = std::max(widest, pl.level_offset[L + 1] - pl.level_offset[L]);
-  int rc = fsql::ensure_big(*c, per_gate ? 1 : std::min(widest, fsql::kMaxChunk));
+  const size_t chunk = per_gate ? 1 : std::min(widest, fsql::kMaxChunk);
+  int rc = fsql::ensure_big(*c, chunk);
+  if (!rc && pl.ks_first) rc = fsql::ensure_ks_first(*c, chunk);
   if (rc) return rc;
+  auto gates = [&](const fsql::GateDesc* dd, size_t cnt, void* st) -> int {
+    return pl.ks_first ? fsql::launch_gates_ks_first(*c, dd, cnt, c->d_big, st)
+                       : fsql::launch_gates(*c, dd, cnt, c->d_big, st);
+  };
   if (per_gate) {
     for (size_t g = 0; g < pl.total; ++g) {
-      rc = fsql::launch_gates(*c, d_desc + g, 1, c->d_big, stream);
+      rc = gates(d_desc + g, 1, stream);
       if (rc) return rc;
     }
     return fsql::launch_literals(d_lits, pl.n_lits, n, stream);
   }
   auto launch_all = [&](void* st) -> int {
     for (size_t L = 0; L + 1 < pl.level_offset.size(); ++L) {
-      const int r = fsql::launch_gates(*c, d_desc + pl.level_offset[L],
-                                       pl.level_offset[L + 1] - pl.level_offset[L], c->d_big, st);
+      const int r = gates(d_desc + pl.level_offset[L], pl.level_offset[L + 1] - pl.level_offset[L], st);
       if (r) return r;
     }
     return fsql::launch_literals(d_lits, pl.n_lits, n, st);
@@ -1627,6 +1785,45 @@ int fsql_aggregate_min(fsql_ctx* ctx, const uint32_t* d_values, const uint32_t* 
   int rc = prepare_aggregate(*c, kAggMin, d_values, d_match, rows, width, width, d_out, stream);
   if (rc) return rc;
   return execute_plan(c, *c->agg_plan, c->agg_plan->own_desc, c->agg_plan->own_lits, 0, stream);
+}
+
+int fsql_scan_select_ks_first(fsql_ctx* ctx, const uint32_t* d_column, size_t rows, uint32_t width, uint32_t pred,
+                              const uint32_t* d_const, uint32_t n_payloads, const uint32_t* const* d_payloads,
+                              uint32_t payload_width, uint32_t* d_match, uint32_t* const* d_out_payloads,
+                              int per_gate, void* stream) {
+  Ctx* c = device_ctx(ctx);
+  if (!c) return FSQL_ERR_ARG;
+  if (int rc = validate_scan(c, d_column, rows, width, pred, d_const, n_payloads, d_payloads, payload_width,
+                             d_match, d_out_payloads))
+    return rc;
+  if (rows == 0) return FSQL_OK;
+  std::lock_guard<std::mutex> lk(c->mu);
+  int rc = prepare_scan(*c, d_column, rows, width, pred, d_const, n_payloads, d_payloads, payload_width, d_match,
+                        d_out_payloads, stream, false, 0, 0, true);
+  if (rc) return rc;
+  return execute_plan(c, *c->plan, c->d_desc, c->d_lits, per_gate, stream);
+}
+
+int fsql_gate_batch_ks_first(fsql_ctx* ctx, const uint8_t* d_types, const uint32_t* d_a, const uint32_t* d_b,
+                             uint32_t* d_out, size_t count, void* stream) {
+  Ctx* c = device_ctx(ctx);
+  if (!c) return FSQL_ERR_ARG;
+  if (count == 0) return FSQL_OK;
+  if (!d_types || !d_a || !d_b || !d_out) return arg_error("null device pointer");
+  if (int rc = check_types_host(count)) return rc;
+  std::lock_guard<std::mutex> lk(c->mu);
+  const size_t chunk = std::min(count, fsql::kMaxChunk);
+  int rc = fsql::ensure_desc(*c, count);
+  if (!rc) rc = fsql::ensure_big(*c, chunk);
+  if (!rc) rc = fsql::ensure_ks_first(*c, chunk);
+  if (rc) return rc;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  fsql::make_desc_kernel<<<static_cast<unsigned>((count + 255) / 256), 256, 0, st>>>(
+      c->d_desc, d_types, d_a, d_b, d_out, static_cast<int>(count), static_cast<int>(c->p.N + 1));
+  if (cudaGetLastError() != cudaSuccess) return arg_error("descriptor kernel launch failed");
+  delete c->plan;  // descriptors overwritten
+  c->plan = nullptr;
+  return fsql::launch_gates_ks_first(*c, c->d_desc, count, c->d_big, stream);
 }
 
 int fsql_scan_select_plain(fsql_ctx* ctx, const uint32_t* d_column, size_t rows, uint32_t width, uint32_t pred,

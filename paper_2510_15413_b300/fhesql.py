@@ -29,6 +29,7 @@ API = ["fsql_params_default", "fsql_params_toy", "fsql_ctx_create", "fsql_ctx_cr
        "fsql_phase", "fsql_decrypt_bits", "fsql_decrypt_uint", "fsql_gate_batch", "fsql_blind_rotate_extract",
        "fsql_keyswitch", "fsql_debug_ntt_mul", "fsql_plan_info", "fsql_scan_select", "fsql_scan_select_host",
        "fsql_scan_select_plain", "fsql_plan_info_plain", "fsql_aggregate_sum", "fsql_sum_plan_info",
+       "fsql_encrypt_big_bits", "fsql_decrypt_big_bits", "fsql_gate_batch_ks_first", "fsql_scan_select_ks_first",
        "fsql_aggregate_max", "fsql_aggregate_min", "fsql_extreme_plan_info",
        "fsql_profile_begin", "fsql_profile_end", "fsql_gate_batch_noalloc", "fsql_server_create",
        "fsql_server_submit", "fsql_server_status", "fsql_server_wait", "fsql_server_cancel",
@@ -109,6 +110,10 @@ def load() -> C.CDLL:
         "fsql_scan_select_host": (i32, [vp, vp, sz, u32, u32, vp, u32, vp, u32, vp, vp, vp]),
         "fsql_scan_select_plain": (i32, [vp, vp, sz, u32, u32, vp, u32, vp, u32, vp, vp, i32, vp]),
         "fsql_aggregate_sum": (i32, [vp, vp, sz, u32, u32, vp, vp]),
+        "fsql_encrypt_big_bits": (i32, [vp, vp, sz, u64, u64, vp]),
+        "fsql_decrypt_big_bits": (i32, [vp, vp, sz, vp]),
+        "fsql_gate_batch_ks_first": (i32, [vp, vp, vp, vp, vp, sz, vp]),
+        "fsql_scan_select_ks_first": (i32, [vp, vp, sz, u32, u32, vp, u32, vp, u32, vp, vp, i32, vp]),
         "fsql_aggregate_max": (i32, [vp, vp, sz, u32, vp, vp]),
         "fsql_aggregate_min": (i32, [vp, vp, vp, sz, u32, vp, vp]),
         "fsql_extreme_plan_info": (i32, [i32, sz, u32, C.POINTER(u32), C.POINTER(u32)]),
@@ -351,6 +356,37 @@ class Context:
         pout = (C.c_void_p * max(1, k))(*[_ptr(p) for p in out_payloads])
         _check(load().fsql_scan_select(self._h, _ptr(column), rows, width, pred, _ptr(const), k, pin,
                                        payload_width, _ptr(match), pout, int(bool(per_gate)), _stream(stream)))
+
+    # ---- keyswitch-first order: ciphertexts of N + 1 words under the N-bit key
+    @property
+    def big_words(self) -> int:
+        return int(self.params.N) + 1
+
+    def encrypt_big_bits(self, bits, stream: int, first_index: int = 0) -> np.ndarray:
+        bits = np.ascontiguousarray(bits, dtype=np.uint8).ravel()
+        out = np.zeros((bits.size, self.big_words), np.uint32)
+        _check(load().fsql_encrypt_big_bits(self._h, bits.ctypes.data, bits.size, stream, first_index,
+                                            out.ctypes.data))
+        return out
+
+    def decrypt_big_bits(self, ct) -> np.ndarray:
+        ct = np.ascontiguousarray(ct, dtype=np.uint32).reshape(-1, self.big_words)
+        out = np.zeros(ct.shape[0], np.uint8)
+        _check(load().fsql_decrypt_big_bits(self._h, ct.ctypes.data, ct.shape[0], out.ctypes.data))
+        return out
+
+    def gate_batch_ks_first(self, types, a, b, out, stream=None) -> None:
+        _check(load().fsql_gate_batch_ks_first(self._h, _ptr(types), _ptr(a), _ptr(b), _ptr(out), _count(types),
+                                               _stream(stream)))
+
+    def scan_select_ks_first(self, column, rows: int, width: int, pred: int, const, payloads, payload_width: int,
+                             match, out_payloads, per_gate: bool = False, stream=None) -> None:
+        k = len(payloads)
+        pin = (C.c_void_p * max(1, k))(*[_ptr(p) for p in payloads])
+        pout = (C.c_void_p * max(1, k))(*[_ptr(p) for p in out_payloads])
+        _check(load().fsql_scan_select_ks_first(self._h, _ptr(column), rows, width, pred, _ptr(const), k, pin,
+                                                payload_width, _ptr(match), pout, int(bool(per_gate)),
+                                                _stream(stream)))
 
     def aggregate_sum(self, values, rows: int, width: int, out_width: int, out, stream=None) -> None:
         """fsql_aggregate_sum: values [rows, width, n+1] -> out [out_width, n+1], sum mod 2^out_width."""

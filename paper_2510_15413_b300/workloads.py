@@ -12,6 +12,7 @@ generators stand in for them with the shapes of the benchmark workloads:
   <name>maj     the same table with the majority-chain comparator
   <name>plain   the same table with the query constants given as plaintexts
   <name>sum     the same scan followed by the SUM of each masked payload column
+  <name>ksfirst the same scan in keyswitch-first order (N + 1-word ciphertexts)
   gates(B)      B independent gates: random bit pairs, gate type uniform in
                 {NAND, AND, OR, XOR, XNOR}
 
@@ -43,6 +44,7 @@ class Table:
     consts: tuple = ()                 # (k,) or (lo, hi)
     plain: bool = False                # constants given to the server as plaintexts
     aggregate: bool = False            # SUM of each masked payload column after the scan
+    ks_first: bool = False             # keyswitch-first order: ciphertexts under the N-bit key
 
     @property
     def sum_width(self) -> int:
@@ -95,6 +97,11 @@ def table(name: str, seed: int = 1, rows: int | None = None) -> Table:
     majority-chain comparator (LT_MAJ / RANGE_MAJ) instead of the ripple one,
     the suffix "plain" the same table with plaintext query constants, the
     suffix "sum" the same scan followed by a SUM of its masked payloads."""
+    if name.endswith("ksfirst"):
+        t = table(name[:-7], seed, rows)
+        t.ks_first = True
+        t.name = name
+        return t
     if name.endswith("sum"):
         t = table(name[:-3], seed, rows)
         t.aggregate = True
@@ -177,9 +184,10 @@ def gates(batch: int, seed: int = 1):
 
 def encrypt_table(enc, t: Table):
     """Encrypt a table with any object exposing encrypt_bits(bits, stream, first_index)
-    (the library context or the oracle) -> (column, const, [payloads])."""
-    col = enc.encrypt_bits(t.column_bits(), STREAM_COLUMN, 0)
-    cst = enc.encrypt_bits(t.const_bits(), STREAM_CONST, 0)
-    pays = [enc.encrypt_bits(t.payload_bits(q), STREAM_PAYLOAD, q * t.rows * t.payload_width)
-            for q in range(len(t.payloads))]
+    (the library context or the oracle) -> (column, const, [payloads]); a
+    keyswitch-first table uses encrypt_big_bits (N + 1-word ciphertexts)."""
+    fn = enc.encrypt_big_bits if t.ks_first else enc.encrypt_bits
+    col = fn(t.column_bits(), STREAM_COLUMN, 0)
+    cst = fn(t.const_bits(), STREAM_CONST, 0)
+    pays = [fn(t.payload_bits(q), STREAM_PAYLOAD, q * t.rows * t.payload_width) for q in range(len(t.payloads))]
     return col, cst, pays

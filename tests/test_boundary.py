@@ -198,3 +198,16 @@ def test_extreme_circuits_equal_oracle_circuits(is_min, rows, width):
         depth.append(1 + max(depth[a[k]], depth[b[k]], depth[c[k]] if c[k] >= 0 else 0))
     levels = max(depth[ninp:]) if t.size else 0
     assert F.extreme_plan_info(is_min, rows, width) == (int(t.size), levels)
+
+
+def test_big_key_encryption_equals_oracle():
+    """Keyswitch-first ciphertexts (N + 1 words under the N-bit key): the
+    library's encryption equals the oracle's word for word and decrypts."""
+    ctx = F.Context(11, device=-1)
+    o = O.Oracle(11)
+    bits = np.random.default_rng(8).integers(0, 2, 64).astype(np.uint8)
+    a = ctx.encrypt_big_bits(bits, 5, 7)
+    assert a.shape == (64, 1025)
+    assert np.array_equal(a, o.encrypt_big_bits(bits, 5, 7))
+    assert np.array_equal(ctx.decrypt_big_bits(a), bits)
+    assert np.array_equal(o.decrypt_big_bits(a), bits)

@@ -300,6 +300,91 @@ def test_latency_mode_equals_group_mode_and_oracle(env):
         assert np.array_equal(res[0][:k], o.gate_batch(types[:k].astype(np.int32), a[:k], b[:k]))
 
 
+# ---------------------------------------------------------------- keyswitch-first order
+def encrypt_table_big(enc, t):
+    """WL.encrypt_table with N + 1-word ciphertexts under the N-bit key."""
+    col = enc.encrypt_big_bits(t.column_bits(), WL.STREAM_COLUMN, 0)
+    cst = enc.encrypt_big_bits(t.const_bits(), WL.STREAM_CONST, 0)
+    pays = [enc.encrypt_big_bits(t.payload_bits(q), WL.STREAM_PAYLOAD, q * t.rows * t.payload_width)
+            for q in range(len(t.payloads))]
+    return col, cst, pays
+
+
+def test_ks_first_gates_bit_exact(env):
+    ctx, o = env
+    rng = np.random.default_rng(23)
+    count = 40  # all ten two-input types, four times
+    types = (np.arange(count) % 10).astype(np.uint8)
+    xb, yb = rng.integers(0, 2, count).astype(np.uint8), rng.integers(0, 2, count).astype(np.uint8)
+    x, y = ctx.encrypt_big_bits(xb, 74), ctx.encrypt_big_bits(yb, 75)
+    assert np.array_equal(x, o.encrypt_big_bits(xb, 74))
+    out = torch.zeros((count, ctx.big_words), dtype=torch.int32, device="cuda")
+    ctx.gate_batch_ks_first(dev(types), dev(x.view(np.int32)), dev(y.view(np.int32)), out)
+    got = host(out).view(np.uint32)
+    for g in range(0, count, 7):
+        assert np.array_equal(got[g], o.gate3_ks_first(int(types[g]), x[g], y[g])), g
+    truth = np.array([O.gate_plain(int(t), int(a), int(b)) for t, a, b in zip(types, xb, yb)], np.uint8)
+    assert np.array_equal(ctx.decrypt_big_bits(got), truth)
+
+
+@pytest.mark.parametrize("name,rows", [("eq4x16", 6), ("range4x16maj", 5), ("lt8x64", 3)])
+def test_ks_first_scan_bit_exact(env, name, rows):
+    ctx, o = env
+    t = WL.table(name, seed=8, rows=rows)
+    col, cst, pays = encrypt_table_big(ctx, t)
+    ocol, ocst, opays = encrypt_table_big(o, t)
+    assert np.array_equal(col, ocol) and np.array_equal(cst, ocst)
+    W = ctx.big_words
+    match = torch.zeros((t.rows, W), dtype=torch.int32, device="cuda")
+    outs = [torch.zeros((t.rows, t.payload_width, W), dtype=torch.int32, device="cuda") for _ in pays]
+    ctx.scan_select_ks_first(dev(col.view(np.int32)), t.rows, t.width, t.pred, dev(cst.view(np.int32)),
+                             [dev(p.view(np.int32)) for p in pays], t.payload_width, match, outs)
+    om, oouts = o.scan_ks_first(t.pred, t.width, ocol, ocst, opays, t.payload_width)
+    assert np.array_equal(host(match).view(np.uint32), om)
+    for a, b in zip(outs, oouts):
+        assert np.array_equal(host(a).view(np.uint32).reshape(b.shape), b)
+    m_want, (p_want,) = t.expected()
+    assert np.array_equal(ctx.decrypt_big_bits(om), m_want)
+    got_p = ctx.decrypt_big_bits(oouts[0].reshape(-1, W)).reshape(t.rows, t.payload_width)
+    assert np.array_equal((got_p.astype(np.uint64) << np.arange(t.payload_width, dtype=np.uint64)).sum(axis=1), p_want)
+    # one gate per launch gives the same words
+    m2 = torch.zeros_like(match)
+    o2 = [torch.zeros_like(x) for x in outs]
+    ctx.scan_select_ks_first(dev(col.view(np.int32)), t.rows, t.width, t.pred, dev(cst.view(np.int32)),
+                             [dev(p.view(np.int32)) for p in pays], t.payload_width, m2, o2, per_gate=True)
+    assert np.array_equal(host(m2), host(match)) and all(np.array_equal(host(a), host(b)) for a, b in zip(o2, outs))
+
+
+def test_ks_first_scan_eq32x4096_full_size_sampled_rows(env):
+    """The equality workload at full size in keyswitch-first order: every row
+    decrypted against the SQL answer; the matching and last rows recomputed
+    by the oracle word for word (default engine only, for time)."""
+    ctx, o = env
+    if ctx.engine != F.FSQL_ENGINE_DUAL_PRIME:
+        pytest.skip("full-size keyswitch-first scan runs on the default engine")
+    t = WL.table("eq32x4096", seed=1)
+    col, cst, pays = encrypt_table_big(ctx, t)
+    W = ctx.big_words
+    match = torch.zeros((t.rows, W), dtype=torch.int32, device="cuda")
+    outs = [torch.zeros((t.rows, t.payload_width, W), dtype=torch.int32, device="cuda")]
+    ctx.scan_select_ks_first(dev(col.view(np.int32)), t.rows, t.width, t.pred, dev(cst.view(np.int32)),
+                             [dev(pays[0].view(np.int32))], t.payload_width, match, outs)
+    gm, go = host(match).view(np.uint32), host(outs[0]).view(np.uint32)
+    m_want, (p_want,) = t.expected()
+    assert np.array_equal(ctx.decrypt_big_bits(gm), m_want)
+    bits = ctx.decrypt_big_bits(go.reshape(-1, W)).reshape(t.rows, t.payload_width)
+    assert np.array_equal((bits.astype(np.uint64) << np.arange(32, dtype=np.uint64)).sum(axis=1), p_want)
+    rows = sorted({int(np.argmax(m_want)), t.rows - 1})
+    ocol = np.concatenate([o.encrypt_big_bits(t.column_bits().reshape(t.rows, 32)[r], WL.STREAM_COLUMN, r * 32)
+                           for r in rows])
+    opay = np.concatenate([o.encrypt_big_bits(t.payload_bits(0).reshape(t.rows, 32)[r], WL.STREAM_PAYLOAD, r * 32)
+                           for r in rows])
+    ocst = o.encrypt_big_bits(t.const_bits(), WL.STREAM_CONST, 0)
+    om, (oout,) = o.scan_ks_first(t.pred, 32, ocol, ocst, [opay], 32)
+    assert np.array_equal(gm[rows], om)
+    assert np.array_equal(go.reshape(t.rows, 32, W)[rows], oout)
+
+
 # ---------------------------------------------------------------- SUM aggregation
 @pytest.mark.parametrize("rows,width,out_width", [(6, 3, 6), (1, 4, 6), (24, 8, 13), (9, 4, 3)])
 def test_aggregate_sum_bit_exact(env, rows, width, out_width):
