@@ -365,8 +365,9 @@ def run_gates(args, dist):
                        "l2": "inputs %s L2 (%.0f MB)" % ("larger than" if 2 * B * 2524 > 126e6 else "within",
                                                           2 * B * 2524 / 1e6)},
             "correct": correct, "roofline": roof, "cpu_baseline": cpu,
-            "e2e": {"value": dist.world * B * args.e2e_steps / (e2e_ms / 1e3), "unit": "gate bootstraps/s",
-                    "h2d_bytes_per_step": (2 * B * ctx.words * 4 + B), "d2h_bytes_per_step": B * ctx.words * 4},
+            "e2e": ({"value": dist.world * B * args.e2e_steps / (e2e_ms / 1e3), "unit": "gate bootstraps/s",
+                     "h2d_bytes_per_step": (2 * B * ctx.words * 4 + B), "d2h_bytes_per_step": B * ctx.words * 4}
+                    if args.e2e_steps > 0 and e2e_ms > 0 else None),
             "gpu_launches": int(kt["blind_rotate_launches"] + kt["keyswitch_launches"]) + args.steps,
             "clocks": clocks, "peaks": {"kind": peak_kind, "hbm_gbs": peaks.get("hbm_gbs"), "sms": sms}}
     ctx.close()
