@@ -932,6 +932,7 @@ struct Plan {
   const uint32_t* graph_big = nullptr;
   const OutDesc* graph_lits = nullptr;
   int graph_br_gates = 0;  // launch shape: 2 x gates per CTA + latency mode
+  const GateDesc* graph_ks_desc = nullptr;  // keyswitch-first scratch the graph reads
   // aggregation plans (SUM, MAX, MIN): key and the buffers they own
   int agg_kind = -1;
   const uint32_t* agg_in = nullptr;
@@ -1629,7 +1630,8 @@ int execute_plan(Ctx* c, fsql::Plan& pl, const fsql::GateDesc* d_desc, const fsq
   if (prof && prof->recording) return launch_all(stream);  // per-launch events need plain launches
   fsql::Plan& mp = pl;
   if (!mp.graph || mp.graph_desc != d_desc || mp.graph_big != c->d_big || mp.graph_lits != d_lits ||
-      mp.graph_br_gates != 2 * c->br_gates + (c->latency_mode ? 1 : 0)) {
+      mp.graph_br_gates != 2 * c->br_gates + (c->latency_mode ? 1 : 0) ||
+      (pl.ks_first && mp.graph_ks_desc != c->d_ks_desc)) {
     if (mp.graph) cudaGraphExecDestroy(mp.graph);
     mp.graph = nullptr;
     cudaStream_t cs = static_cast<cudaStream_t>(c->capture_stream);
@@ -1657,6 +1659,7 @@ int execute_plan(Ctx* c, fsql::Plan& pl, const fsql::GateDesc* d_desc, const fsq
     mp.graph_big = c->d_big;
     mp.graph_lits = d_lits;
     mp.graph_br_gates = 2 * c->br_gates + (c->latency_mode ? 1 : 0);
+    mp.graph_ks_desc = c->d_ks_desc;
   }
   if (cudaGraphLaunch(mp.graph, static_cast<cudaStream_t>(stream)) != cudaSuccess) {
     fsql::set_error("scan graph launch failed");
