@@ -27,9 +27,11 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-MODMULS_PER_BOOTSTRAP = 630 * (8 * 5120 + 12 * 1024)  # n CMux x (8 NTTs x N/2 log N + 2l*2*N MAC)
-IMAD_PER_CLK_PER_SM = 64   # 32-bit integer multiply-add throughput per SM per clock
-WIDE_MULS_PER_MODMUL = 4   # 64x64 -> 128-bit product from four 32x32 -> 64-bit products
+# Algorithmic modular multiplications of one gate bootstrap: n CMux x (8
+# transforms x N/2 log N butterflies + 2l x 2 x N multiply-accumulate
+# products), one multiplication mod p per item with one transform prime; the
+# two-prime engine does each of them once per prime.
+MODMULS_PER_BOOTSTRAP = 630 * (8 * 5120 + 12 * 1024)
 
 
 def parse():
@@ -53,8 +55,9 @@ def parse():
     ap.add_argument("--cpu-rows", type=int, default=1, help="rows of the workload the oracle times")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-per-gate", action="store_true", help="skip the per-gate-launch baseline")
-    ap.add_argument("--verify-rows", type=int, default=0,
+    ap.add_argument("--verify-rows", type=int, default=2,
                     help="rows of the timed scan the CPU oracle recomputes word for word (first, matching, last...)")
+    ap.add_argument("--no-autotune", action="store_true", help="keep the default launch shape")
     ap.add_argument("--seed", type=int, default=1)
     return ap.parse_args()
 
@@ -182,6 +185,17 @@ def gates_per_row(table) -> int:
     return F.plan_info(table.pred, table.width, npay, table.payload_width)[0]
 
 
+def oracle_gates_per_row(table) -> int:
+    """Gate bootstraps per row from the oracle's own netlist (the reference
+    arm loads nothing of the library)."""
+    from oracle import oracle as O
+
+    npay = len(table.payloads)
+    if table.plain:
+        return int(O.netlist_plain(table.pred, table.width, npay, table.payload_width, table.consts)[0].size)
+    return int(O.netlist3(table.pred, table.width, npay, table.payload_width)[0].size)
+
+
 def oracle_scan(o, table, col, cst, pays):
     if table.ks_first:
         return o.scan_ks_first(table.pred, table.width, col, cst, pays, table.payload_width)
@@ -212,7 +226,7 @@ def oracle_rate(table, seed: int, rows: int):
     t0 = time.perf_counter()
     oracle_scan(o, table, col, cst, pays)
     dt = time.perf_counter() - t0
-    gates = rows * gates_per_row(table)
+    gates = rows * oracle_gates_per_row(table)
     o.close()
     return gates / dt, O.max_threads(), dt, gates
 
@@ -260,14 +274,16 @@ def run_reference(args, dist):
     if dist.rank != 0:
         return
     t = WL.table(args.workload, seed=args.seed, rows=args.rows)
-    rates = []
+    rates, secs = [], []
     for _ in range(args.warmup):
         oracle_rate(t, args.seed, args.cpu_rows)
     for _ in range(args.steps):
         r, threads, dt, gates = oracle_rate(t, args.seed, args.cpu_rows)
         rates.append(r)
+        secs.append(dt)
     value = statistics.median(rates)
-    gpr = gates_per_row(t)
+    dt = statistics.median(secs)
+    gpr = oracle_gates_per_row(t)
     sample = f"{args.cpu_rows} row(s) of {args.workload} = {args.cpu_rows * gpr} gate bootstraps per step"
     line = {"impl": "reference", "metric": "gate bootstraps/s", "value": value, "unit": "gate bootstraps/s",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt,
@@ -295,6 +311,8 @@ def run_gates(args, dist):
     peaks, peak_kind = measured_peaks()
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
     ctx = F.Context(args.seed, device=dev, engine=args.engine)
+    alu = F.measure_alu_peaks(dev)
+    tuned = None if args.no_autotune else ctx.autotune()
     B = args.batch
     types, xb, yb = WL.gates(B, seed=args.seed)
     x = ctx.encrypt_bits(xb, WL.STREAM_GATES, 0)
@@ -326,7 +344,7 @@ def run_gates(args, dist):
     value = dist.world * B * args.steps / (ms / 1e3)
     truth = np.array([[1, 1, 1, 0], [0, 0, 0, 1], [0, 1, 1, 1], [0, 1, 1, 0], [1, 0, 0, 1]], np.uint8)[types, 2 * xb + yb]
     correct = bool(np.array_equal(ctx.decrypt_bits(out.cpu().numpy().view(np.uint32)), truth))
-    roof = roofline_of(kt, ms, sms, peaks, f"gates{B}")
+    roof = roofline_of(kt, ms, sms, peaks, f"gates{B}", alu, ctx.engine, args.steps)
     # end to end: pinned host inputs -> device -> gates -> host, copies timed
     hx, hy, ht = (torch.from_numpy(x.view(np.int32)).pin_memory(), torch.from_numpy(y.view(np.int32)).pin_memory(),
                   torch.from_numpy(types).pin_memory())
@@ -361,6 +379,7 @@ def run_gates(args, dist):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32 (exact integer)",
             "data": "synthetic (seeded random gates, seeded keys)",
             "config": {"workload": f"gates x{B}", "engine": ["goldilocks", "dual_prime"][ctx.engine],
+                       "launch_shape": {"gates_per_cta": ctx.br_gates, "autotune_ms": tuned[1] if tuned else None},
                        "gate_types": "NAND/AND/OR/XOR/XNOR uniform",
                        "l2": "inputs %s L2 (%.0f MB)" % ("larger than" if 2 * B * 2524 > 126e6 else "within",
                                                           2 * B * 2524 / 1e6)},
@@ -390,6 +409,7 @@ def run_gate_sweep(args, dist):
     peaks, peak_kind = measured_peaks()
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
     ctx = F.Context(args.seed, device=dev, engine=args.engine)
+    alu = F.measure_alu_peaks(dev)
     st = torch.cuda.current_stream()
     truth_tab = np.array([[1, 1, 1, 0], [0, 0, 0, 1], [0, 1, 1, 1], [0, 1, 1, 0], [1, 0, 0, 1]], np.uint8)
     sizes = [int(v) for v in args.sweep.split(",") if v]
@@ -429,7 +449,7 @@ def run_gate_sweep(args, dist):
         ok = bool(np.array_equal(ctx.decrypt_bits(out.cpu().numpy().view(np.uint32)),
                                  truth_tab[types, 2 * xb + yb]))
         all_ok &= ok
-        roof = roofline_of(kt, ms, sms, peaks, f"gates{B}")
+        roof = roofline_of(kt, ms, sms, peaks, f"gates{B}", alu, ctx.engine, steps)
         points.append({"batch": B, "gate_bootstraps_per_s": dist.world * B * steps / (ms / 1e3),
                        "ms_per_batch": ms / steps, "steps": steps, "warmup": warm, "correct": ok,
                        "br_ms_per_launch": roof["avg_launch_ms"], "frac": roof["frac"]})
@@ -568,19 +588,40 @@ def measured_traffic(workload: str):
         return None
 
 
-def roofline_of(kt, ms, sms, peaks, workload=None):
+def roofline_of(kt, ms, sms, peaks, workload=None, alu=None, engine=1, steps=1):
+    """Roofline of the blind rotation (the dominant kernel): algorithmic
+    modular multiplications per second over its CUDA-event time, against the
+    measured rate of the engine's butterfly (one modular multiplication each)
+    from the library's in-register microkernel.  Two-prime engine: every
+    algorithmic multiplication is done once per prime, so it counts twice,
+    against the 32-bit Shoup butterfly rate; the one-prime engine counts it
+    once, against the 64-bit-prime butterfly rate (the definition of the
+    per-bootstrap figure)."""
     br_ms = kt["blind_rotate_ms"]
     launches = max(1, kt["blind_rotate_launches"])
-    sm_max_mhz = float(peaks.get("sm_max_mhz", 2032.0))
-    peak = sms * IMAD_PER_CLK_PER_SM * sm_max_mhz * 1e6 / WIDE_MULS_PER_MODMUL / 1e12
-    achieved = MODMULS_PER_BOOTSTRAP * kt["gates"] / (br_ms / 1e3) / 1e12 if br_ms > 0 else 0.0
-    return {"bound": "alu", "kernel": "blind_rotate_kernel", "achieved": achieved, "peak": peak, "unit": "Tmodmul/s",
-            "frac": achieved / peak if peak else None,
-            "traffic": measured_traffic(workload) if workload else None, "traffic_unit": "DRAM bytes per launch",
-            "peak_kind": f"derived: {sms} SMs x {IMAD_PER_CLK_PER_SM} IMAD/clk x {sm_max_mhz:.0f} MHz / "
-                         f"{WIDE_MULS_PER_MODMUL} wide multiplies per modmul",
-            "avg_launch_ms": br_ms / launches, "share_of_step": br_ms / ms if ms else None,
-            "keyswitch_ms": kt["keyswitch_ms"]}
+    per_bootstrap = MODMULS_PER_BOOTSTRAP * (2 if engine == 1 else 1)
+    achieved = per_bootstrap * kt["gates"] / (br_ms / 1e3) / 1e12 if br_ms > 0 else 0.0
+    out = {"bound": "alu", "kernel": "blind_rotate_kernel", "achieved": achieved, "unit": "Tmodmul/s",
+           "modmuls_per_bootstrap": per_bootstrap,
+           "traffic": measured_traffic(workload) if workload else None, "traffic_unit": "DRAM bytes per launch",
+           "avg_launch_ms": br_ms / launches, "share_of_step": br_ms / ms if ms else None,
+           "keyswitch_ms_total": kt["keyswitch_ms"], "keyswitch_ms_per_step": kt["keyswitch_ms"] / max(1, steps)}
+    if alu:
+        peak = (alu["dual_prime_bfly_per_s"] if engine == 1 else alu["goldilocks_bfly_per_s"]) / 1e12
+        out.update({"peak": peak, "frac": achieved / peak if peak else None,
+                    "peak_kind": "measured: in-register %s butterfly rate of this GPU (library microkernel)"
+                                 % ("two-prime Shoup" if engine == 1 else "64-bit-prime"),
+                    "alu_rates_per_s": {k: alu[k] for k in ("imad_per_s", "imad_hi_per_s", "imad_wide_per_s",
+                                                            "dual_prime_bfly_per_s", "goldilocks_bfly_per_s")}})
+        if engine == 1 and br_ms > 0:
+            # the same kernel against the planned single-prime definition:
+            # 33.55 M multiplications mod 2^64 - 2^32 + 1 per bootstrap
+            g_ach = MODMULS_PER_BOOTSTRAP * kt["gates"] / (br_ms / 1e3) / 1e12
+            g_peak = alu["goldilocks_bfly_per_s"] / 1e12
+            out["goldilocks_equivalent"] = {"achieved": g_ach, "peak": g_peak, "frac": g_ach / g_peak}
+    else:
+        out.update({"peak": None, "frac": None, "peak_kind": "unavailable"})
+    return out
 
 
 # ------------------------------------------------------------------ GPU run
@@ -597,6 +638,8 @@ def run_ours(args, dist):
     sms = props.multi_processor_count
 
     ctx = F.Context(args.seed, device=dev, engine=args.engine)
+    alu = F.measure_alu_peaks(dev)
+    tuned = None if args.no_autotune else ctx.autotune()
     t = WL.table(args.workload, seed=args.seed, rows=args.rows)
     col, cst, pays = WL.encrypt_table(ctx, t)
     W = ctx.big_words if t.ks_first else ctx.words
@@ -666,7 +709,7 @@ def run_ours(args, dist):
         correct &= got_sum == int(p_want[q].astype(object).sum()) % (1 << t.sum_width)
 
     # ---- roofline of the dominant kernel (blind rotation)
-    roofline = roofline_of(ktimes, ms, sms, peaks, args.workload)
+    roofline = roofline_of(ktimes, ms, sms, peaks, args.workload, alu, ctx.engine, args.steps)
 
     # ---- end to end through the public C-ABI with host buffers (copies inside the timed region)
     h2d = (col.size + (0 if t.plain else cst.size) + sum(p.size for p in pays)) * 4
@@ -765,6 +808,7 @@ def run_ours(args, dist):
                    "sum_gate_bootstraps_per_step": sum_gates,
                    "params": "n=630 N=1024 Bg=2^7 l=3 ks 4^8 Torus32",
                    "engine": ["goldilocks", "dual_prime"][ctx.engine],
+                   "launch_shape": {"gates_per_cta": ctx.br_gates, "autotune_ms": tuned[1] if tuned else None},
                    "l2": "inputs larger than L2 (%.0f MB column+payload per step)" % (h2d / 1e6),
                    "parallelism": f"replica per GPU x{dist.world}"},
         "correct": correct,

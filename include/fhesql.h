@@ -195,8 +195,9 @@ FSQL_API int fsql_decrypt_big_bits(const fsql_ctx* ctx, const uint32_t* ct, size
 /* Gate bootstraps of `count` independent gates: out[g] = gate types[g] of
  * (a[g], b[g]).  d_types: uint8 [count]; d_a, d_b, d_out: [count][n+1].
  * Steps: linear combination, modulus switch, blind rotation (n CMux external
- * products in the NTT domain over p = 2^64 - 2^32 + 1), sample extraction,
- * keyswitch.  d_out may alias neither input.  Types must be FSQL_NAND ..
+ * products through an exact negacyclic NTT: by default over two primes
+ * below 2^28 with a CRT lift, or over p = 2^64 - 2^32 + 1 with the
+ * Goldilocks engine), sample extraction, keyswitch.  d_out may alias neither input.  Types must be FSQL_NAND ..
  * FSQL_ORYN (a device array is not checked: other values compute ORYN). */
 FSQL_API int fsql_gate_batch(fsql_ctx* ctx, const uint8_t* d_types, const uint32_t* d_a, const uint32_t* d_b,
                     uint32_t* d_out, size_t count, void* stream);
@@ -214,7 +215,10 @@ FSQL_API int fsql_gate_batch(fsql_ctx* ctx, const uint8_t* d_types, const uint32
  * looks up that array's device address (cudaGetSymbolAddress), so make that
  * first call before any stream capture.  All calls on one GPU share the
  * array: calls that can overlap on the GPU (other streams, other contexts on
- * the same device) race and must be ordered by the caller. */
+ * the same device) race and must be ordered by the caller.  Its launches are
+ * timed by fsql_profile_begin/end like fsql_gate_batch's; it always uses the
+ * single-pass keyswitch (small batches of fsql_gate_batch split theirs over
+ * more CTAs for latency; the words are the same). */
 FSQL_API int fsql_gate_batch_noalloc(fsql_ctx* ctx, const uint8_t* d_types, const uint32_t* d_a, const uint32_t* d_b,
                                      uint32_t* d_out, size_t count, void* stream);
 
@@ -431,6 +435,28 @@ typedef struct fsql_kernel_times {
 } fsql_kernel_times;
 FSQL_API int fsql_profile_begin(fsql_ctx* ctx);
 FSQL_API int fsql_profile_end(fsql_ctx* ctx, fsql_kernel_times* out);
+
+/* Integer-ALU rates of this GPU, measured by short in-register
+ * microkernels (no paper counterpart: the denominators of the blind
+ * rotation's roofline).  Rates are operations per second over the whole GPU:
+ * 32-bit multiply-add, high-half multiply-add, widening 32x32+64 multiply-add,
+ * forward butterflies of the two-prime engine (one Shoup product by a twiddle
+ * plus the lazy add and subtract; one 32-bit modular multiplication each) and
+ * butterflies mod 2^64 - 2^32 + 1 (one 64-bit modular multiplication each).
+ * Runs about half a second of kernels on `device` (the calling thread's
+ * current device is changed to it); allocates 0.6 MB for the kernels'
+ * outputs and frees it.  Errors: FSQL_ERR_ARG (null output, bad device),
+ * FSQL_ERR_CUDA. */
+typedef struct fsql_alu_peaks {
+    double imad_per_s;
+    double imad_hi_per_s;
+    double imad_wide_per_s;
+    double dual_prime_bfly_per_s;
+    double goldilocks_bfly_per_s;
+    int sm_count;
+    double clock_mhz;  /* the device's reported maximum SM clock */
+} fsql_alu_peaks;
+FSQL_API int fsql_measure_alu_peaks(int device, fsql_alu_peaks* out);
 
 /* Message for the last failed call on this thread ("" if none). */
 FSQL_API const char* fsql_last_error(void);

@@ -87,6 +87,7 @@ struct Ctx {
   GateDesc* d_ks_desc = nullptr;
   uint32_t* d_true = nullptr;
   size_t ks_small_cap = 0;
+  uint64_t ks_gen = 0;           // bumped whenever the keyswitch-first scratch is reallocated
   void* d_tables = nullptr;      // NttTablesT of the engine
   std::vector<uint8_t> tables;   // host copy
   size_t key_bytes = 0;

@@ -8,18 +8,18 @@
 // steps; each thread holds 8 of the 1024 coefficients of every polynomial it
 // transforms (ntt.cuh).  A CTA runs G gates in lockstep so that the
 // bootstrapping-key slice of each CMux step and gadget row (16 KB in the NTT
-// domain) is staged once into shared memory by cp.async (3-slot ring) and
-// read by all G groups.  Per CMux step a group:
-//   for each of the 2l = 6 rows (u, j): forms digit j of X^a*ACC_u - ACC_u,
-//     runs the forward NTT, and multiply-accumulates with the staged key row
-//     into two NTT-domain accumulators (one per output polynomial) held in
-//     registers;
+// domain) is staged once into shared memory by cp.async (2-slot ring) and
+// read by all G groups.  Per CMux a group:
+//   for each of the 2l = 6 rows (u, j), P rows per step: forms digit j of
+//     X^a*ACC_u - ACC_u, runs the forward NTT, and multiply-accumulates with
+//     the staged key row into two NTT-domain accumulators (one per output
+//     polynomial) held in registers;
 //   runs the two inverse NTTs, lifts the exact integers mod 2^32 and adds
 //   them into its accumulator polynomials in shared memory.
-// Keyswitch kernel.  A CTA takes 16 gates and all output columns; each
-// thread owns 4 columns, walks the (i, j) digit positions once and streams
-// the three nonzero-digit key rows for its columns, so each key row read from
-// L2 serves 16 gates.
+// Keyswitch kernel.  A CTA takes 16 gates and one tile of 128 output
+// columns; each thread owns one column of the tile, walks the (i, j) digit
+// positions once and reads the three nonzero-digit key words of its column,
+// so each key row read from L2 serves 16 gates.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -932,7 +932,7 @@ struct Plan {
   const uint32_t* graph_big = nullptr;
   const OutDesc* graph_lits = nullptr;
   int graph_br_gates = 0;  // launch shape: 2 x gates per CTA + latency mode
-  const GateDesc* graph_ks_desc = nullptr;  // keyswitch-first scratch the graph reads
+  uint64_t graph_ks_gen = 0;  // keyswitch-first scratch generation the graph was captured with
   // aggregation plans (SUM, MAX, MIN): key and the buffers they own
   int agg_kind = -1;
   const uint32_t* agg_in = nullptr;
@@ -1261,6 +1261,7 @@ static int ensure_ks_first(Ctx& c, size_t count) {
   CK(cudaGetLastError());
   CK(cudaDeviceSynchronize());
   c.ks_small_cap = count;
+  ++c.ks_gen;  // a captured graph holds the old addresses of all three buffers
   return FSQL_OK;
 }
 
@@ -1631,7 +1632,7 @@ int execute_plan(Ctx* c, fsql::Plan& pl, const fsql::GateDesc* d_desc, const fsq
   fsql::Plan& mp = pl;
   if (!mp.graph || mp.graph_desc != d_desc || mp.graph_big != c->d_big || mp.graph_lits != d_lits ||
       mp.graph_br_gates != 2 * c->br_gates + (c->latency_mode ? 1 : 0) ||
-      (pl.ks_first && mp.graph_ks_desc != c->d_ks_desc)) {
+      (pl.ks_first && mp.graph_ks_gen != c->ks_gen)) {
     if (mp.graph) cudaGraphExecDestroy(mp.graph);
     mp.graph = nullptr;
     cudaStream_t cs = static_cast<cudaStream_t>(c->capture_stream);
@@ -1659,7 +1660,7 @@ int execute_plan(Ctx* c, fsql::Plan& pl, const fsql::GateDesc* d_desc, const fsq
     mp.graph_big = c->d_big;
     mp.graph_lits = d_lits;
     mp.graph_br_gates = 2 * c->br_gates + (c->latency_mode ? 1 : 0);
-    mp.graph_ks_desc = c->d_ks_desc;
+    mp.graph_ks_gen = c->ks_gen;
   }
   if (cudaGraphLaunch(mp.graph, static_cast<cudaStream_t>(stream)) != cudaSuccess) {
     fsql::set_error("scan graph launch failed");
@@ -1980,12 +1981,18 @@ int fsql_gate_batch_noalloc(fsql_ctx* ctx, const uint8_t* d_types, const uint32_
   fsql::make_desc_kernel<<<static_cast<unsigned>((count + 255) / 256), 256, 0, st>>>(
       scr.desc, d_types, d_a, d_b, d_out, static_cast<int>(count), n + 1);
   cudaError_t e = cudaGetLastError();
-  if (e == cudaSuccess) e = fsql::launch_br_any(*c, scr.desc, count, scr.big, st);
   if (e == cudaSuccess) {
+    fsql::LaunchTimer tm(*c, st);
+    e = fsql::launch_br_any(*c, scr.desc, count, scr.big, st);
+    if (e == cudaSuccess) tm.done(true, count);
+  }
+  if (e == cudaSuccess) {
+    fsql::LaunchTimer tm(*c, st);
     const dim3 grid(static_cast<unsigned>((count + fsql::kKsGates - 1) / fsql::kKsGates), fsql::kKsTiles);
     fsql::keyswitch_kernel<<<grid, fsql::kKsCols, 0, st>>>(scr.big, scr.desc, nullptr, static_cast<int>(count),
                                                                c->d_ksk, n);
     e = cudaGetLastError();
+    if (e == cudaSuccess) tm.done(false, count);
   }
   if (e != cudaSuccess) {
     fsql::set_error(std::string("no-allocation gate path launch: ") + cudaGetErrorString(e));

@@ -62,6 +62,12 @@ class fsql_server_stats(C.Structure):
                 ("scratch_used", C.c_size_t)]
 
 
+class fsql_alu_peaks(C.Structure):
+    _fields_ = [("imad_per_s", C.c_double), ("imad_hi_per_s", C.c_double), ("imad_wide_per_s", C.c_double),
+                ("dual_prime_bfly_per_s", C.c_double), ("goldilocks_bfly_per_s", C.c_double),
+                ("sm_count", C.c_int), ("clock_mhz", C.c_double)]
+
+
 class fsql_params(C.Structure):
     _fields_ = [("n", C.c_uint32), ("N", C.c_uint32), ("bg_bits", C.c_uint32), ("l", C.c_uint32),
                 ("ks_base_bits", C.c_uint32), ("ks_t", C.c_uint32),
@@ -129,6 +135,7 @@ def load() -> C.CDLL:
         "fsql_server_cancel": (i32, [vp, u64]),
         "fsql_server_get_stats": (i32, [vp, C.POINTER(fsql_server_stats)]),
         "fsql_server_destroy": (None, [vp]),
+        "fsql_measure_alu_peaks": (i32, [i32, C.POINTER(fsql_alu_peaks)]),
         "fsql_last_error": (C.c_char_p, []),
     }
     for name, (res, args) in sig.items():
@@ -169,6 +176,14 @@ def _stream(stream) -> int:
         except Exception:
             return 0
     return int(getattr(stream, "cuda_stream", stream))
+
+
+def measure_alu_peaks(device: int = 0) -> dict:
+    """Integer-ALU rates of the GPU (operations per second), from the
+    library's in-register microkernels."""
+    out = fsql_alu_peaks()
+    _check(load().fsql_measure_alu_peaks(device, C.byref(out)))
+    return {name: getattr(out, name) for name, _ in fsql_alu_peaks._fields_}
 
 
 def params_default() -> fsql_params:

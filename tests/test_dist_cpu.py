@@ -61,3 +61,17 @@ def test_torchrun_reference_arm_prints_once():
     assert len(lines) == 1
     rec = json.loads(lines[0])
     assert rec["impl"] == "reference" and rec["value"] > 0 and rec["cpu_baseline"]["kind"] == "oracle"
+
+
+def test_reference_arm_loads_no_product_library():
+    """bench.py --impl reference times the oracle only: the process never
+    maps the CUDA library (gate counts come from the oracle's own netlist)."""
+    code = ("import runpy, sys; sys.argv = ['bench.py', '--impl', 'reference', '--workload', 'eq4x16', "
+            "'--steps', '1', '--warmup', '0', '--cpu-rows', '1']; "
+            "runpy.run_path('bench.py', run_name='__main__'); "
+            "maps = open('/proc/self/maps').read(); "
+            "assert 'libfhesql' not in maps, 'product library mapped'")
+    r = subprocess.run([sys.executable, "-c", code], cwd=ROOT, capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0, r.stderr[-2000:]
+    line = json.loads(r.stdout.strip().splitlines()[-1])
+    assert line["impl"] == "reference" and line["config"]["gates_per_row"] == 11 and line["value"] > 0

@@ -75,7 +75,7 @@ def test_ntt_product_matches_schoolbook(env):
 def test_blind_rotate_extract_matches_oracle(env):
     ctx, o = env
     rng = np.random.default_rng(2)
-    count = 11  # one full 8-warp group plus a ragged one
+    count = 11  # several CTAs of the small-batch kernel, the last one partly idle
     types = rng.integers(0, 10, count).astype(np.uint8)
     x = both_encrypt_bits(ctx, o, rng.integers(0, 2, count).astype(np.uint8), 30)
     y = both_encrypt_bits(ctx, o, rng.integers(0, 2, count).astype(np.uint8), 31)
@@ -122,7 +122,7 @@ def test_gate_batch_every_type_and_input_pair(env):
 
 def test_gate_batch_random_microbench_inputs(env):
     ctx, o = env
-    B = 150  # > one CTA wave of 8-gate groups on a partial grid, ragged tails everywhere
+    B = 150  # about one gate per SM: the small-batch kernels, a partial last wave
     types, xb, yb = WL.gates(B, seed=5)
     x = both_encrypt_bits(ctx, o, xb, WL.STREAM_GATES, 0)
     y = both_encrypt_bits(ctx, o, yb, WL.STREAM_GATES, B)

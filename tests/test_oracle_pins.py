@@ -271,6 +271,82 @@ def test_keyswitch_preserves_phase(real_oracle):
         assert abs(err) < (1 << 26), err
 
 
+def ks_digits_closed_form(x):
+    """Keyswitch digits of the word x, from the definition of rounding to the
+    nearest multiple of 2^16 with ties up: v = floor((x + 2^15) / 2^16) mod
+    2^16, written in base 4, most significant digit first (weights 2^30,
+    2^28, ..., 2^16)."""
+    v = ((int(x) + (1 << 15)) // (1 << 16)) % (1 << 16)
+    return [(v >> (14 - 2 * j)) & 3 for j in range(8)]
+
+
+# words whose low 16 bits sit on, just below and just above the rounding tie
+# (truncation and ties-down give other digits there), the wrap to zero at the
+# top, and random words
+KS_PIN_WORDS = [0x00008000, 0x00007FFF, 0x00008001, 0x12348000, 0x1234FFFF, 0xFFFF8000, 0xFFFF7FFF,
+                0x7FFF8000, 0x55558000, 0xAAAA7FFF, 0x00000000, 0xFFFFFFFF, 0xC0DE1234, 0x3FFFC000]
+
+
+def test_keyswitch_rounding_digits_exact(real_oracle):
+    """One nonzero mask word: the keyswitch must return exactly (0, .., 0, b)
+    minus the key rows KSK[i][j][d_j - 1] selected by the closed-form digits
+    (a row per nonzero digit).  Plain truncation, ties-down rounding, a
+    reversed digit order or a wrong row index gives other words."""
+    o = real_oracle
+    ksk = o.ksk().astype(np.int64)
+    rng = np.random.default_rng(31)
+    body = 0x0BADF00D
+    words = KS_PIN_WORDS + [int(w) for w in rng.integers(0, Q, 10)]
+    for k, x in enumerate(words):
+        i = [0, 1, 511, 1023][k % 4]
+        big = np.zeros(o.N + 1, np.uint32)
+        big[i] = x
+        big[o.N] = body
+        want = np.zeros(o.n + 1, np.int64)
+        want[o.n] = body
+        for j, d in enumerate(ks_digits_closed_form(x)):
+            if d:
+                want -= ksk[i, j, d - 1]
+        assert np.array_equal(o.keyswitch(big), (want % Q).astype(np.uint32)), hex(x)
+    # ties: the digits of 2^15 are those of 2^16 (rounded up), not of 0
+    assert ks_digits_closed_form(0x8000) == [0] * 7 + [1]
+    assert ks_digits_closed_form(0xFFFF8000) == [0] * 8
+
+
+def test_keyswitch_exact_phase_relation(real_oracle):
+    """For any input, phase(KS(c)) = b - sum_i S_i round16(a_i) - (sum of the
+    noise of the selected key rows), exactly mod q, where round16 is the
+    closed-form rounding above and each row's noise is its phase minus
+    d S_i 2^(30 - 2j).  The mean of the rounding part over many inputs is
+    about zero; truncation would shift it by about 2^24."""
+    o = real_oracle
+    S = o.glwe_key().astype(np.int64)
+    ksk = o.ksk()
+    nd = ksk.shape[2]
+    rows = ksk.reshape(-1, o.n + 1)
+    row_phase = o.phase(rows).astype(np.int64).reshape(o.N, 8, nd)
+    dv = np.arange(1, nd + 1, dtype=np.int64)
+    weight = np.array([1 << (30 - 2 * j) for j in range(8)], np.int64)
+    row_noise = (row_phase - (dv[None, None, :] * S[:, None, None] * weight[None, :, None])) % Q
+    rng = np.random.default_rng(77)
+    rounding_parts = []
+    for _ in range(24):
+        a = rng.integers(0, Q, o.N).astype(np.int64)
+        b = int(rng.integers(0, Q))
+        big = np.concatenate([a, [b]]).astype(np.uint32)
+        got = int(o.phase(o.keyswitch(big))[0])
+        rounded = np.array([((int(x) + (1 << 15)) >> 16) % (1 << 16) for x in a], np.int64) << 16
+        noise = 0
+        for i in range(o.N):
+            for j, d in enumerate(ks_digits_closed_form(a[i])):
+                if d:
+                    noise += int(row_noise[i, j, d - 1])
+        want = (b - int((S * rounded).sum()) - noise) % Q
+        assert got == want
+        rounding_parts.append(int(centered(int((S * ((a - rounded) % Q)).sum()) % Q)))
+    assert abs(np.mean(rounding_parts)) < (1 << 21), np.mean(rounding_parts)
+
+
 # --------------------------------------------------------------------------
 # gates: full truth tables
 # --------------------------------------------------------------------------
