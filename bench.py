@@ -379,7 +379,8 @@ def run_gates(args, dist):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32 (exact integer)",
             "data": "synthetic (seeded random gates, seeded keys)",
             "config": {"workload": f"gates x{B}", "engine": ["goldilocks", "dual_prime"][ctx.engine],
-                       "launch_shape": {"gates_per_cta": ctx.br_gates, "autotune_ms": tuned[1] if tuned else None},
+                       "launch_shape": dict(F.br_shape_info(ctx.br_shape), index=ctx.br_shape,
+                                         autotune_ms=tuned[1] if tuned else None),
                        "gate_types": "NAND/AND/OR/XOR/XNOR uniform",
                        "l2": "inputs %s L2 (%.0f MB)" % ("larger than" if 2 * B * 2524 > 126e6 else "within",
                                                           2 * B * 2524 / 1e6)},
@@ -808,7 +809,8 @@ def run_ours(args, dist):
                    "sum_gate_bootstraps_per_step": sum_gates,
                    "params": "n=630 N=1024 Bg=2^7 l=3 ks 4^8 Torus32",
                    "engine": ["goldilocks", "dual_prime"][ctx.engine],
-                   "launch_shape": {"gates_per_cta": ctx.br_gates, "autotune_ms": tuned[1] if tuned else None},
+                   "launch_shape": dict(F.br_shape_info(ctx.br_shape), index=ctx.br_shape,
+                                         autotune_ms=tuned[1] if tuned else None),
                    "l2": "inputs larger than L2 (%.0f MB column+payload per step)" % (h2d / 1e6),
                    "parallelism": f"replica per GPU x{dist.world}"},
         "correct": correct,

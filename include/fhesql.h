@@ -127,10 +127,23 @@ FSQL_API int fsql_ctx_create(const fsql_params* params, uint64_t seed, int devic
 FSQL_API int fsql_ctx_create_engine(const fsql_params* params, uint64_t seed, int device, int engine,
                                     fsql_ctx** out);
 FSQL_API int fsql_ctx_engine(const fsql_ctx* ctx, int* engine);
-/* Launch shape of the blind rotation for large batches: gates per CTA, each
- * gate 128 threads (1, 2 or 4 for the Goldilocks engine, 1 to 4 for the
- * dual-prime engine; batches under two gates per SM always use 1).  Results
- * do not depend on it. */
+/* Launch shape of the blind rotation for batches of at least two gates per
+ * SM (smaller batches always run one gate per CTA).  Results never depend
+ * on it.  Shapes (index: kernel, gates per CTA, gadget rows per step, slots
+ * of the key-staging ring):
+ *   0-3: packed kernel (each 128-thread group holds both primes' residues of
+ *        a gate, or the 64-bit prime's), 1-4 gates per CTA, 2 rows per step
+ *        (two-prime engine) or 1 (Goldilocks engine, which offers 0, 1, 3);
+ *   4: prime-split kernel (two-prime engine: a gate is 256 threads, the two
+ *      primes' transforms on separate warps), 2 gates, 2 rows, 2 slots;
+ *   5: prime-split, 2 gates, 2 rows, 3 slots;
+ *   6: prime-split, 3 gates, 2 rows, 2 slots;
+ *   7: prime-split, 2 gates, 3 rows, 2 slots.
+ * fsql_ctx_set_br_gates(g) selects the packed shape g - 1 (g = 1..4). */
+#define FSQL_BR_SHAPES 8
+FSQL_API int fsql_ctx_set_br_shape(fsql_ctx* ctx, int shape);
+FSQL_API int fsql_ctx_br_shape(const fsql_ctx* ctx, int* shape);
+FSQL_API int fsql_br_shape_info(int shape, int* kind, int* gates_per_cta, int* rows_per_step, int* stages);
 FSQL_API int fsql_ctx_set_br_gates(fsql_ctx* ctx, int gates_per_cta);
 FSQL_API int fsql_ctx_br_gates(const fsql_ctx* ctx, int* gates_per_cta);
 /* Latency mode for batches smaller than two gates per SM (two-prime engine;
@@ -140,14 +153,16 @@ FSQL_API int fsql_ctx_br_gates(const fsql_ctx* ctx, int* gates_per_cta);
 FSQL_API int fsql_ctx_set_latency_mode(fsql_ctx* ctx, int on);
 
 /* Autotuner: times the blind rotation of `probe_gates` synthetic gates
- * (0 = 4 x SMs x 4) for every launch shape the context's engine offers,
- * keeps the fastest in the context and in a per-process table keyed by
- * (device, engine), and returns the chosen gates per CTA and the timings
- * (ms, in the order 1, 2, 3, 4 gates per CTA; -1 where not offered) in
- * ms_out[4] (may be NULL).  Synchronises `stream`; allocates its probe
- * buffers for the duration of the call.  A later context on the same device
- * and engine starts from the tuned value. */
-FSQL_API int fsql_autotune(fsql_ctx* ctx, size_t probe_gates, void* stream, int* best_gates, double* ms_out);
+ * (0 = 48 x SMs, a whole number of waves of every shape; at least 2 x SMs,
+ * at most 2^20) for every launch shape the
+ * context's engine offers (kernel, gates per CTA, gadget rows per step,
+ * staging depth), keeps the fastest in the context and in a per-process
+ * table keyed by (device, engine), and returns the chosen shape index and
+ * the timings (ms per shape index, -1 where not offered) in
+ * ms_out[FSQL_BR_SHAPES] (may be NULL).  Synchronises `stream`; allocates
+ * its probe buffers for the duration of the call.  A later context on the
+ * same device and engine starts from the tuned shape. */
+FSQL_API int fsql_autotune(fsql_ctx* ctx, size_t probe_gates, void* stream, int* best_shape, double* ms_out);
 FSQL_API void fsql_ctx_destroy(fsql_ctx* ctx);
 FSQL_API int fsql_ctx_params(const fsql_ctx* ctx, fsql_params* out);
 /* Device bytes held by the context for keys (bootstrapping key in the NTT
@@ -453,6 +468,8 @@ typedef struct fsql_alu_peaks {
     double imad_wide_per_s;
     double dual_prime_bfly_per_s;
     double goldilocks_bfly_per_s;
+    double dual_prime_bfly_wide_per_s;    /* the quotient from a widening multiply's high word */
+    double dual_prime_bfly_madwide_per_s; /* ... from a widening multiply-add */
     int sm_count;
     double clock_mhz;  /* the device's reported maximum SM clock */
 } fsql_alu_peaks;

@@ -25,6 +25,26 @@ constexpr int kKsDigits = (1 << kKsBaseBits) - 1;  // nonzero digit values
 constexpr int kKsRowWords = 640;  // n+1 padded to a multiple of 4 words (16 B)
 constexpr int kMaxN = 1024;  // largest LWE dimension the kernels take
 
+// Launch shapes of the blind rotation for batches of at least two gates per
+// SM.  kind 0: the packed kernel (each thread holds both primes' residues;
+// one gadget row per step for the 64-bit prime, two for the two primes);
+// kind 1: the prime-split kernel of the two-prime engine.  stages: slots of
+// the key-staging ring.
+struct BrShape {
+  int kind, gates, rows, stages;
+};
+constexpr int kBrShapeCount = 8;
+constexpr BrShape kBrShapes[kBrShapeCount] = {
+    {0, 1, 0, 2}, {0, 2, 0, 2}, {0, 3, 0, 2}, {0, 4, 0, 2},  // packed, 1-4 gates per CTA (rows per engine)
+    {1, 2, 2, 2}, {1, 2, 2, 3}, {1, 3, 2, 2}, {1, 2, 3, 2},  // prime-split
+};
+// Whether an engine offers a shape (the 64-bit prime: packed 1, 2 or 4 gates per CTA).
+inline bool shape_offered(int engine, int shape) {
+  if (shape < 0 || shape >= kBrShapeCount) return false;
+  if (engine == FSQL_ENGINE_GOLDILOCKS) return shape == 0 || shape == 1 || shape == 3;
+  return true;
+}
+
 // One bootstrapped gate: inputs a, b (and c for three-input gates, else
 // null) and output pointer, all [n+1] words.
 struct GateDesc {
@@ -70,7 +90,7 @@ struct Ctx {
   uint64_t seed = 0;
   int device = -1;
   int engine = FSQL_ENGINE_DUAL_PRIME;
-  int br_gates = 3;              // gates per blind-rotation CTA for large batches
+  int br_shape = 2;              // launch shape of the blind rotation for large batches (index into kBrShapes)
   bool latency_mode = true;      // small batches: one gate per CTA of three groups (two-prime engine)
   // host-side secrets and standard-domain keys (client side)
   std::vector<uint8_t> s;    // LWE key [n]
@@ -89,6 +109,8 @@ struct Ctx {
   size_t ks_small_cap = 0;
   uint64_t ks_gen = 0;           // bumped whenever the keyswitch-first scratch is reallocated
   void* d_tables = nullptr;      // NttTablesT of the engine
+  uint32_t* d_bks = nullptr;     // two-prime engine: the key split by prime [n][2l][2 primes][8][128][2] u32
+  void* d_tables_split = nullptr;  // two-prime engine: NttTablesT<uint2> per prime (each padded to 128 B)
   std::vector<uint8_t> tables;   // host copy
   size_t key_bytes = 0;
   // scratch (grown on demand, freed with the context)

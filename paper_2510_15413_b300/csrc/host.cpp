@@ -533,7 +533,7 @@ int fsql_ctx_create_engine(const fsql_params* params, uint64_t seed, int device,
     c->seed = seed;
     c->device = device;
     c->engine = engine;
-    c->br_gates = engine == FSQL_ENGINE_GOLDILOCKS ? 4 : 3;
+    c->br_shape = engine == FSQL_ENGINE_GOLDILOCKS ? 3 : 2;
     fsql::keygen(*c);
     if (device >= 0) {
       const int rc = fsql::device_init(*c);
@@ -555,11 +555,33 @@ int fsql_ctx_create(const fsql_params* params, uint64_t seed, int device, fsql_c
 int fsql_ctx_set_br_gates(fsql_ctx* ctx, int gates_per_cta) {
   if (!ctx) return arg_error("null context");
   Ctx* c = reinterpret_cast<Ctx*>(ctx);
-  const bool ok = c->engine == FSQL_ENGINE_GOLDILOCKS
-                      ? (gates_per_cta == 1 || gates_per_cta == 2 || gates_per_cta == 4)
-                      : (gates_per_cta >= 1 && gates_per_cta <= 4);
-  if (!ok) return arg_error("gates per CTA: 1, 2 or 4 (Goldilocks engine), 1 to 4 (dual-prime engine)");
-  c->br_gates = gates_per_cta;
+  if (gates_per_cta < 1 || gates_per_cta > 4 || !fsql::shape_offered(c->engine, gates_per_cta - 1))
+    return arg_error("gates per CTA: 1, 2 or 4 (Goldilocks engine), 1 to 4 (dual-prime engine)");
+  c->br_shape = gates_per_cta - 1;  // the packed kernel with that many gates per CTA
+  return FSQL_OK;
+}
+
+int fsql_ctx_set_br_shape(fsql_ctx* ctx, int shape) {
+  if (!ctx) return arg_error("null context");
+  Ctx* c = reinterpret_cast<Ctx*>(ctx);
+  if (!fsql::shape_offered(c->engine, shape)) return arg_error("launch shape not offered by this engine");
+  c->br_shape = shape;
+  return FSQL_OK;
+}
+
+int fsql_ctx_br_shape(const fsql_ctx* ctx, int* shape) {
+  if (!ctx || !shape) return arg_error("null argument");
+  *shape = reinterpret_cast<const Ctx*>(ctx)->br_shape;
+  return FSQL_OK;
+}
+
+int fsql_br_shape_info(int shape, int* kind, int* gates_per_cta, int* rows_per_step, int* stages) {
+  if (shape < 0 || shape >= fsql::kBrShapeCount) return arg_error("no such launch shape");
+  const fsql::BrShape& s = fsql::kBrShapes[shape];
+  if (kind) *kind = s.kind;
+  if (gates_per_cta) *gates_per_cta = s.gates;
+  if (rows_per_step) *rows_per_step = s.rows;
+  if (stages) *stages = s.stages;
   return FSQL_OK;
 }
 
@@ -571,7 +593,7 @@ int fsql_ctx_set_latency_mode(fsql_ctx* ctx, int on) {
 
 int fsql_ctx_br_gates(const fsql_ctx* ctx, int* gates_per_cta) {
   if (!ctx || !gates_per_cta) return arg_error("null argument");
-  *gates_per_cta = reinterpret_cast<const Ctx*>(ctx)->br_gates;
+  *gates_per_cta = fsql::kBrShapes[reinterpret_cast<const Ctx*>(ctx)->br_shape].gates;
   return FSQL_OK;
 }
 

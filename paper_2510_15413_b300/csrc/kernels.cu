@@ -26,6 +26,7 @@
 #include <cstring>
 #include <vector>
 
+#include "br_split.cuh"
 #include "engine.h"
 #include "ntt.cuh"
 
@@ -177,6 +178,30 @@ bool make_tables_dual(std::vector<uint8_t>* out) {
   out->assign(sizeof(dev::DualPrime::Tables), 0);
   fill_tables(reinterpret_cast<dev::DualPrime::Tables*>(out->data()), f, g, scale);
   return true;
+}
+
+// The two-prime tables split by prime: NttTablesT<uint2> {w, w'} for p1 then
+// for p2, each padded to kSplitBytes.
+template <int kSplitBytes>
+void split_tables(const std::vector<uint8_t>& dual, std::vector<uint8_t>* out) {
+  using TD = NttTablesT<uint4>;
+  using TS = NttTablesT<uint2>;
+  static_assert(sizeof(TS) <= static_cast<size_t>(kSplitBytes), "split table padding");
+  const TD& d = *reinterpret_cast<const TD*>(dual.data());
+  out->assign(2 * kSplitBytes, 0);
+  for (int pr = 0; pr < 2; ++pr) {
+    TS& o = *reinterpret_cast<TS*>(out->data() + pr * kSplitBytes);
+    auto pick = [&](const uint4& w) { return pr == 0 ? make_uint2(w.x, w.y) : make_uint2(w.z, w.w); };
+    for (int k = 0; k < 64; ++k) o.f_small[k] = pick(d.f_small[k]);
+    for (int k = 0; k < 128; ++k) o.g_small[k] = pick(d.g_small[k]);
+    for (int t = 0; t < kGroup; ++t) {
+      for (int c = 0; c < 7; ++c) o.f3[c][t] = pick(d.f3[c][t]);
+      for (int c = 0; c < 4; ++c) o.f4[c][t] = pick(d.f4[c][t]);
+      for (int c = 0; c < 7; ++c) o.i1[c][t] = pick(d.i1[c][t]);
+    }
+    o.n_inv = pr == 0 ? (d.n_inv & 0xFFFFFFFFull) : (d.n_inv >> 32);
+    o.pad = 0;
+  }
 }
 
 // ------------------------------------------------------------------ device helpers
@@ -414,6 +439,194 @@ __global__ void __launch_bounds__(G * kGroup, 1)
       }
       if (t == 0) out[kN] = acc_poly[kN];
     }
+  }
+}
+
+// Prime-split blind rotation (br_split.cuh): G gates per CTA of 256 threads
+// each (half 0: residues mod p1, half 1: mod p2), P gadget rows per step.
+constexpr int kSplitTabBytes = (sizeof(dev::SplitTables) + 127) / 128 * 128;
+template <int P>
+__host__ __device__ constexpr int split_gate_bytes() {
+  // per half one exchange buffer (32-bit residues); the CRT buffer [2][N];
+  // the accumulator; the switched mask; the switched body
+  return 2 * xbuf_polys<P>() * kN * 4 + 2 * kN * 4 + kGateAcc + kGateAbar + 16;
+}
+template <int G, int P, int S>
+__host__ __device__ constexpr int split_smem() {
+  return 2 * kSplitTabBytes + S * P * kChunkU64 * 8 + G * split_gate_bytes<P>();
+}
+
+// G gates per CTA, P gadget rows per step, S slots in the key-staging ring
+// (cp.async of step k + S - 1 is in flight while step k computes).
+template <int G, int P, int S>
+__global__ void __launch_bounds__(G * 2 * kGroup, 1)
+    blind_rotate_split_kernel(const GateDesc* __restrict__ desc, int count, const uint32_t* __restrict__ bks,
+                              const void* __restrict__ gtab, int n, int bg_bits, uint32_t* __restrict__ big) {
+  static_assert(kRows % P == 0 && P <= kL, "gadget rows per step must divide 2l and not exceed l");
+  constexpr int kThreads = G * 2 * kGroup;
+  constexpr int kStepsPerCmux = kRows / P;
+  constexpr int kRowU32 = 2 * kChunkU64;  // one key row, both primes (16 KB)
+  constexpr int kStepU32 = P * kRowU32;
+  constexpr int kBufPolys = xbuf_polys<P>();
+  constexpr int kGateBytes = split_gate_bytes<P>();
+  extern __shared__ __align__(128) uint8_t smem[];
+  const int grp = threadIdx.x / (2 * kGroup), h = (threadIdx.x / kGroup) & 1, t = threadIdx.x % kGroup;
+  const dev::SplitTables& T = *reinterpret_cast<const dev::SplitTables*>(smem + h * kSplitTabBytes);
+  uint32_t* stage = reinterpret_cast<uint32_t*>(smem + 2 * kSplitTabBytes);
+  uint8_t* gb = smem + 2 * kSplitTabBytes + S * kStepU32 * 4 + grp * kGateBytes;
+  uint32_t* xbuf = reinterpret_cast<uint32_t*>(gb) + h * kBufPolys * kN;  // this half's exchange buffer
+  uint32_t* crt = reinterpret_cast<uint32_t*>(gb) + 2 * kBufPolys * kN;   // [2][N]: residues for the other half
+  uint32_t* acc_poly = crt + 2 * kN;                                        // [2][N]
+  uint16_t* abar = reinterpret_cast<uint16_t*>(acc_poly + 2 * kN);          // [kMaxN]
+  uint32_t* bbar_slot = reinterpret_cast<uint32_t*>(abar + kMaxN);
+  const int bar_half = 1 + 2 * grp + h;  // this half's 128 threads
+  const int bar_gate = 1 + 2 * G + grp;  // the gate's 256 threads
+  const uint32_t p = h ? dev::kP2 : dev::kP1, p2 = 2 * p, pinv = h ? dev::kP2inv : dev::kP1inv;
+  const uint64_t* bks64 = reinterpret_cast<const uint64_t*>(bks);
+
+  for (int k = threadIdx.x; k < 2 * kSplitTabBytes / 16; k += kThreads)
+    reinterpret_cast<uint4*>(smem)[k] = reinterpret_cast<const uint4*>(gtab)[k];
+
+  uint32_t off = 1u << (31 - bg_bits * kL);
+  for (int j = 1; j <= kL; ++j) off += (1u << (bg_bits - 1)) << (32 - bg_bits * j);
+  const uint32_t dmask = (1u << bg_bits) - 1, lift = p - (1u << (bg_bits - 1));  // digit u - half -> u + p - half
+  const int total = n * kStepsPerCmux;
+
+  for (int g0 = blockIdx.x * G; g0 < count; g0 += gridDim.x * G) {
+    const int gi = g0 + grp;
+    const bool active = gi < count;
+    __syncthreads();  // tables loaded; previous gates finished with the stages
+#pragma unroll
+    for (int k = 0; k < S - 1; ++k) {  // the first S - 1 steps in flight
+      if (k < total) issue_step<kThreads, P * kChunkU64>(reinterpret_cast<uint64_t*>(stage + k * kStepU32), bks64, k);
+      cp_async_commit();
+    }
+
+    if (active) {
+      const GateDesc d = desc[gi];
+      const Lin lin = gate_lin(d.type);
+      const uint32_t* c3 = lin.cc ? d.c : nullptr;  // a missing third input counts as zero
+      for (int x = h * kGroup + t; x <= n; x += 2 * kGroup) {
+        uint32_t v = lin.ca * d.a[x] + lin.cb * d.b[x];
+        if (c3) v += lin.cc * c3[x];
+        if (x == n) v += lin.k;
+        const uint32_t ms = ((v + (1u << 20)) >> 21) & (2 * kN - 1);
+        if (x < n) abar[x] = static_cast<uint16_t>(ms);
+        else *bbar_slot = ms;
+      }
+      dev::named_sync_n(bar_gate, 2 * kGroup);
+      // ACC = (0, X^{-bbar} v), v_k = q/8: half h writes polynomial h
+      const uint32_t e = (2 * kN - *bbar_slot) & (2 * kN - 1);
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const uint32_t c = t + 128 * q;
+        const uint32_t idx = (c - e) & (2 * kN - 1);
+        acc_poly[h * kN + c] = h == 0 ? 0u : (idx < static_cast<uint32_t>(kN) ? (1u << 29) : (0u - (1u << 29)));
+      }
+    }
+
+    int parity = 0;
+    uint64_t acc0[8], acc1[8];
+    uint32_t diff0[8], diff1[8];
+    for (int i = 0; i < n; ++i) {
+#pragma unroll 1
+      for (int s = 0; s < kStepsPerCmux; ++s) {
+        const int k = i * kStepsPerCmux + s;
+        cp_async_wait<S - 2>();  // this thread's copies of step k have landed
+        __syncthreads();  // everyone's copies of step k visible; slot (k - 1) % S free; ACC of the previous CMux complete
+        if (k + S - 1 < total)
+          issue_step<kThreads, P * kChunkU64>(
+              reinterpret_cast<uint64_t*>(stage + ((k + S - 1) % S) * kStepU32), bks64, k + S - 1);
+        cp_async_commit();
+        if (active) {
+          // X^a ACC_u - ACC_u (plus the decomposition offset) for the
+          // polynomial(s) of this step's rows
+          if (s == 0 || s == kL / P) {
+            const uint32_t a_i = abar[i];
+            const uint32_t* Pu = acc_poly + (s == 0 ? 0 : kN);
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+              const uint32_t c = t + 128 * q;
+              const uint32_t idx = (c - a_i) & (2 * kN - 1);
+              const uint32_t rot = idx < static_cast<uint32_t>(kN) ? Pu[idx] : 0u - Pu[idx - kN];
+              const uint32_t v = rot - Pu[c] + off;
+              if (s == 0) diff0[q] = v;
+              else diff1[q] = v;
+            }
+          }
+          uint32_t x[P][8];
+#pragma unroll
+          for (int r = 0; r < P; ++r) {
+            const int row = s * P + r;
+            const int shift = 32 - bg_bits * (row % kL + 1);
+#pragma unroll
+            for (int q = 0; q < 8; ++q) x[r][q] = (((row < kL ? diff0[q] : diff1[q]) >> shift) & dmask) + lift;
+          }
+          dev::ntt_forward32<P, kBufPolys, 1>(x, xbuf, parity, T, t, bar_half, p, p2);
+          const uint32_t* ch = stage + (k % S) * kStepU32 + h * kChunkU64;
+#pragma unroll
+          for (int q = 0; q < 8; ++q) {
+#pragma unroll
+            for (int r = 0; r < P; ++r) {
+              const uint2 w = *reinterpret_cast<const uint2*>(ch + r * kRowU32 + (q * kGroup + t) * 2);
+              const bool first = s == 0 && r == 0;
+              acc0[q] = static_cast<uint64_t>(x[r][q]) * w.x + (first ? 0ull : acc0[q]);
+              acc1[q] = static_cast<uint64_t>(x[r][q]) * w.y + (first ? 0ull : acc1[q]);
+            }
+          }
+        }
+      }
+      if (active) {
+        uint32_t y[2][8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          y[0][q] = dev::DualPrime::settle(acc0[q], p, pinv);
+          y[1][q] = dev::DualPrime::settle(acc1[q], p, pinv);
+        }
+        dev::ntt_inverse32<2, kBufPolys, 1>(y, xbuf, parity, T, t, bar_half, p, p2);
+        // CRT: half 0 lifts output polynomial 0, half 1 polynomial 1; each
+        // passes its residues of the other polynomial through crt[]
+        if (h == 0) {
+#pragma unroll
+          for (int q = 0; q < 8; ++q) crt[t + 128 * q] = y[1][q];
+        } else {
+#pragma unroll
+          for (int q = 0; q < 8; ++q) crt[kN + t + 128 * q] = y[0][q];
+        }
+        dev::named_sync_n(bar_gate, 2 * kGroup);
+        if (h == 0) {
+#pragma unroll
+          for (int q = 0; q < 8; ++q) acc_poly[t + 128 * q] += dev::crt_torus(y[0][q], crt[kN + t + 128 * q]);
+        } else {
+#pragma unroll
+          for (int q = 0; q < 8; ++q) acc_poly[kN + t + 128 * q] += dev::crt_torus(crt[t + 128 * q], y[1][q]);
+        }
+      }
+    }
+
+    if (active) {
+      dev::named_sync_n(bar_gate, 2 * kGroup);
+      // sample extraction of coefficient 0: a'_0 = A_0, a'_c = -A_{N-c}, b' = B_0
+      uint32_t* out = big + static_cast<size_t>(gi) * (kN + 1);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int c = h * kGroup + t + 256 * q;
+        out[c] = c == 0 ? acc_poly[0] : 0u - acc_poly[kN - c];
+      }
+      if (h == 0 && t == 0) out[kN] = acc_poly[kN];
+    }
+  }
+}
+
+// Packed key (u64: p1 residue low, p2 residue high) -> key split by prime.
+__global__ void split_key_kernel(const uint64_t* __restrict__ bkhat, uint32_t* __restrict__ bks, size_t rows) {
+  const size_t total = rows * kChunkU64;
+  for (size_t e = blockIdx.x * static_cast<size_t>(blockDim.x) + threadIdx.x; e < total;
+       e += static_cast<size_t>(gridDim.x) * blockDim.x) {
+    const size_t r = e / kChunkU64, w = e % kChunkU64;
+    const uint64_t v = bkhat[e];
+    bks[r * 2 * kChunkU64 + w] = static_cast<uint32_t>(v);
+    bks[r * 2 * kChunkU64 + kChunkU64 + w] = static_cast<uint32_t>(v >> 32);
   }
 }
 
@@ -805,15 +1018,16 @@ __global__ void __launch_bounds__(kGroup) ntt_mul_kernel(const int32_t* __restri
 
 // ------------------------------------------------------------------ host side
 
-// Tuned gates per CTA, per (device, engine), for later contexts of this process.
+// Tuned launch shape (index + 1; 0 = none), per (device, engine), for later
+// contexts of this process.
 static std::mutex g_tune_mu;
 static int g_tuned[64][2] = {};
-void remember_tuning(int device, int engine, int gates) {
+void remember_tuning(int device, int engine, int shape) {
   if (device < 0 || device >= 64 || engine < 0 || engine > 1) return;
   std::lock_guard<std::mutex> lk(g_tune_mu);
-  g_tuned[device][engine] = gates;
+  g_tuned[device][engine] = shape + 1;
 }
-static int tuned_gates(int device, int engine) {
+static int tuned_shape(int device, int engine) {
   if (device < 0 || device >= 64 || engine < 0 || engine > 1) return 0;
   std::lock_guard<std::mutex> lk(g_tune_mu);
   return g_tuned[device][engine];
@@ -931,7 +1145,7 @@ struct Plan {
   const GateDesc* graph_desc = nullptr;
   const uint32_t* graph_big = nullptr;
   const OutDesc* graph_lits = nullptr;
-  int graph_br_gates = 0;  // launch shape: 2 x gates per CTA + latency mode
+  int graph_br_shape = -1;  // launch shape: 2 x shape index + latency mode
   uint64_t graph_ks_gen = 0;  // keyswitch-first scratch generation the graph was captured with
   // aggregation plans (SUM, MAX, MIN): key and the buffers they own
   int agg_kind = -1;
@@ -1006,8 +1220,8 @@ int device_init(Ctx& c) {
   }
   CK(cudaSetDevice(c.device));
   // gates per CTA for large batches: measured best on B300 unless tuned in this process
-  c.br_gates = c.engine == FSQL_ENGINE_GOLDILOCKS ? 4 : 3;
-  if (const int g = tuned_gates(c.device, c.engine)) c.br_gates = g;
+  c.br_shape = c.engine == FSQL_ENGINE_GOLDILOCKS ? 3 : 2;  // packed 4 / 3 gates per CTA
+  if (const int g = tuned_shape(c.device, c.engine)) c.br_shape = g - 1;
   int sms = 0;
   CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c.device));
   c.sm_count = sms;
@@ -1048,6 +1262,19 @@ int device_init(Ctx& c) {
     set_error(std::string("bootstrapping key conversion: ") + cudaGetErrorString(e));
     return FSQL_ERR_CUDA;
   }
+  if (c.engine == FSQL_ENGINE_DUAL_PRIME) {
+    // the prime-split kernel's copy of the key and its per-prime twiddle tables
+    std::vector<uint8_t> st;
+    split_tables<kSplitTabBytes>(c.tables, &st);
+    CK(cudaMalloc(&c.d_tables_split, st.size()));
+    CK(cudaMemcpy(c.d_tables_split, st.data(), st.size(), cudaMemcpyHostToDevice));
+    CK(cudaMalloc(&c.d_bks, bkhat_words * 8));
+    const size_t key_rows = static_cast<size_t>(p.n) * kRows;
+    split_key_kernel<<<1184, 256>>>(c.d_bkhat, c.d_bks, key_rows);
+    CK(cudaGetLastError());
+    CK(cudaDeviceSynchronize());
+    c.key_bytes += bkhat_words * 8 + st.size();
+  }
   CK(cudaEventCreateWithFlags(reinterpret_cast<cudaEvent_t*>(&c.desc_event), cudaEventDisableTiming));
   return FSQL_OK;
 }
@@ -1058,6 +1285,10 @@ void device_free(Ctx& c) {
   cudaFree(c.d_bkhat);
   cudaFree(c.d_ksk);
   cudaFree(c.d_tables);
+  cudaFree(c.d_bks);
+  cudaFree(c.d_tables_split);
+  c.d_bks = nullptr;
+  c.d_tables_split = nullptr;
   cudaFree(c.d_big);
   cudaFree(c.d_desc);
   cudaFree(c.d_wires);
@@ -1118,6 +1349,29 @@ static cudaError_t launch_br_engine(int sm_count, const GateDesc* d_desc, size_t
   return cudaGetLastError();
 }
 
+// Prime-split kernel: G gates per CTA (2 x 128 threads each), P gadget rows
+// per step, persistent grid of at most one CTA per SM.
+template <int G, int P, int S>
+static cudaError_t launch_br_split(int sm_count, const GateDesc* d_desc, size_t count, const uint32_t* bks,
+                                   const void* tables, int n, int bg_bits, uint32_t* d_big, cudaStream_t st) {
+  static_assert(split_smem<G, P, S>() <= 227 * 1024, "prime-split shared memory over budget");
+  static bool attr_set[64] = {};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+  if (!attr_set[dev]) {
+    const cudaError_t e = cudaFuncSetAttribute(blind_rotate_split_kernel<G, P, S>,
+                                               cudaFuncAttributeMaxDynamicSharedMemorySize, split_smem<G, P, S>());
+    if (e != cudaSuccess) return e;
+    attr_set[dev] = true;
+  }
+  const size_t groups = (count + G - 1) / G;
+  const int grid = static_cast<int>(std::min<size_t>(groups, static_cast<size_t>(sm_count)));
+  blind_rotate_split_kernel<G, P, S><<<grid, G * 2 * kGroup, split_smem<G, P, S>(), st>>>(
+      d_desc, static_cast<int>(count), bks, tables, n, bg_bits, d_big);
+  return cudaGetLastError();
+}
+
 // Latency mode (two-prime engine): one gate per CTA of three groups.
 template <class F>
 static cudaError_t launch_br_latency(int sm_count, const GateDesc* d_desc, size_t count, const uint64_t* bkhat,
@@ -1148,22 +1402,31 @@ static cudaError_t launch_br_latency(int sm_count, const GateDesc* d_desc, size_
 static cudaError_t launch_br_any(Ctx& c, const GateDesc* d_desc, size_t count, uint32_t* d_big, cudaStream_t st) {
   const int n = static_cast<int>(c.p.n), bg = static_cast<int>(c.p.bg_bits);
   const bool small = count < static_cast<size_t>(2 * c.sm_count);
+  const BrShape sh = kBrShapes[c.br_shape];
   if (c.engine == FSQL_ENGINE_GOLDILOCKS) {
     using F = dev::Goldilocks;
-    if (small || c.br_gates == 1)
+    if (small || sh.gates == 1)
       return launch_br_engine<F, 1, 1>(c.sm_count, d_desc, count, c.d_bkhat, c.d_tables, n, bg, d_big, st);
-    if (c.br_gates == 2)
+    if (sh.gates == 2)
       return launch_br_engine<F, 2, 1>(c.sm_count, d_desc, count, c.d_bkhat, c.d_tables, n, bg, d_big, st);
     return launch_br_engine<F, 4, 1>(c.sm_count, d_desc, count, c.d_bkhat, c.d_tables, n, bg, d_big, st);
   }
   using F = dev::DualPrime;
   if (small && c.latency_mode)
     return launch_br_latency<F>(c.sm_count, d_desc, count, c.d_bkhat, c.d_tables, n, bg, d_big, st);
-  if (small || c.br_gates == 1)
+  if (!small && sh.kind == 1) {
+    const uint32_t* k = c.d_bks;
+    const void* tb = c.d_tables_split;
+    if (sh.rows == 3) return launch_br_split<2, 3, 2>(c.sm_count, d_desc, count, k, tb, n, bg, d_big, st);
+    if (sh.gates == 3) return launch_br_split<3, 2, 2>(c.sm_count, d_desc, count, k, tb, n, bg, d_big, st);
+    if (sh.stages == 3) return launch_br_split<2, 2, 3>(c.sm_count, d_desc, count, k, tb, n, bg, d_big, st);
+    return launch_br_split<2, 2, 2>(c.sm_count, d_desc, count, k, tb, n, bg, d_big, st);
+  }
+  if (small || sh.gates == 1)
     return launch_br_engine<F, 1, 2>(c.sm_count, d_desc, count, c.d_bkhat, c.d_tables, n, bg, d_big, st);
-  if (c.br_gates == 3)
+  if (sh.gates == 3)
     return launch_br_engine<F, 3, 2>(c.sm_count, d_desc, count, c.d_bkhat, c.d_tables, n, bg, d_big, st);
-  if (c.br_gates == 4)
+  if (sh.gates == 4)
     return launch_br_engine<F, 4, 2>(c.sm_count, d_desc, count, c.d_bkhat, c.d_tables, n, bg, d_big, st);
   return launch_br_engine<F, 2, 2>(c.sm_count, d_desc, count, c.d_bkhat, c.d_tables, n, bg, d_big, st);
 }
@@ -1631,7 +1894,7 @@ int execute_plan(Ctx* c, fsql::Plan& pl, const fsql::GateDesc* d_desc, const fsq
   if (prof && prof->recording) return launch_all(stream);  // per-launch events need plain launches
   fsql::Plan& mp = pl;
   if (!mp.graph || mp.graph_desc != d_desc || mp.graph_big != c->d_big || mp.graph_lits != d_lits ||
-      mp.graph_br_gates != 2 * c->br_gates + (c->latency_mode ? 1 : 0) ||
+      mp.graph_br_shape != 2 * c->br_shape + (c->latency_mode ? 1 : 0) ||
       (pl.ks_first && mp.graph_ks_gen != c->ks_gen)) {
     if (mp.graph) cudaGraphExecDestroy(mp.graph);
     mp.graph = nullptr;
@@ -1659,7 +1922,7 @@ int execute_plan(Ctx* c, fsql::Plan& pl, const fsql::GateDesc* d_desc, const fsq
     mp.graph_desc = d_desc;
     mp.graph_big = c->d_big;
     mp.graph_lits = d_lits;
-    mp.graph_br_gates = 2 * c->br_gates + (c->latency_mode ? 1 : 0);
+    mp.graph_br_shape = 2 * c->br_shape + (c->latency_mode ? 1 : 0);
     mp.graph_ks_gen = c->ks_gen;
   }
   if (cudaGraphLaunch(mp.graph, static_cast<cudaStream_t>(stream)) != cudaSuccess) {
@@ -2001,13 +2264,17 @@ int fsql_gate_batch_noalloc(fsql_ctx* ctx, const uint8_t* d_types, const uint32_
   return FSQL_OK;
 }
 
-int fsql_autotune(fsql_ctx* ctx, size_t probe_gates, void* stream, int* best_gates, double* ms_out) {
+int fsql_autotune(fsql_ctx* ctx, size_t probe_gates, void* stream, int* best_shape, double* ms_out) {
   Ctx* c = device_ctx(ctx);
   if (!c) return FSQL_ERR_ARG;
-  const size_t count = probe_gates ? probe_gates : static_cast<size_t>(16 * c->sm_count);
+  // default probe: 48 gates per SM, a whole number of waves for every shape
+  // (1, 2, 3 or 4 gates per CTA), so no shape is favoured by its last wave
+  const size_t count = probe_gates ? probe_gates : static_cast<size_t>(48 * c->sm_count);
   if (count > (size_t(1) << 20)) return arg_error("probe_gates above 2^20");
+  if (count < static_cast<size_t>(2 * c->sm_count)) return arg_error("probe_gates below two gates per SM");
   const size_t words = c->p.n + 1;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
+  std::lock_guard<std::mutex> lk(c->mu);
   // probe inputs: arbitrary words (the work per gate does not depend on the data)
   uint32_t* d_in = nullptr;
   uint8_t* d_types = nullptr;
@@ -2015,9 +2282,9 @@ int fsql_autotune(fsql_ctx* ctx, size_t probe_gates, void* stream, int* best_gat
   fsql::GateDesc* d_desc = nullptr;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   int rc = FSQL_OK;
-  double ms[4] = {-1.0, -1.0, -1.0, -1.0};
-  const int shapes[4] = {1, 2, 3, 4};
-  const int saved = c->br_gates;
+  double ms[fsql::kBrShapeCount];
+  for (double& v : ms) v = -1.0;
+  const int saved = c->br_shape;
   int best = saved;
   double best_ms = 0.0;
   auto fail = [&](const char* what, cudaError_t e) {
@@ -2036,9 +2303,9 @@ int fsql_autotune(fsql_ctx* ctx, size_t probe_gates, void* stream, int* best_gat
   if (rc == FSQL_OK) {
     fsql::make_desc_kernel<<<static_cast<unsigned>((count + 255) / 256), 256, 0, st>>>(
         d_desc, d_types, d_in, d_in + count * words, nullptr, static_cast<int>(count), static_cast<int>(words));
-    for (int si = 0; si < 4 && rc == FSQL_OK; ++si) {
-      const int g = shapes[si];
-      if (fsql_ctx_set_br_gates(ctx, g) != FSQL_OK) continue;  // shape not offered by this engine
+    for (int si = 0; si < fsql::kBrShapeCount && rc == FSQL_OK; ++si) {
+      if (!fsql::shape_offered(c->engine, si)) continue;
+      c->br_shape = si;
       float t = 0.f;
       e = fsql::launch_br_any(*c, d_desc, count, d_big, st);  // warm-up
       if (e == cudaSuccess) e = cudaEventRecord(e0, st);
@@ -2053,11 +2320,11 @@ int fsql_autotune(fsql_ctx* ctx, size_t probe_gates, void* stream, int* best_gat
       ms[si] = t;
       if (best_ms == 0.0 || t < best_ms) {
         best_ms = t;
-        best = g;
+        best = si;
       }
     }
   }
-  c->br_gates = rc == FSQL_OK ? best : saved;
+  c->br_shape = rc == FSQL_OK ? best : saved;
   if (rc == FSQL_OK) fsql::remember_tuning(c->device, c->engine, best);
   if (e0) cudaEventDestroy(e0);
   if (e1) cudaEventDestroy(e1);
@@ -2065,9 +2332,9 @@ int fsql_autotune(fsql_ctx* ctx, size_t probe_gates, void* stream, int* best_gat
   cudaFree(d_types);
   cudaFree(d_big);
   cudaFree(d_desc);
-  if (best_gates) *best_gates = c->br_gates;
+  if (best_shape) *best_shape = c->br_shape;
   if (ms_out)
-    for (int i = 0; i < 4; ++i) ms_out[i] = ms[i];
+    for (int i = 0; i < fsql::kBrShapeCount; ++i) ms_out[i] = ms[i];
   return rc;
 }
 

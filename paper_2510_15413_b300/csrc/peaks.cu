@@ -132,6 +132,68 @@ __global__ void __launch_bounds__(kPeakThreads) shoup_bfly_kernel(uint32_t* out,
   out[blockIdx.x * blockDim.x + threadIdx.x] = s;
 }
 
+// The same butterflies with the Shoup quotient taken from the high word of
+// a widening 32 x 32 -> 64-bit multiply (mode 1) or multiply-add with a
+// zero addend that is only known at run time (mode 2), instead of the
+// high-half multiply: the three ways the engine can form floor(a w' / 2^32).
+template <int kMode>
+__device__ __forceinline__ uint32_t quot(uint32_t a, uint32_t ws, uint64_t zero) {
+  if (kMode == 0) return __umulhi(a, ws);
+  uint64_t r;
+  if (kMode == 1) asm("mul.wide.u32 %0, %1, %2;" : "=l"(r) : "r"(a), "r"(ws));
+  else asm("mad.wide.u32 %0, %1, %2, %3;" : "=l"(r) : "r"(a), "r"(ws), "l"(zero));
+  return static_cast<uint32_t>(r >> 32);
+}
+template <int kMode, int D>
+__device__ __forceinline__ void dpw_stage(uint32_t (&x)[8], const uint32_t (&w)[4], const uint32_t (&ws)[4],
+                                          uint64_t zero) {
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    if (k & D) continue;
+    const uint32_t hi = x[k + D];
+    const uint32_t t = hi * w[k & 3] - quot<kMode>(hi, ws[k & 3], zero) * dev::kP1;
+    x[k + D] = x[k] - t + 2 * dev::kP1;
+    x[k] = x[k] + t;
+  }
+}
+template <int kMode>
+__global__ void __launch_bounds__(kPeakThreads) shoup_mode_kernel(uint32_t* out, int iters, uint32_t seed) {
+  uint32_t x[8], y[8], w[4], ws[4];
+  const uint64_t zero = seed >> 31;  // 0 for the seeds used here, unknown to the compiler
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    x[k] = (seed + threadIdx.x * 13u + k) & 0x3FFFFFFu;
+    y[k] = (seed ^ (threadIdx.x * 29u + 5u * k)) & 0x3FFFFFFu;
+  }
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    w[k] = (seed * 2654435761u + 977u * k) % dev::kP1;
+    ws[k] = static_cast<uint32_t>((static_cast<uint64_t>(w[k]) << 32) / dev::kP1);
+  }
+  for (int it = 0; it < iters; ++it) {
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+      dpw_stage<kMode, 4>(x, w, ws, zero);
+      dpw_stage<kMode, 4>(y, w, ws, zero);
+      dpw_stage<kMode, 2>(x, w, ws, zero);
+      dpw_stage<kMode, 2>(y, w, ws, zero);
+      dpw_stage<kMode, 1>(x, w, ws, zero);
+      dpw_stage<kMode, 1>(y, w, ws, zero);
+    }
+    dpw_stage<kMode, 1>(x, w, ws, zero);
+    dpw_stage<kMode, 1>(y, w, ws, zero);
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      x[k] &= 0x3FFFFFFu;
+      y[k] &= 0x3FFFFFFu;
+    }
+  }
+  uint32_t s = 0;
+#pragma unroll
+  for (int k = 0; k < 8; ++k) s ^= x[k] ^ y[k];
+  out[blockIdx.x * blockDim.x + threadIdx.x] = s;
+}
+
 // Butterflies mod the 64-bit prime (the Goldilocks engine's forward step:
 // one modular product, a modular add and subtract; canonical residues, so
 // no masking), the same 10-stage pattern over 8 registers.
@@ -216,6 +278,10 @@ extern "C" int fsql_measure_alu_peaks(int device, fsql_alu_peaks* out) {
   if (e == cudaSuccess) out->imad_wide_per_s = threads * per_iter * it_mul / (ms * 1e-3);
   if (e == cudaSuccess) e = time_kernel(shoup_bfly_kernel, grid, d_out, it_bfly, e0, e1, &ms);
   if (e == cudaSuccess) out->dual_prime_bfly_per_s = threads * 80.0 * it_bfly / (ms * 1e-3);
+  if (e == cudaSuccess) e = time_kernel(shoup_mode_kernel<1>, grid, d_out, it_bfly, e0, e1, &ms);
+  if (e == cudaSuccess) out->dual_prime_bfly_wide_per_s = threads * 80.0 * it_bfly / (ms * 1e-3);
+  if (e == cudaSuccess) e = time_kernel(shoup_mode_kernel<2>, grid, d_out, it_bfly, e0, e1, &ms);
+  if (e == cudaSuccess) out->dual_prime_bfly_madwide_per_s = threads * 80.0 * it_bfly / (ms * 1e-3);
   if (e == cudaSuccess) e = time_kernel(goldilocks_bfly_kernel, grid, d_out, it_gl, e0, e1, &ms);
   if (e == cudaSuccess) out->goldilocks_bfly_per_s = threads * 40.0 * it_gl / (ms * 1e-3);
   out->sm_count = sms;

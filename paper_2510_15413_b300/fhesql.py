@@ -23,7 +23,8 @@ ENGINES = {"default": -1, "goldilocks": 0, "dual_prime": 1}
 
 # every symbol include/fhesql.h declares
 API = ["fsql_params_default", "fsql_params_toy", "fsql_ctx_create", "fsql_ctx_create_engine", "fsql_ctx_engine",
-       "fsql_ctx_set_br_gates", "fsql_ctx_br_gates", "fsql_ctx_set_latency_mode", "fsql_autotune",
+       "fsql_ctx_set_br_gates", "fsql_ctx_br_gates", "fsql_ctx_set_br_shape", "fsql_ctx_br_shape",
+       "fsql_br_shape_info", "fsql_ctx_set_latency_mode", "fsql_autotune", "fsql_measure_alu_peaks",
        "fsql_ctx_destroy", "fsql_ctx_params",
        "fsql_ctx_device_bytes", "fsql_export_keys", "fsql_encrypt", "fsql_encrypt_bits", "fsql_encrypt_uint",
        "fsql_phase", "fsql_decrypt_bits", "fsql_decrypt_uint", "fsql_gate_batch", "fsql_blind_rotate_extract",
@@ -65,6 +66,7 @@ class fsql_server_stats(C.Structure):
 class fsql_alu_peaks(C.Structure):
     _fields_ = [("imad_per_s", C.c_double), ("imad_hi_per_s", C.c_double), ("imad_wide_per_s", C.c_double),
                 ("dual_prime_bfly_per_s", C.c_double), ("goldilocks_bfly_per_s", C.c_double),
+                ("dual_prime_bfly_wide_per_s", C.c_double), ("dual_prime_bfly_madwide_per_s", C.c_double),
                 ("sm_count", C.c_int), ("clock_mhz", C.c_double)]
 
 
@@ -95,6 +97,9 @@ def load() -> C.CDLL:
         "fsql_ctx_set_br_gates": (i32, [vp, i32]),
         "fsql_ctx_set_latency_mode": (i32, [vp, i32]),
         "fsql_ctx_br_gates": (i32, [vp, C.POINTER(i32)]),
+        "fsql_ctx_set_br_shape": (i32, [vp, i32]),
+        "fsql_ctx_br_shape": (i32, [vp, C.POINTER(i32)]),
+        "fsql_br_shape_info": (i32, [i32, C.POINTER(i32), C.POINTER(i32), C.POINTER(i32), C.POINTER(i32)]),
         "fsql_autotune": (i32, [vp, sz, vp, C.POINTER(i32), C.POINTER(C.c_double)]),
         "fsql_ctx_destroy": (None, [vp]),
         "fsql_ctx_params": (i32, [vp, C.POINTER(fsql_params)]),
@@ -176,6 +181,17 @@ def _stream(stream) -> int:
         except Exception:
             return 0
     return int(getattr(stream, "cuda_stream", stream))
+
+
+BR_SHAPES = 8
+
+
+def br_shape_info(shape: int) -> dict:
+    """(kernel kind, gates per CTA, gadget rows per step, staging slots) of a launch shape."""
+    k, g, r, st = C.c_int(), C.c_int(), C.c_int(), C.c_int()
+    _check(load().fsql_br_shape_info(int(shape), C.byref(k), C.byref(g), C.byref(r), C.byref(st)))
+    return {"kind": ["packed", "prime_split"][k.value], "gates_per_cta": g.value, "rows_per_step": r.value,
+            "stages": st.value}
 
 
 def measure_alu_peaks(device: int = 0) -> dict:
@@ -278,12 +294,23 @@ class Context:
         """Small batches on one gate per CTA of three groups (default on)."""
         _check(load().fsql_ctx_set_latency_mode(self._h, int(bool(on))))
 
+    @property
+    def br_shape(self) -> int:
+        """Launch shape index of the blind rotation for large batches (see br_shape_info)."""
+        v = C.c_int()
+        _check(load().fsql_ctx_br_shape(self._h, C.byref(v)))
+        return int(v.value)
+
+    @br_shape.setter
+    def br_shape(self, shape: int) -> None:
+        _check(load().fsql_ctx_set_br_shape(self._h, int(shape)))
+
     def autotune(self, probe_gates: int = 0, stream=None):
-        """Pick the fastest blind-rotation launch shape; returns (gates per CTA, {shape: ms})."""
+        """Pick the fastest blind-rotation launch shape; returns (shape index, {shape: ms})."""
         best = C.c_int()
-        ms = (C.c_double * 4)()
+        ms = (C.c_double * BR_SHAPES)()
         _check(load().fsql_autotune(self._h, probe_gates, _stream(stream), C.byref(best), ms))
-        return int(best.value), {g: ms[i] for i, g in enumerate((1, 2, 3, 4)) if ms[i] >= 0}
+        return int(best.value), {i: float(ms[i]) for i in range(BR_SHAPES) if ms[i] >= 0}
 
     @property
     def handle(self) -> C.c_void_p:

@@ -529,6 +529,7 @@ def test_autotune_picks_a_shape_and_keeps_results(env):
     b = torch.zeros((40, 631), dtype=torch.int32, device="cuda")
     ctx.gate_batch(dev(types), dev(x.view(np.int32)), dev(y.view(np.int32)), a)
     best, ms = ctx.autotune(probe_gates=1184)
-    assert best in ms and ctx.br_gates == best and all(v > 0 for v in ms.values())
+    assert best in ms and ctx.br_shape == best and all(v > 0 for v in ms.values())
+    assert set(ms) == ({0, 1, 3} if ctx.engine == F.FSQL_ENGINE_GOLDILOCKS else set(range(F.BR_SHAPES)))
     ctx.gate_batch(dev(types), dev(x.view(np.int32)), dev(y.view(np.int32)), b)
     assert np.array_equal(host(a), host(b))
