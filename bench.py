@@ -45,7 +45,14 @@ def parse():
                              "range4x16maj", "eq32x4096plain", "range16x65536plain", "eq4x16plain", "eq32x4096sum",
                              "eq32x4096plainsum", "eq32x4096ksfirst", "gates",
                              "serving"])
-    ap.add_argument("--queries", type=int, default=16, help="queries per serving phase")
+    ap.add_argument("--queries", type=int, default=200, help="measured queries per serving phase")
+    ap.add_argument("--warm-queries", type=int, default=20, help="warm-up queries per serving phase")
+    ap.add_argument("--serve-log2", default="8,10",
+                    help="serving tables: rows = round(2^U[lo, hi]) (the serving workload statement: 8,16)")
+    ap.add_argument("--catalog", type=int, default=8, help="distinct encrypted tables the served queries scan")
+    ap.add_argument("--serve-inflight", type=int, default=8, help="outstanding queries in the saturated phase")
+    ap.add_argument("--serve-budget-gb", type=float, default=96.0, help="server scratch budget (GiB)")
+    ap.add_argument("--verify-queries", type=int, default=2, help="served queries per phase checked by the oracle")
     ap.add_argument("--batch", type=int, default=65536, help="gates per step of the gate microbenchmark")
     ap.add_argument("--sweep", default="",
                     help="gate microbenchmark over these batch sizes (comma separated, e.g. 1,16,256,4096,65536,1048576)")
@@ -58,6 +65,8 @@ def parse():
     ap.add_argument("--verify-rows", type=int, default=2,
                     help="rows of the timed scan the CPU oracle recomputes word for word (first, matching, last...)")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default launch shape")
+    ap.add_argument("--br-shape", type=int, default=None,
+                    help="blind-rotation launch shape index (implies --no-autotune)")
     ap.add_argument("--seed", type=int, default=1)
     return ap.parse_args()
 
@@ -196,6 +205,16 @@ def oracle_gates_per_row(table) -> int:
     return int(O.netlist3(table.pred, table.width, npay, table.payload_width)[0].size)
 
 
+def pick_shape(ctx, args):
+    """The blind-rotation launch shape: given on the command line, else the
+    library's autotuner (timed on synthetic gates before anything is timed
+    here), else the context's default."""
+    if args.br_shape is not None:
+        ctx.br_shape = args.br_shape
+        return None
+    return None if args.no_autotune else ctx.autotune()
+
+
 def oracle_scan(o, table, col, cst, pays):
     if table.ks_first:
         return o.scan_ks_first(table.pred, table.width, col, cst, pays, table.payload_width)
@@ -312,7 +331,7 @@ def run_gates(args, dist):
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
     ctx = F.Context(args.seed, device=dev, engine=args.engine)
     alu = F.measure_alu_peaks(dev)
-    tuned = None if args.no_autotune else ctx.autotune()
+    tuned = pick_shape(ctx, args)
     B = args.batch
     types, xb, yb = WL.gates(B, seed=args.seed)
     x = ctx.encrypt_bits(xb, WL.STREAM_GATES, 0)
@@ -478,8 +497,16 @@ def run_gate_sweep(args, dist):
 
 # ------------------------------------------------------------------ serving
 def run_serving(args, dist):
-    """Continuous batching: a saturated burst, then Poisson arrivals at 0.5x
-    and 0.9x of the saturated query rate; reports rows/s and p50/p99."""
+    """Continuous batching under load (the serving workload).  A catalog of
+    seeded encrypted tables with rows = round(2^U[lo, hi]), widths {8, 16,
+    32}, EQ or RANGE (50/50), 1-2 payload columns of the column's width
+    stays resident; every query scans one catalog table with its own
+    encrypted constants and its own output buffers.  Phases: saturated
+    (closed loop, --serve-inflight queries outstanding), then Poisson
+    arrivals at 0.5x and 0.9x of the saturated query rate; each phase runs
+    --warm-queries warm-up queries, then --queries measured ones (latency =
+    submit to done, as the server records it).  Sampled finished queries have
+    one row recomputed by the CPU oracle, word for word."""
     import random
 
     import torch
@@ -490,65 +517,150 @@ def run_serving(args, dist):
     dev = dist.local
     torch.cuda.set_device(dev)
     ctx = F.Context(args.seed, device=dev, engine=args.engine)
+    tuned = pick_shape(ctx, args)
     W = ctx.words
+    lo2, hi2 = (float(v) for v in args.serve_log2.split(","))
+    catalog = WL.serving_queries(args.catalog, seed=args.seed, min_log2=lo2, max_log2=hi2)
+    d = lambda a: torch.from_numpy(a.view(np.int32)).to(f"cuda:{dev}")
+    tabs = []
+    for t in catalog:
+        col, _, pays = WL.encrypt_table(ctx, t)
+        tabs.append({"t": t, "column": d(col), "payloads": [d(p) for p in pays]})
+    torch.cuda.synchronize()
+    budget = int(args.serve_budget_gb * (1 << 30))
+    rng = np.random.default_rng(args.seed + 17)
+    qcount = [0]
 
-    def prepare(tables):
-        ios = []
-        for t in tables:
-            col, cst, pays = WL.encrypt_table(ctx, t)
-            d = lambda a: torch.from_numpy(a.view(np.int32)).to(f"cuda:{dev}")
-            ios.append({"column": d(col), "const": d(cst), "payloads": [d(p) for p in pays],
-                        "match": torch.zeros((t.rows, W), dtype=torch.int32, device=f"cuda:{dev}"),
-                        "outs": [torch.zeros((t.rows, t.payload_width, W), dtype=torch.int32,
-                                             device=f"cuda:{dev}") for _ in pays]})
-        return ios
+    def make_query():
+        """A query on a random catalog table: fresh constants, encrypted at
+        their own positions of the constant stream, and fresh outputs."""
+        i = int(rng.integers(0, len(tabs)))
+        base = tabs[i]["t"]
+        w = base.width
+        if base.pred == WL.PRED_EQ:
+            consts = (int(base.column[int(rng.integers(0, base.rows))]),)
+        else:
+            span = max(1, (1 << w) // 10)
+            lo = int(rng.integers(0, (1 << w) - span + 1))
+            consts = (lo, lo + span)
+        t = WL.Table(base.name, base.rows, w, base.pred, base.column, base.payloads, base.payload_width, consts)
+        k = qcount[0]
+        qcount[0] += 1
+        cst_first = k * 2 * w
+        cst = ctx.encrypt_bits(t.const_bits(), WL.STREAM_CONST, cst_first)
+        return {"i": i, "t": t, "k": k, "cst_first": cst_first, "const": d(cst),
+                "match": torch.zeros((t.rows, W), dtype=torch.int32, device=f"cuda:{dev}"),
+                "outs": [torch.zeros((t.rows, t.payload_width, W), dtype=torch.int32, device=f"cuda:{dev}")
+                         for _ in t.payloads]}
 
-    def phase(tables, ios, rate_qps):
-        srv = F.Server(ctx, scratch_budget_bytes=8 << 30)
+    def submit(srv, q):
+        tb = tabs[q["i"]]
+        q["id"] = srv.submit(tb["column"], q["t"].rows, q["t"].width, q["t"].pred, q["const"], tb["payloads"],
+                             q["t"].payload_width, q["match"], q["outs"])
+
+    def finish(srv, q, keep):
+        state, lat = srv.status(q["id"])
+        q["lat_ms"] = lat
+        q["ok"] = state == F.Q_DONE
+        m_want, p_want = q["t"].expected()
+        got = ctx.decrypt_bits(q["match"].cpu().numpy().view(np.uint32))
+        q["correct"] = bool(np.array_equal(got, m_want))
+        if keep:  # keep the outputs of queries the oracle will check
+            q["match_h"] = q["match"].cpu().numpy().view(np.uint32)
+            q["outs_h"] = [o.cpu().numpy().view(np.uint32) for o in q["outs"]]
+        del q["match"], q["outs"], q["const"]
+
+    def phase(rate_qps):
+        """rate 0: saturated closed loop; else Poisson arrivals at that rate."""
+        srv = F.Server(ctx, scratch_budget_bytes=budget)
+        total = args.warm_queries + args.queries
         rnd = random.Random(args.seed + int(rate_qps * 1000))
-        ids = []
+        pending, done = [], []
         t0 = time.perf_counter()
         next_t = 0.0
-        for t, io in zip(tables, ios):
-            if rate_qps > 0:
-                next_t += rnd.expovariate(rate_qps)
-                delay = t0 + next_t - time.perf_counter()
-                if delay > 0:
-                    time.sleep(delay)
-            ids.append(srv.submit(io["column"], t.rows, t.width, t.pred, io["const"], io["payloads"],
-                                  t.payload_width, io["match"], io["outs"]))
-        for q in ids:
-            srv.wait(q, 3.6e6)
-        wall = time.perf_counter() - t0
+        submitted = 0
+        while submitted < total or pending:
+            now = time.perf_counter() - t0
+            can_submit = submitted < total and (
+                (rate_qps == 0 and len(pending) < args.serve_inflight) or (rate_qps > 0 and now >= next_t))
+            if can_submit:
+                q = make_query()
+                q["measured"] = submitted >= args.warm_queries
+                submit(srv, q)
+                q["t_sub"] = time.perf_counter() - t0
+                pending.append(q)
+                submitted += 1
+                if rate_qps > 0:
+                    next_t += rnd.expovariate(rate_qps)
+                continue
+            still = []
+            for q in pending:
+                if srv.status(q["id"])[0] in (F.Q_DONE, F.Q_FAILED, F.Q_CANCELLED):
+                    q["t_done"] = time.perf_counter() - t0
+                    finish(srv, q, keep=q["measured"] and sum(1 for x in done if "match_h" in x) < args.verify_queries)
+                    done.append(q)
+                else:
+                    still.append(q)
+            pending = still
+            time.sleep(0.002)
         st = srv.stats()
-        lat = [srv.status(q)[1] for q in ids]
         srv.close()
-        ok = True
-        for t, io in zip(tables, ios):
-            m_want, _ = t.expected()
-            ok &= bool(np.array_equal(ctx.decrypt_bits(io["match"].cpu().numpy().view(np.uint32)), m_want))
-        rows = sum(t.rows for t in tables)
-        return {"rate_qps": rate_qps, "queries": len(tables), "wall_s": wall, "rows_per_s": rows / wall,
-                "gate_bootstraps_per_s": st["gates"] / wall, "p50_ms": float(np.percentile(lat, 50)),
-                "p99_ms": float(np.percentile(lat, 99)), "rounds": st["rounds"], "correct": ok}
+        meas = [q for q in done if q["measured"]]
+        wall = max(q["t_done"] for q in meas) - min(q["t_sub"] for q in meas)
+        lat = [q["lat_ms"] for q in meas]
+        rows = sum(q["t"].rows for q in meas)
+        gates = sum(q["t"].rows * q["t"].gates_per_row for q in meas)
+        return {"rate_qps": rate_qps, "warm_queries": args.warm_queries, "queries": len(meas), "wall_s": wall,
+                "rows_per_s": rows / wall, "gate_bootstraps_per_s": gates / wall,
+                "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+                "max_ms": float(max(lat)), "rounds": st["rounds"], "server_busy_ms": st["busy_ms"],
+                "correct": all(q["ok"] and q["correct"] for q in done)}, [q for q in done if "match_h" in q]
 
-    tables = WL.serving_queries(args.queries, seed=args.seed)
-    ios = prepare(tables)
-    sat = phase(tables, ios, 0.0)
-    q_rate = args.queries / sat["wall_s"]
+    sat, checked = phase(0.0)
+    q_rate = sat["queries"] / sat["wall_s"]
     runs = [sat]
     for frac in (0.5, 0.9):
-        t2 = WL.serving_queries(args.queries, seed=args.seed + int(frac * 10))
-        runs.append(phase(t2, prepare(t2), frac * q_rate))
+        r, c = phase(frac * q_rate)
+        r["load"] = frac
+        runs.append(r)
+        checked += c
+    # oracle recomputation of one row of each kept query (the first matching row, else row 0)
+    verified = None
+    if args.verify_queries > 0 and checked and dist.rank == 0:
+        from oracle import oracle as O
+        O.set_threads(os.cpu_count() or 1)
+        o = O.Oracle(args.seed)
+        same, rows_checked = True, 0
+        for q in checked:
+            t = q["t"]
+            m_want, _ = t.expected()
+            r = int(np.argmax(m_want)) if m_want.any() else 0
+            w, pw = t.width, t.payload_width
+            ocol = o.encrypt_bits(t.column_bits().reshape(t.rows, w)[r], WL.STREAM_COLUMN, r * w)
+            opays = [o.encrypt_bits(t.payload_bits(k).reshape(t.rows, pw)[r], WL.STREAM_PAYLOAD,
+                                    k * t.rows * pw + r * pw) for k in range(len(t.payloads))]
+            ocst = o.encrypt_bits(t.const_bits(), WL.STREAM_CONST, q["cst_first"])
+            om, oouts = o.scan(t.pred, w, ocol, ocst, opays, pw)
+            same &= bool(np.array_equal(q["match_h"][r], om[0]))
+            for gout, oo in zip(q["outs_h"], oouts):
+                same &= bool(np.array_equal(gout.reshape(t.rows, pw, W)[r], oo.reshape(pw, W)))
+            rows_checked += 1
+        o.close()
+        verified = {"queries_checked": rows_checked, "words_equal": same}
     head = runs[-1]
     line = {"metric": "served encrypted rows/s", "value": head["rows_per_s"], "unit": "rows/s",
-            "n_gpus": dist.world, "steps": len(runs), "warmup": 0, "ms_per_step": head["wall_s"] * 1e3,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32 (exact integer)",
-            "data": "synthetic (seeded query mix)", "p50_ms": head["p50_ms"], "p99_ms": head["p99_ms"],
-            "config": {"workload": "serving", "queries_per_phase": args.queries,
-                       "rows": "round(2^U[8,10])", "widths": [8, 16, 32], "preds": "EQ/RANGE 50/50",
-                       "payload_columns": "1-2", "engine": ["goldilocks", "dual_prime"][ctx.engine]},
-            "phases": runs}
+            "n_gpus": dist.world, "steps": len(runs), "warmup": args.warm_queries,
+            "ms_per_step": head["wall_s"] * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "u32 (exact integer)", "data": "synthetic (seeded table catalog and query mix)",
+            "p50_ms": head["p50_ms"], "p99_ms": head["p99_ms"],
+            "config": {"workload": "serving", "queries_per_phase": args.queries, "warm_queries": args.warm_queries,
+                       "rows": f"round(2^U[{lo2:g},{hi2:g}])", "catalog_tables": len(catalog),
+                       "widths": [8, 16, 32], "preds": "EQ/RANGE 50/50 (ripple comparator)",
+                       "payload_columns": "1-2", "saturated_inflight": args.serve_inflight,
+                       "scratch_budget_gb": args.serve_budget_gb, "engine": ["goldilocks", "dual_prime"][ctx.engine],
+                       "launch_shape": dict(F.br_shape_info(ctx.br_shape), index=ctx.br_shape)},
+            "phases": runs, "oracle_rows": verified,
+            "correct": all(r["correct"] for r in runs)}
     ctx.close()
     if dist.rank == 0:
         print(json.dumps(line), flush=True)
@@ -640,7 +752,7 @@ def run_ours(args, dist):
 
     ctx = F.Context(args.seed, device=dev, engine=args.engine)
     alu = F.measure_alu_peaks(dev)
-    tuned = None if args.no_autotune else ctx.autotune()
+    tuned = pick_shape(ctx, args)
     t = WL.table(args.workload, seed=args.seed, rows=args.rows)
     col, cst, pays = WL.encrypt_table(ctx, t)
     W = ctx.big_words if t.ks_first else ctx.words

@@ -152,6 +152,26 @@ FSQL_API int fsql_ctx_br_gates(const fsql_ctx* ctx, int* gates_per_cta);
  * 128-thread CTA.  The output words are the same either way. */
 FSQL_API int fsql_ctx_set_latency_mode(fsql_ctx* ctx, int on);
 
+/* Device level walker for batched scans (two-prime engine, packed launch
+ * shapes with 2 or 3 gates per CTA; off by default).  When on, a scan whose every
+ * circuit level holds at least two gates per SM runs as ONE cooperative
+ * launch (one CTA per SM) that walks the levels on the device: per level,
+ * the CTAs bootstrap its gates, meet at a grid barrier, keyswitch them, and
+ * meet again (Alg. 2 evaluates each row's tree level by level).  Each
+ * barrier wait gives up after timeout_ms of device time (default 2000): the
+ * kernel then raises an error word and every CTA returns, leaving the
+ * context usable; fsql_walk_status reports it.  Results are bit-identical
+ * to the per-level launches.  Errors: FSQL_ERR_ARG (timeout not in
+ * (0, 600000]). */
+FSQL_API int fsql_ctx_set_walk(fsql_ctx* ctx, int on, double timeout_ms);
+/* Synchronises `stream`, then FSQL_ERR_TIMEOUT if a walker launch on this
+ * context since its last scan started timed out at a grid barrier
+ * (*barrier = its index, may be NULL), else FSQL_OK. */
+FSQL_API int fsql_walk_status(fsql_ctx* ctx, void* stream, unsigned int* barrier);
+/* Test hook: CTA `block` of later walker launches never arrives at a grid
+ * barrier (-1: off), so the waits of the others run out of time. */
+FSQL_API int fsql_debug_walk_skip_block(fsql_ctx* ctx, int block);
+
 /* Autotuner: times the blind rotation of `probe_gates` synthetic gates
  * (0 = 48 x SMs, a whole number of waves of every shape; at least 2 x SMs,
  * at most 2^20) for every launch shape the

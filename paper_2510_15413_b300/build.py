@@ -15,7 +15,8 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libfhesql.so")
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["host.cpp", "kernels.cu", "server.cu", "plain.cu", "peaks.cu", "engine.h", "ntt.cuh"]
+SOURCES = ["host.cpp", "kernels.cu", "server.cu", "plain.cu", "peaks.cu", "schedule.cu", "engine.h", "ntt.cuh",
+           "br_split.cuh"]
 
 
 def _stale() -> bool:
@@ -36,6 +37,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
     srv_o = os.path.join(BUILD, "server.o")
     lit_o = os.path.join(BUILD, "plain.o")
     pk_o = os.path.join(BUILD, "peaks.o")
+    sc_o = os.path.join(BUILD, "schedule.o")
     run = lambda cmd: subprocess.run(cmd, check=True, capture_output=not verbose)
     run(["g++", "-std=c++17", "-O2", "-fPIC", "-fvisibility=hidden", "-fno-fast-math", "-ffp-contract=off",
          "-pthread", "-Wall", "-Wextra", *inc, "-c", os.path.join(CSRC, "host.cpp"), "-o", host_o])
@@ -47,8 +49,10 @@ def build(force: bool = False, verbose: bool = False) -> str:
          *inc, "-c", os.path.join(CSRC, "plain.cu"), "-o", lit_o])
     run([NVCC, "-std=c++17", "-O3", *ARCH, "-lineinfo", "-Xcompiler", "-fPIC,-fvisibility=hidden",
          *inc, "-c", os.path.join(CSRC, "peaks.cu"), "-o", pk_o])
+    run([NVCC, "-std=c++17", "-O3", *ARCH, "-lineinfo", "-Xcompiler", "-fPIC,-fvisibility=hidden",
+         *inc, "-c", os.path.join(CSRC, "schedule.cu"), "-o", sc_o])
     tmp = LIB + f".tmp{os.getpid()}"
-    run([NVCC, "-shared", *ARCH, host_o, dev_o, srv_o, lit_o, pk_o, "-o", tmp, "-lpthread"])
+    run([NVCC, "-shared", *ARCH, host_o, dev_o, srv_o, lit_o, pk_o, sc_o, "-o", tmp, "-lpthread"])
     os.replace(tmp, LIB)
     return LIB
 

@@ -85,6 +85,16 @@ struct OutDesc {
 
 struct Plan;  // scan plan (kernels.cu)
 
+// Grid-barrier state of one scan_walk_kernel launch (zeroed before it):
+// CTA arrivals (barrier b completes at (b + 1) x CTAs), the error word (1: a
+// barrier wait ran out of time) and the index of the barrier where it did.
+struct WalkSync {
+  unsigned int arrived;
+  unsigned int error;
+  unsigned int barrier;
+  unsigned int pad;
+};
+
 struct Ctx {
   fsql_params p{};
   uint64_t seed = 0;
@@ -92,6 +102,10 @@ struct Ctx {
   int engine = FSQL_ENGINE_DUAL_PRIME;
   int br_shape = 2;              // launch shape of the blind rotation for large batches (index into kBrShapes)
   bool latency_mode = true;      // small batches: one gate per CTA of three groups (two-prime engine)
+  bool walk_mode = false;        // batched scans as one device-walked launch (scan_walk_kernel)
+  double walk_timeout_ms = 2000.0;  // limit of each grid-barrier wait of the walker
+  int walk_skip_block = -1;      // test hook: this CTA never arrives at the walker's barriers
+  WalkSync* d_walk_sync = nullptr;
   // host-side secrets and standard-domain keys (client side)
   std::vector<uint8_t> s;    // LWE key [n]
   std::vector<uint8_t> S;    // GLWE key [N]
@@ -120,9 +134,8 @@ struct Ctx {
   size_t desc_cap = 0;
   uint32_t* d_wires = nullptr;   // intermediate wires of a scan
   size_t wires_cap = 0;          // in words
-  GateDesc* h_desc = nullptr;    // pinned staging for descriptor uploads
-  size_t h_desc_cap = 0;
-  void* desc_event = nullptr;    // cudaEvent_t guarding h_desc reuse
+  void* d_prog = nullptr;        // the current scan plan's program (netlist + pointers), see schedule.cu
+  size_t prog_cap = 0;           // in bytes
   uint32_t* d_stage = nullptr;   // device staging for the host-buffer scan
   size_t stage_cap = 0;
   OutDesc* d_lits = nullptr;     // scan outputs no gate writes (plaintext constants)
@@ -187,11 +200,20 @@ struct ScanIO {
 };
 // Gates of a row that are neither the match bit nor a mask gate (they need scratch).
 long scan_internal_wires(const Netlist& nl);
-// Descriptors of every gate of every row, level by level, gate-major within a
-// level; level_offset receives levels + 1 offsets into out.
-void scan_descriptors(const Netlist& nl, const ScanIO& io, GateDesc* out, std::vector<size_t>* level_offset);
 // Descriptors of the outputs no gate writes, every row.
 void scan_literals(const Netlist& nl, const ScanIO& io, std::vector<OutDesc>* out);
+
+// schedule.cu: descriptors generated on the device from a scan program
+// (the per-row netlist plus the scan's buffer pointers, a few KB).
+size_t scan_program_bytes(const Netlist& nl);
+// The program of a scan (host bytes to copy to the device as they are) and
+// the descriptor offsets of its levels (levels + 1 entries); false if the
+// scan has more payload columns than a program holds (64).
+bool build_scan_program(const Netlist& nl, const ScanIO& io, std::vector<uint8_t>* out,
+                        std::vector<size_t>* level_offset);
+// Writes all rows x gates descriptors of the program at d_prog to d_out
+// (level by level, gate-major within a level, rows in order), on `stream`.
+int launch_gen_desc(const void* d_prog, GateDesc* d_out, size_t total, void* stream);
 
 // kernels.cu
 int device_init(Ctx& c);     // tables, BK -> NTT domain, KSK upload

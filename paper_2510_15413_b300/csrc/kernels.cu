@@ -60,9 +60,14 @@ template <int G>
 __host__ __device__ constexpr int xbufs_for() {
   return G >= 3 ? 1 : 2;
 }
+// digit tables of the first two forward stages (two-prime engine)
+template <class F>
+__host__ __device__ constexpr int digit_tab_bytes() {
+  return F::kEngine == FSQL_ENGINE_DUAL_PRIME ? dev::kDigitTabs * dev::kDigitTabSize * 8 : 0;
+}
 template <class F, int G, int P>
 __host__ __device__ constexpr int br_smem() {
-  return tab_bytes<F>() + kStages * P * kChunkU64 * 8 + G * gate_bytes<P, xbufs_for<G>()>();
+  return tab_bytes<F>() + digit_tab_bytes<F>() + kStages * P * kChunkU64 * 8 + G * gate_bytes<P, xbufs_for<G>()>();
 }
 
 constexpr int kKsGates = 16;                     // gates per keyswitch CTA
@@ -296,12 +301,14 @@ __device__ __forceinline__ void issue_step(uint64_t* slot, const uint64_t* __res
   for (int q = threadIdx.x; q < kStepU64 * 8 / 16; q += kThreads) cp_async16(dst + q, src + q);
 }
 
-// Blind rotation + sample extraction for `count` gates (see file comment).
-// big: [count][N+1] extracted samples under the GLWE key.
+// Blind rotation + sample extraction for `count` gates (see file comment),
+// the body of blind_rotate_kernel and of each segment of scan_walk_kernel.
+// big: [count][N+1] extracted samples under the GLWE key.  prepare: load the
+// twiddle tables into shared memory first (and build the digit tables).
 template <class F, int G, int kPolys>
-__global__ void __launch_bounds__(G * kGroup, 1)
-    blind_rotate_kernel(const GateDesc* __restrict__ desc, int count, const uint64_t* __restrict__ bkhat,
-                        const void* __restrict__ gtab, int n, int bg_bits, uint32_t* __restrict__ big) {
+__device__ __forceinline__ void br_body(const GateDesc* __restrict__ desc, int count,
+                                        const uint64_t* __restrict__ bkhat, const void* __restrict__ gtab, int n,
+                                        int bg_bits, uint32_t* __restrict__ big, bool prepare) {
   static_assert(kRows % kPolys == 0 && kPolys <= kL, "gadget rows per step must divide 2l and not exceed l");
   constexpr int kThreads = G * kGroup;
   constexpr int kTabBytes = tab_bytes<F>();
@@ -311,18 +318,18 @@ __global__ void __launch_bounds__(G * kGroup, 1)
   constexpr int kNB = xbufs_for<G>();
   constexpr int kGateXbuf = kNB * kBufPolys * kN * 8;
   constexpr int kGateBytes = gate_bytes<kPolys, kNB>();
+  constexpr bool kDigitTab = F::kEngine == FSQL_ENGINE_DUAL_PRIME;
   extern __shared__ __align__(128) uint8_t smem[];
   typename F::Tables& T = *reinterpret_cast<typename F::Tables*>(smem);
-  uint64_t* stage = reinterpret_cast<uint64_t*>(smem + kTabBytes);
+  uint64_t* dtab = reinterpret_cast<uint64_t*>(smem + kTabBytes);  // digit tables (two-prime engine)
+  uint64_t* stage = reinterpret_cast<uint64_t*>(smem + kTabBytes + digit_tab_bytes<F>());
   const int grp = threadIdx.x / kGroup, t = threadIdx.x % kGroup;
   const int bar = 1 + grp;  // named barrier of this gate's 128 threads
-  uint8_t* gb = smem + kTabBytes + kStages * kStepU64 * 8 + grp * kGateBytes;
+  uint8_t* gb = smem + kTabBytes + digit_tab_bytes<F>() + kStages * kStepU64 * 8 + grp * kGateBytes;
   uint64_t* xbufs = reinterpret_cast<uint64_t*>(gb);                         // [2][kBufPolys][N] u64
   uint32_t* acc_poly = reinterpret_cast<uint32_t*>(gb + kGateXbuf);          // [2][N] u32
   uint16_t* abar = reinterpret_cast<uint16_t*>(gb + kGateXbuf + kGateAcc);   // [n]
   uint32_t* bbar_slot = reinterpret_cast<uint32_t*>(gb + kGateXbuf + kGateAcc + kGateAbar);
-
-  load_tables(T, gtab);
 
   // Signed gadget digits by the offset form: y = x + sum_j 2^(bg-1) 2^(32-bg j)
   // + 2^(31 - bg l); digit j = ((y >> (32 - bg j)) mod 2^bg) - 2^(bg-1).
@@ -330,6 +337,13 @@ __global__ void __launch_bounds__(G * kGroup, 1)
   for (int j = 1; j <= kL; ++j) off += (1u << (bg_bits - 1)) << (32 - bg_bits * j);
   const uint32_t dmask = (1u << bg_bits) - 1, dhalf = 1u << (bg_bits - 1);
   const int total = n * kStepsPerCmux;
+  if (prepare) {
+    load_tables(T, gtab);
+    if constexpr (kDigitTab) {
+      __syncthreads();  // twiddle tables loaded
+      dev::build_digit_tables(dtab, T, dhalf, threadIdx.x, kThreads);
+    }
+  }
 
   for (int g0 = blockIdx.x * G; g0 < count; g0 += gridDim.x * G) {
     const int gi = g0 + grp;
@@ -395,13 +409,20 @@ __global__ void __launch_bounds__(G * kGroup, 1)
           for (int p = 0; p < kPolys; ++p) {
             const int row = s * kPolys + p;
             const int shift = 32 - bg_bits * (row % kL + 1);
+            if constexpr (kDigitTab) {
+              uint32_t u[8];
 #pragma unroll
-            for (int q = 0; q < 8; ++q) {
-              const uint32_t v = row < kL ? diff0[q] : diff1[q];
-              x[p][q] = F::from_digit((v >> shift) & dmask, dhalf);
+              for (int q = 0; q < 8; ++q) u[q] = ((row < kL ? diff0[q] : diff1[q]) >> shift) & dmask;
+              dev::digit_stages12(u, x[p], dhalf, dtab);
+            } else {
+#pragma unroll
+              for (int q = 0; q < 8; ++q) {
+                const uint32_t v = row < kL ? diff0[q] : diff1[q];
+                x[p][q] = F::from_digit((v >> shift) & dmask, dhalf);
+              }
             }
           }
-          dev::ntt_forward<F, kPolys, kBufPolys, kNB>(x, xbufs, parity, T, t, bar);
+          dev::ntt_forward<F, kPolys, kBufPolys, kNB, kDigitTab>(x, xbufs, parity, T, t, bar);
           const uint64_t* ch = stage + (k % kStages) * kStepU64;
 #pragma unroll
           for (int q = 0; q < 8; ++q) {
@@ -440,6 +461,13 @@ __global__ void __launch_bounds__(G * kGroup, 1)
       if (t == 0) out[kN] = acc_poly[kN];
     }
   }
+}
+
+template <class F, int G, int kPolys>
+__global__ void __launch_bounds__(G * kGroup, 1)
+    blind_rotate_kernel(const GateDesc* __restrict__ desc, int count, const uint64_t* __restrict__ bkhat,
+                        const void* __restrict__ gtab, int n, int bg_bits, uint32_t* __restrict__ big) {
+  br_body<F, G, kPolys>(desc, count, bkhat, gtab, n, bg_bits, big, true);
 }
 
 // Prime-split blind rotation (br_split.cuh): G gates per CTA of 256 threads
@@ -778,24 +806,25 @@ __global__ void __launch_bounds__(kLatGroups * kGroup, 1)
 // one table load indexed by its digit (no compare or select); only the
 // owning thread reads a slot, so no barrier is needed.  Output of gate g goes
 // to desc[g].out when desc is given, else to out_contig + g*(n+1).
-__global__ void __launch_bounds__(kKsCols)
-    keyswitch_kernel(const uint32_t* __restrict__ big, const GateDesc* __restrict__ desc,
-                     uint32_t* __restrict__ out_contig, int count, const uint32_t* __restrict__ ksk, int n) {
-  __shared__ uint16_t dig[kKsGates][kN];
-  __shared__ uint32_t tbl[kKsT][4][kKsCols];  // [level][digit][column of this tile]
-  const int g0 = blockIdx.x * kKsGates;
+// One keyswitch tile: gates [g0, g0 + 16) of the batch (fewer at its end),
+// output columns [tile * 128, tile * 128 + 128), by 128 threads (tc = 0..127)
+// that synchronise on named barrier `bar` (0: the whole 128-thread CTA).
+// dig and tbl are the tile's shared buffers; the caller orders their reuse.
+__device__ __forceinline__ void ks_tile(const uint32_t* __restrict__ big, const GateDesc* __restrict__ desc,
+                                        uint32_t* __restrict__ out_contig, int count, const uint32_t* __restrict__ ksk,
+                                        int n, int g0, int tile, uint16_t (*dig)[kN],
+                                        uint32_t (*tbl)[4][kKsCols], int tc, int bar) {
   const int ng = min(kKsGates, count - g0);
-  for (int q = threadIdx.x; q < kKsGates * kN; q += kKsCols) {
+  for (int q = tc; q < kKsGates * kN; q += kKsCols) {
     const int g = q / kN, i = q % kN;
     uint16_t v = 0;
     if (g < ng) v = static_cast<uint16_t>((big[static_cast<size_t>(g0 + g) * (kN + 1) + i] + (1u << 15)) >> 16);
     dig[g][i] = v;
   }
-  const int tc = threadIdx.x;
 #pragma unroll
   for (int j = 0; j < kKsT; ++j) tbl[j][0][tc] = 0u;
-  __syncthreads();
-  const int col = blockIdx.y * kKsCols + tc;
+  asm volatile("bar.sync %0, %1;\n" ::"r"(bar), "r"(kKsCols) : "memory");
+  const int col = tile * kKsCols + tc;
   uint32_t acc[kKsGates];
 #pragma unroll
   for (int g = 0; g < kKsGates; ++g) acc[g] = 0u;
@@ -823,6 +852,111 @@ __global__ void __launch_bounds__(kKsCols)
     uint32_t* out = desc ? desc[g0 + g].out : out_contig + static_cast<size_t>(g0 + g) * (n + 1);
     const uint32_t body = col == n ? big[static_cast<size_t>(g0 + g) * (kN + 1) + kN] : 0u;
     out[col] = acc[g] + body;
+  }
+}
+
+__global__ void __launch_bounds__(kKsCols)
+    keyswitch_kernel(const uint32_t* __restrict__ big, const GateDesc* __restrict__ desc,
+                     uint32_t* __restrict__ out_contig, int count, const uint32_t* __restrict__ ksk, int n) {
+  __shared__ uint16_t dig[kKsGates][kN];
+  __shared__ uint32_t tbl[kKsT][4][kKsCols];  // [level][digit][column of this tile]
+  ks_tile(big, desc, out_contig, count, ksk, n, blockIdx.x * kKsGates, blockIdx.y, dig, tbl, threadIdx.x, 0);
+}
+
+// ------------------------------------------------------------------ device level walker
+// scan_walk_kernel runs a whole batched scan in one cooperative launch (one
+// CTA per SM, all resident): for each segment (a circuit level, or a part of
+// one no larger than the extracted-sample scratch) the CTAs bootstrap its
+// gates (br_body, persistent over gate groups), meet at a grid barrier, then
+// keyswitch them (16-gate x 128-column tiles spread over every 128-thread
+// group of every CTA), and meet again before the next level, whose gates read
+// the outputs just written.  The host issues one launch per scan instead of
+// two per level.  Every barrier wait is bounded (see grid_barrier): a wait
+// that runs out of time raises an error word and every CTA returns, so the
+// GPU context stays usable and the host reads FSQL_ERR_TIMEOUT.
+struct WalkSeg {
+  uint32_t begin, count;  // descriptors [begin, begin + count)
+};
+constexpr int kKsSmem = kKsGates * kN * 2 + kKsT * 4 * kKsCols * 4;  // dig + tbl of one keyswitch tile
+
+__device__ __forceinline__ long long globaltimer_ns() {
+  long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Grid-wide barrier of a cooperative launch.  Thread 0 of every CTA adds one
+// arrival (unless `skip`: a test hook that makes this CTA never arrive) and
+// polls, with a pause between reads, until the arrivals of this barrier are
+// complete (target = (index + 1) x CTAs; the counter only grows), an error
+// is raised, or timeout_ns of device time (or a fixed number of polls)
+// passes, in which case it raises the error and records the barrier index.
+// The fences make every write of the CTAs before the barrier visible to every
+// read after it.  Returns false on error, the same answer in every thread.
+__device__ bool grid_barrier(WalkSync* sync, unsigned int& target, unsigned int index, long long timeout_ns,
+                             bool skip) {
+  __syncthreads();
+  target += gridDim.x;
+  int ok = 1;
+  if (threadIdx.x == 0) {
+    if (!skip) {
+      __threadfence();
+      atomicAdd(&sync->arrived, 1u);
+    }
+    const long long t0 = globaltimer_ns();
+    for (long long polls = 0;; ++polls) {
+      unsigned int a;
+      asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(a) : "l"(&sync->arrived) : "memory");
+      if (a >= target) break;
+      if (*reinterpret_cast<volatile unsigned int*>(&sync->error)) {
+        ok = 0;
+        break;
+      }
+      if (globaltimer_ns() - t0 > timeout_ns || polls > (1ll << 26)) {
+        if (atomicCAS(&sync->error, 0u, 1u) == 0u) sync->barrier = index;
+        ok = 0;
+        break;
+      }
+      __nanosleep(200);
+    }
+    __threadfence();
+  }
+  return __syncthreads_and(ok) != 0;
+}
+
+template <class F, int G, int kPolys>
+__host__ __device__ constexpr int walk_smem() {
+  return br_smem<F, G, kPolys>() > tab_bytes<F>() + digit_tab_bytes<F>() + G * kKsSmem
+             ? br_smem<F, G, kPolys>()
+             : tab_bytes<F>() + digit_tab_bytes<F>() + G * kKsSmem;
+}
+
+template <class F, int G, int kPolys>
+__global__ void __launch_bounds__(G * kGroup, 1)
+    scan_walk_kernel(const GateDesc* __restrict__ desc, const WalkSeg* __restrict__ segs, int nsegs,
+                     const uint64_t* __restrict__ bkhat, const void* __restrict__ gtab, int n, int bg_bits,
+                     uint32_t* __restrict__ big, const uint32_t* __restrict__ ksk, WalkSync* sync,
+                     long long timeout_ns, int skip_block) {
+  extern __shared__ __align__(128) uint8_t smem[];
+  const bool skip = skip_block == static_cast<int>(blockIdx.x);
+  const int grp = threadIdx.x / kGroup, tc = threadIdx.x % kGroup;
+  // keyswitch buffers after the twiddle and digit tables, which every segment keeps
+  uint8_t* ksb = smem + tab_bytes<F>() + digit_tab_bytes<F>() + grp * kKsSmem;
+  auto* dig = reinterpret_cast<uint16_t(*)[kN]>(ksb);
+  auto* tbl = reinterpret_cast<uint32_t(*)[4][kKsCols]>(ksb + kKsGates * kN * 2);
+  unsigned int target = 0, index = 0;
+  for (int sg = 0; sg < nsegs; ++sg) {
+    const WalkSeg seg = segs[sg];
+    const GateDesc* d = desc + seg.begin;
+    const int count = static_cast<int>(seg.count);
+    br_body<F, G, kPolys>(d, count, bkhat, gtab, n, bg_bits, big, sg == 0);
+    if (!grid_barrier(sync, target, index++, timeout_ns, skip)) return;
+    const int items = (count + kKsGates - 1) / kKsGates * kKsTiles;
+    for (int it = blockIdx.x * G + grp; it < items; it += gridDim.x * G) {
+      dev::named_sync(1 + grp);  // the group's previous tile is done with dig and tbl
+      ks_tile(big, d, nullptr, count, ksk, n, (it / kKsTiles) * kKsGates, it % kKsTiles, dig, tbl, tc, 1 + grp);
+    }
+    if (!grid_barrier(sync, target, index++, timeout_ns, skip)) return;
   }
 }
 
@@ -1040,53 +1174,6 @@ long scan_internal_wires(const Netlist& nl) {
   return k;
 }
 
-void scan_descriptors(const Netlist& nl, const ScanIO& io, GateDesc* out, std::vector<size_t>* level_offset) {
-  const size_t W = io.words;
-  const int G = static_cast<int>(nl.type.size());
-  std::vector<long> scratch_index(G, -1);
-  long n_int = 0;
-  for (int g = 0; g < nl.first_mask_gate; ++g)
-    if (nl.n_inputs + g != nl.match_wire) scratch_index[g] = n_int++;
-  const int w = static_cast<int>(io.width);
-  const int nconst = nl.n_const;
-  const int pw = static_cast<int>(io.payload_width);
-  auto gate_out = [&](int g, size_t row) -> uint32_t* {
-    if (g >= nl.first_mask_gate) {
-      const int m = g - nl.first_mask_gate;
-      return io.outs[m / pw] + (row * pw + m % pw) * W;
-    }
-    if (nl.n_inputs + g == nl.match_wire) return io.match + row * W;
-    return io.wires + (row * n_int + scratch_index[g]) * W;
-  };
-  auto wire_ptr = [&](int id, size_t row) -> const uint32_t* {
-    if (id < w) return io.column + (row * io.width + id) * W;
-    if (id < w + nconst) return io.cst + static_cast<size_t>(id - w) * W;
-    if (id < nl.n_inputs) {
-      const int m = id - w - nconst;
-      return io.payloads[m / pw] + (row * pw + m % pw) * W;
-    }
-    return gate_out(id - nl.n_inputs, row);
-  };
-  level_offset->assign(nl.levels + 1, 0);
-  size_t pos = 0;
-  for (int L = 1; L <= nl.levels; ++L) {
-    (*level_offset)[L - 1] = pos;
-    for (int g = 0; g < G; ++g) {
-      if (nl.level[g] != L) continue;
-      for (size_t row = 0; row < io.rows; ++row) {
-        GateDesc& d = out[pos++];
-        d.a = wire_ptr(nl.a[g], row);
-        d.b = wire_ptr(nl.b[g], row);
-        d.c = nl.c[g] >= 0 ? wire_ptr(nl.c[g], row) : nullptr;
-        d.out = gate_out(g, row);
-        d.type = static_cast<uint32_t>(nl.type[g]);
-        d.pad = 0;
-      }
-    }
-  }
-  (*level_offset)[nl.levels] = pos;
-}
-
 void scan_literals(const Netlist& nl, const ScanIO& io, std::vector<OutDesc>* out) {
   out->clear();
   if (nl.literal_outs.empty()) return;
@@ -1147,6 +1234,11 @@ struct Plan {
   const OutDesc* graph_lits = nullptr;
   int graph_br_shape = -1;  // launch shape: 2 x shape index + latency mode
   uint64_t graph_ks_gen = 0;  // keyswitch-first scratch generation the graph was captured with
+  long long graph_walk = -1;  // walker arguments when the graph was captured (0: no walker)
+  // device walker: the plan's segments (levels split at the sample scratch)
+  WalkSeg* d_segs = nullptr;
+  int nsegs = 0;
+  size_t segs_chunk = 0;      // sample-scratch capacity the segments were cut for
   // aggregation plans (SUM, MAX, MIN): key and the buffers they own
   int agg_kind = -1;
   const uint32_t* agg_in = nullptr;
@@ -1158,6 +1250,7 @@ struct Plan {
   uint32_t* own_wires = nullptr;
   ~Plan() {
     if (graph) cudaGraphExecDestroy(graph);
+    cudaFree(d_segs);
     cudaFree(own_desc);
     cudaFree(own_lits);
     cudaFree(own_wires);
@@ -1262,6 +1355,8 @@ int device_init(Ctx& c) {
     set_error(std::string("bootstrapping key conversion: ") + cudaGetErrorString(e));
     return FSQL_ERR_CUDA;
   }
+  CK(cudaMalloc(&c.d_walk_sync, sizeof(WalkSync)));
+  CK(cudaMemset(c.d_walk_sync, 0, sizeof(WalkSync)));
   if (c.engine == FSQL_ENGINE_DUAL_PRIME) {
     // the prime-split kernel's copy of the key and its per-prime twiddle tables
     std::vector<uint8_t> st;
@@ -1275,7 +1370,6 @@ int device_init(Ctx& c) {
     CK(cudaDeviceSynchronize());
     c.key_bytes += bkhat_words * 8 + st.size();
   }
-  CK(cudaEventCreateWithFlags(reinterpret_cast<cudaEvent_t*>(&c.desc_event), cudaEventDisableTiming));
   return FSQL_OK;
 }
 
@@ -1287,14 +1381,17 @@ void device_free(Ctx& c) {
   cudaFree(c.d_tables);
   cudaFree(c.d_bks);
   cudaFree(c.d_tables_split);
+  cudaFree(c.d_walk_sync);
+  c.d_walk_sync = nullptr;
   c.d_bks = nullptr;
   c.d_tables_split = nullptr;
   cudaFree(c.d_big);
   cudaFree(c.d_desc);
   cudaFree(c.d_wires);
   cudaFree(c.d_stage);
-  if (c.h_desc) cudaFreeHost(c.h_desc);
-  if (c.desc_event) cudaEventDestroy(static_cast<cudaEvent_t>(c.desc_event));
+  cudaFree(c.d_prog);
+  c.d_prog = nullptr;
+  c.prog_cap = 0;
   cudaFree(c.d_ks_part);
   c.d_ks_part = nullptr;
   cudaFree(c.d_ks_small);
@@ -1322,8 +1419,6 @@ void device_free(Ctx& c) {
   c.d_desc = nullptr;
   c.d_wires = nullptr;
   c.d_stage = nullptr;
-  c.h_desc = nullptr;
-  c.desc_event = nullptr;
 }
 
 // Launch the blind rotation with G gates per CTA and P gadget rows per step
@@ -1429,6 +1524,60 @@ static cudaError_t launch_br_any(Ctx& c, const GateDesc* d_desc, size_t count, u
   if (sh.gates == 4)
     return launch_br_engine<F, 4, 2>(c.sm_count, d_desc, count, c.d_bkhat, c.d_tables, n, bg, d_big, st);
   return launch_br_engine<F, 2, 2>(c.sm_count, d_desc, count, c.d_bkhat, c.d_tables, n, bg, d_big, st);
+}
+
+// The device level walker over nsegs segments (cooperative launch, one CTA
+// per SM), for the packed two-prime kernel with G gates per CTA.
+template <int G>
+static cudaError_t launch_walk_engine(Ctx& c, const GateDesc* d_desc, const WalkSeg* d_segs, int nsegs,
+                                      uint32_t* d_big, cudaStream_t st) {
+  using F = dev::DualPrime;
+  constexpr int kP = 2;
+  static_assert(walk_smem<F, G, kP>() <= 227 * 1024, "walker shared memory over budget");
+  static bool attr_set[64] = {};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+  if (!attr_set[dev]) {
+    const cudaError_t e = cudaFuncSetAttribute(scan_walk_kernel<F, G, kP>,
+                                               cudaFuncAttributeMaxDynamicSharedMemorySize, walk_smem<F, G, kP>());
+    if (e != cudaSuccess) return e;
+    attr_set[dev] = true;
+  }
+  cudaError_t e = cudaMemsetAsync(c.d_walk_sync, 0, sizeof(WalkSync), st);
+  if (e != cudaSuccess) return e;
+  int n = static_cast<int>(c.p.n), bg = static_cast<int>(c.p.bg_bits), skip = c.walk_skip_block;
+  long long tmo = static_cast<long long>(c.walk_timeout_ms * 1e6);
+  const uint64_t* bk = c.d_bkhat;
+  const void* tb = c.d_tables;
+  const uint32_t* ksk = c.d_ksk;
+  WalkSync* sy = c.d_walk_sync;
+  void* args[] = {&d_desc, &d_segs, &nsegs, &bk, &tb, &n, &bg, &d_big, &ksk, &sy, &tmo, &skip};
+  return cudaLaunchCooperativeKernel(reinterpret_cast<const void*>(scan_walk_kernel<F, G, kP>), dim3(c.sm_count),
+                                     dim3(G * kGroup), args, walk_smem<F, G, kP>(), st);
+}
+
+// Whether a scan's levels can run on the device walker: the two-prime engine
+// on a packed launch shape, and every segment large enough for the
+// persistent multi-gate kernel (at least two gates per SM).
+bool walk_supported(const Ctx& c) {
+  const BrShape sh = kBrShapes[c.br_shape];
+  return c.walk_mode && c.engine == FSQL_ENGINE_DUAL_PRIME && sh.kind == 0 && (sh.gates == 2 || sh.gates == 3) &&
+         c.d_walk_sync;
+}
+
+int launch_walk(Ctx& c, const GateDesc* d_desc, const WalkSeg* d_segs, int nsegs, uint32_t* d_big, void* stream) {
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  LaunchTimer tm(c, st);
+  const int g = kBrShapes[c.br_shape].gates;
+  cudaError_t e = g == 2 ? launch_walk_engine<2>(c, d_desc, d_segs, nsegs, d_big, st)
+                         : launch_walk_engine<3>(c, d_desc, d_segs, nsegs, d_big, st);
+  if (e != cudaSuccess) {
+    set_error(std::string("walker launch: ") + cudaGetErrorString(e));
+    return FSQL_ERR_CUDA;
+  }
+  tm.done(true, 0);
+  return FSQL_OK;
 }
 
 int launch_blind_rotate(Ctx& c, const GateDesc* d_desc, size_t count, uint32_t* d_big, void* stream) {
@@ -1691,22 +1840,6 @@ int prepare_scan(Ctx& c, const uint32_t* d_column, size_t rows, uint32_t width, 
   pl->ks_first = ks_first;
 
   const size_t total = rows * static_cast<size_t>(G);
-  if (total > c.h_desc_cap) {
-    if (c.h_desc) {
-      cudaEventSynchronize(static_cast<cudaEvent_t>(c.desc_event));
-      cudaFreeHost(c.h_desc);
-    }
-    c.h_desc = nullptr;
-    c.h_desc_cap = 0;
-    if (cudaMallocHost(&c.h_desc, total * sizeof(GateDesc)) != cudaSuccess) {
-      fsql::set_error("pinned staging allocation failed");
-      delete pl;
-      return FSQL_ERR_OOM;
-    }
-    c.h_desc_cap = total;
-  } else {
-    cudaEventSynchronize(static_cast<cudaEvent_t>(c.desc_event));  // previous upload done
-  }
   fsql::ScanIO io;
   io.column = d_column;
   io.rows = rows;
@@ -1720,8 +1853,25 @@ int prepare_scan(Ctx& c, const uint32_t* d_column, size_t rows, uint32_t width, 
   io.outs = d_out_payloads;
   io.wires = c.d_wires;
   io.words = W;
-  fsql::scan_descriptors(nl, io, c.h_desc, &pl->level_offset);
+  // the scan program (netlist + pointers, a few KB): descriptors are
+  // generated from it on the device
+  std::vector<uint8_t> prog;
+  if (!fsql::build_scan_program(nl, io, &prog, &pl->level_offset)) {
+    delete pl;
+    return arg_error("too many payload columns for a scan program");
+  }
   pl->total = pl->level_offset.back();
+  if (prog.size() > c.prog_cap) {
+    cudaFree(c.d_prog);
+    c.d_prog = nullptr;
+    c.prog_cap = 0;
+    if (cudaMalloc(&c.d_prog, prog.size()) != cudaSuccess) {
+      fsql::set_error("scan program allocation failed");
+      delete pl;
+      return FSQL_ERR_OOM;
+    }
+    c.prog_cap = prog.size();
+  }
   int rc = fsql::ensure_desc(c, total);
   if (rc) {
     delete pl;
@@ -1751,9 +1901,10 @@ int prepare_scan(Ctx& c, const uint32_t* d_column, size_t rows, uint32_t width, 
       return FSQL_ERR_CUDA;
     }
   }
-  if (cudaMemcpyAsync(c.d_desc, c.h_desc, total * sizeof(GateDesc), cudaMemcpyHostToDevice, st) != cudaSuccess ||
-      cudaEventRecord(static_cast<cudaEvent_t>(c.desc_event), st) != cudaSuccess) {
-    fsql::set_error("descriptor upload failed");
+  // pageable source: the copy is staged before cudaMemcpyAsync returns
+  if (cudaMemcpyAsync(c.d_prog, prog.data(), prog.size(), cudaMemcpyHostToDevice, st) != cudaSuccess ||
+      fsql::launch_gen_desc(c.d_prog, c.d_desc, total, st) != FSQL_OK) {
+    fsql::set_error("scan program upload or descriptor generation failed");
     delete pl;
     return FSQL_ERR_CUDA;
   }
@@ -1883,7 +2034,37 @@ int execute_plan(Ctx* c, fsql::Plan& pl, const fsql::GateDesc* d_desc, const fsq
     }
     return fsql::launch_literals(d_lits, pl.n_lits, n, stream);
   }
+  // the device walker (one launch for all levels) when the context asks for
+  // it and every segment keeps the persistent kernel busy
+  bool walk = !pl.ks_first && fsql::walk_supported(*c);
+  for (size_t L = 0; walk && L + 1 < pl.level_offset.size(); ++L)
+    if (pl.level_offset[L + 1] - pl.level_offset[L] < static_cast<size_t>(2 * c->sm_count)) walk = false;
+  // the walker's kernel arguments a captured graph holds (0: no walker)
+  const long long walk_key =
+      walk ? static_cast<long long>(c->walk_timeout_ms * 1e3) * 4099 + c->walk_skip_block + 2 : 0;
+  if (walk && (pl.nsegs == 0 || pl.segs_chunk != chunk)) {
+    std::vector<fsql::WalkSeg> segs;
+    for (size_t L = 0; L + 1 < pl.level_offset.size(); ++L)
+      for (size_t b = pl.level_offset[L]; b < pl.level_offset[L + 1]; b += chunk)
+        segs.push_back({static_cast<uint32_t>(b), static_cast<uint32_t>(std::min(chunk, pl.level_offset[L + 1] - b))});
+    cudaFree(pl.d_segs);
+    pl.d_segs = nullptr;
+    pl.nsegs = 0;
+    if (cudaMalloc(&pl.d_segs, segs.size() * sizeof(fsql::WalkSeg)) != cudaSuccess ||
+        cudaMemcpy(pl.d_segs, segs.data(), segs.size() * sizeof(fsql::WalkSeg), cudaMemcpyHostToDevice) !=
+            cudaSuccess) {
+      fsql::set_error("walker segment upload failed");
+      return FSQL_ERR_CUDA;
+    }
+    pl.nsegs = static_cast<int>(segs.size());
+    pl.segs_chunk = chunk;
+  }
   auto launch_all = [&](void* st) -> int {
+    if (walk) {
+      const int r = fsql::launch_walk(*c, d_desc, pl.d_segs, pl.nsegs, c->d_big, st);
+      if (r) return r;
+      return fsql::launch_literals(d_lits, pl.n_lits, n, st);
+    }
     for (size_t L = 0; L + 1 < pl.level_offset.size(); ++L) {
       const int r = gates(d_desc + pl.level_offset[L], pl.level_offset[L + 1] - pl.level_offset[L], st);
       if (r) return r;
@@ -1895,7 +2076,7 @@ int execute_plan(Ctx* c, fsql::Plan& pl, const fsql::GateDesc* d_desc, const fsq
   fsql::Plan& mp = pl;
   if (!mp.graph || mp.graph_desc != d_desc || mp.graph_big != c->d_big || mp.graph_lits != d_lits ||
       mp.graph_br_shape != 2 * c->br_shape + (c->latency_mode ? 1 : 0) ||
-      (pl.ks_first && mp.graph_ks_gen != c->ks_gen)) {
+      (pl.ks_first && mp.graph_ks_gen != c->ks_gen) || mp.graph_walk != walk_key) {
     if (mp.graph) cudaGraphExecDestroy(mp.graph);
     mp.graph = nullptr;
     cudaStream_t cs = static_cast<cudaStream_t>(c->capture_stream);
@@ -1924,6 +2105,7 @@ int execute_plan(Ctx* c, fsql::Plan& pl, const fsql::GateDesc* d_desc, const fsq
     mp.graph_lits = d_lits;
     mp.graph_br_shape = 2 * c->br_shape + (c->latency_mode ? 1 : 0);
     mp.graph_ks_gen = c->ks_gen;
+    mp.graph_walk = walk_key;
   }
   if (cudaGraphLaunch(mp.graph, static_cast<cudaStream_t>(stream)) != cudaSuccess) {
     fsql::set_error("scan graph launch failed");
@@ -2173,6 +2355,44 @@ int fsql_scan_select_host(fsql_ctx* ctx, const uint32_t* h_column, size_t rows, 
   if (!ok || cudaStreamSynchronize(st) != cudaSuccess) {
     fsql::set_error(std::string("device to host copy or scan failed: ") + cudaGetErrorString(cudaGetLastError()));
     return FSQL_ERR_CUDA;
+  }
+  return FSQL_OK;
+}
+
+int fsql_ctx_set_walk(fsql_ctx* ctx, int on, double timeout_ms) {
+  Ctx* c = device_ctx(ctx);
+  if (!c) return FSQL_ERR_ARG;
+  if (!(timeout_ms > 0.0) || timeout_ms > 600000.0) return arg_error("walker timeout must be in (0, 600000] ms");
+  std::lock_guard<std::mutex> lk(c->mu);
+  c->walk_mode = on != 0;
+  c->walk_timeout_ms = timeout_ms;
+  return FSQL_OK;
+}
+
+int fsql_debug_walk_skip_block(fsql_ctx* ctx, int block) {
+  Ctx* c = device_ctx(ctx);
+  if (!c) return FSQL_ERR_ARG;
+  std::lock_guard<std::mutex> lk(c->mu);
+  c->walk_skip_block = block < 0 ? -1 : block;
+  return FSQL_OK;
+}
+
+int fsql_walk_status(fsql_ctx* ctx, void* stream, unsigned int* barrier) {
+  Ctx* c = device_ctx(ctx);
+  if (!c) return FSQL_ERR_ARG;
+  if (barrier) *barrier = 0;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  fsql::WalkSync h{};
+  if (cudaStreamSynchronize(st) != cudaSuccess ||
+      cudaMemcpy(&h, c->d_walk_sync, sizeof(h), cudaMemcpyDeviceToHost) != cudaSuccess) {
+    fsql::set_error(std::string("walker status: ") + cudaGetErrorString(cudaGetLastError()));
+    return FSQL_ERR_CUDA;
+  }
+  if (h.error) {
+    if (barrier) *barrier = h.barrier;
+    fsql::set_error("a grid-barrier wait of the level walker ran out of time (barrier " + std::to_string(h.barrier) +
+                    "); the scan's outputs are incomplete");
+    return FSQL_ERR_TIMEOUT;
   }
   return FSQL_OK;
 }

@@ -320,17 +320,74 @@ __device__ __forceinline__ void gs_stage(uint64_t (&x)[P][8], TwOf tw) {
   }
 }
 
+// First two forward stages of a digit polynomial by table lookup (two-prime
+// engine).  A thread's registers 0..7 hold elements t + 128k; stages 1 and 2
+// (distances 512 and 256, twiddles w1 = f[1], w2a = f[2] for registers 0-3,
+// w2b = f[3] for 4-7) combine the four digits d0..d3 of registers
+// (a, a+2, a+4, a+6), a = 0, 1, into
+//   z_a   = d0 + w1 d2 + w2a d1 + w2a w1 d3     z_a+2 = d0 + w1 d2 - w2a d1 - w2a w1 d3
+//   z_a+4 = d0 - w1 d2 + w2b d1 - w2b w1 d3     z_a+6 = d0 - w1 d2 - w2b d1 + w2b w1 d3
+// (mod each prime).  A digit takes 2^bg <= 128 values, so each product is
+// read from a table of (u - 2^(bg-1)) m mod p for the five multipliers m
+// (tab[m][u], both residues packed, canonical), built once per CTA by
+// build_digit_tables: five lookups and adds replace eight Shoup products per
+// group.  Outputs stay below 6p, the bound the lazy transform has after two
+// stages from digits below 2p, so the remaining stages are unchanged.
+constexpr int kDigitTabs = 5;
+constexpr int kDigitTabSize = 128;
+__device__ __forceinline__ void digit_stages12(const uint32_t (&u)[8], uint64_t (&z)[8], uint32_t half,
+                                               const uint64_t* __restrict__ tab) {
+  const uint64_t off2 = pack(2 * kP1, 2 * kP2);
+#pragma unroll
+  for (int a = 0; a < 2; ++a) {
+    const uint64_t d0 = DualPrime::from_digit(u[a], half);
+    const uint64_t A = tab[0 * kDigitTabSize + u[a + 4]];
+    const uint64_t Bv = tab[1 * kDigitTabSize + u[a + 2]];
+    const uint64_t C = tab[2 * kDigitTabSize + u[a + 6]];
+    const uint64_t D = tab[3 * kDigitTabSize + u[a + 2]];
+    const uint64_t E = tab[4 * kDigitTabSize + u[a + 6]];
+    // every lane stays in [0, 2^32): the packed 64-bit sums carry nothing across lanes
+    z[a] = d0 + A + Bv + C;
+    z[a + 2] = d0 + A + off2 - Bv - C;
+    z[a + 4] = d0 + off2 - A + D - E + off2;
+    z[a + 6] = d0 + off2 - A - D + E + off2;
+  }
+}
+// tab[m][u] = (u - half) * m mod p for m = w1, w2a, w2a w1, w2b, w2b w1
+// (the residues of the stage twiddles f[1], f[2], f[3]), both primes packed.
+template <class Tab>
+__device__ __forceinline__ void build_digit_tables(uint64_t* tab, const Tab& T, uint32_t half, int tid,
+                                                   int nthreads) {
+  for (int e = tid; e < kDigitTabs * kDigitTabSize; e += nthreads) {
+    const int m = e / kDigitTabSize, u = e % kDigitTabSize;
+    uint32_t r[2];
+#pragma unroll
+    for (int pr = 0; pr < 2; ++pr) {
+      const uint64_t p = pr ? kP2 : kP1;
+      const uint64_t w1 = pr ? T.f_small[1].z : T.f_small[1].x;
+      const uint64_t w2a = pr ? T.f_small[2].z : T.f_small[2].x;
+      const uint64_t w2b = pr ? T.f_small[3].z : T.f_small[3].x;
+      const uint64_t mult = m == 0 ? w1 : m == 1 ? w2a : m == 2 ? w2a * w1 % p : m == 3 ? w2b : w2b * w1 % p;
+      const uint64_t d = (static_cast<uint64_t>(u) + p - half) % p;
+      r[pr] = static_cast<uint32_t>(d * mult % p);
+    }
+    tab[e] = pack(r[0], r[1]);
+  }
+}
+
 // Forward transform of P polynomials: layout F1 -> layout F4.  bufs: this
 // group's two exchange buffers of B polynomials each; parity: which one the
 // next exchange uses.  Its first exchange writes across warps, so the caller
 // separates it from the exchanges of an earlier transform by a group-wide
-// barrier.
-template <class F, int P, int B, int NB = 2>
+// barrier.  kFrom3: the first two stages were done already (digit_stages12).
+template <class F, int P, int B, int NB = 2, bool kFrom3 = false>
 __device__ __forceinline__ void ntt_forward(uint64_t (&x)[P][8], uint64_t* bufs, int& parity,
                                             const typename F::Tables& T, int t, int bar) {
   // F1: distances 512, 256, 128 (register bits 2, 1, 0), twiddles uniform
-  ct_stage<F, P, 4>(x, [&](int) { return T.f_small[1]; });
-  ct_stage<F, P, 2>(x, [&](int k) { return T.f_small[2 + (k >> 2)]; });
+  if (!kFrom3) {
+    ct_stage<F, P, 4>(x, [&](int) { return T.f_small[1]; });
+    ct_stage<F, P, 2>(x, [&](int k) { return T.f_small[2 + (k >> 2)]; });
+  }
   ct_stage<F, P, 1>(x, [&](int k) { return T.f_small[4 + (k >> 1)]; });
   exchange<P, B, NB, LF1, LF2, false>(x, bufs, parity, t, bar);
   // F2: distances 64, 32, 16

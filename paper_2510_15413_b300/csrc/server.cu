@@ -12,6 +12,17 @@
 // budget, and joins the following launches (continuous batching); a finished
 // query frees its scratch at once.  Results are independent of the mix: each
 // gate's output depends only on its own inputs and the keys.
+//
+// Pipelining.  All device work of the server goes to one stream, so a round
+// that reads the outputs of an earlier round is ordered after it by the
+// stream itself.  The worker therefore enqueues round r + 1 (its descriptor
+// gather, its launches, the outputs no gate writes of queries that finish in
+// it) while round r runs, and only then waits for round r's completion event
+// to time-stamp and release the queries that finished in it; admission
+// copies a query's scan program (its netlist and buffer pointers, a few KB)
+// asynchronously and generates its descriptors on the device.  The GPU is
+// never idle between rounds while there is work, and no round waits for the
+// host's bookkeeping.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -82,12 +93,14 @@ struct Query {
   Netlist nl;
   std::vector<size_t> level_offset;
   size_t total_gates = 0;
-  size_t bytes = 0, off = 0;  // pool block: gate descriptors, output descriptors, wires
+  size_t bytes = 0, off = 0;  // pool block: scan program, gate descriptors, output descriptors, wires
   GateDesc* d_desc = nullptr;
   OutDesc* d_lits = nullptr;  // outputs no gate writes (plaintext constants)
   size_t n_lits = 0;
-  int level = 0;              // next level to bootstrap
-  size_t done_in_level = 0;   // gates of that level already launched
+  int level = 0;              // next level to enqueue
+  size_t done_in_level = 0;   // gates of that level already enqueued
+  bool all_issued = false;    // every gate and the literal outputs enqueued
+  int inflight = 0;           // enqueued rounds holding work of this query, not yet seen complete
   int state = Q_WAITING;
   bool cancel = false;
   Clock::time_point t_submit, t_done;
@@ -96,11 +109,21 @@ struct Query {
 size_t round256(size_t b) { return (b + 255) / 256 * 256; }
 
 size_t query_bytes(const Netlist& nl, const fsql_query& q, size_t words) {
+  const size_t prog = scan_program_bytes(nl);
   const size_t desc = q.rows * nl.type.size() * sizeof(GateDesc);
   const size_t lits = q.rows * nl.literal_outs.size() * sizeof(OutDesc);
   const size_t wires = q.rows * static_cast<size_t>(scan_internal_wires(nl)) * words * 4;
-  return round256(desc) + round256(lits) + wires;
+  return round256(prog) + round256(desc) + round256(lits) + wires;
 }
+
+// One enqueued round: its queries and the events around its device work.
+struct Round {
+  cudaEvent_t start = nullptr, end = nullptr;
+  std::vector<Query*> queries;
+  size_t gates = 0;
+};
+
+constexpr int kPipelineDepth = 2;  // rounds enqueued ahead of the one being waited for
 
 }  // namespace
 
@@ -112,6 +135,7 @@ struct Server {
   GateDesc* d_round = nullptr;
   uint32_t* d_big = nullptr;
   cudaStream_t stream = nullptr;
+  std::vector<cudaEvent_t> free_events;
   std::mutex mu;
   std::condition_variable cv;
   std::thread worker;
@@ -119,6 +143,7 @@ struct Server {
   uint64_t next_id = 1;
   std::deque<Query*> waiting;
   std::vector<Query*> running;
+  std::deque<Round> inflight;
   std::map<uint64_t, Query*> all;
   // statistics
   uint64_t rounds = 0, gates = 0, completed = 0;
@@ -126,7 +151,20 @@ struct Server {
   std::vector<double> latencies_ms;
   std::string error;
 
-  // Admit waiting queries in arrival order while their blocks fit (caller holds mu).
+  cudaEvent_t get_event() {
+    if (!free_events.empty()) {
+      cudaEvent_t e = free_events.back();
+      free_events.pop_back();
+      return e;
+    }
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+    return e;
+  }
+
+  // Admit waiting queries in arrival order while their blocks fit (caller
+  // holds mu): copy the scan program, generate the descriptors on the device,
+  // copy the descriptors of the outputs no gate writes (all on the stream).
   void admit_locked() {
     while (!waiting.empty()) {
       Query* q = waiting.front();
@@ -138,10 +176,12 @@ struct Server {
       size_t off = 0;
       if (!pool.alloc(q->bytes, &off)) break;
       q->off = off;
-      q->d_desc = reinterpret_cast<GateDesc*>(d_pool + off);
+      uint8_t* base = d_pool + off;
+      const size_t prog_bytes = round256(scan_program_bytes(q->nl));
       const size_t desc_bytes = round256(q->total_gates * sizeof(GateDesc));
       const size_t lit_bytes = round256(q->q.rows * q->nl.literal_outs.size() * sizeof(OutDesc));
-      q->d_lits = reinterpret_cast<OutDesc*>(d_pool + off + desc_bytes);
+      q->d_desc = reinterpret_cast<GateDesc*>(base + prog_bytes);
+      q->d_lits = reinterpret_cast<OutDesc*>(base + prog_bytes + desc_bytes);
       ScanIO io;
       io.column = q->q.d_column;
       io.rows = q->q.rows;
@@ -153,18 +193,22 @@ struct Server {
       io.payload_width = q->q.payload_width;
       io.match = q->q.d_match;
       io.outs = q->q.d_out_payloads;
-      io.wires = reinterpret_cast<uint32_t*>(d_pool + off + desc_bytes + lit_bytes);
+      io.wires = reinterpret_cast<uint32_t*>(base + prog_bytes + desc_bytes + lit_bytes);
       io.words = ctx->p.n + 1;
-      std::vector<GateDesc> h(q->total_gates);
-      scan_descriptors(q->nl, io, h.data(), &q->level_offset);
+      std::vector<uint8_t> prog;
       std::vector<OutDesc> hl;
       scan_literals(q->nl, io, &hl);
       q->n_lits = hl.size();
-      if (cudaMemcpy(q->d_desc, h.data(), h.size() * sizeof(GateDesc), cudaMemcpyHostToDevice) != cudaSuccess ||
-          (!hl.empty() &&
-           cudaMemcpy(q->d_lits, hl.data(), hl.size() * sizeof(OutDesc), cudaMemcpyHostToDevice) != cudaSuccess)) {
+      // pageable sources: each copy is staged before cudaMemcpyAsync returns
+      const bool ok = build_scan_program(q->nl, io, &prog, &q->level_offset) &&
+                      cudaMemcpyAsync(base, prog.data(), prog.size(), cudaMemcpyHostToDevice, stream) == cudaSuccess &&
+                      launch_gen_desc(base, q->d_desc, q->total_gates, stream) == FSQL_OK &&
+                      (hl.empty() || cudaMemcpyAsync(q->d_lits, hl.data(), hl.size() * sizeof(OutDesc),
+                                                     cudaMemcpyHostToDevice, stream) == cudaSuccess);
+      if (!ok) {
         pool.release(q->off, q->bytes);
         q->state = Q_FAILED;
+        error = "admission copy failed";
         waiting.pop_front();
         continue;
       }
@@ -174,13 +218,12 @@ struct Server {
     }
   }
 
-  // A query whose gates are all done: write the outputs no gate writes, then
-  // mark it done (caller holds mu; the literal kernel is short).
-  void finish_locked(Query* q) {
-    if (q->n_lits && (launch_literals(q->d_lits, q->n_lits, static_cast<int>(ctx->p.n), stream) != FSQL_OK ||
-                      cudaStreamSynchronize(stream) != cudaSuccess)) {
-      error = "literal outputs failed";
-      q->state = Q_FAILED;
+  // A query whose last work completed (caller holds mu).
+  void complete_locked(Query* q) {
+    pool.release(q->off, q->bytes);
+    if (q->state == Q_FAILED) return;
+    if (q->cancel) {
+      q->state = Q_CANCELLED;
       return;
     }
     q->state = Q_DONE;
@@ -189,15 +232,30 @@ struct Server {
     latencies_ms.push_back(std::chrono::duration<double, std::milli>(q->t_done - q->t_submit).count());
   }
 
-  void release_finished_locked() {
-    for (auto it = running.begin(); it != running.end();) {
-      if ((*it)->state == Q_DONE || (*it)->state == Q_FAILED) {
-        pool.release((*it)->off, (*it)->bytes);
-        it = running.erase(it);
-      } else {
-        ++it;
+  // Wait for the oldest enqueued round and retire the queries it finishes
+  // (called with lk held; waits without it).
+  void retire_oldest(std::unique_lock<std::mutex>& lk) {
+    Round r = std::move(inflight.front());
+    inflight.pop_front();
+    lk.unlock();
+    cudaError_t e = cudaEventSynchronize(r.end);
+    float ms = 0.f;
+    if (e == cudaSuccess && r.start) e = cudaEventElapsedTime(&ms, r.start, r.end);
+    lk.lock();
+    busy_ms += ms;
+    if (e != cudaSuccess) {
+      error = std::string("round failed: ") + cudaGetErrorString(e);
+      for (Query* q : r.queries) q->state = Q_FAILED;
+    }
+    for (Query* q : r.queries) {
+      if (--q->inflight == 0 && (q->all_issued || q->cancel || q->state == Q_FAILED)) {
+        complete_locked(q);
+        running.erase(std::find(running.begin(), running.end(), q));
       }
     }
+    if (r.start) free_events.push_back(r.start);
+    free_events.push_back(r.end);
+    cv.notify_all();
   }
 
   void run() {
@@ -207,38 +265,33 @@ struct Server {
       size_t start, n;
     };
     std::unique_lock<std::mutex> lk(mu);
-    while (!stop) {
-      admit_locked();
-      // drop cancelled running queries at the round boundary
+    while (!stop || !inflight.empty()) {
+      if (!stop) admit_locked();
+      // cancelled or failed queries with nothing in flight leave now
       for (auto it = running.begin(); it != running.end();) {
-        if ((*it)->cancel) {
-          pool.release((*it)->off, (*it)->bytes);
-          (*it)->state = Q_CANCELLED;
+        Query* q = *it;
+        if ((q->cancel || q->state == Q_FAILED) && q->inflight == 0) {
+          complete_locked(q);
           it = running.erase(it);
         } else {
           ++it;
         }
       }
-      // queries with no gate left (a plaintext constant can leave none at all)
-      bool finished = false;
-      for (Query* q : running)
-        if (q->state == Q_RUNNING && q->level == q->nl.levels) {
-          finish_locked(q);
-          finished = true;
-        }
-      if (finished) {
-        release_finished_locked();
-        cv.notify_all();
-      }
-      if (running.empty()) {
-        cv.wait_for(lk, std::chrono::milliseconds(50));
+      if (stop) {  // no new round after a stop: wait for the enqueued ones
+        if (!inflight.empty()) retire_oldest(lk);
         continue;
       }
       // gather the next level (part) of every running query, oldest first
       std::vector<Seg> segs;
+      std::vector<Query*> lit_only;  // queries whose only remaining work is their literal outputs
       size_t total = 0;
       for (Query* q : running) {
-        if (total >= max_batch) break;
+        if (q->all_issued || q->cancel || q->state == Q_FAILED) continue;
+        if (q->level == q->nl.levels) {
+          lit_only.push_back(q);
+          continue;
+        }
+        if (total >= max_batch) continue;
         const size_t lb = q->level_offset[q->level], le = q->level_offset[q->level + 1];
         const size_t start = lb + q->done_in_level;
         const size_t n = std::min(le - start, max_batch - total);
@@ -246,41 +299,66 @@ struct Server {
         segs.push_back({q, start, n});
         total += n;
       }
-      lk.unlock();
-      const auto t0 = Clock::now();
-      bool ok = true;
-      size_t pos = 0;
-      for (const Seg& s : segs) {
-        ok = ok && cudaMemcpyAsync(d_round + pos, s.q->d_desc + s.start, s.n * sizeof(GateDesc),
-                                   cudaMemcpyDeviceToDevice, stream) == cudaSuccess;
-        pos += s.n;
+      if (segs.empty() && lit_only.empty()) {
+        if (!inflight.empty()) {
+          retire_oldest(lk);
+        } else if (!stop) {
+          cv.wait_for(lk, std::chrono::milliseconds(50));
+        }
+        continue;
       }
-      if (ok) {
-        std::lock_guard<std::mutex> ctx_lk(ctx->mu);  // the context's launch bookkeeping is shared
-        ok = launch_gates(*ctx, d_round, total, d_big, stream) == FSQL_OK;
-      }
-      if (ok) ok = cudaStreamSynchronize(stream) == cudaSuccess;
-      const auto t1 = Clock::now();
-      lk.lock();
-      busy_ms += std::chrono::duration<double, std::milli>(t1 - t0).count();
-      ++rounds;
-      gates += total;
-      if (!ok) {
-        error = std::string("round failed: ") + cudaGetErrorString(cudaGetLastError());
-        for (const Seg& s : segs) s.q->state = Q_FAILED;
-      }
-      for (const Seg& s : segs) {
-        Query* q = s.q;
-        if (q->state == Q_FAILED) continue;
-        q->done_in_level += s.n;
+      // advance the bookkeeping as enqueued; a query whose last gates are in
+      // this round also gets its literal outputs enqueued after them
+      Round r;
+      r.gates = total;
+      std::vector<Query*> finishing;
+      for (const Seg& sg : segs) {
+        Query* q = sg.q;
+        q->done_in_level += sg.n;
         if (q->level_offset[q->level] + q->done_in_level == q->level_offset[q->level + 1]) {
           ++q->level;
           q->done_in_level = 0;
         }
-        if (q->level == q->nl.levels) finish_locked(q);
+        if (q->level == q->nl.levels) finishing.push_back(q);
       }
-      release_finished_locked();
-      cv.notify_all();
+      for (Query* q : lit_only) finishing.push_back(q);
+      for (const Seg& sg : segs) r.queries.push_back(sg.q);
+      for (Query* q : lit_only) r.queries.push_back(q);
+      for (Query* q : finishing) q->all_issued = true;
+      for (Query* q : r.queries) ++q->inflight;
+      r.start = get_event();
+      r.end = get_event();
+      lk.unlock();
+      bool ok = r.end != nullptr;
+      if (ok && r.start) ok = cudaEventRecord(r.start, stream) == cudaSuccess;
+      size_t pos = 0;
+      for (const Seg& sg : segs) {
+        ok = ok && cudaMemcpyAsync(d_round + pos, sg.q->d_desc + sg.start, sg.n * sizeof(GateDesc),
+                                   cudaMemcpyDeviceToDevice, stream) == cudaSuccess;
+        pos += sg.n;
+      }
+      if (ok && total) {
+        std::lock_guard<std::mutex> ctx_lk(ctx->mu);  // the context's launch bookkeeping is shared
+        ok = launch_gates(*ctx, d_round, total, d_big, stream) == FSQL_OK;
+      }
+      for (Query* q : finishing)
+        if (ok && q->n_lits) ok = launch_literals(q->d_lits, q->n_lits, static_cast<int>(ctx->p.n), stream) == FSQL_OK;
+      if (ok) ok = cudaEventRecord(r.end, stream) == cudaSuccess;
+      lk.lock();
+      ++rounds;
+      gates += total;
+      if (!ok) {
+        error = std::string("round launch failed: ") + cudaGetErrorString(cudaGetLastError());
+        for (Query* q : r.queries) q->state = Q_FAILED;
+        // nothing of this round can be waited for: undo its in-flight marks
+        for (Query* q : r.queries) --q->inflight;
+        if (r.start) free_events.push_back(r.start);
+        if (r.end) free_events.push_back(r.end);
+        cv.notify_all();
+        continue;
+      }
+      inflight.push_back(std::move(r));
+      while (static_cast<int>(inflight.size()) > kPipelineDepth) retire_oldest(lk);
     }
   }
 };
@@ -453,6 +531,7 @@ void fsql_server_destroy(fsql_server* server) {
   if (s->worker.joinable()) s->worker.join();
   cudaSetDevice(s->ctx->device);
   cudaStreamSynchronize(s->stream);
+  for (cudaEvent_t e : s->free_events) cudaEventDestroy(e);
   cudaStreamDestroy(s->stream);
   cudaFree(s->d_pool);
   cudaFree(s->d_round);

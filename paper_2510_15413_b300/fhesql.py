@@ -25,6 +25,7 @@ ENGINES = {"default": -1, "goldilocks": 0, "dual_prime": 1}
 API = ["fsql_params_default", "fsql_params_toy", "fsql_ctx_create", "fsql_ctx_create_engine", "fsql_ctx_engine",
        "fsql_ctx_set_br_gates", "fsql_ctx_br_gates", "fsql_ctx_set_br_shape", "fsql_ctx_br_shape",
        "fsql_br_shape_info", "fsql_ctx_set_latency_mode", "fsql_autotune", "fsql_measure_alu_peaks",
+       "fsql_ctx_set_walk", "fsql_walk_status", "fsql_debug_walk_skip_block",
        "fsql_ctx_destroy", "fsql_ctx_params",
        "fsql_ctx_device_bytes", "fsql_export_keys", "fsql_encrypt", "fsql_encrypt_bits", "fsql_encrypt_uint",
        "fsql_phase", "fsql_decrypt_bits", "fsql_decrypt_uint", "fsql_gate_batch", "fsql_blind_rotate_extract",
@@ -98,6 +99,9 @@ def load() -> C.CDLL:
         "fsql_ctx_set_latency_mode": (i32, [vp, i32]),
         "fsql_ctx_br_gates": (i32, [vp, C.POINTER(i32)]),
         "fsql_ctx_set_br_shape": (i32, [vp, i32]),
+        "fsql_ctx_set_walk": (i32, [vp, i32, C.c_double]),
+        "fsql_walk_status": (i32, [vp, vp, C.POINTER(C.c_uint)]),
+        "fsql_debug_walk_skip_block": (i32, [vp, i32]),
         "fsql_ctx_br_shape": (i32, [vp, C.POINTER(i32)]),
         "fsql_br_shape_info": (i32, [i32, C.POINTER(i32), C.POINTER(i32), C.POINTER(i32), C.POINTER(i32)]),
         "fsql_autotune": (i32, [vp, sz, vp, C.POINTER(i32), C.POINTER(C.c_double)]),
@@ -304,6 +308,18 @@ class Context:
     @br_shape.setter
     def br_shape(self, shape: int) -> None:
         _check(load().fsql_ctx_set_br_shape(self._h, int(shape)))
+
+    def set_walk(self, on: bool, timeout_ms: float = 2000.0) -> None:
+        """Batched scans as one device-walked launch (bounded grid barriers)."""
+        _check(load().fsql_ctx_set_walk(self._h, int(bool(on)), float(timeout_ms)))
+
+    def walk_status(self, stream=None) -> None:
+        """Raises FsqlError(FSQL_ERR_TIMEOUT) if a walker barrier wait ran out of time."""
+        b = C.c_uint()
+        _check(load().fsql_walk_status(self._h, _stream(stream), C.byref(b)))
+
+    def debug_walk_skip_block(self, block: int) -> None:
+        _check(load().fsql_debug_walk_skip_block(self._h, int(block)))
 
     def autotune(self, probe_gates: int = 0, stream=None):
         """Pick the fastest blind-rotation launch shape; returns (shape index, {shape: ms})."""
