@@ -65,6 +65,7 @@ def parse():
     ap.add_argument("--verify-rows", type=int, default=2,
                     help="rows of the timed scan the CPU oracle recomputes word for word (first, matching, last...)")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default launch shape")
+    ap.add_argument("--walk", action="store_true", help="batched scans as one device-walked launch")
     ap.add_argument("--br-shape", type=int, default=None,
                     help="blind-rotation launch shape index (implies --no-autotune)")
     ap.add_argument("--seed", type=int, default=1)
@@ -208,7 +209,9 @@ def oracle_gates_per_row(table) -> int:
 def pick_shape(ctx, args):
     """The blind-rotation launch shape: given on the command line, else the
     library's autotuner (timed on synthetic gates before anything is timed
-    here), else the context's default."""
+    here), else the context's default; and the device level walker if asked."""
+    if args.walk:
+        ctx.set_walk(True)
     if args.br_shape is not None:
         ctx.br_shape = args.br_shape
         return None
@@ -555,6 +558,9 @@ def run_serving(args, dist):
 
     def submit(srv, q):
         tb = tabs[q["i"]]
+        # the server's stream does not wait for torch's: the new outputs'
+        # zero-fill and the constant's copy must be complete first
+        torch.cuda.current_stream().synchronize()
         q["id"] = srv.submit(tb["column"], q["t"].rows, q["t"].width, q["t"].pred, q["const"], tb["payloads"],
                              q["t"].payload_width, q["match"], q["outs"])
 
@@ -805,6 +811,8 @@ def run_ours(args, dist):
     ktimes = ctx.profile_end()
     clocks = sampler.stop()
     ms = dist.max(e0.elapsed_time(e1))
+    if args.walk:
+        ctx.walk_status()  # raises if a grid-barrier wait of the walker ran out of time
     gpr = gates_per_row(t)
     sum_gates = len(sums) * F.sum_plan_info(t.rows, t.payload_width, t.sum_width)[0] if t.aggregate else 0
     gates_per_step = t.rows * gpr + sum_gates
@@ -823,6 +831,8 @@ def run_ours(args, dist):
 
     # ---- roofline of the dominant kernel (blind rotation)
     roofline = roofline_of(ktimes, ms, sms, peaks, args.workload, alu, ctx.engine, args.steps)
+    if args.walk:
+        roofline["kernel"] = "scan_walk_kernel (blind rotations and keyswitches of every level, one launch)"
 
     # ---- end to end through the public C-ABI with host buffers (copies inside the timed region)
     h2d = (col.size + (0 if t.plain else cst.size) + sum(p.size for p in pays)) * 4
@@ -923,6 +933,7 @@ def run_ours(args, dist):
                    "engine": ["goldilocks", "dual_prime"][ctx.engine],
                    "launch_shape": dict(F.br_shape_info(ctx.br_shape), index=ctx.br_shape,
                                          autotune_ms=tuned[1] if tuned else None),
+                   "level_walk": "device walker (one launch per scan)" if args.walk else "one launch pair per level",
                    "l2": "inputs larger than L2 (%.0f MB column+payload per step)" % (h2d / 1e6),
                    "parallelism": f"replica per GPU x{dist.world}"},
         "correct": correct,

@@ -138,18 +138,25 @@ FSQL_API int fsql_ctx_engine(const fsql_ctx* ctx, int* engine);
  *      primes' transforms on separate warps), 2 gates, 2 rows, 2 slots;
  *   5: prime-split, 2 gates, 2 rows, 3 slots;
  *   6: prime-split, 3 gates, 2 rows, 2 slots;
- *   7: prime-split, 2 gates, 3 rows, 2 slots.
+ *   7: prime-split, 2 gates, 3 rows, 2 slots;
+ *   8: packed kernel, 3 gates, 2 rows, one key slot per gate group (the
+ *      groups of a CTA then run without a CTA-wide barrier per step).
  * fsql_ctx_set_br_gates(g) selects the packed shape g - 1 (g = 1..4). */
-#define FSQL_BR_SHAPES 8
+#define FSQL_BR_SHAPES 9
 FSQL_API int fsql_ctx_set_br_shape(fsql_ctx* ctx, int shape);
 FSQL_API int fsql_ctx_br_shape(const fsql_ctx* ctx, int* shape);
 FSQL_API int fsql_br_shape_info(int shape, int* kind, int* gates_per_cta, int* rows_per_step, int* stages);
 FSQL_API int fsql_ctx_set_br_gates(fsql_ctx* ctx, int gates_per_cta);
 FSQL_API int fsql_ctx_br_gates(const fsql_ctx* ctx, int* gates_per_cta);
-/* Latency mode for batches smaller than two gates per SM (two-prime engine;
- * on by default): one gate per CTA of three 128-thread groups that run the
- * three gadget-row steps of every CMux side by side, instead of one gate per
- * 128-thread CTA.  The output words are the same either way. */
+/* Latency mode for batches smaller than two gates per SM (two-prime
+ * engine).  0: one gate per 128-thread CTA.  1 (default): one gate per CTA of
+ * three 128-thread groups that run the three gadget-row steps of every CMux
+ * side by side.  2: one gate per thread-block cluster of six CTAs on six
+ * SMs (each one prime and two gadget rows; partial sums, residues and the
+ * accumulator update exchanged through distributed shared memory with three
+ * cluster barriers per CMux), used while the batch holds at most two gates
+ * per cluster the GPU can run at once, mode 1 above that.  The output words
+ * are the same in every mode.  FSQL_ERR_ARG for other values. */
 FSQL_API int fsql_ctx_set_latency_mode(fsql_ctx* ctx, int on);
 
 /* Device level walker for batched scans (two-prime engine, packed launch
@@ -443,7 +450,11 @@ typedef struct fsql_server_stats {
  * destroyed before the server. */
 FSQL_API int fsql_server_create(fsql_ctx* ctx, size_t scratch_budget_bytes, size_t max_batch_gates,
                                 fsql_server** out);
-/* Queue a query; FSQL_ERR_ADMISSION if its scratch exceeds the whole budget. */
+/* Queue a query; FSQL_ERR_ADMISSION if its scratch exceeds the whole budget.
+ * The server runs on a stream of its own that does not wait for the
+ * caller's streams: the query's inputs (and anything the caller still
+ * writes into its output buffers) must be complete before this call, e.g.
+ * by synchronising the stream that produced them. */
 FSQL_API int fsql_server_submit(fsql_server* server, const fsql_query* query, uint64_t* id);
 /* State (FSQL_Q_*) and, once done, the submit-to-done latency in ms (else -1). */
 FSQL_API int fsql_server_status(fsql_server* server, uint64_t id, int* state, double* latency_ms);

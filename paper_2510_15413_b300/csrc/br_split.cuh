@@ -107,13 +107,47 @@ __device__ __forceinline__ void gs32_stage(uint32_t (&x)[P][8], TwOf tw, uint32_
   }
 }
 
+// First two forward stages of a digit polynomial by table lookup, one prime
+// (the 32-bit form of digit_stages12 in ntt.cuh): tab[m][u] = (u - half) m
+// mod p, canonical, for m = w1, w2a, w2a w1, w2b, w2b w1.
+__device__ __forceinline__ void digit_stages12_32(const uint32_t (&u)[8], uint32_t (&z)[8], uint32_t half,
+                                                  const uint32_t* __restrict__ tab, uint32_t p, uint32_t p2) {
+#pragma unroll
+  for (int a = 0; a < 2; ++a) {
+    const uint32_t d0 = u[a] + p - half;
+    const uint32_t A = tab[0 * kDigitTabSize + u[a + 4]];
+    const uint32_t Bv = tab[1 * kDigitTabSize + u[a + 2]];
+    const uint32_t C = tab[2 * kDigitTabSize + u[a + 6]];
+    const uint32_t D = tab[3 * kDigitTabSize + u[a + 2]];
+    const uint32_t E = tab[4 * kDigitTabSize + u[a + 6]];
+    z[a] = d0 + A + Bv + C;
+    z[a + 2] = d0 + A + p2 - Bv - C;
+    z[a + 4] = d0 + p2 - A + D - E + p2;
+    z[a + 6] = d0 + p2 - A - D + E + p2;
+  }
+}
+// The tables of digit_stages12_32 for prime p from its twiddle table.
+__device__ __forceinline__ void build_digit_tables32(uint32_t* tab, const SplitTables& T, uint32_t half, uint32_t p,
+                                                     int tid, int nthreads) {
+  for (int e = tid; e < kDigitTabs * kDigitTabSize; e += nthreads) {
+    const int m = e / kDigitTabSize, u = e % kDigitTabSize;
+    const uint64_t w1 = T.f_small[1].x, w2a = T.f_small[2].x, w2b = T.f_small[3].x;
+    const uint64_t mult = m == 0 ? w1 : m == 1 ? w2a : m == 2 ? w2a * w1 % p : m == 3 ? w2b : w2b * w1 % p;
+    const uint64_t d = (static_cast<uint64_t>(u) + p - half) % p;
+    tab[e] = static_cast<uint32_t>(d * mult % p);
+  }
+}
+
 // Forward transform of P polynomials mod p (layout F1 -> F4), the passes of
-// ntt_forward on 32-bit residues.
-template <int P, int B, int NB>
+// ntt_forward on 32-bit residues.  kFrom3: the first two stages were done by
+// digit_stages12_32.
+template <int P, int B, int NB, bool kFrom3 = false>
 __device__ __forceinline__ void ntt_forward32(uint32_t (&x)[P][8], uint32_t* bufs, int& parity, const SplitTables& T,
                                               int t, int bar, uint32_t p, uint32_t p2) {
-  ct32_stage<P, 4>(x, [&](int) { return T.f_small[1]; }, p, p2);
-  ct32_stage<P, 2>(x, [&](int k) { return T.f_small[2 + (k >> 2)]; }, p, p2);
+  if (!kFrom3) {
+    ct32_stage<P, 4>(x, [&](int) { return T.f_small[1]; }, p, p2);
+    ct32_stage<P, 2>(x, [&](int k) { return T.f_small[2 + (k >> 2)]; }, p, p2);
+  }
   ct32_stage<P, 1>(x, [&](int k) { return T.f_small[4 + (k >> 1)]; }, p, p2);
   xch32<P, B, NB, LF1, LF2, false>(x, bufs, parity, t, bar);
   const int h3 = t >> 4;

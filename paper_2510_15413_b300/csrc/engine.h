@@ -28,15 +28,17 @@ constexpr int kMaxN = 1024;  // largest LWE dimension the kernels take
 // Launch shapes of the blind rotation for batches of at least two gates per
 // SM.  kind 0: the packed kernel (each thread holds both primes' residues;
 // one gadget row per step for the 64-bit prime, two for the two primes);
-// kind 1: the prime-split kernel of the two-prime engine.  stages: slots of
-// the key-staging ring.
+// kind 1: the prime-split kernel of the two-prime engine; kind 2: the packed
+// kernel with one key slot per gate group (groups run unsynchronised).
+// stages: slots of the key-staging ring (per group for kind 2).
 struct BrShape {
   int kind, gates, rows, stages;
 };
-constexpr int kBrShapeCount = 8;
+constexpr int kBrShapeCount = 9;
 constexpr BrShape kBrShapes[kBrShapeCount] = {
     {0, 1, 0, 2}, {0, 2, 0, 2}, {0, 3, 0, 2}, {0, 4, 0, 2},  // packed, 1-4 gates per CTA (rows per engine)
     {1, 2, 2, 2}, {1, 2, 2, 3}, {1, 3, 2, 2}, {1, 2, 3, 2},  // prime-split
+    {2, 3, 2, 1},                                            // packed, 3 gates, each group its own key slot
 };
 // Whether an engine offers a shape (the 64-bit prime: packed 1, 2 or 4 gates per CTA).
 inline bool shape_offered(int engine, int shape) {
@@ -101,7 +103,8 @@ struct Ctx {
   int device = -1;
   int engine = FSQL_ENGINE_DUAL_PRIME;
   int br_shape = 2;              // launch shape of the blind rotation for large batches (index into kBrShapes)
-  bool latency_mode = true;      // small batches: one gate per CTA of three groups (two-prime engine)
+  int latency_mode = 1;          // small batches (two-prime engine): 0 one gate per 128-thread CTA,
+                                 // 1 one gate per CTA of three groups, 2 one gate per cluster of 6 CTAs
   bool walk_mode = false;        // batched scans as one device-walked launch (scan_walk_kernel)
   double walk_timeout_ms = 2000.0;  // limit of each grid-barrier wait of the walker
   int walk_skip_block = -1;      // test hook: this CTA never arrives at the walker's barriers

@@ -587,7 +587,8 @@ int fsql_br_shape_info(int shape, int* kind, int* gates_per_cta, int* rows_per_s
 
 int fsql_ctx_set_latency_mode(fsql_ctx* ctx, int on) {
   if (!ctx) return arg_error("null context");
-  reinterpret_cast<Ctx*>(ctx)->latency_mode = on != 0;
+  if (on < 0 || on > 2) return arg_error("latency mode: 0, 1 or 2");
+  reinterpret_cast<Ctx*>(ctx)->latency_mode = on;
   return FSQL_OK;
 }
 

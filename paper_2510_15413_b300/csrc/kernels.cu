@@ -20,6 +20,7 @@
 // columns; each thread owns one column of the tile, walks the (i, j) digit
 // positions once and reads the three nonzero-digit key words of its column,
 // so each key row read from L2 serves 16 gates.
+#include <cooperative_groups.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -65,9 +66,14 @@ template <class F>
 __host__ __device__ constexpr int digit_tab_bytes() {
   return F::kEngine == FSQL_ENGINE_DUAL_PRIME ? dev::kDigitTabs * dev::kDigitTabSize * 8 : 0;
 }
-template <class F, int G, int P>
+// kOwn: every gate group stages its own key rows (one slot per group, no
+// CTA-wide barrier per step, so the groups drift apart and their butterfly
+// and exchange phases overlap); else one ring of kStages slots shared by all
+// groups of the CTA.
+template <class F, int G, int P, bool kOwn = false>
 __host__ __device__ constexpr int br_smem() {
-  return tab_bytes<F>() + digit_tab_bytes<F>() + kStages * P * kChunkU64 * 8 + G * gate_bytes<P, xbufs_for<G>()>();
+  return tab_bytes<F>() + digit_tab_bytes<F>() + (kOwn ? G : kStages) * P * kChunkU64 * 8 +
+         G * gate_bytes<P, xbufs_for<G>()>();
 }
 
 constexpr int kKsGates = 16;                     // gates per keyswitch CTA
@@ -305,7 +311,7 @@ __device__ __forceinline__ void issue_step(uint64_t* slot, const uint64_t* __res
 // the body of blind_rotate_kernel and of each segment of scan_walk_kernel.
 // big: [count][N+1] extracted samples under the GLWE key.  prepare: load the
 // twiddle tables into shared memory first (and build the digit tables).
-template <class F, int G, int kPolys>
+template <class F, int G, int kPolys, bool kOwn = false>
 __device__ __forceinline__ void br_body(const GateDesc* __restrict__ desc, int count,
                                         const uint64_t* __restrict__ bkhat, const void* __restrict__ gtab, int n,
                                         int bg_bits, uint32_t* __restrict__ big, bool prepare) {
@@ -325,7 +331,8 @@ __device__ __forceinline__ void br_body(const GateDesc* __restrict__ desc, int c
   uint64_t* stage = reinterpret_cast<uint64_t*>(smem + kTabBytes + digit_tab_bytes<F>());
   const int grp = threadIdx.x / kGroup, t = threadIdx.x % kGroup;
   const int bar = 1 + grp;  // named barrier of this gate's 128 threads
-  uint8_t* gb = smem + kTabBytes + digit_tab_bytes<F>() + kStages * kStepU64 * 8 + grp * kGateBytes;
+  if constexpr (kOwn) stage += grp * kStepU64;  // this group's own slot
+  uint8_t* gb = smem + kTabBytes + digit_tab_bytes<F>() + (kOwn ? G : kStages) * kStepU64 * 8 + grp * kGateBytes;
   uint64_t* xbufs = reinterpret_cast<uint64_t*>(gb);                         // [2][kBufPolys][N] u64
   uint32_t* acc_poly = reinterpret_cast<uint32_t*>(gb + kGateXbuf);          // [2][N] u32
   uint16_t* abar = reinterpret_cast<uint16_t*>(gb + kGateXbuf + kGateAcc);   // [n]
@@ -345,11 +352,21 @@ __device__ __forceinline__ void br_body(const GateDesc* __restrict__ desc, int c
     }
   }
 
+  // copies of step k into a slot: all the CTA's threads (shared ring) or the group's
+  auto issue = [&](uint64_t* slot, int k) {
+    if constexpr (kOwn) {
+      const uint4* src = reinterpret_cast<const uint4*>(bkhat + static_cast<size_t>(k) * kStepU64);
+      uint4* dst = reinterpret_cast<uint4*>(slot);
+      for (int q = t; q < kStepU64 * 8 / 16; q += kGroup) cp_async16(dst + q, src + q);
+    } else {
+      issue_step<kThreads, kStepU64>(slot, bkhat, k);
+    }
+  };
   for (int g0 = blockIdx.x * G; g0 < count; g0 += gridDim.x * G) {
     const int gi = g0 + grp;
     const bool active = gi < count;
     __syncthreads();  // tables loaded; previous group finished with the stages
-    issue_step<kThreads, kStepU64>(stage, bkhat, 0);
+    if (!kOwn || active) issue(stage, 0);
     cp_async_commit();
 
     if (active) {
@@ -384,10 +401,16 @@ __device__ __forceinline__ void br_body(const GateDesc* __restrict__ desc, int c
 #pragma unroll 1
       for (int s = 0; s < kStepsPerCmux; ++s) {
         const int k = i * kStepsPerCmux + s;
-        cp_async_wait<0>();
-        __syncthreads();  // key rows of step k visible; everyone done with step k-1 and the ACC update
-        if (k + 1 < total) issue_step<kThreads, kStepU64>(stage + ((k + 1) % kStages) * kStepU64, bkhat, k + 1);
-        cp_async_commit();
+        if constexpr (kOwn) {
+          if (!active) continue;
+          cp_async_wait<0>();
+          dev::named_sync(bar);  // the group's key rows of step k visible; its ACC update done
+        } else {
+          cp_async_wait<0>();
+          __syncthreads();  // key rows of step k visible; everyone done with step k-1 and the ACC update
+          if (k + 1 < total) issue(stage + ((k + 1) % kStages) * kStepU64, k + 1);
+          cp_async_commit();
+        }
         if (active) {
           // X^a ACC_u - ACC_u, formed by the step holding row 3u and reused by
           // the l gadget levels of polynomial u (rows 3u .. 3u+2)
@@ -423,7 +446,7 @@ __device__ __forceinline__ void br_body(const GateDesc* __restrict__ desc, int c
             }
           }
           dev::ntt_forward<F, kPolys, kBufPolys, kNB, kDigitTab>(x, xbufs, parity, T, t, bar);
-          const uint64_t* ch = stage + (k % kStages) * kStepU64;
+          const uint64_t* ch = kOwn ? stage : stage + (k % kStages) * kStepU64;
 #pragma unroll
           for (int q = 0; q < 8; ++q) {
 #pragma unroll
@@ -432,6 +455,11 @@ __device__ __forceinline__ void br_body(const GateDesc* __restrict__ desc, int c
               F::mac(acc[q], x[p][q], w, s == 0 && p == 0);
             }
           }
+        }
+        if constexpr (kOwn) {
+          dev::named_sync(bar);  // the group is done reading its slot
+          if (k + 1 < total) issue(stage, k + 1);  // lands while the next step forms and transforms digits
+          cp_async_commit();
         }
       }
       if (active) {
@@ -463,11 +491,11 @@ __device__ __forceinline__ void br_body(const GateDesc* __restrict__ desc, int c
   }
 }
 
-template <class F, int G, int kPolys>
+template <class F, int G, int kPolys, bool kOwn = false>
 __global__ void __launch_bounds__(G * kGroup, 1)
     blind_rotate_kernel(const GateDesc* __restrict__ desc, int count, const uint64_t* __restrict__ bkhat,
                         const void* __restrict__ gtab, int n, int bg_bits, uint32_t* __restrict__ big) {
-  br_body<F, G, kPolys>(desc, count, bkhat, gtab, n, bg_bits, big, true);
+  br_body<F, G, kPolys, kOwn>(desc, count, bkhat, gtab, n, bg_bits, big, true);
 }
 
 // Prime-split blind rotation (br_split.cuh): G gates per CTA of 256 threads
@@ -646,6 +674,183 @@ __global__ void __launch_bounds__(G * 2 * kGroup, 1)
   }
 }
 
+// Cluster blind rotation: one gate per thread-block cluster of 6 CTAs of 128
+// threads, on 6 SMs, for batches too small to fill the GPU (the per-gate
+// path and the narrow levels of deep circuits).  A gate's 630 CMux steps are
+// a dependent chain, so one gate on one SM is bound by that SM's integer
+// pipes; here its work per CMux is spread over 6 SMs that exchange through
+// distributed shared memory.  CTA rank r = 3 pr + s: prime pr (p1 or p2,
+// 32-bit residues), gadget rows 2s and 2s + 1.  Per CMux:
+//   1. every CTA keeps a full copy of ACC; it forms the digits of its two
+//      rows, transforms them mod its prime (first two stages by digit table)
+//      and multiply-accumulates them with its two staged key rows into
+//      per-slot sums of the two output polynomials, reduced to [0, 2p)
+//      (part[c][slot]);
+//   2. cluster barrier; CTA (pr, c), c = 0, 1, sums the three partial
+//      polynomials c of its prime from the CTAs (pr, 0..2) (distributed
+//      shared memory reads), folds to [0, 2p) and runs the inverse transform;
+//      the residues go to resid[];
+//   3. cluster barrier; CTA (0, c) reads the p2 residues of polynomial c
+//      from CTA (1, c), lifts the exact integers by CRT into delta[];
+//   4. cluster barrier; every CTA adds delta of ranks 0 and 1 into its ACC.
+// The residues summed are those the packed kernel sums (the same integer mod
+// each prime), so the CRT gives the same exact integer and the same words.
+constexpr int kClusterCtas = 6;
+constexpr int kClusterSmem = kSplitTabBytes + dev::kDigitTabs * dev::kDigitTabSize * 4 +  // tables
+                             2 * 2 * kChunkU64 * 4 +                                        // key rows, 2 slots
+                             2 * kN * 4 +                                                   // exchange buffer
+                             2 * kN * 4 + 2 * kN * 4 +                                      // ACC, partial sums
+                             kN * 4 + kN * 4 +                                              // residues, delta
+                             kMaxN * 2 + 16;                                                // switched mask, body
+
+__global__ void __cluster_dims__(kClusterCtas, 1, 1) __launch_bounds__(kGroup, 1)
+    blind_rotate_cluster_kernel(const GateDesc* __restrict__ desc, int count, const uint32_t* __restrict__ bks,
+                                const void* __restrict__ gtab, int n, int bg_bits, uint32_t* __restrict__ big) {
+  namespace cg = cooperative_groups;
+  cg::cluster_group cl = cg::this_cluster();
+  const int rank = static_cast<int>(cl.block_rank());
+  const int pr = rank / 3, s = rank % 3, t = threadIdx.x;
+  extern __shared__ __align__(128) uint8_t smem[];
+  dev::SplitTables& T = *reinterpret_cast<dev::SplitTables*>(smem);
+  uint32_t* dtab = reinterpret_cast<uint32_t*>(smem + kSplitTabBytes);
+  uint32_t* keys = dtab + dev::kDigitTabs * dev::kDigitTabSize;  // [2 slots][2 rows][kChunkU64]
+  uint32_t* xbuf = keys + 2 * 2 * kChunkU64;                       // [2][N]
+  uint32_t* acc_poly = xbuf + 2 * kN;                              // [2][N]
+  uint32_t* part = acc_poly + 2 * kN;                              // [2][N], slot-major (q * 128 + t)
+  uint32_t* resid = part + 2 * kN;                                 // [N]
+  uint32_t* delta = resid + kN;                                    // [N]
+  uint16_t* abar = reinterpret_cast<uint16_t*>(delta + kN);        // [kMaxN]
+  uint32_t* bbar_slot = reinterpret_cast<uint32_t*>(abar + kMaxN);
+  const uint32_t p = pr ? dev::kP2 : dev::kP1, p2 = 2 * p, pinv = pr ? dev::kP2inv : dev::kP1inv;
+
+  for (int k = t; k < kSplitTabBytes / 16; k += kGroup)
+    reinterpret_cast<uint4*>(smem)[k] = reinterpret_cast<const uint4*>(gtab)[pr * (kSplitTabBytes / 16) + k];
+  uint32_t off = 1u << (31 - bg_bits * kL);
+  for (int j = 1; j <= kL; ++j) off += (1u << (bg_bits - 1)) << (32 - bg_bits * j);
+  const uint32_t dmask = (1u << bg_bits) - 1, dhalf = 1u << (bg_bits - 1);
+  __syncthreads();
+  dev::build_digit_tables32(dtab, T, dhalf, p, t, kGroup);
+  // rows 2s and 2s+1 of CMux i for this prime: two 8 KB pieces of the split key
+  const int row0 = 2 * s, row1 = 2 * s + 1, u0 = row0 / kL, u1 = row1 / kL;
+  const int shift0 = 32 - bg_bits * (row0 % kL + 1), shift1 = 32 - bg_bits * (row1 % kL + 1);
+  auto issue_rows = [&](int i, int slot) {
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+      const uint4* src = reinterpret_cast<const uint4*>(bks + ((static_cast<size_t>(i) * kRows + 2 * s + r) * 2 + pr) *
+                                                                  kChunkU64);
+      uint4* dst = reinterpret_cast<uint4*>(keys + (slot * 2 + r) * kChunkU64);
+      for (int q = t; q < kChunkU64 * 4 / 16; q += kGroup) cp_async16(dst + q, src + q);
+    }
+    cp_async_commit();
+  };
+  uint32_t* part_r[3];   // partial sums of this prime's three CTAs
+  uint32_t* resid_other;  // CTA (1, c)'s residues, read by CTA (0, c)
+  uint32_t* delta_r[2];  // the two CRT results
+  for (int m = 0; m < 3; ++m) part_r[m] = cl.map_shared_rank(part, pr * 3 + m);
+  resid_other = cl.map_shared_rank(resid, 3 + s);
+  delta_r[0] = cl.map_shared_rank(delta, 0);
+  delta_r[1] = cl.map_shared_rank(delta, 1);
+
+  for (int gi = static_cast<int>(blockIdx.x) / kClusterCtas; gi < count;
+       gi += static_cast<int>(gridDim.x) / kClusterCtas) {
+    __syncthreads();
+    issue_rows(0, 0);
+    const GateDesc d = desc[gi];
+    const Lin lin = gate_lin(d.type);
+    const uint32_t* c3 = lin.cc ? d.c : nullptr;
+    for (int x = t; x <= n; x += kGroup) {
+      uint32_t v = lin.ca * d.a[x] + lin.cb * d.b[x];
+      if (c3) v += lin.cc * c3[x];
+      if (x == n) v += lin.k;
+      const uint32_t ms = ((v + (1u << 20)) >> 21) & (2 * kN - 1);
+      if (x < n) abar[x] = static_cast<uint16_t>(ms);
+      else *bbar_slot = ms;
+    }
+    __syncthreads();
+    {
+      const uint32_t e = (2 * kN - *bbar_slot) & (2 * kN - 1);
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const uint32_t c = t + 128 * q;
+        acc_poly[c] = 0u;
+        const uint32_t idx = (c - e) & (2 * kN - 1);
+        acc_poly[kN + c] = idx < static_cast<uint32_t>(kN) ? (1u << 29) : (0u - (1u << 29));
+      }
+    }
+    int parity = 0;
+    for (int i = 0; i < n; ++i) {
+      cp_async_wait<0>();
+      __syncthreads();  // key rows of CMux i landed; ACC updated
+      if (i + 1 < n) issue_rows(i + 1, (i + 1) & 1);
+      else cp_async_commit();
+      const uint32_t a_i = abar[i];
+      uint32_t d0[8], d1[8];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const uint32_t c = t + 128 * q;
+        const uint32_t idx = (c - a_i) & (2 * kN - 1);
+        const uint32_t* P0 = acc_poly + u0 * kN;
+        const uint32_t* P1 = acc_poly + u1 * kN;
+        const uint32_t r0 = idx < static_cast<uint32_t>(kN) ? P0[idx] : 0u - P0[idx - kN];
+        const uint32_t r1 = idx < static_cast<uint32_t>(kN) ? P1[idx] : 0u - P1[idx - kN];
+        d0[q] = ((r0 - P0[c] + off) >> shift0) & dmask;
+        d1[q] = ((r1 - P1[c] + off) >> shift1) & dmask;
+      }
+      uint32_t x[2][8];
+      dev::digit_stages12_32(d0, x[0], dhalf, dtab, p, p2);
+      dev::digit_stages12_32(d1, x[1], dhalf, dtab, p, p2);
+      dev::ntt_forward32<2, 2, 1, true>(x, xbuf, parity, T, t, 1, p, p2);
+      const uint32_t* ch = keys + (i & 1) * 2 * kChunkU64;
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        uint64_t s0 = 0, s1 = 0;
+#pragma unroll
+        for (int r = 0; r < 2; ++r) {
+          const uint2 w = *reinterpret_cast<const uint2*>(ch + r * kChunkU64 + (q * kGroup + t) * 2);
+          s0 += static_cast<uint64_t>(x[r][q]) * w.x;
+          s1 += static_cast<uint64_t>(x[r][q]) * w.y;
+        }
+        part[q * kGroup + t] = dev::DualPrime::settle(s0, p, pinv);
+        part[kN + q * kGroup + t] = dev::DualPrime::settle(s1, p, pinv);
+      }
+      cl.sync();  // 1: every CTA's partial sums visible
+      uint32_t y[1][8];
+      if (s < 2) {
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          const int o = s * kN + q * kGroup + t;
+          const uint32_t v = part_r[0][o] + part_r[1][o] + part_r[2][o];  // below 6p
+          y[0][q] = dev::fold(dev::fold(v, 2 * p2), p2);
+        }
+        dev::ntt_inverse32<1, 2, 1>(y, xbuf, parity, T, t, 1, p, p2);
+#pragma unroll
+        for (int q = 0; q < 8; ++q) resid[t + 128 * q] = y[0][q];
+      }
+      cl.sync();  // 2: residues of both primes visible
+      if (pr == 0 && s < 2) {
+#pragma unroll
+        for (int q = 0; q < 8; ++q) delta[t + 128 * q] = dev::crt_torus(y[0][q], resid_other[t + 128 * q]);
+      }
+      cl.sync();  // 3: the two lifted polynomials visible
+#pragma unroll
+      for (int c = 0; c < 2; ++c)
+#pragma unroll
+        for (int q = 0; q < 8; ++q) acc_poly[c * kN + t + 128 * q] += delta_r[c][t + 128 * q];
+    }
+    __syncthreads();
+    if (rank == 0) {
+      uint32_t* out = big + static_cast<size_t>(gi) * (kN + 1);
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const int c = t + 128 * q;
+        out[c] = c == 0 ? acc_poly[0] : 0u - acc_poly[kN - c];
+      }
+      if (t == 0) out[kN] = acc_poly[kN];
+    }
+  }
+  cl.sync();  // no CTA leaves while another may still read its shared memory
+}
+
 // Packed key (u64: p1 residue low, p2 residue high) -> key split by prime.
 __global__ void split_key_kernel(const uint64_t* __restrict__ bkhat, uint32_t* __restrict__ bks, size_t rows) {
   const size_t total = rows * kChunkU64;
@@ -675,7 +880,8 @@ constexpr int kLatGroups = kRows / 2;  // three groups of two gadget rows
 
 template <class F>
 __host__ __device__ constexpr int lat_smem() {
-  return tab_bytes<F>() + kLatGroups * 2 * kChunkU64 * 8 + kLatGroups * 2 * kN * 8 + kGateAcc + kGateAbar + 16;
+  return tab_bytes<F>() + kLatGroups * 2 * kChunkU64 * 8 + kLatGroups * 2 * kN * 8 + kGateAcc + kGateAbar + 16 +
+         digit_tab_bytes<F>();
 }
 
 template <class F>
@@ -691,6 +897,7 @@ __global__ void __launch_bounds__(kLatGroups * kGroup, 1)
   uint32_t* acc_poly = reinterpret_cast<uint32_t*>(xb_all + kLatGroups * 2 * kN);  // [2][N]
   uint16_t* abar = reinterpret_cast<uint16_t*>(acc_poly + 2 * kN);                 // [n]
   uint32_t* bbar_slot = reinterpret_cast<uint32_t*>(abar + kMaxN);
+  uint64_t* dtab = reinterpret_cast<uint64_t*>(bbar_slot + 4);  // digit tables of the first two stages
   const int grp = threadIdx.x / kGroup, t = threadIdx.x % kGroup;
   const int bar = 1 + grp;
   uint64_t* xbufs = xb_all + grp * 2 * kN;
@@ -700,6 +907,8 @@ __global__ void __launch_bounds__(kLatGroups * kGroup, 1)
   uint32_t off = 1u << (31 - bg_bits * kL);
   for (int j = 1; j <= kL; ++j) off += (1u << (bg_bits - 1)) << (32 - bg_bits * j);
   const uint32_t dmask = (1u << bg_bits) - 1, dhalf = 1u << (bg_bits - 1);
+  __syncthreads();  // twiddle tables loaded
+  dev::build_digit_tables(dtab, T, dhalf, threadIdx.x, kThreads);
   // rows 2 grp and 2 grp + 1 belong to polynomials (2 grp) / l and (2 grp + 1) / l
   const int row0 = 2 * grp, row1 = 2 * grp + 1;
   const int u0 = row0 / kL, u1 = row1 / kL;
@@ -738,6 +947,7 @@ __global__ void __launch_bounds__(kLatGroups * kGroup, 1)
       }
       const uint32_t a_i = abar[i];
       uint64_t x[2][8];
+      uint32_t d0[8], d1[8];
 #pragma unroll
       for (int q = 0; q < 8; ++q) {
         const uint32_t c = t + 128 * q;
@@ -749,10 +959,12 @@ __global__ void __launch_bounds__(kLatGroups * kGroup, 1)
           const uint32_t rot = idx < static_cast<uint32_t>(kN) ? Pu[idx] : 0u - Pu[idx - kN];
           v[r] = rot - Pu[c] + off;
         }
-        x[0][q] = F::from_digit((v[0] >> shift0) & dmask, dhalf);
-        x[1][q] = F::from_digit((v[1] >> shift1) & dmask, dhalf);
+        d0[q] = (v[0] >> shift0) & dmask;
+        d1[q] = (v[1] >> shift1) & dmask;
       }
-      dev::ntt_forward<F, 2, 2, 1>(x, xbufs, parity, T, t, bar);
+      dev::digit_stages12(d0, x[0], dhalf, dtab);
+      dev::digit_stages12(d1, x[1], dhalf, dtab);
+      dev::ntt_forward<F, 2, 2, 1, true>(x, xbufs, parity, T, t, bar);
       cp_async_wait<0>();
       dev::named_sync(bar);  // the group's key rows are visible to all its threads
       typename F::Acc acc[8];
@@ -1232,7 +1444,7 @@ struct Plan {
   const GateDesc* graph_desc = nullptr;
   const uint32_t* graph_big = nullptr;
   const OutDesc* graph_lits = nullptr;
-  int graph_br_shape = -1;  // launch shape: 2 x shape index + latency mode
+  int graph_br_shape = -1;  // launch shape: 4 x shape index + latency mode
   uint64_t graph_ks_gen = 0;  // keyswitch-first scratch generation the graph was captured with
   long long graph_walk = -1;  // walker arguments when the graph was captured (0: no walker)
   // device walker: the plan's segments (levels split at the sample scratch)
@@ -1423,23 +1635,23 @@ void device_free(Ctx& c) {
 
 // Launch the blind rotation with G gates per CTA and P gadget rows per step
 // (persistent grid of at most one CTA per SM).
-template <class F, int G, int P>
+template <class F, int G, int P, bool kOwn = false>
 static cudaError_t launch_br_engine(int sm_count, const GateDesc* d_desc, size_t count, const uint64_t* bkhat,
                                     const void* tables, int n, int bg_bits, uint32_t* d_big, cudaStream_t st) {
-  static_assert(br_smem<F, G, P>() <= 227 * 1024, "blind-rotation shared memory over budget");
+  static_assert(br_smem<F, G, P, kOwn>() <= 227 * 1024, "blind-rotation shared memory over budget");
   static bool attr_set[64] = {};
   int dev = 0;
   cudaGetDevice(&dev);
   if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
   if (!attr_set[dev]) {
-    const cudaError_t e = cudaFuncSetAttribute(blind_rotate_kernel<F, G, P>,
-                                               cudaFuncAttributeMaxDynamicSharedMemorySize, br_smem<F, G, P>());
+    const cudaError_t e = cudaFuncSetAttribute(blind_rotate_kernel<F, G, P, kOwn>,
+                                               cudaFuncAttributeMaxDynamicSharedMemorySize, br_smem<F, G, P, kOwn>());
     if (e != cudaSuccess) return e;
     attr_set[dev] = true;
   }
   const size_t groups = (count + G - 1) / G;
   const int grid = static_cast<int>(std::min<size_t>(groups, static_cast<size_t>(sm_count)));
-  blind_rotate_kernel<F, G, P><<<grid, G * kGroup, br_smem<F, G, P>(), st>>>(
+  blind_rotate_kernel<F, G, P, kOwn><<<grid, G * kGroup, br_smem<F, G, P, kOwn>(), st>>>(
       d_desc, static_cast<int>(count), bkhat, tables, n, bg_bits, d_big);
   return cudaGetLastError();
 }
@@ -1467,7 +1679,45 @@ static cudaError_t launch_br_split(int sm_count, const GateDesc* d_desc, size_t 
   return cudaGetLastError();
 }
 
-// Latency mode (two-prime engine): one gate per CTA of three groups.
+// Cluster mode (two-prime engine): one gate per cluster of 6 CTAs, each on an
+// SM of its own (the dynamic shared memory requested, above half an SM's,
+// keeps a second CTA off the SM).  Returns cudaErrorNotSupported when the
+// device cannot hold a cluster, so the caller falls back.
+constexpr int kClusterSmemLaunch = kClusterSmem > 120 * 1024 ? kClusterSmem : 120 * 1024;
+static cudaError_t cluster_capacity(int* clusters) {
+  static int cap[64] = {};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+  if (cap[dev] == 0) {
+    cudaError_t e = cudaFuncSetAttribute(blind_rotate_cluster_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         kClusterSmemLaunch);
+    if (e != cudaSuccess) return e;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(kClusterCtas);
+    cfg.blockDim = dim3(kGroup);
+    cfg.dynamicSmemBytes = kClusterSmemLaunch;
+    int n = 0;
+    e = cudaOccupancyMaxActiveClusters(&n, blind_rotate_cluster_kernel, &cfg);
+    if (e != cudaSuccess) return e;
+    cap[dev] = n > 0 ? n : -1;
+  }
+  *clusters = cap[dev];
+  return cap[dev] > 0 ? cudaSuccess : cudaErrorNotSupported;
+}
+
+static cudaError_t launch_br_cluster(size_t count, const GateDesc* d_desc, const uint32_t* bks, const void* tables,
+                                     int n, int bg_bits, uint32_t* d_big, cudaStream_t st) {
+  int clusters = 0;
+  const cudaError_t e = cluster_capacity(&clusters);
+  if (e != cudaSuccess) return e;
+  const int grid = static_cast<int>(std::min<size_t>(count, static_cast<size_t>(clusters))) * kClusterCtas;
+  blind_rotate_cluster_kernel<<<grid, kGroup, kClusterSmemLaunch, st>>>(d_desc, static_cast<int>(count), bks, tables,
+                                                                        n, bg_bits, d_big);
+  return cudaGetLastError();
+}
+
+// Latency mode (two-prime engine): one gate per CTA of three groups.// Latency mode (two-prime engine): one gate per CTA of three groups.
 template <class F>
 static cudaError_t launch_br_latency(int sm_count, const GateDesc* d_desc, size_t count, const uint64_t* bkhat,
                                      const void* tables, int n, int bg_bits, uint32_t* d_big, cudaStream_t st) {
@@ -1507,6 +1757,12 @@ static cudaError_t launch_br_any(Ctx& c, const GateDesc* d_desc, size_t count, u
     return launch_br_engine<F, 4, 1>(c.sm_count, d_desc, count, c.d_bkhat, c.d_tables, n, bg, d_big, st);
   }
   using F = dev::DualPrime;
+  if (small && c.latency_mode == 2) {
+    // a cluster per gate while there are at most two clusters' worth of gates per cluster slot
+    int clusters = 0;
+    if (cluster_capacity(&clusters) == cudaSuccess && count <= static_cast<size_t>(2 * clusters))
+      return launch_br_cluster(count, d_desc, c.d_bks, c.d_tables_split, n, bg, d_big, st);
+  }
   if (small && c.latency_mode)
     return launch_br_latency<F>(c.sm_count, d_desc, count, c.d_bkhat, c.d_tables, n, bg, d_big, st);
   if (!small && sh.kind == 1) {
@@ -1519,6 +1775,8 @@ static cudaError_t launch_br_any(Ctx& c, const GateDesc* d_desc, size_t count, u
   }
   if (small || sh.gates == 1)
     return launch_br_engine<F, 1, 2>(c.sm_count, d_desc, count, c.d_bkhat, c.d_tables, n, bg, d_big, st);
+  if (sh.kind == 2)
+    return launch_br_engine<F, 3, 2, true>(c.sm_count, d_desc, count, c.d_bkhat, c.d_tables, n, bg, d_big, st);
   if (sh.gates == 3)
     return launch_br_engine<F, 3, 2>(c.sm_count, d_desc, count, c.d_bkhat, c.d_tables, n, bg, d_big, st);
   if (sh.gates == 4)
@@ -1566,7 +1824,8 @@ bool walk_supported(const Ctx& c) {
          c.d_walk_sync;
 }
 
-int launch_walk(Ctx& c, const GateDesc* d_desc, const WalkSeg* d_segs, int nsegs, uint32_t* d_big, void* stream) {
+int launch_walk(Ctx& c, const GateDesc* d_desc, const WalkSeg* d_segs, int nsegs, size_t gates, uint32_t* d_big,
+                void* stream) {
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   LaunchTimer tm(c, st);
   const int g = kBrShapes[c.br_shape].gates;
@@ -1576,7 +1835,7 @@ int launch_walk(Ctx& c, const GateDesc* d_desc, const WalkSeg* d_segs, int nsegs
     set_error(std::string("walker launch: ") + cudaGetErrorString(e));
     return FSQL_ERR_CUDA;
   }
-  tm.done(true, 0);
+  tm.done(true, gates);  // one launch: blind rotations and keyswitches of every level
   return FSQL_OK;
 }
 
@@ -2061,7 +2320,7 @@ int execute_plan(Ctx* c, fsql::Plan& pl, const fsql::GateDesc* d_desc, const fsq
   }
   auto launch_all = [&](void* st) -> int {
     if (walk) {
-      const int r = fsql::launch_walk(*c, d_desc, pl.d_segs, pl.nsegs, c->d_big, st);
+      const int r = fsql::launch_walk(*c, d_desc, pl.d_segs, pl.nsegs, pl.total, c->d_big, st);
       if (r) return r;
       return fsql::launch_literals(d_lits, pl.n_lits, n, st);
     }
@@ -2075,7 +2334,7 @@ int execute_plan(Ctx* c, fsql::Plan& pl, const fsql::GateDesc* d_desc, const fsq
   if (prof && prof->recording) return launch_all(stream);  // per-launch events need plain launches
   fsql::Plan& mp = pl;
   if (!mp.graph || mp.graph_desc != d_desc || mp.graph_big != c->d_big || mp.graph_lits != d_lits ||
-      mp.graph_br_shape != 2 * c->br_shape + (c->latency_mode ? 1 : 0) ||
+      mp.graph_br_shape != 4 * c->br_shape + c->latency_mode ||
       (pl.ks_first && mp.graph_ks_gen != c->ks_gen) || mp.graph_walk != walk_key) {
     if (mp.graph) cudaGraphExecDestroy(mp.graph);
     mp.graph = nullptr;
@@ -2103,7 +2362,7 @@ int execute_plan(Ctx* c, fsql::Plan& pl, const fsql::GateDesc* d_desc, const fsq
     mp.graph_desc = d_desc;
     mp.graph_big = c->d_big;
     mp.graph_lits = d_lits;
-    mp.graph_br_shape = 2 * c->br_shape + (c->latency_mode ? 1 : 0);
+    mp.graph_br_shape = 4 * c->br_shape + c->latency_mode;
     mp.graph_ks_gen = c->ks_gen;
     mp.graph_walk = walk_key;
   }

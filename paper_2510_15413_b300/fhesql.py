@@ -187,14 +187,15 @@ def _stream(stream) -> int:
     return int(getattr(stream, "cuda_stream", stream))
 
 
-BR_SHAPES = 8
+BR_SHAPES = 9
 
 
 def br_shape_info(shape: int) -> dict:
     """(kernel kind, gates per CTA, gadget rows per step, staging slots) of a launch shape."""
     k, g, r, st = C.c_int(), C.c_int(), C.c_int(), C.c_int()
     _check(load().fsql_br_shape_info(int(shape), C.byref(k), C.byref(g), C.byref(r), C.byref(st)))
-    return {"kind": ["packed", "prime_split"][k.value], "gates_per_cta": g.value, "rows_per_step": r.value,
+    return {"kind": ["packed", "prime_split", "packed_own_slot"][k.value], "gates_per_cta": g.value,
+            "rows_per_step": r.value,
             "stages": st.value}
 
 
@@ -294,9 +295,11 @@ class Context:
     def br_gates(self, g: int) -> None:
         _check(load().fsql_ctx_set_br_gates(self._h, int(g)))
 
-    def set_latency_mode(self, on: bool) -> None:
-        """Small batches on one gate per CTA of three groups (default on)."""
-        _check(load().fsql_ctx_set_latency_mode(self._h, int(bool(on))))
+    def set_latency_mode(self, mode) -> None:
+        """Kernel for batches under two gates per SM: 0 (or False) one gate per
+        128-thread CTA, 1 (or True, the default) one gate per CTA of three
+        groups, 2 one gate per cluster of six CTAs."""
+        _check(load().fsql_ctx_set_latency_mode(self._h, int(mode)))
 
     @property
     def br_shape(self) -> int:

@@ -151,6 +151,7 @@ def test_served_mix_large_rounds_match_oracle(env):
                     "match": torch.zeros((t.rows, W), dtype=torch.int32, device="cuda"),
                     "outs": [torch.zeros((t.rows, t.payload_width, W), dtype=torch.int32, device="cuda")
                              for _ in pays]})
+    torch.cuda.synchronize()  # inputs and zeroed outputs complete before the server stream reads them
     srv = F.Server(ctx, scratch_budget_bytes=256 << 20, max_batch_gates=8192)
     ids = [srv.submit(io["column"], t.rows, t.width, t.pred, io["const"], io["payloads"], t.payload_width,
                       io["match"], io["outs"]) for t, io in zip(tables, ios)]
@@ -243,3 +244,90 @@ def test_every_launch_shape_gives_the_same_words(env):
     sample = np.unique(np.concatenate([[0, B - 1], np.random.default_rng(9).choice(B, 38, replace=False)]))
     want = o.gate_batch(types[sample].astype(np.int32), x[sample], y[sample])
     assert np.array_equal(words[0][sample], want)
+
+
+def _scan(ctx, t, col, cst, pays):
+    W = ctx.words
+    match = torch.zeros((t.rows, W), dtype=torch.int32, device="cuda")
+    outs = [torch.zeros((t.rows, t.payload_width, W), dtype=torch.int32, device="cuda") for _ in pays]
+    ctx.scan_select(col, t.rows, t.width, t.pred, cst, pays, t.payload_width, match, outs)
+    return match, outs
+
+
+def test_device_walker_equals_level_launches_and_oracle(env):
+    """The device level walker (one cooperative launch for the whole scan)
+    gives the words of the per-level launches, and two rows equal the
+    oracle's; a replay of the captured walker graph gives them again."""
+    ctx, o = env
+    t = WL.table("eq32x4096", seed=41, rows=300)  # every level at least two gates per SM
+    col, cst, pays = WL.encrypt_table(ctx, t)
+    dcol, dcst, dp = dev(col.view(np.int32)), dev(cst.view(np.int32)), [dev(p.view(np.int32)) for p in pays]
+    m_lv, o_lv = _scan(ctx, t, dcol, dcst, dp)
+    ref_m, ref_o = host(m_lv).copy(), host(o_lv[0]).copy()
+    try:
+        ctx.set_walk(True)
+        for _ in range(2):
+            m_w, o_w = _scan(ctx, t, dcol, dcst, dp)
+            ctx.walk_status()
+            assert np.array_equal(host(m_w), ref_m) and np.array_equal(host(o_w[0]), ref_o)
+    finally:
+        ctx.set_walk(False)
+    om, (oout,) = oracle_rows(o, t, [0, t.rows - 1])
+    assert np.array_equal(ref_m.view(np.uint32)[[0, t.rows - 1]], om)
+    assert np.array_equal(ref_o.view(np.uint32).reshape(t.rows, 32, -1)[[0, t.rows - 1]],
+                          oout.reshape(2, 32, -1))
+
+
+def test_device_walker_barrier_timeout_is_reported(env):
+    """A CTA that never arrives at the walker's grid barriers (test hook):
+    the other CTAs' waits run out after 200 ms, the kernel returns, the host
+    reads FSQL_ERR_TIMEOUT, and the context keeps working (the next walked
+    scan equals the per-level launches)."""
+    ctx, _ = env
+    t = WL.table("eq32x4096", seed=42, rows=300)
+    col, cst, pays = WL.encrypt_table(ctx, t)
+    dcol, dcst, dp = dev(col.view(np.int32)), dev(cst.view(np.int32)), [dev(p.view(np.int32)) for p in pays]
+    m_lv, o_lv = _scan(ctx, t, dcol, dcst, dp)
+    ref_m = host(m_lv).copy()
+    try:
+        ctx.set_walk(True, timeout_ms=200.0)
+        ctx.debug_walk_skip_block(5)
+        _scan(ctx, t, dcol, dcst, dp)
+        with pytest.raises(F.FsqlError) as e:
+            ctx.walk_status()
+        assert e.value.code == F.FSQL_ERR_TIMEOUT
+        ctx.debug_walk_skip_block(-1)
+        m_w, _ = _scan(ctx, t, dcol, dcst, dp)
+        ctx.walk_status()
+        assert np.array_equal(host(m_w), ref_m)
+    finally:
+        ctx.debug_walk_skip_block(-1)
+        ctx.set_walk(False)
+
+
+def test_cluster_latency_mode_equals_other_modes_and_oracle(env):
+    """Small batches on the cluster kernel (one gate per cluster of six CTAs
+    exchanging through distributed shared memory): the words of the three-group
+    latency kernel and of one gate per CTA, and the oracle's on samples, for
+    one gate, one cluster wave and more gates than clusters."""
+    ctx, o = env
+    rng = np.random.default_rng(29)
+    try:
+        for count in (1, 7, 48):
+            types = rng.integers(0, 10, count).astype(np.uint8)
+            xb, yb = rng.integers(0, 2, count).astype(np.uint8), rng.integers(0, 2, count).astype(np.uint8)
+            a = ctx.encrypt_bits(xb, 62, 0)
+            b = ctx.encrypt_bits(yb, 63, 0)
+            res = {}
+            for mode in (2, 1, 0):
+                ctx.set_latency_mode(mode)
+                out = torch.full((count, ctx.words), -1, dtype=torch.int32, device="cuda")
+                ctx.gate_batch(dev(types), dev(a.view(np.int32)), dev(b.view(np.int32)), out)
+                res[mode] = host(out).view(np.uint32)
+            assert np.array_equal(res[2], res[1]) and np.array_equal(res[2], res[0]), count
+            k = min(count, 3)
+            assert np.array_equal(res[2][:k], o.gate_batch(types[:k].astype(np.int32), a[:k], b[:k]))
+            truth = np.array([O.gate_plain(int(t), int(x), int(y)) for t, x, y in zip(types, xb, yb)], np.uint8)
+            assert np.array_equal(ctx.decrypt_bits(res[2]), truth)
+    finally:
+        ctx.set_latency_mode(1)

@@ -47,6 +47,7 @@ def test_mixed_queries_equal_their_solo_runs(ctx):
               WL.table("eq32x4096", seed=4, rows=9), WL.table("range16x65536", seed=5, rows=3)]
     ios = [prepare(ctx, t) for t in tables]
     # budget for about two queries at a time and small rounds: forces queueing, chunked levels and merging
+    torch.cuda.synchronize()  # inputs and zeroed outputs complete before the server stream reads them
     srv = F.Server(ctx, scratch_budget_bytes=2 << 20, max_batch_gates=96)
     ids = [srv.submit(io["column"], t.rows, t.width, t.pred, io["const"], io["payloads"], t.payload_width,
                       io["match"], io["outs"]) for t, io in zip(tables, ios)]
@@ -72,6 +73,7 @@ def test_mixed_queries_equal_their_solo_runs(ctx):
 def test_admission_rejects_query_larger_than_budget(ctx):
     t = WL.table("eq32x4096", seed=6, rows=64)
     io = prepare(ctx, t)
+    torch.cuda.synchronize()  # inputs and zeroed outputs complete before the server stream reads them
     srv = F.Server(ctx, scratch_budget_bytes=1 << 20)
     with pytest.raises(F.FsqlError) as e:
         srv.submit(io["column"], t.rows, t.width, t.pred, io["const"], io["payloads"], t.payload_width,
@@ -83,6 +85,7 @@ def test_admission_rejects_query_larger_than_budget(ctx):
 def test_cancel_waiting_query(ctx):
     t = WL.table("eq32x4096", seed=7, rows=32)
     io1, io2 = prepare(ctx, t), prepare(ctx, t)
+    torch.cuda.synchronize()  # inputs and zeroed outputs complete before the server stream reads them
     srv = F.Server(ctx, scratch_budget_bytes=6 << 20)  # one such query at a time
     a = srv.submit(io1["column"], t.rows, t.width, t.pred, io1["const"], io1["payloads"], t.payload_width,
                    io1["match"], io1["outs"])
@@ -107,6 +110,7 @@ def test_served_plain_constant_queries_equal_solo(ctx):
             t.consts = consts
         tables.append(t)
     ios = [prepare(ctx, t) for t in tables]
+    torch.cuda.synchronize()  # inputs and zeroed outputs complete before the server stream reads them
     srv = F.Server(ctx, scratch_budget_bytes=2 << 20, max_batch_gates=64)
     ids = [srv.submit(io["column"], t.rows, t.width, t.pred, None if t.plain else io["const"], io["payloads"],
                       t.payload_width, io["match"], io["outs"], plain_consts=t.consts if t.plain else None)
