@@ -690,9 +690,9 @@ __global__ void __launch_bounds__(G * 2 * kGroup, 1)
 //      polynomials c of its prime from the CTAs (pr, 0..2) (distributed
 //      shared memory reads), folds to [0, 2p) and runs the inverse transform;
 //      the residues go to resid[];
-//   3. cluster barrier; CTA (0, c) reads the p2 residues of polynomial c
-//      from CTA (1, c), lifts the exact integers by CRT into delta[];
-//   4. cluster barrier; every CTA adds delta of ranks 0 and 1 into its ACC.
+//   3. cluster barrier; every CTA reads the four residue polynomials (both
+//      output polynomials mod both primes), lifts both by CRT and adds them
+//      into its own ACC.
 // The residues summed are those the packed kernel sums (the same integer mod
 // each prime), so the CRT gives the same exact integer and the same words.
 constexpr int kClusterCtas = 6;
@@ -700,7 +700,7 @@ constexpr int kClusterSmem = kSplitTabBytes + dev::kDigitTabs * dev::kDigitTabSi
                              2 * 2 * kChunkU64 * 4 +                                        // key rows, 2 slots
                              2 * kN * 4 +                                                   // exchange buffer
                              2 * kN * 4 + 2 * kN * 4 +                                      // ACC, partial sums
-                             kN * 4 + kN * 4 +                                              // residues, delta
+                             kN * 4 +                                                       // residues
                              kMaxN * 2 + 16;                                                // switched mask, body
 
 __global__ void __cluster_dims__(kClusterCtas, 1, 1) __launch_bounds__(kGroup, 1)
@@ -718,8 +718,7 @@ __global__ void __cluster_dims__(kClusterCtas, 1, 1) __launch_bounds__(kGroup, 1
   uint32_t* acc_poly = xbuf + 2 * kN;                              // [2][N]
   uint32_t* part = acc_poly + 2 * kN;                              // [2][N], slot-major (q * 128 + t)
   uint32_t* resid = part + 2 * kN;                                 // [N]
-  uint32_t* delta = resid + kN;                                    // [N]
-  uint16_t* abar = reinterpret_cast<uint16_t*>(delta + kN);        // [kMaxN]
+  uint16_t* abar = reinterpret_cast<uint16_t*>(resid + kN);        // [kMaxN]
   uint32_t* bbar_slot = reinterpret_cast<uint32_t*>(abar + kMaxN);
   const uint32_t p = pr ? dev::kP2 : dev::kP1, p2 = 2 * p, pinv = pr ? dev::kP2inv : dev::kP1inv;
 
@@ -744,12 +743,9 @@ __global__ void __cluster_dims__(kClusterCtas, 1, 1) __launch_bounds__(kGroup, 1
     cp_async_commit();
   };
   uint32_t* part_r[3];   // partial sums of this prime's three CTAs
-  uint32_t* resid_other;  // CTA (1, c)'s residues, read by CTA (0, c)
-  uint32_t* delta_r[2];  // the two CRT results
+  uint32_t* resid_r[4];  // residues of output polynomial c mod prime pr: CTA (pr, c) = rank 3 pr + c
   for (int m = 0; m < 3; ++m) part_r[m] = cl.map_shared_rank(part, pr * 3 + m);
-  resid_other = cl.map_shared_rank(resid, 3 + s);
-  delta_r[0] = cl.map_shared_rank(delta, 0);
-  delta_r[1] = cl.map_shared_rank(delta, 1);
+  for (int m = 0; m < 4; ++m) resid_r[m] = cl.map_shared_rank(resid, 3 * (m >> 1) + (m & 1));
 
   for (int gi = static_cast<int>(blockIdx.x) / kClusterCtas; gi < count;
        gi += static_cast<int>(gridDim.x) / kClusterCtas) {
@@ -826,16 +822,21 @@ __global__ void __cluster_dims__(kClusterCtas, 1, 1) __launch_bounds__(kGroup, 1
 #pragma unroll
         for (int q = 0; q < 8; ++q) resid[t + 128 * q] = y[0][q];
       }
-      cl.sync();  // 2: residues of both primes visible
-      if (pr == 0 && s < 2) {
+      cl.sync();  // 2: the residues of both output polynomials mod both primes visible
+      // every CTA lifts both polynomials by CRT from the four residue
+      // buffers and updates its own ACC (reads done before the next CMux's
+      // barrier 1, after which the buffers are written again)
 #pragma unroll
-        for (int q = 0; q < 8; ++q) delta[t + 128 * q] = dev::crt_torus(y[0][q], resid_other[t + 128 * q]);
+      for (int c = 0; c < 2; ++c) {
+        uint32_t r1[8], r2[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          r1[q] = resid_r[c][t + 128 * q];
+          r2[q] = resid_r[2 + c][t + 128 * q];
+        }
+#pragma unroll
+        for (int q = 0; q < 8; ++q) acc_poly[c * kN + t + 128 * q] += dev::crt_torus(r1[q], r2[q]);
       }
-      cl.sync();  // 3: the two lifted polynomials visible
-#pragma unroll
-      for (int c = 0; c < 2; ++c)
-#pragma unroll
-        for (int q = 0; q < 8; ++q) acc_poly[c * kN + t + 128 * q] += delta_r[c][t + 128 * q];
     }
     __syncthreads();
     if (rank == 0) {
@@ -1136,14 +1137,14 @@ __device__ bool grid_barrier(WalkSync* sync, unsigned int& target, unsigned int 
   return __syncthreads_and(ok) != 0;
 }
 
-template <class F, int G, int kPolys>
+template <class F, int G, int kPolys, bool kOwn>
 __host__ __device__ constexpr int walk_smem() {
-  return br_smem<F, G, kPolys>() > tab_bytes<F>() + digit_tab_bytes<F>() + G * kKsSmem
-             ? br_smem<F, G, kPolys>()
+  return br_smem<F, G, kPolys, kOwn>() > tab_bytes<F>() + digit_tab_bytes<F>() + G * kKsSmem
+             ? br_smem<F, G, kPolys, kOwn>()
              : tab_bytes<F>() + digit_tab_bytes<F>() + G * kKsSmem;
 }
 
-template <class F, int G, int kPolys>
+template <class F, int G, int kPolys, bool kOwn>
 __global__ void __launch_bounds__(G * kGroup, 1)
     scan_walk_kernel(const GateDesc* __restrict__ desc, const WalkSeg* __restrict__ segs, int nsegs,
                      const uint64_t* __restrict__ bkhat, const void* __restrict__ gtab, int n, int bg_bits,
@@ -1161,7 +1162,7 @@ __global__ void __launch_bounds__(G * kGroup, 1)
     const WalkSeg seg = segs[sg];
     const GateDesc* d = desc + seg.begin;
     const int count = static_cast<int>(seg.count);
-    br_body<F, G, kPolys>(d, count, bkhat, gtab, n, bg_bits, big, sg == 0);
+    br_body<F, G, kPolys, kOwn>(d, count, bkhat, gtab, n, bg_bits, big, sg == 0);
     if (!grid_barrier(sync, target, index++, timeout_ns, skip)) return;
     const int items = (count + kKsGates - 1) / kKsGates * kKsTiles;
     for (int it = blockIdx.x * G + grp; it < items; it += gridDim.x * G) {
@@ -1525,7 +1526,7 @@ int device_init(Ctx& c) {
   }
   CK(cudaSetDevice(c.device));
   // gates per CTA for large batches: measured best on B300 unless tuned in this process
-  c.br_shape = c.engine == FSQL_ENGINE_GOLDILOCKS ? 3 : 2;  // packed 4 / 3 gates per CTA
+  c.br_shape = c.engine == FSQL_ENGINE_GOLDILOCKS ? 3 : 8;  // packed 4 gates / 3 gates with a key slot per group
   if (const int g = tuned_shape(c.device, c.engine)) c.br_shape = g - 1;
   int sms = 0;
   CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c.device));
@@ -1758,9 +1759,9 @@ static cudaError_t launch_br_any(Ctx& c, const GateDesc* d_desc, size_t count, u
   }
   using F = dev::DualPrime;
   if (small && c.latency_mode == 2) {
-    // a cluster per gate while there are at most two clusters' worth of gates per cluster slot
+    // a cluster per gate while every gate gets a cluster of its own at once
     int clusters = 0;
-    if (cluster_capacity(&clusters) == cudaSuccess && count <= static_cast<size_t>(2 * clusters))
+    if (cluster_capacity(&clusters) == cudaSuccess && count <= static_cast<size_t>(clusters))
       return launch_br_cluster(count, d_desc, c.d_bks, c.d_tables_split, n, bg, d_big, st);
   }
   if (small && c.latency_mode)
@@ -1786,19 +1787,19 @@ static cudaError_t launch_br_any(Ctx& c, const GateDesc* d_desc, size_t count, u
 
 // The device level walker over nsegs segments (cooperative launch, one CTA
 // per SM), for the packed two-prime kernel with G gates per CTA.
-template <int G>
+template <int G, bool kOwn>
 static cudaError_t launch_walk_engine(Ctx& c, const GateDesc* d_desc, const WalkSeg* d_segs, int nsegs,
                                       uint32_t* d_big, cudaStream_t st) {
   using F = dev::DualPrime;
   constexpr int kP = 2;
-  static_assert(walk_smem<F, G, kP>() <= 227 * 1024, "walker shared memory over budget");
+  static_assert(walk_smem<F, G, kP, kOwn>() <= 227 * 1024, "walker shared memory over budget");
   static bool attr_set[64] = {};
   int dev = 0;
   cudaGetDevice(&dev);
   if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
   if (!attr_set[dev]) {
-    const cudaError_t e = cudaFuncSetAttribute(scan_walk_kernel<F, G, kP>,
-                                               cudaFuncAttributeMaxDynamicSharedMemorySize, walk_smem<F, G, kP>());
+    const cudaError_t e = cudaFuncSetAttribute(scan_walk_kernel<F, G, kP, kOwn>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               walk_smem<F, G, kP, kOwn>());
     if (e != cudaSuccess) return e;
     attr_set[dev] = true;
   }
@@ -1811,8 +1812,8 @@ static cudaError_t launch_walk_engine(Ctx& c, const GateDesc* d_desc, const Walk
   const uint32_t* ksk = c.d_ksk;
   WalkSync* sy = c.d_walk_sync;
   void* args[] = {&d_desc, &d_segs, &nsegs, &bk, &tb, &n, &bg, &d_big, &ksk, &sy, &tmo, &skip};
-  return cudaLaunchCooperativeKernel(reinterpret_cast<const void*>(scan_walk_kernel<F, G, kP>), dim3(c.sm_count),
-                                     dim3(G * kGroup), args, walk_smem<F, G, kP>(), st);
+  return cudaLaunchCooperativeKernel(reinterpret_cast<const void*>(scan_walk_kernel<F, G, kP, kOwn>),
+                                     dim3(c.sm_count), dim3(G * kGroup), args, walk_smem<F, G, kP, kOwn>(), st);
 }
 
 // Whether a scan's levels can run on the device walker: the two-prime engine
@@ -1820,17 +1821,18 @@ static cudaError_t launch_walk_engine(Ctx& c, const GateDesc* d_desc, const Walk
 // persistent multi-gate kernel (at least two gates per SM).
 bool walk_supported(const Ctx& c) {
   const BrShape sh = kBrShapes[c.br_shape];
-  return c.walk_mode && c.engine == FSQL_ENGINE_DUAL_PRIME && sh.kind == 0 && (sh.gates == 2 || sh.gates == 3) &&
-         c.d_walk_sync;
+  return c.walk_mode && c.engine == FSQL_ENGINE_DUAL_PRIME &&
+         ((sh.kind == 0 && (sh.gates == 2 || sh.gates == 3)) || sh.kind == 2) && c.d_walk_sync;
 }
 
 int launch_walk(Ctx& c, const GateDesc* d_desc, const WalkSeg* d_segs, int nsegs, size_t gates, uint32_t* d_big,
                 void* stream) {
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   LaunchTimer tm(c, st);
-  const int g = kBrShapes[c.br_shape].gates;
-  cudaError_t e = g == 2 ? launch_walk_engine<2>(c, d_desc, d_segs, nsegs, d_big, st)
-                         : launch_walk_engine<3>(c, d_desc, d_segs, nsegs, d_big, st);
+  const BrShape sh = kBrShapes[c.br_shape];
+  cudaError_t e = sh.kind == 2   ? launch_walk_engine<3, true>(c, d_desc, d_segs, nsegs, d_big, st)
+                  : sh.gates == 2 ? launch_walk_engine<2, false>(c, d_desc, d_segs, nsegs, d_big, st)
+                                  : launch_walk_engine<3, false>(c, d_desc, d_segs, nsegs, d_big, st);
   if (e != cudaSuccess) {
     set_error(std::string("walker launch: ") + cudaGetErrorString(e));
     return FSQL_ERR_CUDA;
