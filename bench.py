@@ -65,6 +65,8 @@ def parse():
     ap.add_argument("--verify-rows", type=int, default=2,
                     help="rows of the timed scan the CPU oracle recomputes word for word (first, matching, last...)")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default launch shape")
+    ap.add_argument("--exact-warmup", action="store_true",
+                    help="run exactly --warmup warm-up steps even below 3 (single long measurements; the line says so)")
     ap.add_argument("--walk", action="store_true", help="batched scans as one device-walked launch")
     ap.add_argument("--br-shape", type=int, default=None,
                     help="blind-rotation launch shape index (implies --no-autotune)")
@@ -206,6 +208,11 @@ def oracle_gates_per_row(table) -> int:
     return int(O.netlist3(table.pred, table.width, npay, table.payload_width)[0].size)
 
 
+def warmups(args) -> int:
+    """Warm-up steps: at least 3 (the timing rule), unless --exact-warmup."""
+    return args.warmup if args.exact_warmup else max(3, args.warmup)
+
+
 def pick_shape(ctx, args):
     """The blind-rotation launch shape: given on the command line, else the
     library's autotuner (timed on synthetic gates before anything is timed
@@ -344,7 +351,7 @@ def run_gates(args, dist):
     db = torch.from_numpy(y.view(np.int32)).to(f"cuda:{dev}")
     out = torch.zeros((B, ctx.words), dtype=torch.int32, device=f"cuda:{dev}")
     st = torch.cuda.current_stream()
-    for _ in range(max(3, args.warmup)):
+    for _ in range(warmups(args)):
         ctx.gate_batch(dt, da, db, out, stream=st)
     torch.cuda.synchronize()
     sampler = ClockSampler(bus_id_of(dev))
@@ -397,7 +404,7 @@ def run_gates(args, dist):
                "sample": f"{m} random gates of the batch in {dt_cpu:.1f} s"}
         o.close()
     line = {"metric": "gate bootstraps/s", "value": value, "unit": "gate bootstraps/s", "n_gpus": dist.world,
-            "steps": args.steps, "warmup": max(3, args.warmup), "ms_per_step": ms / args.steps,
+            "steps": args.steps, "warmup": warmups(args), "ms_per_step": ms / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32 (exact integer)",
             "data": "synthetic (seeded random gates, seeded keys)",
             "config": {"workload": f"gates x{B}", "engine": ["goldilocks", "dual_prime"][ctx.engine],
@@ -790,7 +797,7 @@ def run_ours(args, dist):
         for o_, s_ in zip(outs, sums):
             ctx.aggregate_sum(o_, t.rows, t.payload_width, t.sum_width, s_, stream=st)
 
-    for _ in range(max(3, args.warmup)):
+    for _ in range(warmups(args)):
         step()
     torch.cuda.synchronize()
 
@@ -919,7 +926,7 @@ def run_ours(args, dist):
 
     line = {
         "metric": "gate bootstraps/s", "value": value, "unit": "gate bootstraps/s", "n_gpus": dist.world,
-        "steps": args.steps, "warmup": max(3, args.warmup), "ms_per_step": ms / args.steps,
+        "steps": args.steps, "warmup": warmups(args), "ms_per_step": ms / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32/u64 (exact integer)",
         "data": "synthetic (seeded tables, seeded keys)",
         "rows_per_s": dist.world * t.rows * args.steps / (ms / 1e3),

@@ -149,13 +149,13 @@ FSQL_API int fsql_br_shape_info(int shape, int* kind, int* gates_per_cta, int* r
 FSQL_API int fsql_ctx_set_br_gates(fsql_ctx* ctx, int gates_per_cta);
 FSQL_API int fsql_ctx_br_gates(const fsql_ctx* ctx, int* gates_per_cta);
 /* Latency mode for batches smaller than two gates per SM (two-prime
- * engine).  0: one gate per 128-thread CTA.  1 (default): one gate per CTA of
- * three 128-thread groups that run the three gadget-row steps of every CMux
- * side by side.  2: one gate per thread-block cluster of six CTAs on six
- * SMs (each one prime and two gadget rows; partial sums, residues and the
- * accumulator update exchanged through distributed shared memory with three
- * cluster barriers per CMux), used while the batch holds at most two gates
- * per cluster the GPU can run at once, mode 1 above that.  The output words
+ * engine).  0: one gate per 128-thread CTA.  1: one gate per CTA of three
+ * 128-thread groups that run the three gadget-row steps of every CMux side
+ * by side.  2 (default): one gate per thread-block cluster of six CTAs on six
+ * SMs (each one prime and two gadget rows; partial sums and residues pushed
+ * into the other CTAs' shared memory, two cluster barriers per CMux), used
+ * while every gate of the batch gets a cluster of its own at once, mode 1
+ * above that.  The output words
  * are the same in every mode.  FSQL_ERR_ARG for other values. */
 FSQL_API int fsql_ctx_set_latency_mode(fsql_ctx* ctx, int on);
 

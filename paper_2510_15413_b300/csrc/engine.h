@@ -103,8 +103,9 @@ struct Ctx {
   int device = -1;
   int engine = FSQL_ENGINE_DUAL_PRIME;
   int br_shape = 2;              // launch shape of the blind rotation for large batches (index into kBrShapes)
-  int latency_mode = 1;          // small batches (two-prime engine): 0 one gate per 128-thread CTA,
+  int latency_mode = 2;          // small batches (two-prime engine): 0 one gate per 128-thread CTA,
                                  // 1 one gate per CTA of three groups, 2 one gate per cluster of 6 CTAs
+                                 // (while every gate gets a cluster at once, else 1)
   bool walk_mode = false;        // batched scans as one device-walked launch (scan_walk_kernel)
   double walk_timeout_ms = 2000.0;  // limit of each grid-barrier wait of the walker
   int walk_skip_block = -1;      // test hook: this CTA never arrives at the walker's barriers

@@ -684,23 +684,22 @@ __global__ void __launch_bounds__(G * 2 * kGroup, 1)
 //   1. every CTA keeps a full copy of ACC; it forms the digits of its two
 //      rows, transforms them mod its prime (first two stages by digit table)
 //      and multiply-accumulates them with its two staged key rows into
-//      per-slot sums of the two output polynomials, reduced to [0, 2p)
-//      (part[c][slot]);
-//   2. cluster barrier; CTA (pr, c), c = 0, 1, sums the three partial
-//      polynomials c of its prime from the CTAs (pr, 0..2) (distributed
-//      shared memory reads), folds to [0, 2p) and runs the inverse transform;
-//      the residues go to resid[];
-//   3. cluster barrier; every CTA reads the four residue polynomials (both
-//      output polynomials mod both primes), lifts both by CRT and adds them
-//      into its own ACC.
+//      per-slot sums of the two output polynomials, reduced to [0, 2p) and
+//      stored straight into the shared memory of CTA (pr, c) for output
+//      polynomial c (distributed shared memory);
+//   2. cluster barrier; CTA (pr, c), c = 0, 1, sums the three partials it
+//      received, folds to [0, 2p), runs the inverse transform and stores the
+//      residues into every CTA of the cluster;
+//   3. cluster barrier; every CTA lifts both polynomials by CRT from the four
+//      residue polynomials it holds and adds them into its own ACC.
 // The residues summed are those the packed kernel sums (the same integer mod
 // each prime), so the CRT gives the same exact integer and the same words.
 constexpr int kClusterCtas = 6;
 constexpr int kClusterSmem = kSplitTabBytes + dev::kDigitTabs * dev::kDigitTabSize * 4 +  // tables
                              2 * 2 * kChunkU64 * 4 +                                        // key rows, 2 slots
                              2 * kN * 4 +                                                   // exchange buffer
-                             2 * kN * 4 + 2 * kN * 4 +                                      // ACC, partial sums
-                             kN * 4 +                                                       // residues
+                             2 * kN * 4 + 3 * kN * 4 +                                      // ACC, partial sums
+                             4 * kN * 4 +                                                   // residues
                              kMaxN * 2 + 16;                                                // switched mask, body
 
 __global__ void __cluster_dims__(kClusterCtas, 1, 1) __launch_bounds__(kGroup, 1)
@@ -716,9 +715,9 @@ __global__ void __cluster_dims__(kClusterCtas, 1, 1) __launch_bounds__(kGroup, 1
   uint32_t* keys = dtab + dev::kDigitTabs * dev::kDigitTabSize;  // [2 slots][2 rows][kChunkU64]
   uint32_t* xbuf = keys + 2 * 2 * kChunkU64;                       // [2][N]
   uint32_t* acc_poly = xbuf + 2 * kN;                              // [2][N]
-  uint32_t* part = acc_poly + 2 * kN;                              // [2][N], slot-major (q * 128 + t)
-  uint32_t* resid = part + 2 * kN;                                 // [N]
-  uint16_t* abar = reinterpret_cast<uint16_t*>(resid + kN);        // [kMaxN]
+  uint32_t* part = acc_poly + 2 * kN;                              // [3 senders][N], slot-major (q * 128 + t)
+  uint32_t* resid = part + 3 * kN;                                 // [2 polys][2 primes][N]
+  uint16_t* abar = reinterpret_cast<uint16_t*>(resid + 4 * kN);    // [kMaxN]
   uint32_t* bbar_slot = reinterpret_cast<uint32_t*>(abar + kMaxN);
   const uint32_t p = pr ? dev::kP2 : dev::kP1, p2 = 2 * p, pinv = pr ? dev::kP2inv : dev::kP1inv;
 
@@ -742,10 +741,14 @@ __global__ void __cluster_dims__(kClusterCtas, 1, 1) __launch_bounds__(kGroup, 1
     }
     cp_async_commit();
   };
-  uint32_t* part_r[3];   // partial sums of this prime's three CTAs
-  uint32_t* resid_r[4];  // residues of output polynomial c mod prime pr: CTA (pr, c) = rank 3 pr + c
-  for (int m = 0; m < 3; ++m) part_r[m] = cl.map_shared_rank(part, pr * 3 + m);
-  for (int m = 0; m < 4; ++m) resid_r[m] = cl.map_shared_rank(resid, 3 * (m >> 1) + (m & 1));
+  // exchanges are pushes (stores into the receiver's shared memory), so
+  // every read after a barrier is local: partial sums of output polynomial c
+  // go to CTA (pr, c), slot s; the residues of CTA (pr, c) go to every CTA,
+  // slot [c][pr]
+  uint32_t* part_to[2];
+  for (int c = 0; c < 2; ++c) part_to[c] = cl.map_shared_rank(part, pr * 3 + c) + s * kN;
+  uint32_t* resid_to[kClusterCtas];
+  for (int m = 0; m < kClusterCtas; ++m) resid_to[m] = cl.map_shared_rank(resid, m) + (s * 2 + pr) * kN;
 
   for (int gi = static_cast<int>(blockIdx.x) / kClusterCtas; gi < count;
        gi += static_cast<int>(gridDim.x) / kClusterCtas) {
@@ -806,37 +809,33 @@ __global__ void __cluster_dims__(kClusterCtas, 1, 1) __launch_bounds__(kGroup, 1
           s0 += static_cast<uint64_t>(x[r][q]) * w.x;
           s1 += static_cast<uint64_t>(x[r][q]) * w.y;
         }
-        part[q * kGroup + t] = dev::DualPrime::settle(s0, p, pinv);
-        part[kN + q * kGroup + t] = dev::DualPrime::settle(s1, p, pinv);
+        part_to[0][q * kGroup + t] = dev::DualPrime::settle(s0, p, pinv);
+        part_to[1][q * kGroup + t] = dev::DualPrime::settle(s1, p, pinv);
       }
-      cl.sync();  // 1: every CTA's partial sums visible
-      uint32_t y[1][8];
+      cl.sync();  // 1: every partial sum delivered
       if (s < 2) {
+        uint32_t y[1][8];
 #pragma unroll
         for (int q = 0; q < 8; ++q) {
-          const int o = s * kN + q * kGroup + t;
-          const uint32_t v = part_r[0][o] + part_r[1][o] + part_r[2][o];  // below 6p
+          const int o = q * kGroup + t;
+          const uint32_t v = part[o] + part[kN + o] + part[2 * kN + o];  // below 6p
           y[0][q] = dev::fold(dev::fold(v, 2 * p2), p2);
         }
         dev::ntt_inverse32<1, 2, 1>(y, xbuf, parity, T, t, 1, p, p2);
 #pragma unroll
-        for (int q = 0; q < 8; ++q) resid[t + 128 * q] = y[0][q];
+        for (int m = 0; m < kClusterCtas; ++m)
+#pragma unroll
+          for (int q = 0; q < 8; ++q) resid_to[m][t + 128 * q] = y[0][q];
       }
-      cl.sync();  // 2: the residues of both output polynomials mod both primes visible
-      // every CTA lifts both polynomials by CRT from the four residue
-      // buffers and updates its own ACC (reads done before the next CMux's
-      // barrier 1, after which the buffers are written again)
+      cl.sync();  // 2: the residues of both output polynomials mod both primes delivered
+      // every CTA lifts both polynomials by CRT and updates its own ACC (the
+      // buffers are written again only after the next CMux's barrier 1)
 #pragma unroll
-      for (int c = 0; c < 2; ++c) {
-        uint32_t r1[8], r2[8];
+      for (int c = 0; c < 2; ++c)
 #pragma unroll
-        for (int q = 0; q < 8; ++q) {
-          r1[q] = resid_r[c][t + 128 * q];
-          r2[q] = resid_r[2 + c][t + 128 * q];
-        }
-#pragma unroll
-        for (int q = 0; q < 8; ++q) acc_poly[c * kN + t + 128 * q] += dev::crt_torus(r1[q], r2[q]);
-      }
+        for (int q = 0; q < 8; ++q)
+          acc_poly[c * kN + t + 128 * q] +=
+              dev::crt_torus(resid[(c * 2) * kN + t + 128 * q], resid[(c * 2 + 1) * kN + t + 128 * q]);
     }
     __syncthreads();
     if (rank == 0) {

@@ -297,8 +297,8 @@ class Context:
 
     def set_latency_mode(self, mode) -> None:
         """Kernel for batches under two gates per SM: 0 (or False) one gate per
-        128-thread CTA, 1 (or True, the default) one gate per CTA of three
-        groups, 2 one gate per cluster of six CTAs."""
+        128-thread CTA, 1 (or True) one gate per CTA of three groups, 2 (the
+        default) one gate per cluster of six CTAs."""
         _check(load().fsql_ctx_set_latency_mode(self._h, int(mode)))
 
     @property

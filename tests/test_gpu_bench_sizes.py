@@ -330,4 +330,4 @@ def test_cluster_latency_mode_equals_other_modes_and_oracle(env):
             truth = np.array([O.gate_plain(int(t), int(x), int(y)) for t, x, y in zip(types, xb, yb)], np.uint8)
             assert np.array_equal(ctx.decrypt_bits(res[2]), truth)
     finally:
-        ctx.set_latency_mode(1)
+        ctx.set_latency_mode(2)

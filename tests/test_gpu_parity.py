@@ -294,7 +294,7 @@ def test_latency_mode_equals_group_mode_and_oracle(env):
             out = torch.zeros((count, ctx.words), dtype=torch.int32, device="cuda")
             ctx.gate_batch(dev(types), dev(a.view(np.int32)), dev(b.view(np.int32)), out)
             res.append(host(out).view(np.uint32))
-        ctx.set_latency_mode(True)
+        ctx.set_latency_mode(2)
         assert np.array_equal(res[0], res[1]), count
         k = min(count, 4)
         assert np.array_equal(res[0][:k], o.gate_batch(types[:k].astype(np.int32), a[:k], b[:k]))
