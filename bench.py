@@ -53,6 +53,8 @@ def parse():
     ap.add_argument("--serve-inflight", type=int, default=8, help="outstanding queries in the saturated phase")
     ap.add_argument("--serve-budget-gb", type=float, default=96.0, help="server scratch budget (GiB)")
     ap.add_argument("--verify-queries", type=int, default=2, help="served queries per phase checked by the oracle")
+    ap.add_argument("--serve-loads", default="0.5,0.9",
+                    help="Poisson phases, as fractions of the saturated query rate")
     ap.add_argument("--batch", type=int, default=65536, help="gates per step of the gate microbenchmark")
     ap.add_argument("--sweep", default="",
                     help="gate microbenchmark over these batch sizes (comma separated, e.g. 1,16,256,4096,65536,1048576)")
@@ -632,7 +634,7 @@ def run_serving(args, dist):
     sat, checked = phase(0.0)
     q_rate = sat["queries"] / sat["wall_s"]
     runs = [sat]
-    for frac in (0.5, 0.9):
+    for frac in (float(v) for v in args.serve_loads.split(",") if v):
         r, c = phase(frac * q_rate)
         r["load"] = frac
         runs.append(r)

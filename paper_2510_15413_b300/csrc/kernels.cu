@@ -681,17 +681,20 @@ __global__ void __launch_bounds__(G * 2 * kGroup, 1)
 // pipes; here its work per CMux is spread over 6 SMs that exchange through
 // distributed shared memory.  CTA rank r = 3 pr + s: prime pr (p1 or p2,
 // 32-bit residues), gadget rows 2s and 2s + 1.  Per CMux:
-//   1. every CTA keeps a full copy of ACC; it forms the digits of its two
+//   1. every CTA keeps a copy of the ACC polynomials its rows read (CTA
+//      (pr, 1) both, the others one); it forms the digits of its two
 //      rows, transforms them mod its prime (first two stages by digit table)
 //      and multiply-accumulates them with its two staged key rows into
 //      per-slot sums of the two output polynomials, reduced to [0, 2p) and
-//      stored straight into the shared memory of CTA (pr, c) for output
+//      stored straight into the shared memory of the CTA that reduces output
 //      polynomial c (distributed shared memory);
-//   2. cluster barrier; CTA (pr, c), c = 0, 1, sums the three partials it
-//      received, folds to [0, 2p), runs the inverse transform and stores the
-//      residues into every CTA of the cluster;
-//   3. cluster barrier; every CTA lifts both polynomials by CRT from the four
-//      residue polynomials it holds and adds them into its own ACC.
+//   2. cluster barrier; CTA (pr, 0) for output polynomial 0 and CTA (pr, 2)
+//      for polynomial 1 sum the three partials they received, fold to
+//      [0, 2p), run the inverse transform and store the residues into every
+//      CTA of the cluster;
+//   3. cluster barrier; every CTA lifts by CRT the polynomials its two rows
+//      read (both for CTA (pr, 1), which runs no inverse) and adds them into
+//      its own ACC; the sample is extracted by CTA (0, 1).
 // The residues summed are those the packed kernel sums (the same integer mod
 // each prime), so the CRT gives the same exact integer and the same words.
 constexpr int kClusterCtas = 6;
@@ -745,10 +748,14 @@ __global__ void __cluster_dims__(kClusterCtas, 1, 1) __launch_bounds__(kGroup, 1
   // every read after a barrier is local: partial sums of output polynomial c
   // go to CTA (pr, c), slot s; the residues of CTA (pr, c) go to every CTA,
   // slot [c][pr]
+  // output polynomial 0 is reduced and inverted by CTA (pr, 0), polynomial
+  // 1 by CTA (pr, 2); CTA (pr, 1), whose rows touch both polynomials, only
+  // lifts, so the three CTAs of a prime carry about the same work per CMux
+  const int red_c = s == 0 ? 0 : s == 2 ? 1 : -1;  // the polynomial this CTA reduces, if any
   uint32_t* part_to[2];
-  for (int c = 0; c < 2; ++c) part_to[c] = cl.map_shared_rank(part, pr * 3 + c) + s * kN;
+  for (int c = 0; c < 2; ++c) part_to[c] = cl.map_shared_rank(part, pr * 3 + 2 * c) + s * kN;
   uint32_t* resid_to[kClusterCtas];
-  for (int m = 0; m < kClusterCtas; ++m) resid_to[m] = cl.map_shared_rank(resid, m) + (s * 2 + pr) * kN;
+  for (int m = 0; m < kClusterCtas; ++m) resid_to[m] = cl.map_shared_rank(resid, m) + ((red_c < 0 ? 0 : red_c) * 2 + pr) * kN;
 
   for (int gi = static_cast<int>(blockIdx.x) / kClusterCtas; gi < count;
        gi += static_cast<int>(gridDim.x) / kClusterCtas) {
@@ -813,7 +820,7 @@ __global__ void __cluster_dims__(kClusterCtas, 1, 1) __launch_bounds__(kGroup, 1
         part_to[1][q * kGroup + t] = dev::DualPrime::settle(s1, p, pinv);
       }
       cl.sync();  // 1: every partial sum delivered
-      if (s < 2) {
+      if (red_c >= 0) {
         uint32_t y[1][8];
 #pragma unroll
         for (int q = 0; q < 8; ++q) {
@@ -828,17 +835,20 @@ __global__ void __cluster_dims__(kClusterCtas, 1, 1) __launch_bounds__(kGroup, 1
           for (int q = 0; q < 8; ++q) resid_to[m][t + 128 * q] = y[0][q];
       }
       cl.sync();  // 2: the residues of both output polynomials mod both primes delivered
-      // every CTA lifts both polynomials by CRT and updates its own ACC (the
-      // buffers are written again only after the next CMux's barrier 1)
+      // every CTA lifts by CRT the polynomials its rows read (CTA (pr, 1)
+      // both) and updates its own ACC (the buffers are written again only
+      // after the next CMux's barrier 1)
 #pragma unroll
-      for (int c = 0; c < 2; ++c)
+      for (int c = 0; c < 2; ++c) {
+        if (c != u0 && c != u1) continue;
 #pragma unroll
         for (int q = 0; q < 8; ++q)
           acc_poly[c * kN + t + 128 * q] +=
               dev::crt_torus(resid[(c * 2) * kN + t + 128 * q], resid[(c * 2 + 1) * kN + t + 128 * q]);
+      }
     }
     __syncthreads();
-    if (rank == 0) {
+    if (rank == 1) {  // CTA (0, 1) keeps both polynomials of ACC
       uint32_t* out = big + static_cast<size_t>(gi) * (kN + 1);
 #pragma unroll
       for (int q = 0; q < 8; ++q) {
@@ -1041,14 +1051,24 @@ __device__ __forceinline__ void ks_tile(const uint32_t* __restrict__ big, const 
 #pragma unroll
   for (int g = 0; g < kKsGates; ++g) acc[g] = 0u;
   const uint32_t* base = ksk + col;
+  // the 24 key words of position i + 1 are loaded while position i is summed
+  uint32_t nxt[kKsT][kKsDigits];
+#pragma unroll
+  for (int j = 0; j < kKsT; ++j)
+#pragma unroll
+    for (int v = 0; v < kKsDigits; ++v) nxt[j][v] = __ldg(base + static_cast<size_t>(j * kKsDigits + v) * kKsRowWords);
 #pragma unroll 1
   for (int i = 0; i < kN; ++i) {
 #pragma unroll
-    for (int j = 0; j < kKsT; ++j) {
-      const uint32_t* rows = base + static_cast<size_t>((i * kKsT + j) * kKsDigits) * kKsRowWords;
-      tbl[j][1][tc] = __ldg(rows);
-      tbl[j][2][tc] = __ldg(rows + kKsRowWords);
-      tbl[j][3][tc] = __ldg(rows + 2 * kKsRowWords);
+    for (int j = 0; j < kKsT; ++j)
+#pragma unroll
+      for (int v = 0; v < kKsDigits; ++v) tbl[j][1 + v][tc] = nxt[j][v];
+    if (i + 1 < kN) {
+      const uint32_t* rows = base + static_cast<size_t>((i + 1) * kKsT * kKsDigits) * kKsRowWords;
+#pragma unroll
+      for (int j = 0; j < kKsT; ++j)
+#pragma unroll
+        for (int v = 0; v < kKsDigits; ++v) nxt[j][v] = __ldg(rows + static_cast<size_t>(j * kKsDigits + v) * kKsRowWords);
     }
 #pragma unroll
     for (int g = 0; g < kKsGates; ++g) {
@@ -1271,14 +1291,24 @@ __global__ void __launch_bounds__(kKsCols)
 #pragma unroll
   for (int g = 0; g < kKsGates; ++g) acc[g] = 0u;
   const uint32_t* base = ksk + col;
+  // the 24 key words of position i + 1 are loaded while position i is summed
+  uint32_t nxt[kKsT][kKsDigits];
+#pragma unroll
+  for (int j = 0; j < kKsT; ++j)
+#pragma unroll
+    for (int v = 0; v < kKsDigits; ++v) nxt[j][v] = __ldg(base + static_cast<size_t>(j * kKsDigits + v) * kKsRowWords);
 #pragma unroll 1
   for (int i = 0; i < kN; ++i) {
 #pragma unroll
-    for (int j = 0; j < kKsT; ++j) {
-      const uint32_t* rows = base + static_cast<size_t>((i * kKsT + j) * kKsDigits) * kKsRowWords;
-      tbl[j][1][tc] = __ldg(rows);
-      tbl[j][2][tc] = __ldg(rows + kKsRowWords);
-      tbl[j][3][tc] = __ldg(rows + 2 * kKsRowWords);
+    for (int j = 0; j < kKsT; ++j)
+#pragma unroll
+      for (int v = 0; v < kKsDigits; ++v) tbl[j][1 + v][tc] = nxt[j][v];
+    if (i + 1 < kN) {
+      const uint32_t* rows = base + static_cast<size_t>((i + 1) * kKsT * kKsDigits) * kKsRowWords;
+#pragma unroll
+      for (int j = 0; j < kKsT; ++j)
+#pragma unroll
+        for (int v = 0; v < kKsDigits; ++v) nxt[j][v] = __ldg(rows + static_cast<size_t>(j * kKsDigits + v) * kKsRowWords);
     }
 #pragma unroll
     for (int g = 0; g < kKsGates; ++g) {
