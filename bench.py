@@ -553,7 +553,7 @@ def run_serving(args, dist):
             consts = (int(base.column[int(rng.integers(0, base.rows))]),)
         else:
             span = max(1, (1 << w) // 10)
-            lo = int(rng.integers(0, (1 << w) - span + 1))
+            lo = int(rng.integers(0, (1 << w) - span))  # hi stays a w-bit value
             consts = (lo, lo + span)
         t = WL.Table(base.name, base.rows, w, base.pred, base.column, base.payloads, base.payload_width, consts)
         k = qcount[0]

@@ -249,8 +249,11 @@ struct Server {
     }
     for (Query* q : r.queries) {
       if (--q->inflight == 0 && (q->all_issued || q->cancel || q->state == Q_FAILED)) {
-        complete_locked(q);
-        running.erase(std::find(running.begin(), running.end(), q));
+        auto it = std::find(running.begin(), running.end(), q);
+        if (it != running.end()) {
+          complete_locked(q);
+          running.erase(it);
+        }
       }
     }
     if (r.start) free_events.push_back(r.start);

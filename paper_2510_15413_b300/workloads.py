@@ -135,7 +135,7 @@ def table(name: str, seed: int = 1, rows: int | None = None) -> Table:
         c = g.integers(0, 1 << 16, r, dtype=np.uint64)
         ps = [g.integers(0, 1 << 16, r, dtype=np.uint64) for _ in range(2)]
         span = 6554
-        lo = int(g.integers(0, 65536 - span + 1))
+        lo = int(g.integers(0, 65536 - span))  # hi = lo + span stays below 2^16
         return Table(name, r, 16, PRED_RANGE, c, ps, 16, (lo, lo + span))
     if name == "lt8x64":
         r = rows or 64
@@ -168,7 +168,7 @@ def serving_queries(count: int, seed: int = 1, min_log2: float = 8.0, max_log2: 
             out.append(Table(f"q{i}", rows, w, PRED_EQ, c, pays, w, (int(c[int(g.integers(0, rows))]),)))
         else:
             span = max(1, (1 << w) // 10)
-            lo = int(g.integers(0, (1 << w) - span + 1))
+            lo = int(g.integers(0, (1 << w) - span))  # hi = lo + span stays below 2^w
             out.append(Table(f"q{i}", rows, w, PRED_RANGE, c, pays, w, (lo, lo + span)))
     return out
 

@@ -211,3 +211,16 @@ def test_big_key_encryption_equals_oracle():
     assert np.array_equal(a, o.encrypt_big_bits(bits, 5, 7))
     assert np.array_equal(ctx.decrypt_big_bits(a), bits)
     assert np.array_equal(o.decrypt_big_bits(a), bits)
+
+
+def test_workload_range_bounds_fit_the_column_width():
+    """Every RANGE query of the serving mix and of the named tables has
+    lo <= hi < 2^width: an hi of 2^width would be encrypted as 0 (its w bits)
+    while the SQL answer treats it as 2^width."""
+    for seed in range(1, 6):
+        for t in WL.serving_queries(300, seed=seed, min_log2=8, max_log2=16):
+            if t.pred == WL.PRED_RANGE:
+                assert t.consts[0] <= t.consts[1] < (1 << t.width), (seed, t.name, t.consts)
+        for name in ("range16x65536", "range4x16"):
+            t = WL.table(name, seed=seed)
+            assert t.consts[0] <= t.consts[1] < (1 << t.width)
