@@ -445,7 +445,10 @@ typedef struct fsql_server_stats {
  * most max_batch_gates gate bootstraps (0 = 2^17).  A submitted query waits
  * until its device scratch (descriptors and intermediate wires, about
  * rows x gates_per_row x (32 + 2524) bytes) fits in scratch_budget_bytes,
- * which the server allocates once.  Results are bit-identical to
+ * which the server allocates once, and until the running queries' current
+ * levels no longer fill an efficient round (64 gates per SM, or
+ * max_batch_gates if smaller), so that under load queries finish closer to
+ * arrival order instead of all sharing the GPU equally.  Results are bit-identical to
  * fsql_scan_select of the same query alone.  The context must not be
  * destroyed before the server. */
 FSQL_API int fsql_server_create(fsql_ctx* ctx, size_t scratch_budget_bytes, size_t max_batch_gates,

@@ -130,6 +130,7 @@ constexpr int kPipelineDepth = 2;  // rounds enqueued ahead of the one being wai
 struct Server {
   Ctx* ctx = nullptr;
   size_t max_batch = 0;
+  size_t fill_gates = 0;  // admission stops while the running queries' current levels hold this many gates
   Pool pool{0};
   uint8_t* d_pool = nullptr;
   GateDesc* d_round = nullptr;
@@ -162,10 +163,27 @@ struct Server {
     return e;
   }
 
-  // Admit waiting queries in arrival order while their blocks fit (caller
-  // holds mu): copy the scan program, generate the descriptors on the device,
-  // copy the descriptors of the outputs no gate writes (all on the stream).
+  // Gates the running queries still have in their current levels: the size
+  // of the next round before anything else is admitted.
+  size_t pending_gates_locked() const {
+    size_t g = 0;
+    for (const Query* q : running)
+      if (!q->all_issued && !q->cancel && q->state == Q_RUNNING && q->level < q->nl.levels)
+        g += q->level_offset[q->level + 1] - q->level_offset[q->level] - q->done_in_level;
+    return g;
+  }
+
+  // Admit waiting queries in arrival order while their blocks fit and the
+  // running queries' current levels do not already fill an efficient round
+  // (fill_gates: 64 gates per SM, about 21 waves of the 3-gate kernel, or
+  // max_batch if smaller) (caller holds mu): copy the
+  // scan program, generate the descriptors on the device, copy the
+  // descriptors of the outputs no gate writes (all on the stream).  The
+  // round-fill condition keeps early arrivals from being slowed down by
+  // later ones once the GPU is busy (queries run closer to arrival order),
+  // while every round that can be full still is.
   void admit_locked() {
+    size_t pending = pending_gates_locked();
     while (!waiting.empty()) {
       Query* q = waiting.front();
       if (q->cancel) {
@@ -173,6 +191,7 @@ struct Server {
         waiting.pop_front();
         continue;
       }
+      if (pending >= fill_gates) break;
       size_t off = 0;
       if (!pool.alloc(q->bytes, &off)) break;
       q->off = off;
@@ -215,6 +234,7 @@ struct Server {
       q->state = Q_RUNNING;
       running.push_back(q);
       waiting.pop_front();
+      if (q->nl.levels > 0) pending += q->level_offset[1] - q->level_offset[0];
     }
   }
 
@@ -398,6 +418,7 @@ int fsql_server_create(fsql_ctx* ctx, size_t scratch_budget_bytes, size_t max_ba
   auto* s = new Server();
   s->ctx = c;
   s->max_batch = max_batch_gates;
+  s->fill_gates = std::min<size_t>(max_batch_gates, static_cast<size_t>(64) * std::max(1, c->sm_count));
   s->pool = fsql::Pool(scratch_budget_bytes);
   cudaError_t e = cudaMalloc(&s->d_pool, scratch_budget_bytes);
   if (e == cudaSuccess) e = cudaMalloc(&s->d_round, max_batch_gates * sizeof(fsql::GateDesc));
