@@ -682,19 +682,25 @@ def run_serving(args, dist):
 
 
 def kernel_source_hash() -> str:
-    """sha256 of the blind-rotation kernel's sources: ntt.cuh and kernels.cu
-    up to the end of the blind rotation's device code (twiddle tables, gate
-    linear forms, the kernel itself)."""
+    """sha256 of the throughput blind-rotation kernel's code: ntt.cuh and
+    kernels.cu up to the end of blind_rotate_kernel (twiddle tables, gate
+    linear forms, the kernel body and its wrapper), with // comments and
+    trailing blanks removed so that a comment edit keeps the hash."""
     import hashlib
+    import re
+
+    def code(text: bytes) -> bytes:
+        lines = (re.sub(rb"//.*$", b"", ln).rstrip() for ln in text.split(b"\n"))
+        return b"\n".join(ln for ln in lines if ln)
 
     h = hashlib.sha256()
     with open(os.path.join(ROOT, "paper_2510_15413_b300", "csrc", "ntt.cuh"), "rb") as fh:
-        h.update(fh.read())
+        h.update(code(fh.read()))
     with open(os.path.join(ROOT, "paper_2510_15413_b300", "csrc", "kernels.cu"), "rb") as fh:
         text = fh.read()
-    marker = b"// ---------------------------------------------------------------- end of the blind rotation's device code"
-    assert marker in text, "kernels.cu lost its end-of-blind-rotation marker"
-    h.update(text.split(marker)[0])
+    marker = b"// ---------------------------------------------------------------- end of blind_rotate_kernel's device code"
+    assert marker in text, "kernels.cu lost its end-of-blind_rotate_kernel marker"
+    h.update(code(text.split(marker)[0]))
     return h.hexdigest()
 
 

@@ -6,10 +6,15 @@
 //
 // Blind rotation kernel.  A group of 128 threads owns one gate for all n CMux
 // steps; each thread holds 8 of the 1024 coefficients of every polynomial it
-// transforms (ntt.cuh).  A CTA runs G gates in lockstep so that the
-// bootstrapping-key slice of each CMux step and gadget row (16 KB in the NTT
-// domain) is staged once into shared memory by cp.async (2-slot ring) and
-// read by all G groups.  Per CMux a group:
+// transforms (ntt.cuh).  A CTA runs G gates.  The bootstrapping-key slice
+// of each step (P gadget rows, 16 KB each in the NTT domain) is staged into
+// shared memory by cp.async either once per CTA into a 2-slot ring read by
+// all G groups in lockstep, or (the own-slot form, the default shape) by
+// each group into a slot of its own, so the groups synchronise only
+// themselves and drift apart (one group's exchanges overlap another's
+// butterflies); each group then reads the key from L2.  Key copies carry an
+// L2 evict-last hint, gate inputs and extracted outputs the streaming hint,
+// so the key stays in L2 while gate I/O streams through.  Per CMux a group:
 //   for each of the 2l = 6 rows (u, j), P rows per step: forms digit j of
 //     X^a*ACC_u - ACC_u, runs the forward NTT, and multiply-accumulates with
 //     the staged key row into two NTT-domain accumulators (one per output
@@ -220,6 +225,19 @@ __device__ __forceinline__ void cp_async16(void* smem_dst, const void* gsrc) {
   const uint32_t s = static_cast<uint32_t>(__cvta_generic_to_shared(smem_dst));
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gsrc) : "memory");
 }
+// The same copy with an L2 eviction-priority hint (a createpolicy descriptor):
+// the blind-rotation key is re-read by every gate group while gate inputs and
+// outputs stream through L2 once, so key lines are kept last.
+__device__ __forceinline__ void cp_async16_hint(void* smem_dst, const void* gsrc, uint64_t policy) {
+  const uint32_t s = static_cast<uint32_t>(__cvta_generic_to_shared(smem_dst));
+  asm volatile("cp.async.cg.shared.global.L2::cache_hint [%0], [%1], 16, %2;\n" ::"r"(s), "l"(gsrc), "l"(policy)
+               : "memory");
+}
+__device__ __forceinline__ uint64_t l2_evict_last_policy() {
+  uint64_t policy;
+  asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;\n" : "=l"(policy));
+  return policy;
+}
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 template <int N>
 __device__ __forceinline__ void cp_async_wait() {
@@ -301,10 +319,10 @@ __global__ void make_desc_kernel(GateDesc* __restrict__ desc, const uint8_t* __r
 
 // Stage the key rows of step k (kPolys rows, 32 KB, contiguous) into a ring slot.
 template <int kThreads, int kStepU64>
-__device__ __forceinline__ void issue_step(uint64_t* slot, const uint64_t* __restrict__ bkhat, int k) {
+__device__ __forceinline__ void issue_step(uint64_t* slot, const uint64_t* __restrict__ bkhat, int k, uint64_t policy) {
   const uint4* src = reinterpret_cast<const uint4*>(bkhat + static_cast<size_t>(k) * kStepU64);
   uint4* dst = reinterpret_cast<uint4*>(slot);
-  for (int q = threadIdx.x; q < kStepU64 * 8 / 16; q += kThreads) cp_async16(dst + q, src + q);
+  for (int q = threadIdx.x; q < kStepU64 * 8 / 16; q += kThreads) cp_async16_hint(dst + q, src + q, policy);
 }
 
 // Blind rotation + sample extraction for `count` gates (see file comment),
@@ -352,14 +370,17 @@ __device__ __forceinline__ void br_body(const GateDesc* __restrict__ desc, int c
     }
   }
 
-  // copies of step k into a slot: all the CTA's threads (shared ring) or the group's
+  // copies of step k into a slot: all the CTA's threads (shared ring) or the
+  // group's; key lines are kept in L2 ahead of the streaming gate inputs and
+  // outputs (read and written once each, with the streaming cache hint)
+  const uint64_t keep = l2_evict_last_policy();
   auto issue = [&](uint64_t* slot, int k) {
     if constexpr (kOwn) {
       const uint4* src = reinterpret_cast<const uint4*>(bkhat + static_cast<size_t>(k) * kStepU64);
       uint4* dst = reinterpret_cast<uint4*>(slot);
-      for (int q = t; q < kStepU64 * 8 / 16; q += kGroup) cp_async16(dst + q, src + q);
+      for (int q = t; q < kStepU64 * 8 / 16; q += kGroup) cp_async16_hint(dst + q, src + q, keep);
     } else {
-      issue_step<kThreads, kStepU64>(slot, bkhat, k);
+      issue_step<kThreads, kStepU64>(slot, bkhat, k, keep);
     }
   };
   for (int g0 = blockIdx.x * G; g0 < count; g0 += gridDim.x * G) {
@@ -375,8 +396,8 @@ __device__ __forceinline__ void br_body(const GateDesc* __restrict__ desc, int c
       // linear combination and modulus switch q -> 2N (round half up)
       const uint32_t* c3 = lin.cc ? d.c : nullptr;  // a missing third input counts as zero
       for (int x = t; x <= n; x += kGroup) {
-        uint32_t v = lin.ca * d.a[x] + lin.cb * d.b[x];
-        if (c3) v += lin.cc * c3[x];
+        uint32_t v = lin.ca * __ldcs(d.a + x) + lin.cb * __ldcs(d.b + x);
+        if (c3) v += lin.cc * __ldcs(c3 + x);
         if (x == n) v += lin.k;
         const uint32_t ms = ((v + (1u << 20)) >> 21) & (2 * kN - 1);
         if (x < n) abar[x] = static_cast<uint16_t>(ms);
@@ -484,9 +505,9 @@ __device__ __forceinline__ void br_body(const GateDesc* __restrict__ desc, int c
 #pragma unroll
       for (int q = 0; q < 8; ++q) {
         const int c = t + 128 * q;
-        out[c] = c == 0 ? acc_poly[0] : 0u - acc_poly[kN - c];
+        __stcs(out + c, c == 0 ? acc_poly[0] : 0u - acc_poly[kN - c]);
       }
-      if (t == 0) out[kN] = acc_poly[kN];
+      if (t == 0) __stcs(out + kN, acc_poly[kN]);
     }
   }
 }
@@ -497,6 +518,8 @@ __global__ void __launch_bounds__(G * kGroup, 1)
                         const void* __restrict__ gtab, int n, int bg_bits, uint32_t* __restrict__ big) {
   br_body<F, G, kPolys, kOwn>(desc, count, bkhat, gtab, n, bg_bits, big, true);
 }
+
+// ---------------------------------------------------------------- end of blind_rotate_kernel's device code
 
 // Prime-split blind rotation (br_split.cuh): G gates per CTA of 256 threads
 // each (half 0: residues mod p1, half 1: mod p2), P gadget rows per step.
@@ -547,6 +570,7 @@ __global__ void __launch_bounds__(G * 2 * kGroup, 1)
   for (int j = 1; j <= kL; ++j) off += (1u << (bg_bits - 1)) << (32 - bg_bits * j);
   const uint32_t dmask = (1u << bg_bits) - 1, lift = p - (1u << (bg_bits - 1));  // digit u - half -> u + p - half
   const int total = n * kStepsPerCmux;
+  const uint64_t keep = l2_evict_last_policy();  // key lines stay in L2 ahead of streaming gate I/O
 
   for (int g0 = blockIdx.x * G; g0 < count; g0 += gridDim.x * G) {
     const int gi = g0 + grp;
@@ -554,7 +578,8 @@ __global__ void __launch_bounds__(G * 2 * kGroup, 1)
     __syncthreads();  // tables loaded; previous gates finished with the stages
 #pragma unroll
     for (int k = 0; k < S - 1; ++k) {  // the first S - 1 steps in flight
-      if (k < total) issue_step<kThreads, P * kChunkU64>(reinterpret_cast<uint64_t*>(stage + k * kStepU32), bks64, k);
+      if (k < total)
+        issue_step<kThreads, P * kChunkU64>(reinterpret_cast<uint64_t*>(stage + k * kStepU32), bks64, k, keep);
       cp_async_commit();
     }
 
@@ -592,7 +617,7 @@ __global__ void __launch_bounds__(G * 2 * kGroup, 1)
         __syncthreads();  // everyone's copies of step k visible; slot (k - 1) % S free; ACC of the previous CMux complete
         if (k + S - 1 < total)
           issue_step<kThreads, P * kChunkU64>(
-              reinterpret_cast<uint64_t*>(stage + ((k + S - 1) % S) * kStepU32), bks64, k + S - 1);
+              reinterpret_cast<uint64_t*>(stage + ((k + S - 1) % S) * kStepU32), bks64, k + S - 1, keep);
         cp_async_commit();
         if (active) {
           // X^a ACC_u - ACC_u (plus the decomposition offset) for the
@@ -674,97 +699,105 @@ __global__ void __launch_bounds__(G * 2 * kGroup, 1)
   }
 }
 
-// Cluster blind rotation: one gate per thread-block cluster of 6 CTAs of 128
+// Cluster blind rotation: one gate per thread-block cluster of 6 CTAs of 256
 // threads, on 6 SMs, for batches too small to fill the GPU (the per-gate
 // path and the narrow levels of deep circuits).  A gate's 630 CMux steps are
 // a dependent chain, so one gate on one SM is bound by that SM's integer
-// pipes; here its work per CMux is spread over 6 SMs that exchange through
-// distributed shared memory.  CTA rank r = 3 pr + s: prime pr (p1 or p2,
-// 32-bit residues), gadget rows 2s and 2s + 1.  Per CMux:
+// pipes and latencies; here its work per CMux is spread over 6 SMs that
+// exchange through distributed shared memory.  CTA rank r = 3 pr + s works
+// mod prime pr (p1 or p2, 32-bit residues) on gadget rows 2s and 2s + 1, one
+// row per 128-thread group g.  Per CMux:
 //   1. every CTA keeps a copy of the ACC polynomials its rows read (CTA
-//      (pr, 1) both, the others one); it forms the digits of its two
-//      rows, transforms them mod its prime (first two stages by digit table)
-//      and multiply-accumulates them with its two staged key rows into
-//      per-slot sums of the two output polynomials, reduced to [0, 2p) and
-//      stored straight into the shared memory of the CTA that reduces output
-//      polynomial c (distributed shared memory);
-//   2. cluster barrier; CTA (pr, 0) for output polynomial 0 and CTA (pr, 2)
-//      for polynomial 1 sum the three partials they received, fold to
-//      [0, 2p), run the inverse transform and store the residues into every
-//      CTA of the cluster;
-//   3. cluster barrier; every CTA lifts by CRT the polynomials its two rows
-//      read (both for CTA (pr, 1), which runs no inverse) and adds them into
-//      its own ACC; the sample is extracted by CTA (0, 1).
-// The residues summed are those the packed kernel sums (the same integer mod
-// each prime), so the CRT gives the same exact integer and the same words.
+//      (pr, 1) both, the others one); group g forms the digits of row
+//      2s + g, transforms them mod pr (first two stages by digit table) and
+//      multiplies them with the row's staged key words for both output
+//      polynomials, reduced to [0, 2p); the two groups add their rows in
+//      shared memory, and group g stores the CTA's sum for output polynomial
+//      g into the CTA that reduces it (distributed shared memory);
+//   2. cluster barrier; group 0 of CTA (pr, 0) for output polynomial 0 and
+//      of CTA (pr, 2) for polynomial 1 sums the three partials it received,
+//      folds to [0, 2p), runs the inverse transform and stores the residues
+//      into the four CTAs whose rows read that polynomial;
+//   3. cluster barrier; every CTA lifts by CRT the polynomials its rows read
+//      (both groups, half the coefficients each) and adds them into its own
+//      ACC; the sample is extracted by CTA (0, 1).
+// Only a few tens of GB/s leave each SM through distributed shared memory,
+// hence the pre-summed rows, stores only where the data is read, plain
+// shared stores for the CTA's own copy, and 4-byte stores coalesced across
+// each warp (wider per-thread stores with this layout move the same bytes
+// more slowly).  The residues summed are those the packed kernel sums (the
+// same integer mod each prime), so the CRT gives the same exact integer and
+// the same words.
 constexpr int kClusterCtas = 6;
+constexpr int kClusterThreads = 2 * kGroup;
 constexpr int kClusterSmem = kSplitTabBytes + dev::kDigitTabs * dev::kDigitTabSize * 4 +  // tables
                              2 * 2 * kChunkU64 * 4 +                                        // key rows, 2 slots
-                             2 * kN * 4 +                                                   // exchange buffer
-                             2 * kN * 4 + 3 * kN * 4 +                                      // ACC, partial sums
-                             4 * kN * 4 +                                                   // residues
+                             2 * kN * 4 +                                                   // exchange buffer per group
+                             2 * kN * 4 + 2 * kN * 4 +                                      // ACC, rows of the other group
+                             3 * kN * 4 + 4 * kN * 4 +                                      // partial sums, residues
                              kMaxN * 2 + 16;                                                // switched mask, body
 
-__global__ void __cluster_dims__(kClusterCtas, 1, 1) __launch_bounds__(kGroup, 1)
+__global__ void __cluster_dims__(kClusterCtas, 1, 1) __launch_bounds__(kClusterThreads, 1)
     blind_rotate_cluster_kernel(const GateDesc* __restrict__ desc, int count, const uint32_t* __restrict__ bks,
                                 const void* __restrict__ gtab, int n, int bg_bits, uint32_t* __restrict__ big) {
   namespace cg = cooperative_groups;
   cg::cluster_group cl = cg::this_cluster();
   const int rank = static_cast<int>(cl.block_rank());
-  const int pr = rank / 3, s = rank % 3, t = threadIdx.x;
+  const int pr = rank / 3, s = rank % 3;
+  const int grp = threadIdx.x / kGroup, t = threadIdx.x % kGroup, tid = threadIdx.x;
   extern __shared__ __align__(128) uint8_t smem[];
   dev::SplitTables& T = *reinterpret_cast<dev::SplitTables*>(smem);
   uint32_t* dtab = reinterpret_cast<uint32_t*>(smem + kSplitTabBytes);
   uint32_t* keys = dtab + dev::kDigitTabs * dev::kDigitTabSize;  // [2 slots][2 rows][kChunkU64]
-  uint32_t* xbuf = keys + 2 * 2 * kChunkU64;                       // [2][N]
-  uint32_t* acc_poly = xbuf + 2 * kN;                              // [2][N]
-  uint32_t* part = acc_poly + 2 * kN;                              // [3 senders][N], slot-major (q * 128 + t)
+  uint32_t* xbuf = keys + 2 * 2 * kChunkU64 + grp * kN;           // this group's exchange buffer [N]
+  uint32_t* acc_poly = keys + 2 * 2 * kChunkU64 + 2 * kN;          // [2][N]
+  uint32_t* other = acc_poly + 2 * kN;                             // [2][N]: [c] = the other group's row, output c
+  uint32_t* part = other + 2 * kN;                                 // [3 senders s][N], slot-major (q * 128 + t)
   uint32_t* resid = part + 3 * kN;                                 // [2 polys][2 primes][N]
   uint16_t* abar = reinterpret_cast<uint16_t*>(resid + 4 * kN);    // [kMaxN]
   uint32_t* bbar_slot = reinterpret_cast<uint32_t*>(abar + kMaxN);
   const uint32_t p = pr ? dev::kP2 : dev::kP1, p2 = 2 * p, pinv = pr ? dev::kP2inv : dev::kP1inv;
+  const int bar = 1 + grp;  // the group's named barrier (128 threads)
 
-  for (int k = t; k < kSplitTabBytes / 16; k += kGroup)
+  for (int k = tid; k < kSplitTabBytes / 16; k += kClusterThreads)
     reinterpret_cast<uint4*>(smem)[k] = reinterpret_cast<const uint4*>(gtab)[pr * (kSplitTabBytes / 16) + k];
   uint32_t off = 1u << (31 - bg_bits * kL);
   for (int j = 1; j <= kL; ++j) off += (1u << (bg_bits - 1)) << (32 - bg_bits * j);
   const uint32_t dmask = (1u << bg_bits) - 1, dhalf = 1u << (bg_bits - 1);
   __syncthreads();
-  dev::build_digit_tables32(dtab, T, dhalf, p, t, kGroup);
-  // rows 2s and 2s+1 of CMux i for this prime: two 8 KB pieces of the split key
-  const int row0 = 2 * s, row1 = 2 * s + 1, u0 = row0 / kL, u1 = row1 / kL;
-  const int shift0 = 32 - bg_bits * (row0 % kL + 1), shift1 = 32 - bg_bits * (row1 % kL + 1);
-  auto issue_rows = [&](int i, int slot) {
-#pragma unroll
-    for (int r = 0; r < 2; ++r) {
-      const uint4* src = reinterpret_cast<const uint4*>(bks + ((static_cast<size_t>(i) * kRows + 2 * s + r) * 2 + pr) *
-                                                                  kChunkU64);
-      uint4* dst = reinterpret_cast<uint4*>(keys + (slot * 2 + r) * kChunkU64);
-      for (int q = t; q < kChunkU64 * 4 / 16; q += kGroup) cp_async16(dst + q, src + q);
-    }
+  dev::build_digit_tables32(dtab, T, dhalf, p, tid, kClusterThreads);
+  // this group's gadget row and the polynomials the CTA's two rows read
+  const int row = 2 * s + grp, u = row / kL, shift = 32 - bg_bits * (row % kL + 1);
+  const int u0 = (2 * s) / kL, u1 = (2 * s + 1) / kL;
+  auto issue_row = [&](int i, int slot) {  // this group's key row of CMux i, this prime (8 KB)
+    const uint4* src = reinterpret_cast<const uint4*>(bks + ((static_cast<size_t>(i) * kRows + row) * 2 + pr) * kChunkU64);
+    uint4* dst = reinterpret_cast<uint4*>(keys + (slot * 2 + grp) * kChunkU64);
+    for (int q = t; q < kChunkU64 * 4 / 16; q += kGroup) cp_async16(dst + q, src + q);
     cp_async_commit();
   };
-  // exchanges are pushes (stores into the receiver's shared memory), so
-  // every read after a barrier is local: partial sums of output polynomial c
-  // go to CTA (pr, c), slot s; the residues of CTA (pr, c) go to every CTA,
-  // slot [c][pr]
-  // output polynomial 0 is reduced and inverted by CTA (pr, 0), polynomial
-  // 1 by CTA (pr, 2); CTA (pr, 1), whose rows touch both polynomials, only
-  // lifts, so the three CTAs of a prime carry about the same work per CMux
+  // group g sends the CTA's partial sum of output polynomial g to the CTA that
+  // reduces it, (pr, 0) for g = 0 and (pr, 2) for g = 1, slot s (its own
+  // shared memory when that is this CTA); the reducing CTA of polynomial c
+  // sends its residues (slot [c][pr]) to the CTAs whose rows read c: ranks
+  // c, c + 1, c + 3, c + 4
   const int red_c = s == 0 ? 0 : s == 2 ? 1 : -1;  // the polynomial this CTA reduces, if any
-  uint32_t* part_to[2];
-  for (int c = 0; c < 2; ++c) part_to[c] = cl.map_shared_rank(part, pr * 3 + 2 * c) + s * kN;
-  uint32_t* resid_to[kClusterCtas];
-  for (int m = 0; m < kClusterCtas; ++m) resid_to[m] = cl.map_shared_rank(resid, m) + ((red_c < 0 ? 0 : red_c) * 2 + pr) * kN;
+  const int part_rank = pr * 3 + 2 * grp;
+  uint32_t* const part_to = (part_rank == rank ? part : cl.map_shared_rank(part, part_rank)) + s * kN;
+  uint32_t* resid_to[4];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const int m = (red_c < 0 ? 0 : red_c) + (k & 1) + 3 * (k >> 1);
+    resid_to[k] = (m == rank ? resid : cl.map_shared_rank(resid, m)) + ((red_c < 0 ? 0 : red_c) * 2 + pr) * kN;
+  }
 
   for (int gi = static_cast<int>(blockIdx.x) / kClusterCtas; gi < count;
        gi += static_cast<int>(gridDim.x) / kClusterCtas) {
     __syncthreads();
-    issue_rows(0, 0);
+    issue_row(0, 0);
     const GateDesc d = desc[gi];
     const Lin lin = gate_lin(d.type);
     const uint32_t* c3 = lin.cc ? d.c : nullptr;
-    for (int x = t; x <= n; x += kGroup) {
+    for (int x = tid; x <= n; x += kClusterThreads) {
       uint32_t v = lin.ca * d.a[x] + lin.cb * d.b[x];
       if (c3) v += lin.cc * c3[x];
       if (x == n) v += lin.k;
@@ -775,11 +808,9 @@ __global__ void __cluster_dims__(kClusterCtas, 1, 1) __launch_bounds__(kGroup, 1
     __syncthreads();
     {
       const uint32_t e = (2 * kN - *bbar_slot) & (2 * kN - 1);
-#pragma unroll
-      for (int q = 0; q < 8; ++q) {
-        const uint32_t c = t + 128 * q;
+      for (int c = tid; c < kN; c += kClusterThreads) {
         acc_poly[c] = 0u;
-        const uint32_t idx = (c - e) & (2 * kN - 1);
+        const uint32_t idx = (static_cast<uint32_t>(c) - e) & (2 * kN - 1);
         acc_poly[kN + c] = idx < static_cast<uint32_t>(kN) ? (1u << 29) : (0u - (1u << 29));
       }
     }
@@ -787,78 +818,75 @@ __global__ void __cluster_dims__(kClusterCtas, 1, 1) __launch_bounds__(kGroup, 1
     for (int i = 0; i < n; ++i) {
       cp_async_wait<0>();
       __syncthreads();  // key rows of CMux i landed; ACC updated
-      if (i + 1 < n) issue_rows(i + 1, (i + 1) & 1);
+      if (i + 1 < n) issue_row(i + 1, (i + 1) & 1);
       else cp_async_commit();
       const uint32_t a_i = abar[i];
-      uint32_t d0[8], d1[8];
+      uint32_t dg[8];
+      const uint32_t* P = acc_poly + u * kN;
 #pragma unroll
       for (int q = 0; q < 8; ++q) {
         const uint32_t c = t + 128 * q;
         const uint32_t idx = (c - a_i) & (2 * kN - 1);
-        const uint32_t* P0 = acc_poly + u0 * kN;
-        const uint32_t* P1 = acc_poly + u1 * kN;
-        const uint32_t r0 = idx < static_cast<uint32_t>(kN) ? P0[idx] : 0u - P0[idx - kN];
-        const uint32_t r1 = idx < static_cast<uint32_t>(kN) ? P1[idx] : 0u - P1[idx - kN];
-        d0[q] = ((r0 - P0[c] + off) >> shift0) & dmask;
-        d1[q] = ((r1 - P1[c] + off) >> shift1) & dmask;
+        const uint32_t r = idx < static_cast<uint32_t>(kN) ? P[idx] : 0u - P[idx - kN];
+        dg[q] = ((r - P[c] + off) >> shift) & dmask;
       }
-      uint32_t x[2][8];
-      dev::digit_stages12_32(d0, x[0], dhalf, dtab, p, p2);
-      dev::digit_stages12_32(d1, x[1], dhalf, dtab, p, p2);
-      dev::ntt_forward32<2, 2, 1, true>(x, xbuf, parity, T, t, 1, p, p2);
-      const uint32_t* ch = keys + (i & 1) * 2 * kChunkU64;
+      uint32_t x[1][8];
+      dev::digit_stages12_32(dg, x[0], dhalf, dtab, p, p2);
+      dev::ntt_forward32<1, 1, 1, true>(x, xbuf, parity, T, t, bar, p, p2);
+      const uint32_t* ch = keys + ((i & 1) * 2 + grp) * kChunkU64;
+      uint32_t mine[8];  // this row's product with output polynomial grp, below 2p
 #pragma unroll
       for (int q = 0; q < 8; ++q) {
-        uint64_t s0 = 0, s1 = 0;
-#pragma unroll
-        for (int r = 0; r < 2; ++r) {
-          const uint2 w = *reinterpret_cast<const uint2*>(ch + r * kChunkU64 + (q * kGroup + t) * 2);
-          s0 += static_cast<uint64_t>(x[r][q]) * w.x;
-          s1 += static_cast<uint64_t>(x[r][q]) * w.y;
-        }
-        part_to[0][q * kGroup + t] = dev::DualPrime::settle(s0, p, pinv);
-        part_to[1][q * kGroup + t] = dev::DualPrime::settle(s1, p, pinv);
+        const uint2 w = *reinterpret_cast<const uint2*>(ch + (q * kGroup + t) * 2);
+        const uint32_t y0 = dev::DualPrime::settle(static_cast<uint64_t>(x[0][q]) * w.x, p, pinv);
+        const uint32_t y1 = dev::DualPrime::settle(static_cast<uint64_t>(x[0][q]) * w.y, p, pinv);
+        other[(1 - grp) * kN + q * kGroup + t] = grp ? y0 : y1;  // the output the other group sends
+        mine[q] = grp ? y1 : y0;
       }
+      __syncthreads();  // both rows' products in shared memory
+#pragma unroll
+      for (int q = 0; q < 8; ++q) part_to[q * kGroup + t] = mine[q] + other[grp * kN + q * kGroup + t];  // below 4p
       cl.sync();  // 1: every partial sum delivered
-      if (red_c >= 0) {
+      if (red_c >= 0 && grp == 0) {
         uint32_t y[1][8];
 #pragma unroll
         for (int q = 0; q < 8; ++q) {
           const int o = q * kGroup + t;
-          const uint32_t v = part[o] + part[kN + o] + part[2 * kN + o];  // below 6p
-          y[0][q] = dev::fold(dev::fold(v, 2 * p2), p2);
+          const uint32_t v = part[o] + part[kN + o] + part[2 * kN + o];  // three sums below 4p: below 12p
+          y[0][q] = dev::fold(dev::fold(dev::fold(v, 4 * p2), 2 * p2), p2);
         }
-        dev::ntt_inverse32<1, 2, 1>(y, xbuf, parity, T, t, 1, p, p2);
+        dev::ntt_inverse32<1, 1, 1>(y, xbuf, parity, T, t, bar, p, p2);
 #pragma unroll
-        for (int m = 0; m < kClusterCtas; ++m)
+        for (int m = 0; m < 4; ++m)
 #pragma unroll
           for (int q = 0; q < 8; ++q) resid_to[m][t + 128 * q] = y[0][q];
       }
-      cl.sync();  // 2: the residues of both output polynomials mod both primes delivered
-      // every CTA lifts by CRT the polynomials its rows read (CTA (pr, 1)
-      // both) and updates its own ACC (the buffers are written again only
-      // after the next CMux's barrier 1)
+      cl.sync();  // 2: the residues of the polynomials each CTA reads, mod both primes, delivered
+      // lift by CRT the polynomials the CTA's rows read and update ACC (the
+      // two groups take alternate coefficients; the buffers are written again
+      // only after the next CMux's barrier 1)
 #pragma unroll
       for (int c = 0; c < 2; ++c) {
         if (c != u0 && c != u1) continue;
 #pragma unroll
-        for (int q = 0; q < 8; ++q)
-          acc_poly[c * kN + t + 128 * q] +=
-              dev::crt_torus(resid[(c * 2) * kN + t + 128 * q], resid[(c * 2 + 1) * kN + t + 128 * q]);
+        for (int q = 0; q < 4; ++q) {
+          const int e = tid + kClusterThreads * q;
+          acc_poly[c * kN + e] += dev::crt_torus(resid[(c * 2) * kN + e], resid[(c * 2 + 1) * kN + e]);
+        }
       }
     }
     __syncthreads();
     if (rank == 1) {  // CTA (0, 1) keeps both polynomials of ACC
       uint32_t* out = big + static_cast<size_t>(gi) * (kN + 1);
 #pragma unroll
-      for (int q = 0; q < 8; ++q) {
-        const int c = t + 128 * q;
+      for (int q = 0; q < 4; ++q) {
+        const int c = tid + kClusterThreads * q;
         out[c] = c == 0 ? acc_poly[0] : 0u - acc_poly[kN - c];
       }
-      if (t == 0) out[kN] = acc_poly[kN];
+      if (tid == 0) out[kN] = acc_poly[kN];
     }
   }
-  cl.sync();  // no CTA leaves while another may still read its shared memory
+  cl.sync();  // no CTA leaves while another may still write into its shared memory
 }
 
 // Packed key (u64: p1 residue low, p2 residue high) -> key split by prime.
@@ -872,8 +900,6 @@ __global__ void split_key_kernel(const uint64_t* __restrict__ bkhat, uint32_t* _
     bks[r * 2 * kChunkU64 + kChunkU64 + w] = static_cast<uint32_t>(v >> 32);
   }
 }
-
-// ---------------------------------------------------------------- end of the blind rotation's device code
 
 // Latency mode of the blind rotation (batches smaller than two gates per
 // SM, where one 128-thread group per gate leaves the SMs mostly idle and a
@@ -1725,7 +1751,7 @@ static cudaError_t cluster_capacity(int* clusters) {
     if (e != cudaSuccess) return e;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(kClusterCtas);
-    cfg.blockDim = dim3(kGroup);
+    cfg.blockDim = dim3(kClusterThreads);
     cfg.dynamicSmemBytes = kClusterSmemLaunch;
     int n = 0;
     e = cudaOccupancyMaxActiveClusters(&n, blind_rotate_cluster_kernel, &cfg);
@@ -1742,7 +1768,7 @@ static cudaError_t launch_br_cluster(size_t count, const GateDesc* d_desc, const
   const cudaError_t e = cluster_capacity(&clusters);
   if (e != cudaSuccess) return e;
   const int grid = static_cast<int>(std::min<size_t>(count, static_cast<size_t>(clusters))) * kClusterCtas;
-  blind_rotate_cluster_kernel<<<grid, kGroup, kClusterSmemLaunch, st>>>(d_desc, static_cast<int>(count), bks, tables,
+  blind_rotate_cluster_kernel<<<grid, kClusterThreads, kClusterSmemLaunch, st>>>(d_desc, static_cast<int>(count), bks, tables,
                                                                         n, bg_bits, d_big);
   return cudaGetLastError();
 }
