@@ -375,7 +375,8 @@ def run_gates(args, dist):
     value = dist.world * B * args.steps / (ms / 1e3)
     truth = np.array([[1, 1, 1, 0], [0, 0, 0, 1], [0, 1, 1, 1], [0, 1, 1, 0], [1, 0, 0, 1]], np.uint8)[types, 2 * xb + yb]
     correct = bool(np.array_equal(ctx.decrypt_bits(out.cpu().numpy().view(np.uint32)), truth))
-    roof = roofline_of(kt, ms, sms, peaks, f"gates{B}", alu, ctx.engine, args.steps)
+    roof = roofline_of(kt, ms, sms, peaks, f"gates{B}", alu, ctx.engine, args.steps,
+                       shape=ctx.br_shape, sm_mhz=(clocks or {}).get("sm_mhz"))
     # end to end: pinned host inputs -> device -> gates -> host, copies timed
     hx, hy, ht = (torch.from_numpy(x.view(np.int32)).pin_memory(), torch.from_numpy(y.view(np.int32)).pin_memory(),
                   torch.from_numpy(types).pin_memory())
@@ -722,7 +723,26 @@ def measured_traffic(workload: str):
         return None
 
 
-def roofline_of(kt, ms, sms, peaks, workload=None, alu=None, engine=1, steps=1):
+def measured_issue(shape):
+    """Warp instructions of blind_rotate_kernel per gate per CMux (n = 630)
+    from the committed ncu capture of launch shape `shape`, if it was taken on
+    the current kernel code (else None)."""
+    path = os.path.join(ROOT, "profiles", "blind_rotate_own_slot_gates888.md")
+    try:
+        fields = {}
+        with open(path) as f:
+            for line in f:
+                if ":" in line and line.startswith("- "):
+                    k, v = line[2:].split(":", 1)
+                    fields[k.strip()] = v.strip()
+        if fields.get("kernel_source_sha256") != kernel_source_hash() or int(fields["launch_shape"]) != shape:
+            return None
+        return float(fields["warp_instructions"]) / (float(fields["gates"]) * float(fields["cmux_per_gate"]))
+    except Exception:
+        return None
+
+
+def roofline_of(kt, ms, sms, peaks, workload=None, alu=None, engine=1, steps=1, shape=None, sm_mhz=None):
     """Roofline of the blind rotation (the dominant kernel): algorithmic
     modular multiplications per second over its CUDA-event time, against the
     measured rate of the engine's butterfly (one modular multiplication each)
@@ -755,6 +775,18 @@ def roofline_of(kt, ms, sms, peaks, workload=None, alu=None, engine=1, steps=1):
             out["goldilocks_equivalent"] = {"achieved": g_ach, "peak": g_peak, "frac": g_ach / g_peak}
     else:
         out.update({"peak": None, "frac": None, "peak_kind": "unavailable"})
+    # the instruction-issue ceiling beside the ALU one: 4 warp instructions
+    # per SM per clock at the SM clock measured during the timed region
+    inst = measured_issue(shape) if shape is not None else None
+    if inst and sm_mhz and br_ms > 0:
+        full = sms * 4 * sm_mhz * 1e6 / (inst * 630)
+        rate = kt["gates"] / (br_ms / 1e3)
+        out["issue_ceiling"] = {"warp_instructions_per_gate_per_cmux": inst, "sm_mhz": sm_mhz,
+                                "bootstraps_per_s_at_full_issue": full, "achieved_bootstraps_per_s": rate,
+                                "frac": rate / full,
+                                "source": "profiles/blind_rotate_own_slot_gates888.md (ncu, same kernel code)"}
+    else:
+        out["issue_ceiling"] = None
     return out
 
 
@@ -845,7 +877,8 @@ def run_ours(args, dist):
         correct &= got_sum == int(p_want[q].astype(object).sum()) % (1 << t.sum_width)
 
     # ---- roofline of the dominant kernel (blind rotation)
-    roofline = roofline_of(ktimes, ms, sms, peaks, args.workload, alu, ctx.engine, args.steps)
+    roofline = roofline_of(ktimes, ms, sms, peaks, args.workload, alu, ctx.engine, args.steps,
+                           shape=ctx.br_shape, sm_mhz=(clocks or {}).get("sm_mhz"))
     if args.walk:
         roofline["kernel"] = "scan_walk_kernel (blind rotations and keyswitches of every level, one launch)"
 
