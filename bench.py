@@ -14,8 +14,10 @@ max-over-ranks time use torch.distributed.
 from __future__ import annotations
 
 import argparse
+import hashlib
 import json
 import os
+import re
 import statistics
 import subprocess
 import sys
@@ -682,60 +684,61 @@ def run_serving(args, dist):
         print(json.dumps(line), flush=True)
 
 
-def kernel_source_hash() -> str:
+def code_only(text: bytes) -> bytes:
+    """C++ source without // comments, trailing blanks and empty lines (what
+    the kernel hash covers, so that comment edits keep it)."""
+    lines = (re.sub(rb"//.*$", b"", ln).rstrip() for ln in text.split(b"\n"))
+    return b"\n".join(ln for ln in lines if ln)
+
+
+def kernel_source_hash(root: str = ROOT) -> str:
     """sha256 of the throughput blind-rotation kernel's code: ntt.cuh and
     kernels.cu up to the end of blind_rotate_kernel (twiddle tables, gate
-    linear forms, the kernel body and its wrapper), with // comments and
-    trailing blanks removed so that a comment edit keeps the hash."""
-    import hashlib
-    import re
-
-    def code(text: bytes) -> bytes:
-        lines = (re.sub(rb"//.*$", b"", ln).rstrip() for ln in text.split(b"\n"))
-        return b"\n".join(ln for ln in lines if ln)
-
+    linear forms, the kernel body and its wrapper), comments and blank lines
+    removed."""
     h = hashlib.sha256()
-    with open(os.path.join(ROOT, "paper_2510_15413_b300", "csrc", "ntt.cuh"), "rb") as fh:
-        h.update(code(fh.read()))
-    with open(os.path.join(ROOT, "paper_2510_15413_b300", "csrc", "kernels.cu"), "rb") as fh:
+    with open(os.path.join(root, "paper_2510_15413_b300", "csrc", "ntt.cuh"), "rb") as fh:
+        h.update(code_only(fh.read()))
+    with open(os.path.join(root, "paper_2510_15413_b300", "csrc", "kernels.cu"), "rb") as fh:
         text = fh.read()
     marker = b"// ---------------------------------------------------------------- end of blind_rotate_kernel's device code"
     assert marker in text, "kernels.cu lost its end-of-blind_rotate_kernel marker"
-    h.update(code(text.split(marker)[0]))
+    h.update(code_only(text.split(marker)[0]))
     return h.hexdigest()
 
 
-def measured_traffic(workload: str):
+def profile_fields(path: str) -> dict:
+    """The `- key: value` lines of a committed profile summary."""
+    fields = {}
+    with open(path) as f:
+        for line in f:
+            if ":" in line and line.startswith("- "):
+                k, v = line[2:].split(":", 1)
+                fields[k.strip()] = v.strip()
+    return fields
+
+
+def measured_traffic(workload: str, root: str = ROOT, code_hash: str | None = None):
     """Per-launch DRAM bytes of the blind rotation from the committed ncu
-    summary of this workload, if it was taken on the current kernel sources."""
-    path = os.path.join(ROOT, "profiles", f"blind_rotate_{workload}_dram.md")
+    summary of this workload, if it was taken on the current kernel code."""
     try:
-        fields = {}
-        with open(path) as f:
-            for line in f:
-                if ":" in line and line.startswith("- "):
-                    k, v = line[2:].split(":", 1)
-                    fields[k.strip()] = v.strip()
-        if fields.get("kernel_source_sha256") != kernel_source_hash():
+        fields = profile_fields(os.path.join(root, "profiles", f"blind_rotate_{workload}_dram.md"))
+        if fields.get("kernel_source_sha256") != (code_hash or kernel_source_hash(root)):
             return None
         return float(fields["dram_bytes_per_launch"])
     except Exception:
         return None
 
 
-def measured_issue(shape):
-    """Warp instructions of blind_rotate_kernel per gate per CMux (n = 630)
-    from the committed ncu capture of launch shape `shape`, if it was taken on
-    the current kernel code (else None)."""
-    path = os.path.join(ROOT, "profiles", "blind_rotate_own_slot_gates888.md")
+def measured_issue(shape, root: str = ROOT, code_hash: str | None = None):
+    """Warp instructions of blind_rotate_kernel per gate per CMux from the
+    committed ncu capture of launch shape `shape`, if it was taken on the
+    current kernel code (else None)."""
     try:
-        fields = {}
-        with open(path) as f:
-            for line in f:
-                if ":" in line and line.startswith("- "):
-                    k, v = line[2:].split(":", 1)
-                    fields[k.strip()] = v.strip()
-        if fields.get("kernel_source_sha256") != kernel_source_hash() or int(fields["launch_shape"]) != shape:
+        fields = profile_fields(os.path.join(root, "profiles", "blind_rotate_own_slot_gates888.md"))
+        if fields.get("kernel_source_sha256") != (code_hash or kernel_source_hash(root)):
+            return None
+        if int(fields["launch_shape"]) != shape:
             return None
         return float(fields["warp_instructions"]) / (float(fields["gates"]) * float(fields["cmux_per_gate"]))
     except Exception:
