@@ -1819,6 +1819,12 @@ static cudaError_t launch_br_any(Ctx& c, const GateDesc* d_desc, size_t count, u
     if (cluster_capacity(&clusters) == cudaSuccess && count <= static_cast<size_t>(clusters))
       return launch_br_cluster(count, d_desc, c.d_bks, c.d_tables_split, n, bg, d_big, st);
   }
+  // Between one and two gates per SM the one-gate-per-CTA latency kernel
+  // needs two waves (4.6 ms each), and the three-gate CTAs of the large-batch
+  // shapes run their SMs three gates deep (9.2 ms); one wave of two-gate
+  // CTAs takes about 7.3 ms.
+  if (c.latency_mode && count > static_cast<size_t>(c.sm_count) && count <= static_cast<size_t>(2 * c.sm_count))
+    return launch_br_engine<F, 2, 2>(c.sm_count, d_desc, count, c.d_bkhat, c.d_tables, n, bg, d_big, st);
   if (small && c.latency_mode)
     return launch_br_latency<F>(c.sm_count, d_desc, count, c.d_bkhat, c.d_tables, n, bg, d_big, st);
   if (!small && sh.kind == 1) {

@@ -61,12 +61,13 @@ def oracle_rows(o, t, rows):
     return o.scan(t.pred, w, ocol, ocst, opays, pw)
 
 
-@pytest.mark.parametrize("B", [296, 4736, 65536])
+@pytest.mark.parametrize("B", [201, 256, 296, 4736, 65536])
 def test_gate_batch_throughput_kernels_sampled(env, B):
-    """B = 2 gates per SM (smallest batch on the multi-gate-per-CTA kernel),
-    32 per SM and 65,536 (the sweep's large point): 512 seeded samples
-    recomputed by the oracle, including the first and last gates (ragged
-    tails of the persistent grid), every gate decrypted."""
+    """B between one and two gates per SM (201: a ragged last CTA; 256: the
+    sweep's point) and exactly two (one wave of two-gate CTAs), 32 per SM and
+    65,536 (the sweep's large point): 512 seeded samples recomputed by the
+    oracle, including the first and last gates (ragged tails of the
+    persistent grid), every gate decrypted."""
     ctx, o = env
     types, xb, yb = WL.gates(B, seed=B)
     x = ctx.encrypt_bits(xb, WL.STREAM_GATES, 0)
