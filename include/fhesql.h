@@ -155,8 +155,9 @@ FSQL_API int fsql_ctx_br_gates(const fsql_ctx* ctx, int* gates_per_cta);
  * SMs (each one prime and two gadget rows; partial sums and residues pushed
  * into the other CTAs' shared memory, two cluster barriers per CMux), used
  * while every gate of the batch gets a cluster of its own at once, mode 1
- * above that.  The output words
- * are the same in every mode.  FSQL_ERR_ARG for other values. */
+ * above that.  In modes 1 and 2, batches of more than one and at most two
+ * gates per SM run as one wave of two-gate CTAs of the packed kernel.  The
+ * output words are the same in every mode.  FSQL_ERR_ARG for other values. */
 FSQL_API int fsql_ctx_set_latency_mode(fsql_ctx* ctx, int on);
 
 /* Device level walker for batched scans (two-prime engine, packed launch
